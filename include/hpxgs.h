@@ -1,0 +1,231 @@
+/*
+ * hpxgs.h -- C ABI of the B300 HEALPix spherical Gaussian rasterizer
+ * (UniTriSplat, arXiv 2606.29794).
+ *
+ * The library splats 3D Gaussians onto a NESTED HEALPix grid attached to a
+ * camera (Sec. 3.1), composites them front to back per pixel (Sec. 3.4,
+ * Algorithm 1), differentiates the result (Sec. 3.2) and evaluates the
+ * HEALPix-SSIM + L1 training loss (Sec. 4.1).
+ *
+ * Conventions shared by every call
+ *  - Device pointers are owned by the caller. The library never allocates
+ *    device memory: callers size a workspace with the *_workspace_size query
+ *    and pass it in. All calls are asynchronous on the given CUDA stream,
+ *    except where a comment says the call synchronises.
+ *  - Every call returns an int status (HPXGS_OK or a negative HPXGS_E_*).
+ *    Argument errors are detected on the host before anything is launched.
+ *    Conditions that only the device can see (pair-buffer overflow, a
+ *    bounded wait that ran out) are OR-ed as HPXGS_F_* flags into the
+ *    caller's device int32 `status`; read it after synchronising the stream
+ *    and map it with hpxgs_status_error(). No call synchronises in secret.
+ *  - Maps are float32 [Npix, 3] in NESTED order, Npix = 12 * 4^k for
+ *    nside_log2 = k. Several views are packed back to back in one buffer,
+ *    view v starting at pixel sum_{u<v} Npix(u) ("pixel base").
+ *  - Camera frame: t = W mu + b (Sec. 3.2); camera direction d maps to the
+ *    HEALPix unit vector (X, Y, Z) = (d_z, d_x, d_y), i.e. HEALPix longitude
+ *    = omega = atan2(t_x, t_z) and colatitude = pi/2 - phi (Eq. 1).
+ *  - C linkage, POD structs, no exceptions across the ABI.
+ */
+#ifndef HPXGS_H_
+#define HPXGS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* hpxgs_stream_t; /* a cudaStream_t (0 = legacy default stream) */
+
+/* ---- status codes (return values) ---- */
+#define HPXGS_OK 0
+#define HPXGS_E_INVALID_ARG -1   /* bad pointer, size, order, camera or config */
+#define HPXGS_E_CAPACITY -2      /* pair buffer too small (see HPXGS_F_CAPACITY) */
+#define HPXGS_E_TIMEOUT -3       /* a bounded device wait ran out */
+#define HPXGS_E_CUDA -4          /* a CUDA runtime call or launch failed */
+#define HPXGS_E_UNIMPLEMENTED -5 /* feature not built */
+#define HPXGS_E_WORKSPACE -6     /* workspace smaller than the size query returned */
+#define HPXGS_E_CAPTURE -7       /* call needs a host synchronisation inside stream capture */
+
+/* ---- device status flags (OR-ed into the caller's int32 status word) ---- */
+#define HPXGS_F_CAPACITY 1       /* more (Gaussian, tile) pairs than capacity_pairs */
+#define HPXGS_F_TIMEOUT 2        /* a bounded wait gave up */
+
+/* ---- cameras (Sec. 3.1, Sec. D.1) ---- */
+#define HPXGS_CAM_FULL 0     /* omnidirectional: every pixel is valid */
+#define HPXGS_CAM_PINHOLE 1  /* Eq. persp_sphere; valid iff d_z > 0, |d_x/d_z| <= tan(fov_x/2), |d_y/d_z| <= tan(fov_y/2) */
+#define HPXGS_CAM_FISHEYE 2  /* anisotropic equidistant, Eqs. fish_weff..semi_axes; valid iff psi <= (pi/2) w_eff(gamma), w = fov/180 deg */
+
+#define HPXGS_MAX_VIEWS 64
+#define HPXGS_NACC 9         /* per-(view, Gaussian) backward accumulators */
+
+/* Scene (Algorithm 1, Require): P Gaussians, float32, row-major, device memory. */
+typedef struct {
+  const float* means;      /* [P,3] world positions mu */
+  const float* scales;     /* [P,3] linear scales s (caller applies exp) */
+  const float* rotations;  /* [P,4] quaternions (w,x,y,z), need not be normalised */
+  const float* opacities;  /* [P]   o in (0,1) (caller applies sigmoid) */
+  const float* sh;         /* [P,K,3] real SH coefficients, K = (sh_degree+1)^2, 3DGS order/sign convention */
+  int32_t P;
+  int32_t sh_degree;       /* 0..3 */
+} hpxgs_gaussians;
+
+typedef struct {
+  int32_t kind;            /* HPXGS_CAM_* */
+  float fov_x_deg;         /* full horizontal FoV, degrees */
+  float fov_y_deg;         /* full vertical FoV, degrees */
+} hpxgs_camera;
+
+/* One view V = [W | b] (Sec. 3.2) rendered at HEALPix order nside_log2. */
+typedef struct {
+  float W[9];              /* world-to-camera rotation, row-major */
+  float b[3];              /* translation */
+  int32_t nside_log2;      /* k: Nside = 2^k, Npix = 12 * 4^k; tile_level + 0 <= k <= 13 */
+  hpxgs_camera cam;
+} hpxgs_view;
+
+/* Rasterizer settings. The paper fixes B = 16 (Table "resolution") and eps
+ * (Algorithm 1); the others are readings where the paper is silent. */
+typedef struct {
+  int32_t tile_level;      /* b: tiles are NESTED blocks of 4^b pixels (B = 2^b); 3..5, default 4 */
+  float eps_T;             /* early termination T < eps_T (Algorithm 1), default 1e-4 */
+  float alpha_max;         /* alpha clamp, default 0.99 */
+  float cutoff_m;          /* alpha = 0 where d^T conic d > cutoff_m (3-sigma ellipse), default 9 */
+  float blur_rad2;         /* isotropic term added to Sigma_arc; < 0 selects 0.3 * Omega_pix (default) */
+  float near_plane;        /* Gaussians with radial depth r <= near_plane are culled, default 0.2 */
+  float bg[3];             /* background seen through T_final, default 0 */
+  float lambda_ssim;       /* loss weight lambda (Sec. 4.1), default 0.2 */
+  int32_t write_outside;   /* 1: pixels outside the FoV mask get bg, T=1, last=0; 0: inactive tiles untouched */
+} hpxgs_config;
+
+/* Human-readable name of a status code. */
+const char* hpxgs_strerror(int code);
+/* Map a device status word (HPXGS_F_* flags) to a return code. */
+int hpxgs_status_error(int32_t flags);
+/* Fill *cfg with the defaults listed above. */
+void hpxgs_config_default(hpxgs_config* cfg);
+
+/* Adaptive resolution (Sec. 3.1, Table "resolution"):
+ * N* = sqrt(4 pi W H / (12 Omega_in)), Omega_in = 4 pi (full), 2 pi (1 - cos(fov/2))
+ * (fisheye), 4 asin(sin(fov_x/2) sin(fov_y/2)) (pinhole); k = round(log2 N*),
+ * kL = floor, kH = ceil. Host only; any output pointer may be NULL. */
+int hpxgs_nside_for_image(int kind, double W, double H, double fov_x_deg, double fov_y_deg,
+                          double* nstar, int* k, int* kL, int* kH);
+
+/* rho(k, b): the largest angle between a tile centre (order k - b) and a pixel
+ * centre (order k) of that tile, rounded up to a multiple of 2^-20 rad. It
+ * widens the tile-membership test (tile t is listed for Gaussian i iff t has
+ * an in-mask pixel and c_t . g_i >= cos(min(pi, r_s + rho + 1e-7))).
+ * Computed once per (k, b) on the device and cached for the process.
+ * SYNCHRONISES `stream` the first time a pair (k, b) is seen; returns
+ * HPXGS_E_CAPTURE if that first time happens inside stream capture. */
+int hpxgs_tile_rho(int k, int b, double* rho, hpxgs_stream_t stream);
+
+/* Fill the rho cache for every (view order, tile_level) pair of `views`.
+ * Call once before capturing forward/backward calls into a CUDA graph. */
+int hpxgs_prepare(const hpxgs_view* views, int nviews, const hpxgs_config* cfg, hpxgs_stream_t stream);
+
+/* FoV mask M_C(p) (Sec. 3.1) of one view as bits: bit (p & 31) of word p >> 5.
+ * mask_bits: device uint32 [Npix/32]. Decided in FP32 with an FP64 re-check
+ * within 1e-4 of the boundary. */
+int hpxgs_mask_build(const hpxgs_view* view, const hpxgs_config* cfg, uint32_t* mask_bits,
+                     hpxgs_stream_t stream);
+
+/* ---- HEALPix batch utilities (device arrays of n entries) ---- */
+/* Pixel centre unit vectors of NESTED pixels (HEALPix frame), FP32 and/or FP64 (either may be NULL). */
+int hpxgs_pix2vec_nest(int k, const int64_t* pix, int64_t n, float* vec32, double* vec64, hpxgs_stream_t stream);
+/* NESTED pixel containing each direction (FP64 input, need not be normalised). */
+int hpxgs_vec2pix_nest(int k, const double* vec, int64_t n, int64_t* pix, hpxgs_stream_t stream);
+/* NESTED <-> RING index conversion. */
+int hpxgs_nest2ring(int k, const int64_t* in, int64_t n, int64_t* out, hpxgs_stream_t stream);
+int hpxgs_ring2nest(int k, const int64_t* in, int64_t n, int64_t* out, hpxgs_stream_t stream);
+/* 8-neighbourhood (pixels sharing a vertex), out [n,8], -1 where the pixel
+ * has only 7 neighbours; order: (dx,dy) = (-1,-1),(-1,0),(-1,1),(0,-1),(0,1),(1,-1),(1,0),(1,1)
+ * in the face's (x, y) frame. Requires k >= 1. */
+int hpxgs_neighbours_nest(int k, const int64_t* pix, int64_t n, int64_t* out, hpxgs_stream_t stream);
+
+/* ---- rasterizer (Algorithm 1 forward; Sec. 3.2 backward) ---- */
+
+/* Bytes of workspace for hpxgs_forward/hpxgs_backward/hpxgs_count_pairs with
+ * P Gaussians, these views, and room for capacity_pairs (Gaussian, tile) pairs. */
+int hpxgs_forward_workspace_size(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+                                 int64_t capacity_pairs, size_t* bytes);
+
+/* Forward render of nviews views in one batch (Algorithm 1):
+ *  1. preprocess per (view, Gaussian): t, r, Sigma_arc (Eqs. 1-2), conic,
+ *     r_s = 3 sqrt(lambda_max), SH colour;
+ *  2. stable radix sort of the Gaussians by radial depth r;
+ *  3. per Gaussian in depth order: RING query (Algorithm 3) + exact tile
+ *     membership -> counts, exclusive scan, emission of (tile, Gaussian) pairs;
+ *  4. stable radix sort of the pairs by global tile id, per-tile ranges;
+ *  5. per tile, per pixel: front-to-back compositing with early exit at
+ *     T < eps_T (Eq. unified_rendering).
+ * Outputs (packed over views, see "pixel base"): maps [sum Npix, 3],
+ * T_final [sum Npix], last [sum Npix] (number of list entries processed),
+ * mask_bits [sum Npix / 32] (may be NULL), radii [nviews * P] (r_s in rad,
+ * 0 when culled; may be NULL). The workspace keeps what hpxgs_backward needs;
+ * do not modify it in between. If more than capacity_pairs pairs are needed,
+ * HPXGS_F_CAPACITY is set in *status, the extra pairs are dropped and the
+ * outputs are incomplete: grow the capacity and call again. */
+int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+                  void* workspace, size_t workspace_bytes, int64_t capacity_pairs,
+                  float* maps, float* T_final, uint32_t* last, uint32_t* mask_bits, float* radii,
+                  int32_t* status, hpxgs_stream_t stream);
+
+/* Backward (Sec. 3.2, Eqs. backward_lat_scale, grad_via_J_S): from dL/dmaps
+ * (packed like maps) and the forward's T_final/last, walk each tile list in
+ * reverse recovering T by division, accumulate per-(view, Gaussian) partials
+ * (warp shuffles, then one global atomic per block and entry), then chain
+ * them to the parameters. Gradients are written (not accumulated): dmeans
+ * [P,3], dscales [P,3], drotations [P,4] (w.r.t. the unnormalised q),
+ * dopacities [P], dsh [P,K,3], summed over the views. The cull, cutoff, clamp
+ * and termination sets of the forward are held fixed. */
+int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+                   void* workspace, size_t workspace_bytes, int64_t capacity_pairs,
+                   const float* dL_dmaps, const float* T_final, const uint32_t* last,
+                   float* dmeans, float* dscales, float* drotations, float* dopacities, float* dsh,
+                   int32_t* status, hpxgs_stream_t stream);
+
+/* Steps 1-3 of hpxgs_forward without emission: writes the total number of
+ * (Gaussian, tile) pairs the views need to *count (device uint64). Used to
+ * size capacity and for memory-based admission. */
+int hpxgs_count_pairs(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+                      void* workspace, size_t workspace_bytes, uint64_t* count, int32_t* status,
+                      hpxgs_stream_t stream);
+
+/* Device pointers into a forward workspace (for inspection and tests). */
+typedef struct {
+  const float* records;        /* [nviews*P, 16]: g(3), o, e_east(3), conic_a, e_north(3), conic_b, colour(3), conic_c */
+  const float* radii;          /* [nviews*P] r_s */
+  const float* depth;          /* [nviews*P] radial depth r */
+  const uint32_t* pair_tiles;  /* [n_pairs] sorted global tile ids (after hpxgs_forward) */
+  const uint32_t* pair_ids;    /* [n_pairs] Gaussian ids v*P + i in list order */
+  const uint32_t* ranges;      /* [total_tiles, 2] start/end into pair_ids */
+  const uint32_t* n_pairs;     /* device scalar: pairs needed (may exceed capacity) */
+  const float* accum;          /* [nviews*P, HPXGS_NACC] backward partials (after hpxgs_backward) */
+  int64_t total_tiles;
+} hpxgs_workspace_view;
+int hpxgs_workspace_inspect(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+                            int64_t capacity_pairs, const void* workspace, hpxgs_workspace_view* out);
+
+/* ---- HEALPix-SSIM and training loss (Sec. 4.1; Eq. supp_hssim_eval) ----
+ * Window of pixel q: q and its in-mask 8- (7-) neighbours, weights
+ * exp(-theta^2 / (2 sigma^2)) of the centre-to-centre angle, sigma =
+ * 1.5 sqrt(Omega_pix), normalised per window; SSIM constants C1 = 0.01^2,
+ * C2 = 0.03^2; h_q = mean over RGB; HSSIM = masked mean of h_q;
+ * loss = (1 - lambda) mean_mask |I - G| + lambda (1 - HSSIM). */
+int hpxgs_hssim_workspace_size(int k, size_t* bytes);
+/* out3 (device float[3]) = {loss, HSSIM, L1}. I, G: [Npix,3]; mask_bits as hpxgs_mask_build. */
+int hpxgs_hssim_forward(const float* I, const float* G, const uint32_t* mask_bits, int k, float lambda,
+                        void* workspace, size_t workspace_bytes, float* out3, hpxgs_stream_t stream);
+/* dI = dloss * dL/dI (written, zero outside the mask); dloss is a device scalar
+ * (may be NULL for 1). Needs the workspace of the matching hpxgs_hssim_forward. */
+int hpxgs_hssim_backward(const float* I, const float* G, const uint32_t* mask_bits, int k, float lambda,
+                         const void* workspace, size_t workspace_bytes, const float* dloss, float* dI,
+                         hpxgs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPXGS_H_ */

@@ -1,0 +1,412 @@
+// Host API basics, FoV masks (Sec. 3.1, Sec. D.1), HEALPix batch utilities,
+// the tile radius rho(k, b) and the workspace layout of the rasterizer.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "hpx_math.cuh"
+#include "internal.cuh"
+
+using namespace hpx;
+
+namespace hpxgs {
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+  }
+  return n;
+}
+
+// ----------------------------------------------------------------------------
+// FoV mask. Margin >= 0 inside; the FP32 decision is re-taken in FP64 when the
+// FP32 margin is within 1e-4 of the boundary.
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T camera_margin(int kind, T dx, T dy, T dz, T tanx, T tany, T wx, T wy) {
+  if (kind == HPXGS_CAM_PINHOLE) {
+    T mx = tanx * dz - fabs(dx), my = tany * dz - fabs(dy);
+    return mx < my ? mx : my;
+  }
+  // anisotropic equidistant fisheye: psi <= (pi/2) w_eff(gamma),
+  // w_eff = sqrt((wx cos g)^2 + (wy sin g)^2) with cos g = dx / rxy, sin g = dy / rxy
+  T rxy = sqrt(dx * dx + dy * dy);
+  T psi = atan2(rxy, dz);
+  T weff = rxy > T(0) ? sqrt(wx * wx * dx * dx + wy * wy * dy * dy) / rxy : wx;
+  return T(0.5 * kPi) * weff - psi;
+}
+
+__device__ __forceinline__ bool pixel_in_mask(const ViewParams& vp, uint32_t p) {
+  if (vp.kind == HPXGS_CAM_FULL) return true;
+  float3 h = pix2vec_f32(vp.k, p);
+  // camera direction (d_x, d_y, d_z) = HEALPix (Y, Z, X)
+  float m = camera_margin<float>(vp.kind, h.y, h.z, h.x, vp.tanx, vp.tany, vp.wx, vp.wy);
+  if (fabsf(m) > 1e-4f) return m >= 0.0f;
+  double3 hd = pix2vec_f64(vp.k, p);
+  double md = camera_margin<double>(vp.kind, hd.y, hd.z, hd.x, vp.tanx64, vp.tany64, vp.wx64, vp.wy64);
+  return md >= 0.0;
+}
+
+// One thread per pixel; a warp's 32 consecutive NESTED pixels form one mask word.
+// tile_flags (optional) gets bit 0 set for every tile with an in-mask pixel.
+__global__ void k_mask(ViewParams vp, int b, uint32_t* __restrict__ words, uint32_t* __restrict__ tile_flags) {
+  const uint32_t npix = 12u << (2 * vp.k);
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;   // npix is a multiple of 32
+  if (p >= npix) return;
+  bool in = pixel_in_mask(vp, p);
+  uint32_t bits = __ballot_sync(0xffffffffu, in);
+  if ((threadIdx.x & 31) == 0) {
+    words[p >> 5] = bits;
+    if (tile_flags && bits) atomicOr(&tile_flags[p >> (2 * b)], 1u);
+  }
+}
+
+int launch_mask(const ViewParams& vp, int b, uint32_t* words, uint32_t* tile_flags, cudaStream_t s) {
+  const uint32_t npix = 12u << (2 * vp.k);
+  k_mask<<<(npix + 255) / 256, 256, 0, s>>>(vp, b, words, tile_flags);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+
+// ----------------------------------------------------------------------------
+// rho(k, b): per tile, the smallest dot between the tile centre and its pixel
+// centres (FP64), minimised over tiles with an atomic on the double's bits
+// (all dots are positive, so the bit patterns order like the values).
+// ----------------------------------------------------------------------------
+__global__ void k_tile_mindot(int k, int b, unsigned long long* out) {
+  const int kt = k - b;
+  const uint32_t tile = blockIdx.x;
+  const uint32_t per = 1u << (2 * b);
+  double3 c = pix2vec_f64(kt, tile);
+  double best = 2.0;
+  for (uint32_t j = threadIdx.x; j < per; j += blockDim.x) {
+    double3 p = pix2vec_f64(k, tile * per + j);
+    double d = c.x * p.x + c.y * p.y + c.z * p.z;
+    best = fmin(best, d);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
+  __shared__ double wmin[32];
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 2.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m = fmin(m, wmin[w]);
+    atomicMin(out, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+static std::mutex g_rho_mu;
+static std::map<std::pair<int, int>, double> g_rho;
+
+static bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+  return st != cudaStreamCaptureStatusNone;
+}
+
+// Result word of k_tile_mindot. The computation runs once per (k, b) under
+// g_rho_mu, so no two calls use the word at the same time.
+static __device__ unsigned long long d_mindot;
+
+int tile_rho(int k, int b, double* rho, cudaStream_t s) {
+  if (k < b || b < 0 || k > 13) return HPXGS_E_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_rho_mu);
+  auto it = g_rho.find({k, b});
+  if (it != g_rho.end()) { *rho = it->second; return HPXGS_OK; }
+  if (stream_capturing(s)) return HPXGS_E_CAPTURE;
+  const double two = 2.0;
+  unsigned long long init = 0;
+  std::memcpy(&init, &two, sizeof(init));
+  unsigned long long* dptr = nullptr;
+  HPXGS_CUDA_CHECK(cudaGetSymbolAddress((void**)&dptr, d_mindot));
+  HPXGS_CUDA_CHECK(cudaMemcpyAsync(dptr, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  const int ntile = 12 << (2 * (k - b));
+  const int per = 1 << (2 * b);
+  k_tile_mindot<<<ntile, per < 256 ? (per < 32 ? 32 : per) : 256, 0, s>>>(k, b, dptr);
+  HPXGS_LAUNCH_CHECK();
+  unsigned long long res = 0;
+  HPXGS_CUDA_CHECK(cudaMemcpyAsync(&res, dptr, sizeof(res), cudaMemcpyDeviceToHost, s));
+  HPXGS_CUDA_CHECK(cudaStreamSynchronize(s));
+  double mindot = 0;
+  std::memcpy(&mindot, &res, sizeof(mindot));
+  double r = std::acos(std::fmin(1.0, mindot));
+  r = std::ceil(r * 1048576.0) / 1048576.0;
+  g_rho[{k, b}] = r;
+  *rho = r;
+  return HPXGS_OK;
+}
+
+// ----------------------------------------------------------------------------
+// View table and workspace layout
+// ----------------------------------------------------------------------------
+static bool valid_view(const hpxgs_view& v, int b) {
+  if (v.nside_log2 < b || v.nside_log2 > 13) return false;
+  if (v.cam.kind < 0 || v.cam.kind > 2) return false;
+  if (v.cam.kind == HPXGS_CAM_PINHOLE &&
+      !(v.cam.fov_x_deg > 0 && v.cam.fov_x_deg < 180 && v.cam.fov_y_deg > 0 && v.cam.fov_y_deg < 180))
+    return false;
+  if (v.cam.kind == HPXGS_CAM_FISHEYE &&
+      !(v.cam.fov_x_deg > 0 && v.cam.fov_x_deg <= 360 && v.cam.fov_y_deg > 0 && v.cam.fov_y_deg <= 360))
+    return false;
+  for (int i = 0; i < 9; ++i) if (!std::isfinite(v.W[i])) return false;
+  for (int i = 0; i < 3; ++i) if (!std::isfinite(v.b[i])) return false;
+  return true;
+}
+
+static bool valid_cfg(const hpxgs_config* c) {
+  return c && c->tile_level >= 3 && c->tile_level <= 5 && c->eps_T >= 0 && c->eps_T < 1 &&
+         c->alpha_max > 0 && c->alpha_max < 1 && c->cutoff_m > 0 && c->near_plane >= 0;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int make_layout(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg, int64_t cap, Layout* L) {
+  if (!valid_cfg(cfg) || !views || nviews < 1 || nviews > HPXGS_MAX_VIEWS || P < 0 || cap < 0 ||
+      cap > 0xffffffffLL)
+    return HPXGS_E_INVALID_ARG;
+  const int b = cfg->tile_level;
+  int64_t tiles = 0, pix = 0;
+  for (int v = 0; v < nviews; ++v) {
+    if (!valid_view(views[v], b)) return HPXGS_E_INVALID_ARG;
+    tiles += 12LL << (2 * (views[v].nside_log2 - b));
+    pix += 12LL << (2 * views[v].nside_log2);
+  }
+  const int64_t PV = (int64_t)P * nviews;
+  if (PV >= 0xffffffffLL || tiles >= 0x7fffffffLL) return HPXGS_E_INVALID_ARG;
+  L->P = P; L->PV = PV; L->cap = cap; L->total_tiles = tiles; L->total_pix = pix;
+  int G = 2 * num_sms();
+  if (G > kMaxSortBlocks) G = kMaxSortBlocks;
+  L->sort_blocks = G;
+  int bits = 1;
+  while ((1LL << bits) < tiles) ++bits;
+  L->pair_bits = bits;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+  const size_t pv = (size_t)(PV > 0 ? PV : 1);
+  const size_t cp = (size_t)(cap > 0 ? cap : 1);
+  L->tile_flags = take(sizeof(uint32_t) * tiles);
+  L->records = take(64 * pv);
+  L->radii = take(4 * pv);
+  L->depth = take(4 * pv);
+  L->key_a = take(4 * pv);
+  L->key_b = take(4 * pv);
+  L->val_a = take(4 * pv);
+  L->val_b = take(4 * pv);
+  L->counts = take(4 * pv);
+  L->offsets = take(8 * (pv + 1));
+  L->scan_part = take(8 * (G + 1));
+  L->pair_key_a = take(4 * cp);
+  L->pair_key_b = take(4 * cp);
+  L->pair_val_a = take(4 * cp);
+  L->pair_val_b = take(4 * cp);
+  L->hist = take(4 * 256 * (size_t)G);
+  L->ranges = take(8 * tiles);
+  L->counters = take(4 * C_COUNT);
+  L->accum = take(4 * HPXGS_NACC * pv);
+  L->tile_order = take(4 * tiles);
+  L->total = o;
+  return HPXGS_OK;
+}
+
+int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+               cudaStream_t stream, bool need_rho, ViewTable* vt) {
+  if (!valid_cfg(cfg) || !views || nviews < 1 || nviews > HPXGS_MAX_VIEWS) return HPXGS_E_INVALID_ARG;
+  if (g && (g->sh_degree < 0 || g->sh_degree > 3 || g->P != P)) return HPXGS_E_INVALID_ARG;
+  std::memset(vt, 0, sizeof(*vt));
+  vt->nviews = nviews; vt->P = P; vt->b = cfg->tile_level;
+  vt->sh_degree = g ? g->sh_degree : 0;
+  vt->eps_T = cfg->eps_T; vt->alpha_max = cfg->alpha_max; vt->cutoff = cfg->cutoff_m;
+  vt->near_plane = cfg->near_plane;
+  for (int c = 0; c < 3; ++c) vt->bg[c] = cfg->bg[c];
+  vt->write_outside = cfg->write_outside;
+  int64_t tile_base = 0, pix_base = 0;
+  for (int v = 0; v < nviews; ++v) {
+    const hpxgs_view& hv = views[v];
+    if (!valid_view(hv, cfg->tile_level)) return HPXGS_E_INVALID_ARG;
+    ViewParams& p = vt->v[v];
+    for (int i = 0; i < 9; ++i) p.W[i] = hv.W[i];
+    for (int i = 0; i < 3; ++i) p.b[i] = hv.b[i];
+    for (int j = 0; j < 3; ++j) p.cam[j] = -(hv.W[j] * hv.b[0] + hv.W[3 + j] * hv.b[1] + hv.W[6 + j] * hv.b[2]);
+    p.k = hv.nside_log2;
+    p.kind = hv.cam.kind;
+    p.tanx64 = std::tan(0.5 * hv.cam.fov_x_deg * kPi / 180.0);
+    p.tany64 = std::tan(0.5 * hv.cam.fov_y_deg * kPi / 180.0);
+    p.wx64 = hv.cam.fov_x_deg / 180.0;
+    p.wy64 = hv.cam.fov_y_deg / 180.0;
+    p.tanx = (float)p.tanx64; p.tany = (float)p.tany64; p.wx = (float)p.wx64; p.wy = (float)p.wy64;
+    const double omega_pix = 4.0 * kPi / (12.0 * std::ldexp(1.0, 2 * p.k));
+    p.blur = cfg->blur_rad2 < 0 ? (float)(0.3 * omega_pix) : cfg->blur_rad2;
+    p.ntiles = 12 << (2 * (p.k - cfg->tile_level));
+    p.tile_base = (int)tile_base;
+    p.pix_base = pix_base;
+    p.rho = 0;
+    if (need_rho) {
+      int rc = tile_rho(p.k, cfg->tile_level, &p.rho, stream);
+      if (rc != HPXGS_OK) return rc;
+    }
+    tile_base += p.ntiles;
+    pix_base += 12LL << (2 * p.k);
+  }
+  vt->total_tiles = (int)tile_base;
+  vt->total_pix = pix_base;
+  return HPXGS_OK;
+}
+
+// ----------------------------------------------------------------------------
+// HEALPix batch utilities
+// ----------------------------------------------------------------------------
+__global__ void k_pix2vec(int k, const int64_t* pix, int64_t n, float* v32, double* v64) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t p = (uint32_t)pix[i];
+  if (v32) { float3 a = pix2vec_f32(k, p); v32[3 * i] = a.x; v32[3 * i + 1] = a.y; v32[3 * i + 2] = a.z; }
+  if (v64) { double3 a = pix2vec_f64(k, p); v64[3 * i] = a.x; v64[3 * i + 1] = a.y; v64[3 * i + 2] = a.z; }
+}
+__global__ void k_vec2pix(int k, const double* v, int64_t n, int64_t* pix) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  pix[i] = vec2pix_f64(k, make_double3(v[3 * i], v[3 * i + 1], v[3 * i + 2]));
+}
+__global__ void k_nest2ring(int k, const int64_t* in, int64_t n, int64_t* out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = nest2ring(k, (uint32_t)in[i]);
+}
+__global__ void k_ring2nest(int k, const int64_t* in, int64_t n, int64_t* out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = ring2nest(k, in[i]);
+}
+__global__ void k_neighbours(int k, const int64_t* in, int64_t n, int64_t* out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  FaceXY c = nest_to_fxy(k, (uint32_t)in[i]);
+  int s = 0;
+  for (int dx = -1; dx <= 1; ++dx)
+    for (int dy = -1; dy <= 1; ++dy) {
+      if (dx == 0 && dy == 0) continue;
+      out[8 * i + (s++)] = neighbour_nest(k, c.f, c.x, c.y, dx, dy);
+    }
+}
+
+static int grid_for(int64_t n) { return (int)((n + 255) / 256); }
+
+}  // namespace hpxgs
+
+using namespace hpxgs;
+
+extern "C" {
+
+const char* hpxgs_strerror(int code) {
+  switch (code) {
+    case HPXGS_OK: return "ok";
+    case HPXGS_E_INVALID_ARG: return "invalid argument";
+    case HPXGS_E_CAPACITY: return "pair capacity exceeded";
+    case HPXGS_E_TIMEOUT: return "bounded device wait timed out";
+    case HPXGS_E_CUDA: return "CUDA error";
+    case HPXGS_E_UNIMPLEMENTED: return "not implemented";
+    case HPXGS_E_WORKSPACE: return "workspace too small";
+    case HPXGS_E_CAPTURE: return "call needs a host synchronisation inside stream capture";
+    default: return "unknown status";
+  }
+}
+
+int hpxgs_status_error(int32_t flags) {
+  if (flags & HPXGS_F_CAPACITY) return HPXGS_E_CAPACITY;
+  if (flags & HPXGS_F_TIMEOUT) return HPXGS_E_TIMEOUT;
+  return HPXGS_OK;
+}
+
+void hpxgs_config_default(hpxgs_config* c) {
+  if (!c) return;
+  c->tile_level = 4;
+  c->eps_T = 1e-4f;
+  c->alpha_max = 0.99f;
+  c->cutoff_m = 9.0f;
+  c->blur_rad2 = -1.0f;
+  c->near_plane = 0.2f;
+  c->bg[0] = c->bg[1] = c->bg[2] = 0.0f;
+  c->lambda_ssim = 0.2f;
+  c->write_outside = 1;
+}
+
+int hpxgs_nside_for_image(int kind, double W, double H, double fovx, double fovy, double* nstar, int* k,
+                          int* kL, int* kH) {
+  if (!(W > 0 && H > 0)) return HPXGS_E_INVALID_ARG;
+  const double hx = 0.5 * fovx * kPi / 180.0, hy = 0.5 * fovy * kPi / 180.0;
+  double om;
+  if (kind == HPXGS_CAM_FULL) om = 4.0 * kPi;
+  else if (kind == HPXGS_CAM_FISHEYE) om = 2.0 * kPi * (1.0 - std::cos(hx));
+  else if (kind == HPXGS_CAM_PINHOLE) om = 4.0 * std::asin(std::sin(hx) * std::sin(hy));
+  else return HPXGS_E_INVALID_ARG;
+  if (!(om > 0)) return HPXGS_E_INVALID_ARG;
+  const double ns = std::sqrt(4.0 * kPi * W * H / (12.0 * om));
+  const double l2 = std::log2(ns);
+  if (nstar) *nstar = ns;
+  if (k) *k = (int)std::lround(l2);
+  if (kL) *kL = (int)std::floor(l2);
+  if (kH) *kH = (int)std::ceil(l2);
+  return HPXGS_OK;
+}
+
+int hpxgs_tile_rho(int k, int b, double* rho, hpxgs_stream_t stream) {
+  if (!rho) return HPXGS_E_INVALID_ARG;
+  return tile_rho(k, b, rho, (cudaStream_t)stream);
+}
+
+int hpxgs_prepare(const hpxgs_view* views, int nviews, const hpxgs_config* cfg, hpxgs_stream_t stream) {
+  ViewTable* vt = new ViewTable;
+  int rc = make_table(nullptr, 0, views, nviews, cfg, (cudaStream_t)stream, true, vt);
+  delete vt;
+  return rc;
+}
+
+int hpxgs_mask_build(const hpxgs_view* view, const hpxgs_config* cfg, uint32_t* mask_bits, hpxgs_stream_t stream) {
+  if (!view || !mask_bits) return HPXGS_E_INVALID_ARG;
+  ViewTable* vt = new ViewTable;
+  int rc = make_table(nullptr, 0, view, 1, cfg, (cudaStream_t)stream, false, vt);
+  if (rc == HPXGS_OK) rc = launch_mask(vt->v[0], cfg->tile_level, mask_bits, nullptr, (cudaStream_t)stream);
+  delete vt;
+  return rc;
+}
+
+int hpxgs_pix2vec_nest(int k, const int64_t* pix, int64_t n, float* v32, double* v64, hpxgs_stream_t s) {
+  if (k < 0 || k > 13 || n < 0 || (n > 0 && !pix)) return HPXGS_E_INVALID_ARG;
+  if (n == 0) return HPXGS_OK;
+  k_pix2vec<<<grid_for(n), 256, 0, (cudaStream_t)s>>>(k, pix, n, v32, v64);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+int hpxgs_vec2pix_nest(int k, const double* v, int64_t n, int64_t* pix, hpxgs_stream_t s) {
+  if (k < 0 || k > 13 || n < 0 || (n > 0 && (!v || !pix))) return HPXGS_E_INVALID_ARG;
+  if (n == 0) return HPXGS_OK;
+  k_vec2pix<<<grid_for(n), 256, 0, (cudaStream_t)s>>>(k, v, n, pix);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+int hpxgs_nest2ring(int k, const int64_t* in, int64_t n, int64_t* out, hpxgs_stream_t s) {
+  if (k < 0 || k > 13 || n < 0 || (n > 0 && (!in || !out))) return HPXGS_E_INVALID_ARG;
+  if (n == 0) return HPXGS_OK;
+  k_nest2ring<<<grid_for(n), 256, 0, (cudaStream_t)s>>>(k, in, n, out);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+int hpxgs_ring2nest(int k, const int64_t* in, int64_t n, int64_t* out, hpxgs_stream_t s) {
+  if (k < 0 || k > 13 || n < 0 || (n > 0 && (!in || !out))) return HPXGS_E_INVALID_ARG;
+  if (n == 0) return HPXGS_OK;
+  k_ring2nest<<<grid_for(n), 256, 0, (cudaStream_t)s>>>(k, in, n, out);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+int hpxgs_neighbours_nest(int k, const int64_t* in, int64_t n, int64_t* out, hpxgs_stream_t s) {
+  if (k < 1 || k > 13 || n < 0 || (n > 0 && (!in || !out))) return HPXGS_E_INVALID_ARG;
+  if (n == 0) return HPXGS_OK;
+  k_neighbours<<<grid_for(n), 256, 0, (cudaStream_t)s>>>(k, in, n, out);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+
+}  // extern "C"

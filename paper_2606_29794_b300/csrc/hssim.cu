@@ -1,0 +1,221 @@
+// HEALPix-SSIM and the L1 + HSSIM training loss (Sec. 4.1; Eq. supp_hssim_eval).
+//
+// Window of an in-mask pixel q: q and its in-mask 8- (or 7-) neighbours, found
+// with the face-edge neighbour walk; weights exp(-theta^2 / (2 sigma^2)) of the
+// angle between pixel centres (sigma = 1.5 sqrt(Omega_pix)), normalised over the
+// window. Using the true angle gives isotropic kernels near the equator and the
+// anisotropic, renormalised ones at the poles and the 24 seven-neighbour pixels.
+//
+// k_hssim_fwd: per pixel, local statistics, SSIM per channel, block partial sums
+//   of h_q, |I - G| and the mask count, and the per-pixel coefficients of the
+//   gradient (alpha + beta x_p + gamma y_p per channel, divided by the window sum).
+// k_hssim_reduce: fixed-order sum of the block partials -> {loss, HSSIM, L1}.
+// k_hssim_bwd: per pixel, gather over the windows that contain it.
+#include "hpx_math.cuh"
+#include "internal.cuh"
+
+using namespace hpx;
+
+namespace hpxgs {
+
+constexpr float kC1 = 1e-4f, kC2 = 9e-4f;
+constexpr int kHThreads = 256;
+
+__device__ __forceinline__ bool mbit(const uint32_t* m, uint32_t p) { return (m[p >> 5] >> (p & 31)) & 1u; }
+
+__device__ __forceinline__ float pair_weight(float3 a, float3 b, float inv2sig2) {
+  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  const float ch = sqrtf(dx * dx + dy * dy + dz * dz);
+  const float th = 2.f * asinf(fminf(1.f, 0.5f * ch));
+  return __expf(-th * th * inv2sig2);
+}
+
+struct HSSIMWs {
+  size_t coef, part, nmask, total;
+};
+static HSSIMWs hssim_layout(int k) {
+  const size_t npix = 12ull << (2 * k);
+  const size_t nblocks = (npix + kHThreads - 1) / kHThreads;
+  HSSIMWs L;
+  L.coef = 0;
+  L.part = (sizeof(float) * 9 * npix + 255) / 256 * 256;
+  L.nmask = L.part + (sizeof(double) * 3 * nblocks + 255) / 256 * 256;
+  L.total = L.nmask + 256;
+  return L;
+}
+
+__global__ void __launch_bounds__(kHThreads) k_hssim_fwd(int k, const float* __restrict__ I, const float* __restrict__ Gt,
+                                                         const uint32_t* __restrict__ mask, float* __restrict__ coef,
+                                                         double* __restrict__ part) {
+  const uint32_t npix = 12u << (2 * k);
+  const uint32_t p = blockIdx.x * kHThreads + threadIdx.x;
+  double h = 0.0, l1 = 0.0, cnt = 0.0;
+  if (p < npix && mbit(mask, p)) {
+    const float omega = 4.f * (float)kPi / (float)npix;
+    const float inv2sig2 = 1.f / (2.f * 2.25f * omega);
+    const float3 cq = pix2vec_f32(k, p);
+    const FaceXY c = nest_to_fxy(k, p);
+    uint32_t idx[9];
+    float w[9];
+    int n = 0;
+    idx[n] = p; w[n] = 1.f; ++n;
+    for (int dx = -1; dx <= 1; ++dx)
+      for (int dy = -1; dy <= 1; ++dy) {
+        if (dx == 0 && dy == 0) continue;
+        const int64_t nb = neighbour_nest(k, c.f, c.x, c.y, dx, dy);
+        if (nb < 0 || !mbit(mask, (uint32_t)nb)) continue;
+        idx[n] = (uint32_t)nb;
+        w[n] = pair_weight(cq, pix2vec_f32(k, (uint32_t)nb), inv2sig2);
+        ++n;
+      }
+    float Z = 0.f;
+    for (int j = 0; j < n; ++j) Z += w[j];
+    const float iZ = 1.f / Z;
+    float hs = 0.f;
+    for (int ch = 0; ch < 3; ++ch) {
+      float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
+      for (int j = 0; j < n; ++j) {
+        const float wj = w[j] * iZ;
+        const float x = I[3 * (size_t)idx[j] + ch], y = Gt[3 * (size_t)idx[j] + ch];
+        mx += wj * x; my += wj * y; xx += wj * x * x; yy += wj * y * y; xy += wj * x * y;
+      }
+      const float vx = xx - mx * mx, vy = yy - my * my, cxy = xy - mx * my;
+      const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
+      const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
+      const float iB = 1.f / (B1 * B2);
+      const float ssim = A1 * A2 * iB;
+      hs += ssim;
+      // partials w.r.t. (mu_x, var_x, cov_xy)
+      const float dmu = (2.f * my * A2 - ssim * B2 * 2.f * mx) * iB;
+      const float dvar = -ssim / B2;
+      const float dcov = 2.f * A1 * iB;
+      // d ssim_q / d x_p = w_qp (alpha + beta x_p + gamma y_p), w_qp = e_qp / Z
+      coef[9 * (size_t)p + 3 * ch + 0] = (dmu - 2.f * mx * dvar - my * dcov) * iZ;
+      coef[9 * (size_t)p + 3 * ch + 1] = 2.f * dvar * iZ;
+      coef[9 * (size_t)p + 3 * ch + 2] = dcov * iZ;
+      l1 += fabsf(I[3 * (size_t)p + ch] - Gt[3 * (size_t)p + ch]);
+    }
+    h = hs / 3.f;
+    cnt = 1.0;
+  }
+  // block reduction in a fixed order
+  __shared__ double sh[3][kHThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    h += __shfl_xor_sync(0xffffffffu, h, o);
+    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { sh[0][warp] = h; sh[1][warp] = l1; sh[2][warp] = cnt; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, cc = 0;
+    for (int w2 = 0; w2 < kHThreads / 32; ++w2) { a += sh[0][w2]; b += sh[1][w2]; cc += sh[2][w2]; }
+    part[3 * blockIdx.x + 0] = a; part[3 * blockIdx.x + 1] = b; part[3 * blockIdx.x + 2] = cc;
+  }
+}
+
+__global__ void k_hssim_reduce(const double* __restrict__ part, int nblocks, float lambda, float* out3, double* nmask) {
+  __shared__ double s[3][256];
+  double a = 0, b = 0, c = 0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) { a += part[3 * i]; b += part[3 * i + 1]; c += part[3 * i + 2]; }
+  s[0][threadIdx.x] = a; s[1][threadIdx.x] = b; s[2][threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) for (int r = 0; r < 3; ++r) s[r][threadIdx.x] += s[r][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double nm = s[2][0];
+    const double hssim = nm > 0 ? s[0][0] / nm : 0.0;
+    const double l1 = nm > 0 ? s[1][0] / (3.0 * nm) : 0.0;
+    out3[0] = (float)((1.0 - lambda) * l1 + lambda * (1.0 - hssim));
+    out3[1] = (float)hssim;
+    out3[2] = (float)l1;
+    *nmask = nm;
+  }
+}
+
+__global__ void __launch_bounds__(kHThreads) k_hssim_bwd(int k, const float* __restrict__ I, const float* __restrict__ Gt,
+                                                         const uint32_t* __restrict__ mask, const float* __restrict__ coef,
+                                                         const double* __restrict__ nmask, float lambda,
+                                                         const float* __restrict__ dloss, float* __restrict__ dI) {
+  const uint32_t npix = 12u << (2 * k);
+  const uint32_t p = blockIdx.x * kHThreads + threadIdx.x;
+  if (p >= npix) return;
+  if (!mbit(mask, p)) { dI[3 * (size_t)p] = 0.f; dI[3 * (size_t)p + 1] = 0.f; dI[3 * (size_t)p + 2] = 0.f; return; }
+  const float nm = (float)*nmask;
+  const float scale = (dloss ? *dloss : 1.f) / (3.f * nm);
+  const float omega = 4.f * (float)kPi / (float)npix;
+  const float inv2sig2 = 1.f / (2.f * 2.25f * omega);
+  const float3 cp = pix2vec_f32(k, p);
+  const FaceXY c = nest_to_fxy(k, p);
+  float x[3], y[3], g[3];
+  for (int ch = 0; ch < 3; ++ch) {
+    x[ch] = I[3 * (size_t)p + ch]; y[ch] = Gt[3 * (size_t)p + ch];
+    const float cf0 = coef[9 * (size_t)p + 3 * ch], cf1 = coef[9 * (size_t)p + 3 * ch + 1], cf2 = coef[9 * (size_t)p + 3 * ch + 2];
+    g[ch] = cf0 + cf1 * x[ch] + cf2 * y[ch];                 // q = p, e_pp = 1
+  }
+  for (int dx = -1; dx <= 1; ++dx)
+    for (int dy = -1; dy <= 1; ++dy) {
+      if (dx == 0 && dy == 0) continue;
+      const int64_t nb = neighbour_nest(k, c.f, c.x, c.y, dx, dy);
+      if (nb < 0 || !mbit(mask, (uint32_t)nb)) continue;
+      const float e = pair_weight(cp, pix2vec_f32(k, (uint32_t)nb), inv2sig2);
+      const float* cf = coef + 9 * (size_t)nb;
+      for (int ch = 0; ch < 3; ++ch) g[ch] += e * (cf[3 * ch] + cf[3 * ch + 1] * x[ch] + cf[3 * ch + 2] * y[ch]);
+    }
+  for (int ch = 0; ch < 3; ++ch) {
+    const float d = x[ch] - y[ch];
+    const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+    dI[3 * (size_t)p + ch] = scale * ((1.f - lambda) * sgn - lambda * g[ch]);
+  }
+}
+
+}  // namespace hpxgs
+
+using namespace hpxgs;
+
+extern "C" {
+
+int hpxgs_hssim_workspace_size(int k, size_t* bytes) {
+  if (k < 3 || k > 13 || !bytes) return HPXGS_E_INVALID_ARG;
+  *bytes = hssim_layout(k).total;
+  return HPXGS_OK;
+}
+
+int hpxgs_hssim_forward(const float* I, const float* G, const uint32_t* mask, int k, float lambda, void* ws,
+                        size_t ws_bytes, float* out3, hpxgs_stream_t stream) {
+  if (k < 3 || k > 13 || !I || !G || !mask || !ws || !out3 || !(lambda >= 0.f && lambda <= 1.f))
+    return HPXGS_E_INVALID_ARG;
+  HSSIMWs L = hssim_layout(k);
+  if (ws_bytes < L.total) return HPXGS_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t npix = 12u << (2 * k);
+  const int nblocks = (int)((npix + kHThreads - 1) / kHThreads);
+  char* w = static_cast<char*>(ws);
+  k_hssim_fwd<<<nblocks, kHThreads, 0, s>>>(k, I, G, mask, reinterpret_cast<float*>(w + L.coef),
+                                            reinterpret_cast<double*>(w + L.part));
+  k_hssim_reduce<<<1, 256, 0, s>>>(reinterpret_cast<double*>(w + L.part), nblocks, lambda, out3,
+                                   reinterpret_cast<double*>(w + L.nmask));
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+
+int hpxgs_hssim_backward(const float* I, const float* G, const uint32_t* mask, int k, float lambda, const void* ws,
+                         size_t ws_bytes, const float* dloss, float* dI, hpxgs_stream_t stream) {
+  if (k < 3 || k > 13 || !I || !G || !mask || !ws || !dI || !(lambda >= 0.f && lambda <= 1.f))
+    return HPXGS_E_INVALID_ARG;
+  HSSIMWs L = hssim_layout(k);
+  if (ws_bytes < L.total) return HPXGS_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t npix = 12u << (2 * k);
+  const int nblocks = (int)((npix + kHThreads - 1) / kHThreads);
+  const char* w = static_cast<const char*>(ws);
+  k_hssim_bwd<<<nblocks, kHThreads, 0, s>>>(k, I, G, mask, reinterpret_cast<const float*>(w + L.coef),
+                                            reinterpret_cast<const double*>(w + L.nmask), lambda, dloss, dI);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+// Shared host/device definitions of the rasterizer library (not part of the ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/hpxgs.h"
+
+namespace hpxgs {
+
+// Per-view constants, passed to kernels by value (kernel parameter space).
+struct ViewParams {
+  float W[9];          // world -> camera rotation
+  float b[3];
+  float cam[3];        // camera centre -W^T b (world)
+  int k;               // HEALPix order of the view
+  int kind;            // HPXGS_CAM_*
+  float tanx, tany;    // pinhole tan(fov/2)
+  float wx, wy;        // fisheye fov / 180 deg
+  double tanx64, tany64, wx64, wy64;
+  double rho;          // tile rho(k, b)
+  float blur;          // isotropic Sigma_arc term
+  int ntiles;          // 12 * 4^(k-b)
+  int64_t pix_base;    // first pixel of this view in packed outputs
+  int tile_base;       // first global tile id of this view
+  int pad;
+};
+
+struct ViewTable {
+  int nviews;
+  int P;
+  int b;               // tile level
+  int sh_degree;
+  float eps_T, alpha_max, cutoff, near_plane;
+  float bg[3];
+  int write_outside;
+  int total_tiles;
+  int pad;
+  int64_t total_pix;
+  ViewParams v[HPXGS_MAX_VIEWS];
+};
+
+// One record per (view, Gaussian): 4 x float4 = 64 bytes.
+//   r0 = (g.x, g.y, g.z, opacity)     g: unit direction of the centre, HEALPix frame
+//   r1 = (e1.x, e1.y, e1.z, conic_a)  e1: east tangent (increasing longitude)
+//   r2 = (e2.x, e2.y, e2.z, conic_b)  e2: north tangent
+//   r3 = (col.r, col.g, col.b, conic_c)
+// m = conic_a d1^2 + 2 conic_b d1 d2 + conic_c d2^2 in the (e1, e2) frame.
+constexpr int kRecFloat4 = 4;
+
+// Workspace layout of hpxgs_forward / hpxgs_backward. All offsets 256-aligned.
+struct Layout {
+  size_t tile_flags, records, radii, depth, key_a, key_b, val_a, val_b, counts, offsets, scan_part,
+         pair_key_a, pair_key_b, pair_val_a, pair_val_b, hist, ranges, counters, accum, tile_order,
+         total;
+  int64_t P, PV, cap, total_tiles, total_pix;
+  int sort_blocks;
+  int pair_bits;
+};
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;                     // items per thread per tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kMaxSortBlocks = 1024;
+
+// counters block (u32 each)
+enum Counter { C_NPAIRS = 0, C_WORK_FWD = 1, C_WORK_BWD = 2, C_NSORT = 3, C_NPAIRS_HI = 4, C_COUNT = 16 };
+
+int make_layout(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg, int64_t cap, Layout* L);
+int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+               cudaStream_t stream, bool need_rho, ViewTable* vt);
+int num_sms();
+
+}  // namespace hpxgs
+
+#define HPXGS_CUDA_CHECK(expr)                                   \
+  do {                                                           \
+    cudaError_t err__ = (expr);                                  \
+    if (err__ != cudaSuccess) return HPXGS_E_CUDA;               \
+  } while (0)
+
+#define HPXGS_LAUNCH_CHECK()                                     \
+  do {                                                           \
+    cudaError_t err__ = cudaGetLastError();                      \
+    if (err__ != cudaSuccess) return HPXGS_E_CUDA;               \
+  } while (0)

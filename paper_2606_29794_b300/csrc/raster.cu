@@ -1,0 +1,1133 @@
+// HEALPix Gaussian rasterizer: forward (Algorithm 1) and backward (Sec. 3.2).
+//
+// Forward pipeline of hpxgs_forward, all on the caller's stream:
+//   k_preprocess      per (view, Gaussian): record (64 B), depth key, r_s
+//   radix sort        Gaussians by float32 bits of the radial depth r (stable)
+//   k_tiles<count>    per Gaussian in depth order: RING query + exact membership
+//   scan              exclusive scan of the counts -> pair offsets, total
+//   k_tiles<emit>     write (global tile, Gaussian id) pairs in depth order
+//   radix sort        pairs by tile id only (stable: depth order is kept)
+//   k_ranges          per-tile [start, end)
+//   k_blend_fwd       persistent: one block per tile, one thread per pixel
+// Backward (hpxgs_backward): k_blend_bwd (reverse walk, per-Gaussian partials,
+// warp shuffles + one atomic per block and entry), k_preprocess_bwd.
+//
+// Geometry in the tangent-frame form: with g the unit direction of t = W mu + b
+// and (e1, e2) the east/north tangents at g, S_phi J = [e1; e2] / r exactly
+// (Eqs. 1-2), so Sigma_arc = (E W) Sigma3D (E W)^T / r^2. The pixel offset d is
+// the azimuthal-equidistant coordinate of the pixel direction about g, which
+// equals the haversine distance split by the bearing (Sec. 3.4).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "hpx_math.cuh"
+#include "internal.cuh"
+
+using namespace hpx;
+
+namespace hpxgs {
+
+int launch_mask(const ViewParams& vp, int b, uint32_t* words, uint32_t* tile_flags, cudaStream_t s);
+
+// Real SH normalisation constants sqrt((2l+1)/(4pi) (l-|m|)!/(l+|m|)!) (times sqrt2 for m != 0),
+// folded into the Cartesian polynomials of degree <= 3 (3DGS order and signs).
+__constant__ float kSH[10] = {0.28209479177387814f, 0.4886025119029199f, 1.0925484305920792f,
+                              0.31539156525252005f, 0.5462742152960396f, 0.5900435899266435f,
+                              2.890611442640554f,   0.4570457994644658f, 0.3731763325901154f,
+                              1.445305721320277f};
+
+// Basis Y_k(d), k < (deg+1)^2, and (optionally) its gradient in Cartesian coordinates.
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float* Y, float3* dY) {
+  const float C0 = kSH[0], C1 = kSH[1], C2a = kSH[2], C2b = kSH[3], C2c = kSH[4];
+  const float C3a = kSH[5], C3b = kSH[6], C3c = kSH[7], C3d = kSH[8], C3e = kSH[9];
+  Y[0] = C0;
+  if (dY) dY[0] = make_float3(0.f, 0.f, 0.f);
+  if (deg < 1) return;
+  Y[1] = -C1 * y; Y[2] = C1 * z; Y[3] = -C1 * x;
+  if (dY) { dY[1] = make_float3(0, -C1, 0); dY[2] = make_float3(0, 0, C1); dY[3] = make_float3(-C1, 0, 0); }
+  if (deg < 2) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = C2a * x * y; Y[5] = -C2a * y * z; Y[6] = C2b * (2.f * zz - xx - yy); Y[7] = -C2a * x * z;
+  Y[8] = C2c * (xx - yy);
+  if (dY) {
+    dY[4] = make_float3(C2a * y, C2a * x, 0.f);
+    dY[5] = make_float3(0.f, -C2a * z, -C2a * y);
+    dY[6] = make_float3(-2.f * C2b * x, -2.f * C2b * y, 4.f * C2b * z);
+    dY[7] = make_float3(-C2a * z, 0.f, -C2a * x);
+    dY[8] = make_float3(2.f * C2c * x, -2.f * C2c * y, 0.f);
+  }
+  if (deg < 3) return;
+  Y[9] = -C3a * y * (3.f * xx - yy);
+  Y[10] = C3b * x * y * z;
+  Y[11] = -C3c * y * (4.f * zz - xx - yy);
+  Y[12] = C3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  Y[13] = -C3c * x * (4.f * zz - xx - yy);
+  Y[14] = C3e * z * (xx - yy);
+  Y[15] = -C3a * x * (xx - 3.f * yy);
+  if (dY) {
+    dY[9] = make_float3(-6.f * C3a * x * y, -C3a * (3.f * xx - 3.f * yy), 0.f);
+    dY[10] = make_float3(C3b * y * z, C3b * x * z, C3b * x * y);
+    dY[11] = make_float3(2.f * C3c * x * y, -C3c * (4.f * zz - xx - 3.f * yy), -8.f * C3c * y * z);
+    dY[12] = make_float3(-6.f * C3d * x * z, -6.f * C3d * y * z, C3d * (6.f * zz - 3.f * xx - 3.f * yy));
+    dY[13] = make_float3(-C3c * (4.f * zz - 3.f * xx - yy), 2.f * C3c * x * y, -8.f * C3c * x * z);
+    dY[14] = make_float3(2.f * C3e * x * z, -2.f * C3e * y * z, C3e * (xx - yy));
+    dY[15] = make_float3(-C3a * (3.f * xx - 3.f * yy), 6.f * C3a * x * y, 0.f);
+  }
+}
+
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Everything preprocess computes for one (view, Gaussian); shared by forward and backward.
+struct Geo {
+  bool valid;
+  float3 t;          // camera frame
+  float r;
+  float3 g;          // HEALPix frame unit direction
+  float3 e1, e2;     // HEALPix frame east / north
+  float3 gc, e1c, e2c;  // same in the camera frame
+  float a1[3], a2[3];   // rows of S_phi J W = W^T e_c / r (world frame)
+  float R[9], s[3], qn[4], qnorm;
+  float u1[3], u2[3];   // M^T a_i, M = R diag(s)
+  float A, B, C;        // Sigma_arc (with blur)
+  float qa, qb, qc;     // conic
+  float rs;
+};
+
+__device__ __forceinline__ void geo_compute(const ViewParams& vp, float near_plane, const float* __restrict__ mu,
+                                            const float* __restrict__ sc, const float* __restrict__ q, Geo& G) {
+  const float m0 = mu[0], m1 = mu[1], m2 = mu[2];
+  G.t.x = vp.W[0] * m0 + vp.W[1] * m1 + vp.W[2] * m2 + vp.b[0];
+  G.t.y = vp.W[3] * m0 + vp.W[4] * m1 + vp.W[5] * m2 + vp.b[1];
+  G.t.z = vp.W[6] * m0 + vp.W[7] * m1 + vp.W[8] * m2 + vp.b[2];
+  G.r = sqrtf(G.t.x * G.t.x + G.t.y * G.t.y + G.t.z * G.t.z);
+  G.valid = G.r > near_plane;
+  if (!G.valid) return;
+  const float ir = 1.0f / G.r;
+  G.gc = make_float3(G.t.x * ir, G.t.y * ir, G.t.z * ir);
+  G.g = make_float3(G.gc.z, G.gc.x, G.gc.y);              // HEALPix (X, Y, Z) = camera (z, x, y)
+  const float rho = sqrtf(G.g.x * G.g.x + G.g.y * G.g.y);
+  if (rho > 1e-12f) {
+    const float irho = 1.0f / rho;
+    G.e1 = make_float3(-G.g.y * irho, G.g.x * irho, 0.f);
+    G.e2 = make_float3(-G.g.x * G.g.z * irho, -G.g.y * G.g.z * irho, rho);
+  } else {  // at the pole any tangent frame gives the same alpha; take a fixed one
+    G.e1 = make_float3(0.f, 1.f, 0.f);
+    G.e2 = make_float3(G.g.z > 0 ? -1.f : 1.f, 0.f, 0.f);
+  }
+  G.e1c = make_float3(G.e1.y, G.e1.z, G.e1.x);
+  G.e2c = make_float3(G.e2.y, G.e2.z, G.e2.x);
+  for (int j = 0; j < 3; ++j) {
+    G.a1[j] = (vp.W[j] * G.e1c.x + vp.W[3 + j] * G.e1c.y + vp.W[6 + j] * G.e1c.z) * ir;
+    G.a2[j] = (vp.W[j] * G.e2c.x + vp.W[3 + j] * G.e2c.y + vp.W[6 + j] * G.e2c.z) * ir;
+  }
+  G.qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const float iq = 1.0f / G.qnorm;
+  for (int j = 0; j < 4; ++j) G.qn[j] = q[j] * iq;
+  quat_rot(G.qn[0], G.qn[1], G.qn[2], G.qn[3], G.R);
+  for (int j = 0; j < 3; ++j) G.s[j] = sc[j];
+  for (int kk = 0; kk < 3; ++kk) {
+    G.u1[kk] = G.s[kk] * (G.R[kk] * G.a1[0] + G.R[3 + kk] * G.a1[1] + G.R[6 + kk] * G.a1[2]);
+    G.u2[kk] = G.s[kk] * (G.R[kk] * G.a2[0] + G.R[3 + kk] * G.a2[1] + G.R[6 + kk] * G.a2[2]);
+  }
+  G.A = G.u1[0] * G.u1[0] + G.u1[1] * G.u1[1] + G.u1[2] * G.u1[2] + vp.blur;
+  G.B = G.u1[0] * G.u2[0] + G.u1[1] * G.u2[1] + G.u1[2] * G.u2[2];
+  G.C = G.u2[0] * G.u2[0] + G.u2[1] * G.u2[1] + G.u2[2] * G.u2[2] + vp.blur;
+  const float det = G.A * G.C - G.B * G.B;
+  if (!(det > 0.f)) { G.valid = false; return; }
+  const float idet = 1.0f / det;
+  G.qa = G.C * idet; G.qb = -G.B * idet; G.qc = G.A * idet;
+  const float hm = 0.5f * (G.A + G.C), hd = 0.5f * (G.A - G.C);
+  const float lmax = hm + sqrtf(hd * hd + G.B * G.B);
+  G.rs = 3.0f * sqrtf(lmax);
+}
+
+// ----------------------------------------------------------------------------
+// k_preprocess: one thread per (view, Gaussian) id gid = v * P + i.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ ViewTable vt, hpxgs_gaussians gs,
+                                                    float4* __restrict__ rec, float* __restrict__ radii,
+                                                    float* __restrict__ depth, uint32_t* __restrict__ keys,
+                                                    uint32_t* __restrict__ vals) {
+  const int64_t PV = (int64_t)vt.P * vt.nviews;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= PV) return;
+  const int v = (int)(gid / vt.P);
+  const int i = (int)(gid - (int64_t)v * vt.P);
+  const ViewParams& vp = vt.v[v];
+  Geo G;
+  geo_compute(vp, vt.near_plane, gs.means + 3 * (int64_t)i, gs.scales + 3 * (int64_t)i, gs.rotations + 4 * (int64_t)i, G);
+  vals[gid] = (uint32_t)gid;
+  depth[gid] = G.r;
+  if (!G.valid) {
+    keys[gid] = 0xffffffffu;
+    radii[gid] = 0.f;
+    rec[4 * gid + 0] = make_float4(0.f, 0.f, 1.f, 0.f);
+    rec[4 * gid + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    rec[4 * gid + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    rec[4 * gid + 3] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  // colour: SH at the world direction from the camera centre
+  float dx = gs.means[3 * i] - vp.cam[0], dy = gs.means[3 * i + 1] - vp.cam[1], dz = gs.means[3 * i + 2] - vp.cam[2];
+  const float idist = rsqrtf(dx * dx + dy * dy + dz * dz);
+  dx *= idist; dy *= idist; dz *= idist;
+  float Y[16];
+  sh_basis(vt.sh_degree, dx, dy, dz, Y, nullptr);
+  const int K = (vt.sh_degree + 1) * (vt.sh_degree + 1);
+  const float* sh = gs.sh + (int64_t)i * K * 3;
+  float col[3];
+  for (int c = 0; c < 3; ++c) {
+    float acc = 0.5f;
+    for (int kk = 0; kk < K; ++kk) acc += sh[3 * kk + c] * Y[kk];
+    col[c] = fmaxf(acc, 0.f);
+  }
+  rec[4 * gid + 0] = make_float4(G.g.x, G.g.y, G.g.z, gs.opacities[i]);
+  rec[4 * gid + 1] = make_float4(G.e1.x, G.e1.y, G.e1.z, G.qa);
+  rec[4 * gid + 2] = make_float4(G.e2.x, G.e2.y, G.e2.z, G.qb);
+  rec[4 * gid + 3] = make_float4(col[0], col[1], col[2], G.qc);
+  radii[gid] = G.rs;
+  keys[gid] = __float_as_uint(G.r);     // r > 0: the bit pattern orders like the value
+}
+
+// ----------------------------------------------------------------------------
+// Stable LSD radix sort of (u32 key, u32 value) pairs with a fixed grid of G
+// blocks; each block owns a contiguous chunk, so no block waits on another.
+// The element count is read on the device (min(*n, n_max)).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void chunk_of(uint32_t n, int G, int b, uint32_t& begin, uint32_t& end) {
+  uint32_t chunk = (n + G - 1) / G;
+  chunk = (chunk + kSortTile - 1) / kSortTile * kSortTile;
+  uint64_t bb = (uint64_t)chunk * b, ee = bb + chunk;
+  begin = (uint32_t)(bb < n ? bb : n);
+  end = (uint32_t)(ee < n ? ee : n);
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, const uint32_t* n_ptr,
+                                                            uint32_t n_max, int shift, int nbits,
+                                                            uint32_t* __restrict__ hist, int G) {
+  __shared__ uint32_t cnt[256];
+  const uint32_t n = n_ptr ? min(*n_ptr, n_max) : n_max;
+  uint32_t begin, end;
+  chunk_of(n, G, blockIdx.x, begin, end);
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t mask = (1u << nbits) - 1u;
+  for (uint32_t i = begin + threadIdx.x; i < end; i += kSortThreads) atomicAdd(&cnt[(keys[i] >> shift) & mask], 1u);
+  __syncthreads();
+  hist[threadIdx.x * G + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Exclusive scan of len u32 entries in place (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) k_scan_u32_inplace(uint32_t* __restrict__ a, int len) {
+  __shared__ uint32_t wsum[32];
+  const int per = (len + 1023) / 1024;
+  const int lo = threadIdx.x * per, hi = min(len, lo + per);
+  uint32_t s = 0;
+  for (int i = lo; i < hi; ++i) s += a[i];
+  // inclusive warp scan of s
+  uint32_t x = s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) { uint32_t y = __shfl_up_sync(0xffffffffu, x, o); if (lane >= o) x += y; }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) { uint32_t y = __shfl_up_sync(0xffffffffu, w, o); if (lane >= o) w += y; }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  uint32_t run = x - s + (warp > 0 ? wsum[warp - 1] : 0u);
+  for (int i = lo; i < hi; ++i) { uint32_t v = a[i]; a[i] = run; run += v; }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                               const uint32_t* n_ptr, uint32_t n_max, int shift, int nbits,
+                                                               const uint32_t* __restrict__ hist, int G) {
+  constexpr int NW = kSortThreads / 32;
+  __shared__ uint32_t base[256];
+  __shared__ uint32_t wcnt[NW][256];
+  __shared__ uint32_t woff[NW][256];
+  const uint32_t n = n_ptr ? min(*n_ptr, n_max) : n_max;
+  uint32_t begin, end;
+  chunk_of(n, G, blockIdx.x, begin, end);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  base[tid] = hist[tid * G + blockIdx.x];
+  for (int w = 0; w < NW; ++w) wcnt[w][tid] = 0;
+  __syncthreads();
+  const uint32_t mask = (1u << nbits) - 1u;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint32_t t0 = begin; t0 < end; t0 += kSortThreads) {
+    const uint32_t idx = t0 + tid;
+    const bool valid = idx < end;
+    const uint32_t key = valid ? kin[idx] : 0u;
+    const uint32_t digit = valid ? ((key >> shift) & mask) : 0xffffu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+    const uint32_t rank = __popc(peers & lt);
+    if (valid && rank == 0) wcnt[warp][digit] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t run = base[tid];
+      for (int w = 0; w < NW; ++w) { uint32_t c = wcnt[w][tid]; woff[w][tid] = run; run += c; wcnt[w][tid] = 0; }
+      base[tid] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = woff[warp][digit] + rank;
+      kout[pos] = key;
+      vout[pos] = vin[idx];
+    }
+  }
+}
+
+// Sorts n (device count, capped at n_max) pairs by bits [0, bits) of the key.
+// Returns 0 if the result is in (k0, v0), 1 if in (k1, v1).
+static int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev, uint32_t n_max,
+                      int bits, uint32_t* hist, int G, cudaStream_t s, int* which) {
+  int cur = 0;
+  if (n_max == 0) { *which = 0; return HPXGS_OK; }
+  for (int shift = 0; shift < bits; shift += 8) {
+    const int nb = min(8, bits - shift);
+    uint32_t* kin = cur ? k1 : k0; uint32_t* vin = cur ? v1 : v0;
+    uint32_t* kout = cur ? k0 : k1; uint32_t* vout = cur ? v0 : v1;
+    k_sort_hist<<<G, kSortThreads, 0, s>>>(kin, n_dev, n_max, shift, nb, hist, G);
+    k_scan_u32_inplace<<<1, 1024, 0, s>>>(hist, 256 * G);
+    k_sort_scatter<<<G, kSortThreads, 0, s>>>(kin, vin, kout, vout, n_dev, n_max, shift, nb, hist, G);
+    HPXGS_LAUNCH_CHECK();
+    cur ^= 1;
+  }
+  *which = cur;
+  return HPXGS_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Tile query (Algorithm 3 at the tile order) and exact membership:
+// tile t is listed for Gaussian g iff t has an in-mask pixel and
+// c_t . g >= cos(min(pi, r_s + rho + 1e-7)), decided in FP32 when the margin
+// exceeds 1e-5 and in FP64 otherwise.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float ring_of_z(float z, int Nt) {
+  if (z > 2.0f / 3.0f) return Nt * sqrtf(3.0f * (1.0f - z));
+  if (z < -2.0f / 3.0f) return 4.0f * Nt - Nt * sqrtf(3.0f * (1.0f + z));
+  return Nt * (2.0f - 1.5f * z);
+}
+
+// phi / pi of ring pixel (i, j) as num / den (exact integers)
+__device__ __forceinline__ void ring_phi_frac(int k, int i, int j, int& num, int& den) {
+  const int N = 1 << k;
+  if (i < N) { num = 2 * j + 1; den = 4 * i; }
+  else if (i > 3 * N) { num = 2 * j + 1; den = 4 * (4 * N - i); }
+  else { num = 2 * j + 2 - ((i - N + 1) & 1); den = 4 * N; }
+}
+
+template <bool EMIT>
+__device__ uint32_t enumerate_tiles(const ViewParams& vp, int kt, float3 g, float rs, const uint32_t* __restrict__ flags,
+                                    uint32_t* __restrict__ out_tile, uint32_t* __restrict__ out_id, uint64_t base,
+                                    uint64_t cap, uint32_t gid) {
+  const double Rm = fmin(kPi, (double)rs + vp.rho + 1e-7);
+  const double cosRm = cos(Rm);
+  const float cosRm32 = (float)cosRm;
+  const float Re = fminf((float)kPi, (float)Rm + 1e-5f);
+  const float cosRe = cosf(Re);
+  const int Nt = 1 << kt;
+  const float zc = g.z;
+  const float sc = sqrtf(fmaxf(0.f, g.x * g.x + g.y * g.y));
+  const float phic = atan2f(zc, sc);
+  const float omc = atan2f(g.y, g.x);
+  const float phimin = fmaxf(-0.5f * (float)kPi, phic - Re), phimax = fminf(0.5f * (float)kPi, phic + Re);
+  const float zmin = sinf(phimin) - 1e-6f, zmax = sinf(phimax) + 1e-6f;
+  const int ilo = max(1, (int)floorf(ring_of_z(fminf(zmax, 1.f), Nt)) - 1);
+  const int ihi = min(4 * Nt - 1, (int)ceilf(ring_of_z(fmaxf(zmin, -1.f), Nt)) + 1);
+  const double3 g64 = make_double3(g.x, g.y, g.z);
+  uint32_t cnt = 0;
+  for (int i = ilo; i <= ihi; ++i) {
+    RingF rg = ring_f32(kt, i);
+    if (rg.z < zmin || rg.z > zmax) continue;
+    const float delta = sc * rg.sth;
+    int jlo = 0, jhi = -1;
+    bool full = false;
+    if (delta < 1e-6f) {
+      if (zc * rg.z >= cosRe - 1e-5f) full = true; else continue;
+    } else {
+      const float cw = (cosRe - zc * rg.z) / delta;    // Eq. ring_phi_range
+      if (cw <= -1.f) full = true;
+      else if (cw <= 1.f) {
+        const float dw = acosf(fminf(1.f, fmaxf(-1.f, cw)));
+        const float sc2 = rg.npix / (2.0f * (float)kPi);
+        jlo = (int)floorf((omc - dw - rg.phi0) * sc2) - 1;
+        jhi = (int)ceilf((omc + dw - rg.phi0) * sc2) + 1;
+        if (jhi - jlo + 1 >= rg.npix) full = true;
+      } else continue;
+    }
+    if (full) { jlo = 0; jhi = rg.npix - 1; }
+    for (int j = jlo; j <= jhi; ++j) {
+      int jj = j % rg.npix; if (jj < 0) jj += rg.npix;
+      int num, den;
+      ring_phi_frac(kt, i, jj, num, den);
+      float sp, cp;
+      sincospif((float)num / (float)den, &sp, &cp);
+      const float dot = rg.sth * (cp * g.x + sp * g.y) + rg.z * g.z;
+      bool member;
+      if (dot > cosRm32 + 1e-5f) member = true;
+      else if (dot < cosRm32 - 1e-5f) member = false;
+      else {
+        const double3 c = ringpix_vec_f64(kt, i, jj);
+        member = c.x * g64.x + c.y * g64.y + c.z * g64.z >= cosRm;
+      }
+      if (!member) continue;
+      const FaceXY fx = ring_to_fxy(kt, i, jj);
+      const uint32_t tile = fxy_to_nest(kt, fx.f, fx.x, fx.y);
+      const uint32_t gt = (uint32_t)vp.tile_base + tile;
+      if (!(flags[gt] & 1u)) continue;
+      if (EMIT) {
+        const uint64_t pos = base + cnt;
+        if (pos < cap) { out_tile[pos] = gt; out_id[pos] = gid; }
+      }
+      ++cnt;
+    }
+  }
+  return cnt;
+}
+
+template <bool EMIT>
+__global__ void __launch_bounds__(128) k_tiles(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
+                                               const float* __restrict__ radii, const uint32_t* __restrict__ skeys,
+                                               const uint32_t* __restrict__ svals, const uint32_t* __restrict__ flags,
+                                               uint32_t* __restrict__ counts, const uint64_t* __restrict__ offsets,
+                                               uint32_t* __restrict__ out_tile, uint32_t* __restrict__ out_id, uint64_t cap,
+                                               int32_t* status) {
+  const int64_t PV = (int64_t)vt.P * vt.nviews;
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= PV) return;
+  if (skeys[j] == 0xffffffffu) { if (!EMIT) counts[j] = 0; return; }
+  const uint32_t gid = svals[j];
+  const int v = (int)(gid / (uint32_t)vt.P);
+  const ViewParams& vp = vt.v[v];
+  const float4 r0 = rec[4 * (int64_t)gid];
+  const float3 g = make_float3(r0.x, r0.y, r0.z);
+  const uint64_t base = EMIT ? offsets[j] : 0;
+  const uint32_t n = enumerate_tiles<EMIT>(vp, vp.k - vt.b, g, radii[gid], flags, out_tile, out_id, base, cap, gid);
+  if (!EMIT) counts[j] = n;
+  else if (base + n > cap && status) atomicOr(status, HPXGS_F_CAPACITY);
+}
+
+// ----------------------------------------------------------------------------
+// Exclusive scan of u32 counts into u64 offsets (fixed grid, no inter-block waits).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t block_exclusive_scan_u64(uint64_t x, uint64_t* total) {
+  __shared__ uint64_t ws[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  uint64_t inc = x;
+  for (int o = 1; o < 32; o <<= 1) { uint64_t y = __shfl_up_sync(0xffffffffu, inc, o); if (lane >= o) inc += y; }
+  if (lane == 31) ws[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t w = lane < nw ? ws[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) { uint64_t y = __shfl_up_sync(0xffffffffu, w, o); if (lane >= o) w += y; }
+    ws[lane] = w;
+  }
+  __syncthreads();
+  const uint64_t res = inc - x + (warp > 0 ? ws[warp - 1] : 0);
+  *total = ws[nw - 1];
+  __syncthreads();
+  return res;
+}
+
+__global__ void __launch_bounds__(256) k_scan_part(const uint32_t* __restrict__ c, int64_t n, int G, uint64_t* part) {
+  const int64_t chunk = (n + G - 1) / G;
+  const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  uint64_t s = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += c[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ uint64_t ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < 8; ++w) t += ws[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_scan_top(uint64_t* part, int G, uint32_t* counters, uint64_t* total_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint64_t run = 0;
+  for (int b = 0; b < G; ++b) { uint64_t v = part[b]; part[b] = run; run += v; }
+  part[G] = run;
+  counters[C_NPAIRS] = (uint32_t)(run > 0xffffffffull ? 0xffffffffull : run);
+  counters[C_NPAIRS_HI] = (uint32_t)(run >> 32);
+  if (total_out) *total_out = run;
+}
+
+__global__ void __launch_bounds__(256) k_scan_apply(const uint32_t* __restrict__ c, int64_t n, int G,
+                                                    const uint64_t* __restrict__ part, uint64_t* __restrict__ off) {
+  const int64_t chunk = (n + G - 1) / G;
+  const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  uint64_t run = part[blockIdx.x];
+  for (int64_t t0 = lo; t0 < hi; t0 += blockDim.x) {
+    const int64_t i = t0 + threadIdx.x;
+    const uint64_t x = i < hi ? c[i] : 0;
+    uint64_t tot;
+    const uint64_t ex = block_exclusive_scan_u64(x, &tot);
+    if (i < hi) off[i] = run + ex;
+    run += tot;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Per-tile ranges over the sorted tile ids (Algorithm 1: [start_t, end_t)).
+// ----------------------------------------------------------------------------
+__global__ void k_ranges(const uint32_t* __restrict__ tiles, const uint32_t* n_ptr, uint32_t n_max, uint2* ranges) {
+  const uint32_t n = min(*n_ptr, n_max);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t t = tiles[i];
+    if (i == 0 || tiles[i - 1] != t) ranges[t].x = i;
+    if (i == n - 1 || tiles[i + 1] != t) ranges[t].y = i + 1;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Per-pixel weight. m = d^T conic d with d = (theta / s) u, u = (delta.e1, delta.e2),
+// delta = p - g, s = |u| = sin(theta), cos(theta) = 1 - |delta|^2 / 2.
+// (theta/s)^2 = asin(s)^2 / s^2 by its Taylor series near the centre
+// (1 + s^2/3 + 8 s^4/45 + 4 s^6/35 + 128 s^8/1575), atan2 further out.
+// ----------------------------------------------------------------------------
+constexpr float kSeriesN2 = 0.04f;      // |delta|^2 below which the series is used (theta < 0.2)
+
+struct Pix {
+  float u1, u2, n2, s2, q, ser, m;
+  bool series;
+};
+
+__device__ __forceinline__ void pixel_weight(const float3 p, const float4 r0, const float4 r1, const float4 r2,
+                                             const float4 r3, Pix& P) {
+  const float dx = p.x - r0.x, dy = p.y - r0.y, dz = p.z - r0.z;
+  P.u1 = dx * r1.x + dy * r1.y + dz * r1.z;
+  P.u2 = dx * r2.x + dy * r2.y + dz * r2.z;
+  P.n2 = dx * dx + dy * dy + dz * dz;
+  P.s2 = P.u1 * P.u1 + P.u2 * P.u2;
+  P.q = P.u1 * (r1.w * P.u1 + 2.f * r2.w * P.u2) + r3.w * P.u2 * P.u2;
+  P.series = P.n2 < kSeriesN2;
+  if (P.series) {
+    const float s2 = P.s2;
+    P.ser = 1.f + s2 * (1.f / 3.f + s2 * (8.f / 45.f + s2 * (4.f / 35.f + s2 * (128.f / 1575.f))));
+    P.m = P.q * P.ser;
+  } else {
+    const float c = 1.f - 0.5f * P.n2;
+    if (P.s2 < 1e-24f) { P.ser = 0.f; P.m = (c < 0.f) ? 3.0e38f : 0.f; return; }
+    const float s = sqrtf(P.s2);
+    const float ratio = atan2f(s, c) / s;
+    P.ser = ratio * ratio;
+    P.m = P.q * P.ser;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Forward compositing: persistent blocks take tiles from a counter; one thread
+// per pixel (PPT pixels per thread for 1024-pixel tiles); Gaussian records of the
+// tile's list are staged through shared memory in batches of BATCH.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int view_of_tile(const ViewTable& vt, int tile) {
+  int v = 0;
+  while (v + 1 < vt.nviews && tile >= vt.v[v + 1].tile_base) ++v;
+  return v;
+}
+
+template <int NT, int PPT, int BATCH>
+__global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
+                                                  const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
+                                                  const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
+                                                  float* __restrict__ maps, float* __restrict__ Tout,
+                                                  uint32_t* __restrict__ lastout, uint32_t* work) {
+  __shared__ float4 s_rec[BATCH][4];
+  __shared__ int s_tile;
+  const int tid = threadIdx.x;
+  const int b = vt.b;
+  for (;;) {
+    if (tid == 0) s_tile = (int)atomicAdd(work, 1u);
+    __syncthreads();
+    const int tile = s_tile;
+    __syncthreads();
+    if (tile >= vt.total_tiles) break;
+    const int v = view_of_tile(vt, tile);
+    const ViewParams& vp = vt.v[v];
+    const uint32_t lt = (uint32_t)(tile - vp.tile_base);
+    const bool active = flags[tile] & 1u;
+    if (!active && !vt.write_outside) continue;
+    const uint32_t* vmask = mask + (vp.pix_base >> 5);
+    float3 pv[PPT];
+    float C[PPT][3], T[PPT];
+    uint32_t last[PPT];
+    bool done[PPT], inm[PPT];
+    uint32_t lp[PPT];
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      lp[q] = (lt << (2 * b)) + q * NT + tid;
+      inm[q] = active && ((vmask[lp[q] >> 5] >> (lp[q] & 31)) & 1u);
+      done[q] = !inm[q];
+      pv[q] = inm[q] ? pix2vec_f32(vp.k, lp[q]) : make_float3(0.f, 0.f, 1.f);
+      C[q][0] = C[q][1] = C[q][2] = 0.f;
+      T[q] = 1.f;
+      last[q] = 0;
+    }
+    const uint2 rg = active ? ranges[tile] : make_uint2(0, 0);
+    for (uint32_t bs = rg.x; bs < rg.y; bs += BATCH) {
+      const int n = (int)min((uint32_t)BATCH, rg.y - bs);
+      __syncthreads();
+      for (int e = tid; e < n; e += NT) {
+        const float4* src = rec + 4 * (int64_t)ids[bs + e];
+        s_rec[e][0] = src[0]; s_rec[e][1] = src[1]; s_rec[e][2] = src[2]; s_rec[e][3] = src[3];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        if (done[q]) continue;
+        for (int e = 0; e < n; ++e) {
+          const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
+          Pix P;
+          pixel_weight(pv[q], r0, r1, r2, r3, P);
+          if (P.m <= vt.cutoff) {
+            const float a = fminf(vt.alpha_max, r0.w * __expf(-0.5f * P.m));
+            const float w = a * T[q];
+            C[q][0] += w * r3.x; C[q][1] += w * r3.y; C[q][2] += w * r3.z;
+            T[q] = T[q] * (1.f - a);
+            if (T[q] < vt.eps_T) { done[q] = true; last[q] = bs + e + 1 - rg.x; break; }
+          }
+        }
+      }
+      int alive = 0;
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) alive |= !done[q];
+      if (__syncthreads_count(alive) == 0) break;
+    }
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      const int64_t pg = vp.pix_base + lp[q];
+      if (inm[q]) {
+        if (T[q] >= vt.eps_T) last[q] = rg.y - rg.x;     // ran through the whole list
+        maps[3 * pg + 0] = C[q][0] + T[q] * vt.bg[0];
+        maps[3 * pg + 1] = C[q][1] + T[q] * vt.bg[1];
+        maps[3 * pg + 2] = C[q][2] + T[q] * vt.bg[2];
+        Tout[pg] = T[q];
+        lastout[pg] = last[q];
+      } else if (vt.write_outside) {
+        maps[3 * pg + 0] = vt.bg[0]; maps[3 * pg + 1] = vt.bg[1]; maps[3 * pg + 2] = vt.bg[2];
+        Tout[pg] = 1.f;
+        lastout[pg] = 0;
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Backward compositing: reverse walk of each pixel's processed prefix.
+// Per (pixel, entry): T_j = T_{j+1} / (1 - a); dL/dc = T_j a dI;
+// dL/da = dI . (T_j c - S / (1 - a)), S = colour behind entry j incl. background;
+// then through a = o exp(-m/2) and m = q(u) (theta/s)^2 to the conic and to a
+// tangent displacement of the centre g (parallel-transported frame).
+// Accumulators per (view, Gaussian): [dcol(3), dopacity, dconic_a, dconic_b (unique
+// off-diagonal), dconic_c, d_east, d_north].
+// ----------------------------------------------------------------------------
+template <int NT, int PPT, int BATCH>
+__global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
+                                                  const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
+                                                  const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
+                                                  const float* __restrict__ dmaps, const float* __restrict__ Tin,
+                                                  const uint32_t* __restrict__ lastin, float* __restrict__ accum,
+                                                  uint32_t* work) {
+  constexpr int NW = NT / 32;
+  __shared__ float4 s_rec[BATCH][4];
+  __shared__ uint32_t s_id[BATCH];
+  __shared__ float s_part[BATCH][NW][HPXGS_NACC];
+  __shared__ int s_tile;
+  __shared__ uint32_t s_maxlast;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = vt.b;
+  for (;;) {
+    if (tid == 0) { s_tile = (int)atomicAdd(work, 1u); s_maxlast = 0; }
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= vt.total_tiles) break;
+    const bool active = flags[tile] & 1u;
+    if (!active) { __syncthreads(); continue; }
+    const int v = view_of_tile(vt, tile);
+    const ViewParams& vp = vt.v[v];
+    const uint32_t lt = (uint32_t)(tile - vp.tile_base);
+    const uint2 rg = ranges[tile];
+    const uint32_t* vmask = mask + (vp.pix_base >> 5);
+    float3 pv[PPT];
+    float dI[PPT][3], S[PPT][3], T[PPT];
+    uint32_t lastp[PPT];
+    uint32_t mylast = 0;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      const uint32_t lp = (lt << (2 * b)) + q * NT + tid;
+      const bool inm = (vmask[lp >> 5] >> (lp & 31)) & 1u;
+      const int64_t pg = vp.pix_base + lp;
+      lastp[q] = inm ? lastin[pg] : 0u;
+      T[q] = inm ? Tin[pg] : 1.f;
+      pv[q] = inm ? pix2vec_f32(vp.k, lp) : make_float3(0.f, 0.f, 1.f);
+      for (int c = 0; c < 3; ++c) {
+        dI[q][c] = inm ? dmaps[3 * pg + c] : 0.f;
+        S[q][c] = T[q] * vt.bg[c];
+      }
+      mylast = max(mylast, lastp[q]);
+    }
+    if (mylast) atomicMax(&s_maxlast, mylast);
+    __syncthreads();
+    const uint32_t hi = rg.x + s_maxlast;
+    for (uint32_t be = hi; be > rg.x;) {
+      const uint32_t bs = (be - rg.x > (uint32_t)BATCH) ? be - BATCH : rg.x;
+      const int n = (int)(be - bs);
+      __syncthreads();
+      for (int e = tid; e < n; e += NT) {
+        const uint32_t id = ids[bs + e];
+        s_id[e] = id;
+        const float4* src = rec + 4 * (int64_t)id;
+        s_rec[e][0] = src[0]; s_rec[e][1] = src[1]; s_rec[e][2] = src[2]; s_rec[e][3] = src[3];
+      }
+      __syncthreads();
+      for (int e = n - 1; e >= 0; --e) {
+        const uint32_t j = bs + e - rg.x;          // position in the tile list
+        const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
+        float acc[HPXGS_NACC];
+#pragma unroll
+        for (int c = 0; c < HPXGS_NACC; ++c) acc[c] = 0.f;
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+          if (j >= lastp[q]) continue;
+          Pix P;
+          pixel_weight(pv[q], r0, r1, r2, r3, P);
+          if (!(P.m <= vt.cutoff)) continue;
+          const float G = __expf(-0.5f * P.m);
+          const float og = r0.w * G;
+          const float a = fminf(vt.alpha_max, og);
+          const float inv1ma = 1.f / (1.f - a);
+          const float Tj = T[q] * inv1ma;
+          const float wj = Tj * a;
+          float dLda = 0.f;
+          const float col[3] = {r3.x, r3.y, r3.z};
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            acc[c] += wj * dI[q][c];
+            dLda += dI[q][c] * (Tj * col[c] - S[q][c] * inv1ma);
+            S[q][c] += wj * col[c];
+          }
+          T[q] = Tj;
+          any = true;
+          if (og >= vt.alpha_max) continue;         // clamped: no gradient to o, m
+          acc[3] += dLda * G;
+          const float Lm = -0.5f * dLda * og;
+          const float u1 = P.u1, u2 = P.u2;
+          acc[4] += Lm * P.ser * u1 * u1;
+          acc[5] += Lm * P.ser * 2.f * u1 * u2;
+          acc[6] += Lm * P.ser * u2 * u2;
+          const float Qu1 = r1.w * u1 + r2.w * u2, Qu2 = r2.w * u1 + r3.w * u2;
+          const float c = 1.f - 0.5f * P.n2;
+          float Lu1, Lu2, Lc = 0.f;
+          if (P.series) {
+            const float s2 = P.s2;
+            const float dser = 1.f / 3.f + s2 * (16.f / 45.f + s2 * (12.f / 35.f + s2 * (512.f / 1575.f)));
+            Lu1 = Lm * (2.f * P.ser * Qu1 + 2.f * P.q * dser * u1);
+            Lu2 = Lm * (2.f * P.ser * Qu2 + 2.f * P.q * dser * u2);
+          } else {
+            const float s = sqrtf(P.s2);
+            const float ratio = sqrtf(P.ser);
+            const float th = ratio * s;
+            const float kf = (c * s - th) / (P.s2 * s);     // d(theta/s)/du_j = kf u_j
+            Lu1 = Lm * (2.f * P.ser * Qu1 + 2.f * P.q * ratio * kf * u1);
+            Lu2 = Lm * (2.f * P.ser * Qu2 + 2.f * P.q * ratio * kf * u2);
+            Lc = -2.f * Lm * P.q * ratio;                    // d(theta/s)/dc = -1/s^2... times s: -1
+          }
+          // moving g by a tangent step delta: du_i = -c delta_i, dc = u . delta
+          acc[7] += -c * Lu1 + Lc * u1;
+          acc[8] += -c * Lu2 + Lc * u2;
+        }
+        // warp reduction of the 9 partials, then per-warp slot in shared memory
+        const unsigned ball = __ballot_sync(0xffffffffu, any);
+        if (ball) {
+#pragma unroll
+          for (int c = 0; c < HPXGS_NACC; ++c) {
+            float x = acc[c];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            acc[c] = x;
+          }
+        }
+        if (lane == 0) {
+#pragma unroll
+          for (int c = 0; c < HPXGS_NACC; ++c) s_part[e][warp][c] = ball ? acc[c] : 0.f;
+        }
+      }
+      __syncthreads();
+      for (int t = tid; t < n * HPXGS_NACC; t += NT) {
+        const int e = t / HPXGS_NACC, c = t - e * HPXGS_NACC;
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) sum += s_part[e][w][c];
+        if (sum != 0.f) atomicAdd(&accum[(int64_t)s_id[e] * HPXGS_NACC + c], sum);
+      }
+      be = bs;
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Preprocess backward: one thread per Gaussian, summing over views.
+// conic -> Sigma_arc: G_S = -Q G_Q Q; Sigma_arc = U U^T + blur I with rows
+// u_i = M^T a_i, a_i = W^T e_i / r (S_phi J W); the frame (e_i, g) is moved by
+// parallel transport under a change of t (the loss is invariant under a rotation
+// of the tangent frame, so this gives the exact derivative):
+//   d(e_i / r) = -(g (e_i . dt) + e_i (g . dt)) / r^2,  dg = (I - g g^T) dt / r.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ ViewTable vt, hpxgs_gaussians gs,
+                                                        const float* __restrict__ radii, const float* __restrict__ accum,
+                                                        float* __restrict__ dmeans, float* __restrict__ dscales,
+                                                        float* __restrict__ drot, float* __restrict__ dopac,
+                                                        float* __restrict__ dsh) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= vt.P) return;
+  const int K = (vt.sh_degree + 1) * (vt.sh_degree + 1);
+  float dmu[3] = {0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dop = 0.f;
+  float dshl[48];
+  for (int c = 0; c < 3 * K; ++c) dshl[c] = 0.f;
+  const float* mu = gs.means + 3 * (int64_t)i;
+  const float* sh = gs.sh + (int64_t)i * K * 3;
+  for (int v = 0; v < vt.nviews; ++v) {
+    const int64_t gid = (int64_t)v * vt.P + i;
+    if (!(radii[gid] > 0.f)) continue;
+    const ViewParams& vp = vt.v[v];
+    const float* A = accum + gid * HPXGS_NACC;
+    Geo G;
+    geo_compute(vp, vt.near_plane, mu, gs.scales + 3 * (int64_t)i, gs.rotations + 4 * (int64_t)i, G);
+    if (!G.valid) continue;
+    // colour -> SH and the viewing direction
+    float dx = mu[0] - vp.cam[0], dy = mu[1] - vp.cam[1], dz = mu[2] - vp.cam[2];
+    const float dist = sqrtf(dx * dx + dy * dy + dz * dz), idist = 1.f / dist;
+    dx *= idist; dy *= idist; dz *= idist;
+    float Y[16];
+    float3 dY[16];
+    sh_basis(vt.sh_degree, dx, dy, dz, Y, dY);
+    float Lcr[3];
+    for (int c = 0; c < 3; ++c) {
+      float raw = 0.5f;
+      for (int kk = 0; kk < K; ++kk) raw += sh[3 * kk + c] * Y[kk];
+      Lcr[c] = raw > 0.f ? A[c] : 0.f;
+    }
+    float Ld[3] = {0.f, 0.f, 0.f};
+    for (int kk = 0; kk < K; ++kk) {
+      float w = 0.f;
+      for (int c = 0; c < 3; ++c) { dshl[3 * kk + c] += Y[kk] * Lcr[c]; w += Lcr[c] * sh[3 * kk + c]; }
+      Ld[0] += w * dY[kk].x; Ld[1] += w * dY[kk].y; Ld[2] += w * dY[kk].z;
+    }
+    const float pd = Ld[0] * dx + Ld[1] * dy + Ld[2] * dz;
+    dmu[0] += (Ld[0] - dx * pd) * idist;
+    dmu[1] += (Ld[1] - dy * pd) * idist;
+    dmu[2] += (Ld[2] - dz * pd) * idist;
+    dop += A[3];
+    // conic -> Sigma_arc
+    const float GQa = A[4], GQb = 0.5f * A[5], GQc = A[6];
+    // T1 = Q GQ
+    const float t00 = G.qa * GQa + G.qb * GQb, t01 = G.qa * GQb + G.qb * GQc;
+    const float t10 = G.qb * GQa + G.qc * GQb, t11 = G.qb * GQb + G.qc * GQc;
+    const float GS00 = -(t00 * G.qa + t01 * G.qb);
+    const float GS01 = -(t00 * G.qb + t01 * G.qc);
+    const float GS11 = -(t10 * G.qb + t11 * G.qc);
+    // Sigma = U U^T: G_u1 = 2 (GS00 u1 + GS01 u2), G_u2 = 2 (GS01 u1 + GS11 u2)
+    float Gu1[3], Gu2[3];
+    for (int kk = 0; kk < 3; ++kk) {
+      Gu1[kk] = 2.f * (GS00 * G.u1[kk] + GS01 * G.u2[kk]);
+      Gu2[kk] = 2.f * (GS01 * G.u1[kk] + GS11 * G.u2[kk]);
+    }
+    // u_i[k] = s_k sum_j R[j][k] a_i[j]:  G_a_i[j] = sum_k R[j][k] s_k G_u_i[k];
+    // G_R[j][k] = s_k (a1[j] Gu1[k] + a2[j] Gu2[k]);  G_s[k] = sum_j R[j][k] (a1[j] Gu1[k] + a2[j] Gu2[k])
+    float Ga1[3], Ga2[3], GR[9];
+    for (int jj = 0; jj < 3; ++jj) {
+      Ga1[jj] = 0.f; Ga2[jj] = 0.f;
+      for (int kk = 0; kk < 3; ++kk) {
+        const float Rjk = G.R[3 * jj + kk];
+        Ga1[jj] += Rjk * G.s[kk] * Gu1[kk];
+        Ga2[jj] += Rjk * G.s[kk] * Gu2[kk];
+        const float gm = G.a1[jj] * Gu1[kk] + G.a2[jj] * Gu2[kk];
+        GR[3 * jj + kk] = G.s[kk] * gm;
+        ds[kk] += Rjk * gm;
+      }
+    }
+    // a_i = W^T e_ic / r -> gradient w.r.t. (e_ic / r) in the camera frame: W G_a_i
+    float Gc1[3], Gc2[3];
+    for (int r = 0; r < 3; ++r) {
+      Gc1[r] = vp.W[3 * r] * Ga1[0] + vp.W[3 * r + 1] * Ga1[1] + vp.W[3 * r + 2] * Ga1[2];
+      Gc2[r] = vp.W[3 * r] * Ga2[0] + vp.W[3 * r + 1] * Ga2[1] + vp.W[3 * r + 2] * Ga2[2];
+    }
+    const float ir = 1.f / G.r, ir2 = ir * ir;
+    const float g1 = Gc1[0] * G.gc.x + Gc1[1] * G.gc.y + Gc1[2] * G.gc.z;
+    const float g2 = Gc2[0] * G.gc.x + Gc2[1] * G.gc.y + Gc2[2] * G.gc.z;
+    const float h1 = Gc1[0] * G.e1c.x + Gc1[1] * G.e1c.y + Gc1[2] * G.e1c.z;
+    const float h2 = Gc2[0] * G.e2c.x + Gc2[1] * G.e2c.y + Gc2[2] * G.e2c.z;
+    float Lt[3];
+    Lt[0] = -ir2 * (g1 * G.e1c.x + g2 * G.e2c.x + (h1 + h2) * G.gc.x) + ir * (A[7] * G.e1c.x + A[8] * G.e2c.x);
+    Lt[1] = -ir2 * (g1 * G.e1c.y + g2 * G.e2c.y + (h1 + h2) * G.gc.y) + ir * (A[7] * G.e1c.y + A[8] * G.e2c.y);
+    Lt[2] = -ir2 * (g1 * G.e1c.z + g2 * G.e2c.z + (h1 + h2) * G.gc.z) + ir * (A[7] * G.e1c.z + A[8] * G.e2c.z);
+    for (int e = 0; e < 3; ++e) dmu[e] += vp.W[e] * Lt[0] + vp.W[3 + e] * Lt[1] + vp.W[6 + e] * Lt[2];
+    // R(q_hat) -> q_hat -> q
+    const float w = G.qn[0], x = G.qn[1], y = G.qn[2], z = G.qn[3];
+    const float Lw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+    const float Lx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6] + w * GR[7] - 2.f * x * GR[8]);
+    const float Ly = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6] + z * GR[7] - 2.f * y * GR[8]);
+    const float Lz = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] + y * GR[5] + x * GR[6] + y * GR[7]);
+    const float qd = Lw * w + Lx * x + Ly * y + Lz * z;
+    const float iq = 1.f / G.qnorm;
+    dq[0] += (Lw - w * qd) * iq;
+    dq[1] += (Lx - x * qd) * iq;
+    dq[2] += (Ly - y * qd) * iq;
+    dq[3] += (Lz - z * qd) * iq;
+  }
+  for (int c = 0; c < 3; ++c) { dmeans[3 * (int64_t)i + c] = dmu[c]; dscales[3 * (int64_t)i + c] = ds[c]; }
+  for (int c = 0; c < 4; ++c) drot[4 * (int64_t)i + c] = dq[c];
+  dopac[i] = dop;
+  for (int c = 0; c < 3 * K; ++c) dsh[(int64_t)i * K * 3 + c] = dshl[c];
+}
+
+// ----------------------------------------------------------------------------
+// Host side
+// ----------------------------------------------------------------------------
+template <typename T>
+static T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
+
+static int blend_blocks(const void* fn, int nt) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nt, 0) != cudaSuccess || occ < 1) occ = 1;
+  return occ * num_sms();
+}
+
+constexpr int kBatchFwd = 128;
+constexpr int kBatchBwd = 32;
+
+static bool check_gaussians(const hpxgs_gaussians* g) {
+  if (!g || g->P < 0 || g->sh_degree < 0 || g->sh_degree > 3) return false;
+  if (g->P > 0 && (!g->means || !g->scales || !g->rotations || !g->opacities || !g->sh)) return false;
+  return true;
+}
+
+// Steps shared by forward and count: table, mask/flags, preprocess, depth sort,
+// counts, scan. On return `which` tells where the depth-sorted keys/values are.
+static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+                      void* ws, const Layout& L, ViewTable* vt, uint32_t* mask_out, int32_t* status,
+                      uint64_t* total_out, cudaStream_t s, int* which_depth) {
+  int rc = make_table(g, g->P, views, nviews, cfg, s, true, vt);
+  if (rc != HPXGS_OK) return rc;
+  uint32_t* flags = at<uint32_t>(ws, L.tile_flags);
+  uint32_t* counters = at<uint32_t>(ws, L.counters);
+  HPXGS_CUDA_CHECK(cudaMemsetAsync(flags, 0, sizeof(uint32_t) * L.total_tiles, s));
+  HPXGS_CUDA_CHECK(cudaMemsetAsync(counters, 0, sizeof(uint32_t) * C_COUNT, s));
+  // FoV masks (kept in the workspace: the backward reads them) and tile flags
+  for (int v = 0; v < nviews; ++v) {
+    rc = launch_mask(vt->v[v], cfg->tile_level, mask_out + (vt->v[v].pix_base >> 5), flags + vt->v[v].tile_base, s);
+    if (rc != HPXGS_OK) return rc;
+  }
+  const int64_t PV = L.PV;
+  *which_depth = 0;
+  if (PV == 0) return HPXGS_OK;
+  float4* rec = at<float4>(ws, L.records);
+  float* radii = at<float>(ws, L.radii);
+  float* depth = at<float>(ws, L.depth);
+  uint32_t* ka = at<uint32_t>(ws, L.key_a); uint32_t* kb = at<uint32_t>(ws, L.key_b);
+  uint32_t* va = at<uint32_t>(ws, L.val_a); uint32_t* vb = at<uint32_t>(ws, L.val_b);
+  k_preprocess<<<(unsigned)((PV + 255) / 256), 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va);
+  HPXGS_LAUNCH_CHECK();
+  rc = radix_sort(ka, va, kb, vb, nullptr, (uint32_t)PV, 32, at<uint32_t>(ws, L.hist), L.sort_blocks, s, which_depth);
+  if (rc != HPXGS_OK) return rc;
+  const uint32_t* sk = *which_depth ? kb : ka;
+  const uint32_t* sv = *which_depth ? vb : va;
+  uint32_t* counts = at<uint32_t>(ws, L.counts);
+  uint64_t* offsets = at<uint64_t>(ws, L.offsets);
+  uint64_t* part = at<uint64_t>(ws, L.scan_part);
+  k_tiles<false><<<(unsigned)((PV + 127) / 128), 128, 0, s>>>(*vt, rec, radii, sk, sv, flags, counts, nullptr, nullptr,
+                                                             nullptr, 0, status);
+  HPXGS_LAUNCH_CHECK();
+  const int G = L.sort_blocks;
+  k_scan_part<<<G, 256, 0, s>>>(counts, PV, G, part);
+  k_scan_top<<<1, 32, 0, s>>>(part, G, counters, total_out);
+  k_scan_apply<<<G, 256, 0, s>>>(counts, PV, G, part, offsets);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+
+}  // namespace hpxgs
+
+using namespace hpxgs;
+
+extern "C" {
+
+int hpxgs_forward_workspace_size(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+                                 int64_t cap, size_t* bytes) {
+  if (!bytes) return HPXGS_E_INVALID_ARG;
+  Layout L;
+  int rc = make_layout(P, views, nviews, cfg, cap, &L);
+  if (rc != HPXGS_OK) return rc;
+  // the mask area used when the caller passes no mask buffer
+  int64_t pix = L.total_pix;
+  *bytes = L.total + ((size_t)(pix / 32) * 4 + 255) / 256 * 256;
+  return HPXGS_OK;
+}
+
+static uint32_t* internal_mask(void* ws, const Layout& L) { return at<uint32_t>(ws, L.total); }
+
+int hpxgs_workspace_inspect(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg, int64_t cap,
+                            const void* ws, hpxgs_workspace_view* out) {
+  if (!ws || !out) return HPXGS_E_INVALID_ARG;
+  Layout L;
+  int rc = make_layout(P, views, nviews, cfg, cap, &L);
+  if (rc != HPXGS_OK) return rc;
+  void* w = const_cast<void*>(ws);
+  int pbits = L.pair_bits, passes = (pbits + 7) / 8;
+  out->records = at<float>(w, L.records);
+  out->radii = at<float>(w, L.radii);
+  out->depth = at<float>(w, L.depth);
+  out->pair_tiles = (passes & 1) ? at<uint32_t>(w, L.pair_key_b) : at<uint32_t>(w, L.pair_key_a);
+  out->pair_ids = (passes & 1) ? at<uint32_t>(w, L.pair_val_b) : at<uint32_t>(w, L.pair_val_a);
+  out->ranges = at<uint32_t>(w, L.ranges);
+  out->n_pairs = at<uint32_t>(w, L.counters) + C_NPAIRS;
+  out->accum = at<float>(w, L.accum);
+  out->total_tiles = L.total_tiles;
+  return HPXGS_OK;
+}
+
+int hpxgs_count_pairs(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+                      void* ws, size_t ws_bytes, uint64_t* count, int32_t* status, hpxgs_stream_t stream) {
+  if (!check_gaussians(g) || !ws || !count) return HPXGS_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Layout L;
+  int rc = make_layout(g->P, views, nviews, cfg, 0, &L);
+  if (rc != HPXGS_OK) return rc;
+  size_t need = 0;
+  hpxgs_forward_workspace_size(g->P, views, nviews, cfg, 0, &need);
+  if (ws_bytes < need) return HPXGS_E_WORKSPACE;
+  ViewTable* vt = new ViewTable;
+  int which = 0;
+  HPXGS_CUDA_CHECK(cudaMemsetAsync(count, 0, sizeof(uint64_t), s));
+  rc = front_half(g, views, nviews, cfg, ws, L, vt, internal_mask(ws, L), status, count, s, &which);
+  delete vt;
+  return rc;
+}
+
+int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg, void* ws,
+                  size_t ws_bytes, int64_t cap, float* maps, float* T_final, uint32_t* last, uint32_t* mask_bits,
+                  float* radii_out, int32_t* status, hpxgs_stream_t stream) {
+  if (!check_gaussians(g) || !ws || !maps || !T_final || !last) return HPXGS_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Layout L;
+  int rc = make_layout(g->P, views, nviews, cfg, cap, &L);
+  if (rc != HPXGS_OK) return rc;
+  size_t need = 0;
+  hpxgs_forward_workspace_size(g->P, views, nviews, cfg, cap, &need);
+  if (ws_bytes < need) return HPXGS_E_WORKSPACE;
+  ViewTable* vt = new ViewTable;
+  int which = 0;
+  uint32_t* mask = internal_mask(ws, L);
+  rc = front_half(g, views, nviews, cfg, ws, L, vt, mask, status, nullptr, s, &which);
+  if (rc != HPXGS_OK) { delete vt; return rc; }
+  uint32_t* counters = at<uint32_t>(ws, L.counters);
+  uint32_t* flags = at<uint32_t>(ws, L.tile_flags);
+  uint2* ranges = at<uint2>(ws, L.ranges);
+  float4* rec = at<float4>(ws, L.records);
+  uint32_t* pka = at<uint32_t>(ws, L.pair_key_a); uint32_t* pkb = at<uint32_t>(ws, L.pair_key_b);
+  uint32_t* pva = at<uint32_t>(ws, L.pair_val_a); uint32_t* pvb = at<uint32_t>(ws, L.pair_val_b);
+  const int64_t PV = L.PV;
+  if (PV > 0 && cap > 0) {
+    const uint32_t* sk = which ? at<uint32_t>(ws, L.key_b) : at<uint32_t>(ws, L.key_a);
+    const uint32_t* sv = which ? at<uint32_t>(ws, L.val_b) : at<uint32_t>(ws, L.val_a);
+    k_tiles<true><<<(unsigned)((PV + 127) / 128), 128, 0, s>>>(*vt, rec, at<float>(ws, L.radii), sk, sv, flags, nullptr,
+                                                              at<uint64_t>(ws, L.offsets), pka, pva, (uint64_t)cap, status);
+    HPXGS_LAUNCH_CHECK();
+    int wp = 0;
+    rc = radix_sort(pka, pva, pkb, pvb, counters + C_NPAIRS, (uint32_t)cap, L.pair_bits, at<uint32_t>(ws, L.hist),
+                    L.sort_blocks, s, &wp);
+    if (rc != HPXGS_OK) { delete vt; return rc; }
+    const uint32_t* sorted_tiles = wp ? pkb : pka;
+    HPXGS_CUDA_CHECK(cudaMemsetAsync(ranges, 0, sizeof(uint2) * L.total_tiles, s));
+    const int64_t rblocks = std::min<int64_t>((cap + 255) / 256, 64LL * num_sms());
+    k_ranges<<<(unsigned)rblocks, 256, 0, s>>>(sorted_tiles, counters + C_NPAIRS, (uint32_t)cap, ranges);
+    HPXGS_LAUNCH_CHECK();
+  } else {
+    HPXGS_CUDA_CHECK(cudaMemsetAsync(ranges, 0, sizeof(uint2) * L.total_tiles, s));
+  }
+  const int passes = (L.pair_bits + 7) / 8;
+  const uint32_t* ids = (passes & 1) ? pvb : pva;
+  uint32_t* work = counters + C_WORK_FWD;
+  const int b = cfg->tile_level;
+  if (b == 3) {
+    auto fn = k_blend_fwd<64, 1, kBatchFwd>;
+    fn<<<blend_blocks((const void*)fn, 64), 64, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work);
+  } else if (b == 4) {
+    auto fn = k_blend_fwd<256, 1, kBatchFwd>;
+    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work);
+  } else {
+    auto fn = k_blend_fwd<256, 4, kBatchFwd>;
+    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work);
+  }
+  HPXGS_LAUNCH_CHECK();
+  if (mask_bits)
+    HPXGS_CUDA_CHECK(cudaMemcpyAsync(mask_bits, mask, sizeof(uint32_t) * (L.total_pix / 32), cudaMemcpyDeviceToDevice, s));
+  if (radii_out && PV > 0)
+    HPXGS_CUDA_CHECK(cudaMemcpyAsync(radii_out, at<float>(ws, L.radii), sizeof(float) * PV, cudaMemcpyDeviceToDevice, s));
+  delete vt;
+  return HPXGS_OK;
+}
+
+int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg, void* ws,
+                   size_t ws_bytes, int64_t cap, const float* dmaps, const float* T_final, const uint32_t* last,
+                   float* dmeans, float* dscales, float* drot, float* dopac, float* dsh, int32_t* status,
+                   hpxgs_stream_t stream) {
+  (void)status;
+  if (!check_gaussians(g) || !ws || !dmaps || !T_final || !last) return HPXGS_E_INVALID_ARG;
+  if (g->P > 0 && (!dmeans || !dscales || !drot || !dopac || !dsh)) return HPXGS_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  Layout L;
+  int rc = make_layout(g->P, views, nviews, cfg, cap, &L);
+  if (rc != HPXGS_OK) return rc;
+  size_t need = 0;
+  hpxgs_forward_workspace_size(g->P, views, nviews, cfg, cap, &need);
+  if (ws_bytes < need) return HPXGS_E_WORKSPACE;
+  ViewTable* vt = new ViewTable;
+  rc = make_table(g, g->P, views, nviews, cfg, s, true, vt);
+  if (rc != HPXGS_OK) { delete vt; return rc; }
+  const int64_t PV = L.PV;
+  if (PV == 0) { delete vt; return HPXGS_OK; }
+  uint32_t* counters = at<uint32_t>(ws, L.counters);
+  float* accum = at<float>(ws, L.accum);
+  HPXGS_CUDA_CHECK(cudaMemsetAsync(accum, 0, sizeof(float) * HPXGS_NACC * PV, s));
+  HPXGS_CUDA_CHECK(cudaMemsetAsync(counters + C_WORK_BWD, 0, sizeof(uint32_t), s));
+  const int passes = (L.pair_bits + 7) / 8;
+  const uint32_t* ids = (passes & 1) ? at<uint32_t>(ws, L.pair_val_b) : at<uint32_t>(ws, L.pair_val_a);
+  const float4* rec = at<float4>(ws, L.records);
+  const uint2* ranges = at<uint2>(ws, L.ranges);
+  const uint32_t* flags = at<uint32_t>(ws, L.tile_flags);
+  const uint32_t* mask = internal_mask(ws, L);      // written by the forward
+  uint32_t* work = counters + C_WORK_BWD;
+  const int b = cfg->tile_level;
+  if (b == 3) {
+    auto fn = k_blend_bwd<64, 1, kBatchBwd>;
+    fn<<<blend_blocks((const void*)fn, 64), 64, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work);
+  } else if (b == 4) {
+    auto fn = k_blend_bwd<256, 1, kBatchBwd>;
+    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work);
+  } else {
+    auto fn = k_blend_bwd<256, 4, kBatchBwd>;
+    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work);
+  }
+  HPXGS_LAUNCH_CHECK();
+  k_preprocess_bwd<<<(g->P + 127) / 128, 128, 0, s>>>(*vt, *g, at<float>(ws, L.radii), accum, dmeans, dscales, drot,
+                                                       dopac, dsh);
+  HPXGS_LAUNCH_CHECK();
+  delete vt;
+  return HPXGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,221 @@
+"""PyTorch front end of the HEALPix rasterizer: differentiable render and HSSIM loss.
+
+PyTorch supplies device memory and the stream; every step of the path runs in
+libhpxgs.so (see include/hpxgs.h). The autograd Function keeps the forward's
+workspace (records, sorted tile lists, ranges, masks) together with the
+per-pixel final transmittance and last-contributor count, and the backward
+walks the same lists in reverse (Sec. 3.2), so no blend history is stored.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _f32(t):
+    if not (t.is_cuda and t.dtype == torch.float32):
+        raise TypeError("expected a float32 CUDA tensor")
+    return t.contiguous()
+
+
+def npix(k: int) -> int:
+    return 12 * 4 ** k
+
+
+def gaussians_struct(means, scales, rotations, opacities, sh, sh_degree) -> L.Gaussians:
+    g = L.Gaussians()
+    g.means, g.scales, g.rotations = means.data_ptr(), scales.data_ptr(), rotations.data_ptr()
+    g.opacities, g.sh = opacities.data_ptr(), sh.data_ptr()
+    g.P = int(means.shape[0])
+    g.sh_degree = int(sh_degree)
+    return g
+
+
+@dataclass
+class Layout:
+    pix_base: list
+    total_pix: int
+    total_tiles: int
+
+
+def view_layout(views, tile_level=4) -> Layout:
+    base, tot, tiles = [], 0, 0
+    for v in views:
+        base.append(tot)
+        tot += npix(v["nside_log2"])
+        tiles += 12 * 4 ** (v["nside_log2"] - tile_level)
+    return Layout(base, tot, tiles)
+
+
+class Rasterizer:
+    """Holds the config and the pair capacity; each forward gets its own workspace."""
+
+    def __init__(self, tile_level=4, eps_T=1e-4, alpha_max=0.99, cutoff=9.0, blur=None, near=0.2,
+                 bg=(0.0, 0.0, 0.0), lam=0.2, write_outside=1, capacity=None, headroom=1.15):
+        self.cfg = L.default_config(tile_level=tile_level, eps_T=eps_T, alpha_max=alpha_max, cutoff_m=cutoff,
+                                    blur=blur, near_plane=near, bg=bg, lam=lam, write_outside=write_outside)
+        self.capacity = capacity
+        self.headroom = headroom
+
+    @property
+    def tile_level(self):
+        return self.cfg.tile_level
+
+    def workspace_bytes(self, P, cviews, nv, cap) -> int:
+        n = ctypes.c_size_t()
+        L.check(L.lib().hpxgs_forward_workspace_size(P, cviews, nv, ctypes.byref(self.cfg), int(cap), ctypes.byref(n)),
+                "workspace size")
+        return n.value
+
+    def prepare(self, views):
+        cv = L.make_views(views)
+        L.check(L.lib().hpxgs_prepare(cv, len(views), ctypes.byref(self.cfg), ctypes.c_void_p(_stream())), "prepare")
+
+    def count_pairs(self, g: L.Gaussians, cviews, nv, device) -> int:
+        nb = self.workspace_bytes(g.P, cviews, nv, 0)
+        ws = torch.empty(nb, dtype=torch.uint8, device=device)
+        cnt = torch.zeros(1, dtype=torch.int64, device=device)
+        st = torch.zeros(1, dtype=torch.int32, device=device)
+        L.check(L.lib().hpxgs_count_pairs(ctypes.byref(g), cviews, nv, ctypes.byref(self.cfg), _ptr(ws), nb,
+                                          _ptr(cnt), _ptr(st), ctypes.c_void_p(_stream())), "count_pairs")
+        return int(cnt.item())
+
+    def forward_raw(self, means, scales, rotations, opacities, sh, sh_degree, views, check_status=True):
+        """Runs hpxgs_forward; returns a dict of outputs and the state the backward needs."""
+        means, scales, rotations, opacities, sh = map(_f32, (means, scales, rotations, opacities, sh))
+        dev = means.device
+        g = gaussians_struct(means, scales, rotations, opacities, sh, sh_degree)
+        nv = len(views)
+        cv = L.make_views(views)
+        lay = view_layout(views, self.cfg.tile_level)
+        if self.capacity is None:
+            self.capacity = int(self.count_pairs(g, cv, nv, dev) * self.headroom) + 4096
+        for _attempt in range(4):
+            cap = int(self.capacity)
+            nb = self.workspace_bytes(g.P, cv, nv, cap)
+            ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+            maps = torch.empty((lay.total_pix, 3), dtype=torch.float32, device=dev)
+            T = torch.empty(lay.total_pix, dtype=torch.float32, device=dev)
+            last = torch.empty(lay.total_pix, dtype=torch.int32, device=dev)
+            mask = torch.empty(lay.total_pix // 32, dtype=torch.int32, device=dev)
+            radii = torch.empty((nv, g.P), dtype=torch.float32, device=dev)
+            status = torch.zeros(1, dtype=torch.int32, device=dev)
+            L.check(L.lib().hpxgs_forward(ctypes.byref(g), cv, nv, ctypes.byref(self.cfg), _ptr(ws), nb, cap, _ptr(maps),
+                                          _ptr(T), _ptr(last), _ptr(mask), _ptr(radii), _ptr(status),
+                                          ctypes.c_void_p(_stream())), "forward")
+            if not check_status:
+                break
+            flags = int(status.item())
+            if not (flags & L.F_CAPACITY):
+                L.check(L.lib().hpxgs_status_error(flags), "forward (device status)")
+                break
+            need = self.count_pairs(g, cv, nv, dev)
+            self.capacity = int(need * self.headroom) + 4096
+        else:
+            raise L.HpxgsError(L.E_CAPACITY, "forward")
+        state = dict(ws=ws, nb=nb, cap=cap, cviews=cv, nv=nv, g=g, T=T, last=last, status=status,
+                     keep=(means, scales, rotations, opacities, sh), sh_degree=sh_degree)
+        return dict(maps=maps, T=T, last=last, mask=mask, radii=radii, status=status, layout=lay), state
+
+    def backward_raw(self, state, dmaps):
+        means, scales, rotations, opacities, sh = state["keep"]
+        dmaps = _f32(dmaps)
+        dm, ds, dq, do, dsh = (torch.empty_like(t) for t in (means, scales, rotations, opacities, sh))
+        st = torch.zeros(1, dtype=torch.int32, device=means.device)
+        L.check(L.lib().hpxgs_backward(ctypes.byref(state["g"]), state["cviews"], state["nv"], ctypes.byref(self.cfg),
+                                       _ptr(state["ws"]), state["nb"], state["cap"], _ptr(dmaps), _ptr(state["T"]),
+                                       _ptr(state["last"]), _ptr(dm), _ptr(ds), _ptr(dq), _ptr(do), _ptr(dsh), _ptr(st),
+                                       ctypes.c_void_p(_stream())), "backward")
+        return dm, ds, dq, do, dsh
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, scales, rotations, opacities, sh, rast, views, sh_degree, check_status):
+        out, state = rast.forward_raw(means, scales, rotations, opacities, sh, sh_degree, views, check_status)
+        ctx.rast = rast
+        ctx.state = state
+        ctx.mark_non_differentiable(out["T"], out["last"], out["mask"], out["radii"])
+        return out["maps"], out["T"], out["last"], out["mask"], out["radii"]
+
+    @staticmethod
+    def backward(ctx, dmaps, dT, dlast, dmask, dradii):
+        grads = ctx.rast.backward_raw(ctx.state, dmaps if dmaps is not None else torch.zeros_like(ctx.state["T"]).unsqueeze(1).expand(-1, 3).contiguous())
+        ctx.state = None
+        return (*grads, None, None, None, None)
+
+
+def render(means, scales, rotations, opacities, sh, views, rasterizer: Rasterizer | None = None, sh_degree=None,
+           check_status=True):
+    """Differentiable render of `views`: returns (maps, T_final, last, mask_words, radii), packed over views."""
+    rast = rasterizer or Rasterizer()
+    if sh_degree is None:
+        sh_degree = int(round(math.sqrt(sh.shape[1]))) - 1
+    return _RenderFn.apply(means, scales, rotations, opacities, sh, rast, views, sh_degree, check_status)
+
+
+class _HSSIMFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, I, G, mask_words, k, lam):
+        I, G = _f32(I), _f32(G)
+        nb = ctypes.c_size_t()
+        L.check(L.lib().hpxgs_hssim_workspace_size(k, ctypes.byref(nb)), "hssim workspace")
+        ws = torch.empty(nb.value, dtype=torch.uint8, device=I.device)
+        out = torch.empty(3, dtype=torch.float32, device=I.device)
+        L.check(L.lib().hpxgs_hssim_forward(_ptr(I), _ptr(G), _ptr(mask_words), k, float(lam), _ptr(ws), nb.value,
+                                            _ptr(out), ctypes.c_void_p(_stream())), "hssim forward")
+        ctx.save_for_backward(I, G, mask_words, ws)
+        ctx.k, ctx.lam, ctx.nb = k, lam, nb.value
+        ctx.mark_non_differentiable(out)
+        return out[0].clone(), out
+
+    @staticmethod
+    def backward(ctx, gloss, gout):
+        I, G, mask_words, ws = ctx.saved_tensors
+        gl = _f32(gloss.reshape(1)) if gloss is not None else torch.ones(1, device=I.device)
+        dI = torch.empty_like(I)
+        L.check(L.lib().hpxgs_hssim_backward(_ptr(I), _ptr(G), _ptr(mask_words), ctx.k, float(ctx.lam), _ptr(ws),
+                                             ctx.nb, _ptr(gl), _ptr(dI), ctypes.c_void_p(_stream())), "hssim backward")
+        return dI, None, None, None, None
+
+
+def hssim_loss(I, G, mask_words, k, lam=0.2):
+    """(1 - lam) L1 + lam (1 - HSSIM) over the in-mask pixels; returns (loss, [loss, HSSIM, L1])."""
+    return _HSSIMFn.apply(I, G, mask_words, k, lam)
+
+
+def workspace_view(rast: Rasterizer, state) -> L.WorkspaceView:
+    out = L.WorkspaceView()
+    L.check(L.lib().hpxgs_workspace_inspect(state["g"].P, state["cviews"], state["nv"], ctypes.byref(rast.cfg),
+                                            state["cap"], _ptr(state["ws"]), ctypes.byref(out)), "inspect")
+    return out
+
+
+class _DevArray:
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (int(ptr), True),
+                                         "version": 3, "strides": None}
+
+
+_TYPESTR = {torch.float32: "<f4", torch.int32: "<i4", torch.int64: "<i8", torch.uint8: "|u1"}
+
+
+def device_array(ptr, n, dtype, device=None):
+    """Copy n elements at a device pointer into a new tensor (for inspection in tests)."""
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device=device or "cuda")
+    view = torch.as_tensor(_DevArray(ptr, n, _TYPESTR[dtype]), device=device or "cuda")
+    return view.clone()

@@ -1,0 +1,70 @@
+"""The C-ABI library loads and exports every symbol include/hpxgs.h declares, and
+rejects bad arguments on the host (no GPU needed: nothing here launches work)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2606_29794_b300 import _lib as L
+from paper_2606_29794_b300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hpxgs.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hpxgs_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(L.EXPORTS)
+
+
+def test_strerror_and_status(lib):
+    assert L.strerror(0) == "ok"
+    assert "capacity" in L.strerror(L.E_CAPACITY)
+    assert lib.hpxgs_status_error(L.F_CAPACITY) == L.E_CAPACITY
+    assert lib.hpxgs_status_error(0) == 0
+
+
+def test_adaptive_nside(lib):
+    ns = ctypes.c_double(); k = ctypes.c_int(); kl = ctypes.c_int(); kh = ctypes.c_int()
+    assert lib.hpxgs_nside_for_image(0, 6080, 3040, 360, 360, ctypes.byref(ns), ctypes.byref(k), ctypes.byref(kl),
+                                     ctypes.byref(kh)) == 0
+    assert (kl.value, kh.value) == (10, 11)
+    assert lib.hpxgs_nside_for_image(0, -1, 3040, 360, 360, None, None, None, None) == L.E_INVALID_ARG
+
+
+def test_host_argument_checks(lib):
+    cfg = L.default_config()
+    v = L.make_views([dict(W=[1, 0, 0, 0, 1, 0, 0, 0, 1], b=[0, 0, 0], nside_log2=6, cam=0)])
+    n = ctypes.c_size_t()
+    assert lib.hpxgs_forward_workspace_size(1000, v, 1, ctypes.byref(cfg), 10000, ctypes.byref(n)) == 0
+    assert n.value > 0
+    bad = L.default_config(tile_level=2)
+    assert lib.hpxgs_forward_workspace_size(1000, v, 1, ctypes.byref(bad), 10000, ctypes.byref(n)) == L.E_INVALID_ARG
+    vb = L.make_views([dict(W=[1, 0, 0, 0, 1, 0, 0, 0, 1], b=[0, 0, 0], nside_log2=2, cam=0)])
+    assert lib.hpxgs_forward_workspace_size(1000, vb, 1, ctypes.byref(cfg), 10000, ctypes.byref(n)) == L.E_INVALID_ARG
+    vp = L.make_views([dict(W=[1, 0, 0, 0, 1, 0, 0, 0, 1], b=[0, 0, 0], nside_log2=6, cam=1, fov_x=200.0)])
+    assert lib.hpxgs_forward_workspace_size(1000, vp, 1, ctypes.byref(cfg), 10000, ctypes.byref(n)) == L.E_INVALID_ARG
+    assert lib.hpxgs_forward_workspace_size(1000, v, 1, ctypes.byref(cfg), -5, ctypes.byref(n)) == L.E_INVALID_ARG
+    assert lib.hpxgs_forward_workspace_size(1000, v, 0, ctypes.byref(cfg), 10, ctypes.byref(n)) == L.E_INVALID_ARG
+    # null required pointers are rejected before any launch
+    g = L.Gaussians(); g.P = 10; g.sh_degree = 0
+    assert lib.hpxgs_forward(ctypes.byref(g), v, 1, ctypes.byref(cfg), None, 0, 0, None, None, None, None, None, None,
+                             None) == L.E_INVALID_ARG
+    assert lib.hpxgs_hssim_workspace_size(2, ctypes.byref(n)) == L.E_INVALID_ARG
+    assert lib.hpxgs_pix2vec_nest(20, None, 1, None, None, None) == L.E_INVALID_ARG
