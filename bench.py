@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Benchmark of the HEALPix Gaussian rasterizer training step on one B300.
+
+Workload (the paper's training-step shape, Sec. 4): Nside 512 (3,145,728 px)
+masked to a 190-degree equidistant fisheye (1,709,948 in-mask px), 300,000
+Gaussians with SH degree 3, loss = (1 - 0.2) L1 + 0.2 (1 - HSSIM) against a
+target map rendered from a perturbed copy of the scene. One step = forward
+render + loss forward + loss backward + render backward (all §8 hot-path
+stages). Metric: in-mask Mpix/s of fwd+bwd (higher is better).
+
+`value` times the device path with inputs resident in HBM (CUDA events per
+step, L2 flushed between steps). `e2e` times the same step through the public
+API with the step's input (the target map) copied from pinned host memory and
+the loss read back every step. `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+P_GAUSS = 300_000
+K_ORDER = 9
+FOV = 190.0
+SEED = 20261205
+WORKLOAD = "train_step_nside512_fisheye190_P300k_sh3"
+
+# FP32 work per (pixel, list entry), counted from the kernels' inner loops
+# (FMA = 2 flops): weight evaluation 40; forward blend of a contributing entry 13;
+# backward gradient of a contributing entry 83. See DESIGN.md "Roofline".
+F_EVAL, F_BLEND, F_GRAD = 40, 13, 83
+SM_COUNT, FP32_LANES = 148, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile-level", type=int, default=4)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- ours
+def csrc_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2606_29794_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_stage):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if the
+    kernels have not changed since it was taken (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(kernel_stage)
+    if not e or e.get("csrc_sha") != csrc_sha():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def run_ours(args, ws_n, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2606_29794_b300 import _lib as L
+    from paper_2606_29794_b300 import raster as R
+    from paper_2606_29794_b300 import synth as S
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = L.lib()
+    # ---------------- inputs (synthetic, seeded; each rank its own camera pose)
+    sc = S.make_scene(P_GAUSS, 3, seed=SEED)
+    tgt = S.perturb_scene(sc, SEED + 1)
+    rot = None if rank == 0 else S.random_rotation(np.random.default_rng(SEED + 100 + rank))
+    view = S.make_view(K_ORDER, S.CAM_FISHEYE, FOV, R=rot)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev)
+    K = 16
+    params = [t(sc["means"]), t(sc["scales"]), t(sc["rotations"]), t(sc["opacities"]), t(np.asarray(sc["sh"]).reshape(P_GAUSS, K, 3))]
+    tparams = [t(tgt["means"]), t(tgt["scales"]), t(tgt["rotations"]), t(tgt["opacities"]), t(np.asarray(tgt["sh"]).reshape(P_GAUSS, K, 3))]
+    rast = R.Rasterizer(tile_level=args.tile_level)
+    rast.prepare([view])
+    stream = torch.cuda.current_stream(dev)
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    with torch.no_grad():
+        tout, _ = rast.forward_raw(*tparams, 3, [view])
+    G = tout["maps"].clone()
+    # HSSIM workspace
+    nb = ctypes.c_size_t()
+    L.check(lib.hpxgs_hssim_workspace_size(K_ORDER, ctypes.byref(nb)), "hssim ws")
+    hws = torch.empty(nb.value, dtype=torch.uint8, device=dev)
+    out3 = torch.empty(3, dtype=torch.float32, device=dev)
+    dmaps = torch.empty_like(G)
+    p = lambda x: ctypes.c_void_p(x.data_ptr())
+
+    def step(target):
+        out, state = rast.forward_raw(*params, 3, [view], check_status=False)
+        L.check(lib.hpxgs_hssim_forward(p(out["maps"]), p(target), p(out["mask"]), K_ORDER, 0.2, p(hws), nb.value,
+                                        p(out3), sptr), "hssim fwd")
+        L.check(lib.hpxgs_hssim_backward(p(out["maps"]), p(target), p(out["mask"]), K_ORDER, 0.2, p(hws), nb.value,
+                                         None, p(dmaps), sptr), "hssim bwd")
+        grads = rast.backward_raw(state, dmaps)
+        return out, state, grads
+
+    # ---------------- warm-up (and capacity check once)
+    for _ in range(max(1, args.warmup)):
+        out, state, grads = step(G)
+    torch.cuda.synchronize()
+    st = int(out["status"].item())
+    if st & L.F_CAPACITY:
+        raise RuntimeError("pair capacity exceeded after warm-up")
+    n_mask = int(np.unpackbits(out["mask"].cpu().numpy().view(np.uint8)).sum())
+    wv = R.workspace_view(rast, state)
+    n_pairs = int(R.device_array(wv.n_pairs, 1, torch.int32).item())
+    # ---------------- timed region (device path)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)     # > 126 MB L2
+    stage_ev = {s: [] for s in L.STAGES}
+    step_ev = []
+    if ws_n > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = lib.hpxgs_launch_count()
+    for _ in range(args.steps):
+        flush.zero_()
+        evs = {}
+        for i, s in enumerate(L.STAGES):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream); b.record(stream)       # torch creates the CUDA event on first record
+            L.check(lib.hpxgs_profile_arm(i, ctypes.c_void_p(a.cuda_event), ctypes.c_void_p(b.cuda_event)), "arm")
+            evs[s] = (a, b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out, state, grads = step(G)
+        e1.record(stream)
+        step_ev.append((e0, e1))
+        for s in L.STAGES:
+            stage_ev[s].append(evs[s])
+    torch.cuda.synchronize()
+    launches = lib.hpxgs_launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    ms = sum(step_ms) / len(step_ms)
+    if ws_n > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+        torch.distributed.barrier()
+    stage_ms = {}
+    for s, lst in stage_ev.items():
+        vals = []
+        for a, b in lst:
+            try:
+                vals.append(a.elapsed_time(b))
+            except Exception:
+                pass
+        if vals:
+            stage_ms[s] = sum(vals) / len(vals)
+    n_eval = int(R.device_array(wv.n_eval, 1, torch.int64).item())
+    n_contrib = int(R.device_array(wv.n_contrib, 1, torch.int64).item())
+    value = n_mask * ws_n / (ms * 1e-3) / 1e6
+    # ---------------- roofline of the dominant kernel
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2032.0))
+    alu_peak = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12        # TFLOP/s FP32 at max SM clock
+    hbm = float(pk.get("hbm_gbs", 6400.0))
+    work = {
+        "blend_fwd": ("alu", (F_EVAL * n_eval + F_BLEND * n_contrib) / 1e12, "TFLOP/s", alu_peak),
+        "blend_bwd": ("alu", (F_EVAL * n_eval + F_GRAD * n_contrib) / 1e12, "TFLOP/s", alu_peak),
+        "pair_sort": ("hbm", 20.0 * n_pairs * math.ceil(math.log2(12 * 4 ** (K_ORDER - args.tile_level)) / 8) / 1e9, "GB/s", hbm),
+        "depth_sort": ("hbm", 20.0 * P_GAUSS * 4 / 1e9, "GB/s", hbm),
+        "preprocess": ("hbm", (236 + 64 + 16) * P_GAUSS / 1e9, "GB/s", hbm),
+        "hssim_fwd": ("hbm", 60.0 * n_mask / 1e9, "GB/s", hbm),
+        "hssim_bwd": ("hbm", 72.0 * n_mask / 1e9, "GB/s", hbm),
+    }
+    if not any(s in work for s in stage_ms):
+        raise RuntimeError(f"no stage timings recorded: {stage_ms}")
+    dom = max((s for s in stage_ms if s in work), key=lambda s: stage_ms[s])
+    bound, amount, unit, peak = work[dom]
+    achieved = amount / (stage_ms[dom] * 1e-3)
+    traffic = ncu_traffic(dom)
+    roofline = {"kernel": dom, "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": unit,
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": ("derived: 148 SM x 128 FP32 lanes x 2 x max SM clock" if bound == "alu"
+                                else "measured (MEASURED_PEAKS.json hbm_gbs)")}
+    # ---------------- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hostG = torch.empty(G.shape, dtype=torch.float32, pin_memory=True)
+        hostG.copy_(G.cpu())
+        dG = torch.empty_like(G)
+        hloss = torch.empty(1, dtype=torch.float32, pin_memory=True)
+        for _ in range(2):
+            dG.copy_(hostG, non_blocking=True); step(dG); hloss.copy_(out3[:1], non_blocking=True)
+        torch.cuda.synchronize()
+        ev = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dG.copy_(hostG, non_blocking=True)
+            step(dG)
+            hloss.copy_(out3[:1], non_blocking=True)
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        e_ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+        if ws_n > 1:
+            tt = torch.tensor([e_ms], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e2e = {"value": round(n_mask * ws_n / (e_ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
+               "h2d_bytes_per_step": int(hostG.numel() * 4), "d2h_bytes_per_step": 4, "ms_per_step": round(e_ms, 4)}
+    res = {
+        "metric": "Mpix/s fwd+bwd at Nside 512/300k Gaussians (L1+HSSIM training step)",
+        "value": round(value, 2), "unit": "Mpix/s", "n_gpus": ws_n, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded Gaussians shaped like the paper's scenes)",
+        "config": {"workload": WORKLOAD, "nside": 512, "camera": "fisheye 190 deg", "in_mask_px": n_mask,
+                   "gaussians": P_GAUSS, "sh_degree": 3, "tile_level": args.tile_level, "loss": "0.8 L1 + 0.2 (1-HSSIM)",
+                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{ws_n}, no collective",
+                   "pairs": n_pairs, "evals": n_eval, "contrib": n_contrib},
+        "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "roofline": roofline,
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+    }
+    return res
+
+
+# ----------------------------------------------------------------------------- oracle
+def oracle_sample(frac, seed=0, with_bwd=True):
+    """Time the FP64 oracle on a random `frac` of the active tiles of the workload.
+    Returns (seconds for the fixed part, seconds for the sampled part, sampled px, in-mask px)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2606_29794_b300 import synth as S
+
+    sc = S.make_scene(P_GAUSS, 3, seed=SEED)
+    tgt_scene = S.perturb_scene(sc, SEED + 1)
+    view = S.make_view(K_ORDER, S.CAM_FISHEYE, FOV)
+    v64 = dict(view); v64["W"] = np.asarray(view["W"], np.float64); v64["b"] = np.asarray(view["b"], np.float64)
+    cfg = O.Config()
+    nside = 2 ** K_ORDER
+    m, _ = O.mask(nside, view["cam"], FOV)
+    act = O.active_tiles(K_ORDER, cfg.tile_level, m)
+    rng = np.random.default_rng(seed)
+    tiles = np.nonzero(act)[0]
+    pick = rng.choice(tiles, size=max(1, int(round(frac * tiles.size))), replace=False)
+    sub = np.zeros_like(act); sub[pick] = 1
+    per = 4 ** cfg.tile_level
+    pix = (pick[:, None] * per + np.arange(per)[None, :]).ravel()
+    pix = pix[m[pix] == 1].astype(np.int64)
+    rho = O.tile_rho(K_ORDER, cfg.tile_level)
+    t0 = time.perf_counter()
+    pre = O.preprocess(sc, v64, cfg)
+    pre_t = O.preprocess(tgt_scene, v64, cfg)
+    t1 = time.perf_counter()
+    start, ids = O.tile_lists(K_ORDER, cfg.tile_level, pre["g"], pre["rs"], pre["valid"], O.depth_bits(pre["r"]), rho, sub)
+    st2, ids2 = O.tile_lists(K_ORDER, cfg.tile_level, pre_t["g"], pre_t["rs"], pre_t["valid"], O.depth_bits(pre_t["r"]), rho, sub)
+    img, T, last, amb = O.composite(K_ORDER, cfg.tile_level, pre, sc["opacities"], start, ids, pix, cfg)
+    timg, _, _, _ = O.composite(K_ORDER, cfg.tile_level, pre_t, tgt_scene["opacities"], st2, ids2, pix, cfg)
+    N = O.npix(nside)
+    I = np.zeros((N, 3)); Gm = np.zeros((N, 3)); I[pix] = img; Gm[pix] = timg
+    O.hssim_local(nside, I, Gm, m, pix)
+    if with_bwd:
+        dI = np.random.default_rng(1).standard_normal((pix.size, 3)) * 1e-6
+        O.backward(sc, v64, cfg, dI, start, ids, pix)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, int(pix.size), int(m.sum())
+
+
+def cpu_baseline(target_s=12.0):
+    import oracle as O
+    f = 0.002
+    fixed, samp, npx, nmask = oracle_sample(f)
+    # grow the sample to about target_s seconds of sampled work (bounded)
+    if samp < target_s / 4:
+        f = min(0.2, f * target_s / max(samp, 1e-3))
+        fixed, samp, npx, nmask = oracle_sample(f, seed=1)
+    est = fixed + samp * nmask / npx
+    return {"value": round(nmask / est / 1e6, 5), "unit": "Mpix/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": (f"FP64 oracle (C++/OpenMP) on {npx} px of {nmask} in-mask px (random {f:.4f} of active "
+                       f"tiles): preprocess of both scenes + tile lists + composite of render and target + HSSIM "
+                       f"forward + backward on the sample; full step estimated as fixed {fixed:.2f} s + "
+                       f"sample {samp:.2f} s x {nmask / npx:.1f}")}
+
+
+def run_reference(args):
+    import oracle as O
+    f = 0.002
+    for _ in range(args.warmup):
+        oracle_sample(f, seed=99, with_bwd=False)
+    times = []
+    npx = nmask = 0
+    for i in range(args.steps):
+        fixed, samp, npx, nmask = oracle_sample(f, seed=i)
+        times.append(fixed + samp * nmask / npx)
+    est = sum(times) / len(times)
+    value = nmask / est / 1e6
+    cb = {"value": round(value, 5), "unit": "Mpix/s", "cores": O.num_threads(), "kind": "oracle",
+          "sample": f"per step: random {f} of active tiles ({npx} px), full step estimated by scaling the sampled part"}
+    return {"impl": "reference", "metric": "Mpix/s fwd+bwd at Nside 512/300k Gaussians (L1+HSSIM training step)",
+            "value": round(value, 5), "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(est * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD}, "cpu_baseline": cb,
+            "e2e": {"value": round(value, 5), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws_n, rank, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args)))
+        return 0
+    if ws_n > 1:
+        import torch
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, ws_n, rank, local)
+    if rank == 0 and ws_n == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(res))
+    if ws_n > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -194,6 +194,30 @@ int hpxgs_count_pairs(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
                       void* workspace, size_t workspace_bytes, uint64_t* count, int32_t* status,
                       hpxgs_stream_t stream);
 
+/* ---- instrumentation ---- */
+/* Stages that hpxgs_profile_arm can time. */
+#define HPXGS_STAGE_MASK 0
+#define HPXGS_STAGE_PREPROCESS 1
+#define HPXGS_STAGE_DEPTH_SORT 2
+#define HPXGS_STAGE_TILE_COUNT 3
+#define HPXGS_STAGE_SCAN 4
+#define HPXGS_STAGE_TILE_EMIT 5
+#define HPXGS_STAGE_PAIR_SORT 6
+#define HPXGS_STAGE_RANGES 7
+#define HPXGS_STAGE_BLEND_FWD 8
+#define HPXGS_STAGE_BLEND_BWD 9
+#define HPXGS_STAGE_PREPROCESS_BWD 10
+#define HPXGS_STAGE_HSSIM_FWD 11
+#define HPXGS_STAGE_HSSIM_BWD 12
+#define HPXGS_NUM_STAGES 13
+/* Arm a one-shot timing of `stage`: the next call that runs the stage records
+ * start_event (a cudaEvent_t) on its stream right before the stage's first
+ * kernel and stop_event right after its last one, then disarms. Pass NULL
+ * events to disarm. Host only; the events belong to the caller. */
+int hpxgs_profile_arm(int stage, void* start_event, void* stop_event);
+/* Number of kernels this library has launched in this process. */
+uint64_t hpxgs_launch_count(void);
+
 /* Device pointers into a forward workspace (for inspection and tests). */
 typedef struct {
   const float* records;        /* [nviews*P, 16]: g(3), o, e_east(3), conic_a, e_north(3), conic_b, colour(3), conic_c */
@@ -204,6 +228,8 @@ typedef struct {
   const uint32_t* ranges;      /* [total_tiles, 2] start/end into pair_ids */
   const uint32_t* n_pairs;     /* device scalar: pairs needed (may exceed capacity) */
   const float* accum;          /* [nviews*P, HPXGS_NACC] backward partials (after hpxgs_backward) */
+  const uint64_t* n_eval;      /* device scalar: (pixel, list entry) evaluations of the last forward blend */
+  const uint64_t* n_contrib;   /* device scalar: of those, entries with alpha > 0 */
   int64_t total_tiles;
 } hpxgs_workspace_view;
 int hpxgs_workspace_inspect(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,

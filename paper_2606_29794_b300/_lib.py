@@ -19,6 +19,8 @@ F_CAPACITY, F_TIMEOUT = 1, 2
 CAM_FULL, CAM_PINHOLE, CAM_FISHEYE = 0, 1, 2
 MAX_VIEWS = 64
 NACC = 9
+STAGES = ("mask", "preprocess", "depth_sort", "tile_count", "scan", "tile_emit", "pair_sort", "ranges",
+          "blend_fwd", "blend_bwd", "preprocess_bwd", "hssim_fwd", "hssim_bwd")
 
 
 class Gaussians(ctypes.Structure):
@@ -45,7 +47,8 @@ class Config(ctypes.Structure):
 class WorkspaceView(ctypes.Structure):
     _fields_ = [("records", ctypes.c_void_p), ("radii", ctypes.c_void_p), ("depth", ctypes.c_void_p),
                 ("pair_tiles", ctypes.c_void_p), ("pair_ids", ctypes.c_void_p), ("ranges", ctypes.c_void_p),
-                ("n_pairs", ctypes.c_void_p), ("accum", ctypes.c_void_p), ("total_tiles", ctypes.c_int64)]
+                ("n_pairs", ctypes.c_void_p), ("accum", ctypes.c_void_p), ("n_eval", ctypes.c_void_p),
+                ("n_contrib", ctypes.c_void_p), ("total_tiles", ctypes.c_int64)]
 
 
 class HpxgsError(RuntimeError):
@@ -80,6 +83,8 @@ _SIGS = {
     "hpxgs_count_pairs": (ctypes.c_int, [_P(Gaussians), _P(View), ctypes.c_int, _P(Config), _vp, _sz, _vp, _vp, _vp]),
     "hpxgs_workspace_inspect": (ctypes.c_int, [_i32, _P(View), ctypes.c_int, _P(Config), _i64, _vp,
                                                _P(WorkspaceView)]),
+    "hpxgs_profile_arm": (ctypes.c_int, [ctypes.c_int, _vp, _vp]),
+    "hpxgs_launch_count": (ctypes.c_uint64, []),
     "hpxgs_hssim_workspace_size": (ctypes.c_int, [ctypes.c_int, _P(_sz)]),
     "hpxgs_hssim_forward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _f32, _vp, _sz, _vp, _vp]),
     "hpxgs_hssim_backward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _f32, _vp, _sz, _vp, _vp, _vp]),

@@ -2,6 +2,7 @@
 // the tile radius rho(k, b) and the workspace layout of the rasterizer.
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -12,6 +13,26 @@
 using namespace hpx;
 
 namespace hpxgs {
+
+// ----------------------------------------------------------------------------
+// Instrumentation: one-shot stage timing with caller events; launch counter.
+// ----------------------------------------------------------------------------
+static std::mutex g_prof_mu;
+static cudaEvent_t g_prof[HPXGS_NUM_STAGES][2];
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+void prof_begin(int stage, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_prof[stage][0]) cudaEventRecord(g_prof[stage][0], s);
+}
+void prof_end(int stage, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_prof[stage][1]) cudaEventRecord(g_prof[stage][1], s);
+  g_prof[stage][0] = nullptr;
+  g_prof[stage][1] = nullptr;
+}
 
 int num_sms() {
   static int n = 0;
@@ -69,6 +90,7 @@ __global__ void k_mask(ViewParams vp, int b, uint32_t* __restrict__ words, uint3
 int launch_mask(const ViewParams& vp, int b, uint32_t* words, uint32_t* tile_flags, cudaStream_t s) {
   const uint32_t npix = 12u << (2 * vp.k);
   k_mask<<<(npix + 255) / 256, 256, 0, s>>>(vp, b, words, tile_flags);
+  note_launches(1);
   HPXGS_LAUNCH_CHECK();
   return HPXGS_OK;
 }
@@ -128,6 +150,7 @@ int tile_rho(int k, int b, double* rho, cudaStream_t s) {
   const int ntile = 12 << (2 * (k - b));
   const int per = 1 << (2 * b);
   k_tile_mindot<<<ntile, per < 256 ? (per < 32 ? 32 : per) : 256, 0, s>>>(k, b, dptr);
+  note_launches(1);
   HPXGS_LAUNCH_CHECK();
   unsigned long long res = 0;
   HPXGS_CUDA_CHECK(cudaMemcpyAsync(&res, dptr, sizeof(res), cudaMemcpyDeviceToHost, s));
@@ -352,6 +375,16 @@ int hpxgs_nside_for_image(int kind, double W, double H, double fovx, double fovy
   return HPXGS_OK;
 }
 
+int hpxgs_profile_arm(int stage, void* start_event, void* stop_event) {
+  if (stage < 0 || stage >= HPXGS_NUM_STAGES) return HPXGS_E_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof[stage][0] = (cudaEvent_t)start_event;
+  g_prof[stage][1] = (cudaEvent_t)stop_event;
+  return HPXGS_OK;
+}
+
+uint64_t hpxgs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
 int hpxgs_tile_rho(int k, int b, double* rho, hpxgs_stream_t stream) {
   if (!rho) return HPXGS_E_INVALID_ARG;
   return tile_rho(k, b, rho, (cudaStream_t)stream);
@@ -377,6 +410,7 @@ int hpxgs_pix2vec_nest(int k, const int64_t* pix, int64_t n, float* v32, double*
   if (k < 0 || k > 13 || n < 0 || (n > 0 && !pix)) return HPXGS_E_INVALID_ARG;
   if (n == 0) return HPXGS_OK;
   k_pix2vec<<<grid_for(n), 256, 0, (cudaStream_t)s>>>(k, pix, n, v32, v64);
+  note_launches(1);
   HPXGS_LAUNCH_CHECK();
   return HPXGS_OK;
 }
@@ -384,6 +418,7 @@ int hpxgs_vec2pix_nest(int k, const double* v, int64_t n, int64_t* pix, hpxgs_st
   if (k < 0 || k > 13 || n < 0 || (n > 0 && (!v || !pix))) return HPXGS_E_INVALID_ARG;
   if (n == 0) return HPXGS_OK;
   k_vec2pix<<<grid_for(n), 256, 0, (cudaStream_t)s>>>(k, v, n, pix);
+  note_launches(1);
   HPXGS_LAUNCH_CHECK();
   return HPXGS_OK;
 }
@@ -391,6 +426,7 @@ int hpxgs_nest2ring(int k, const int64_t* in, int64_t n, int64_t* out, hpxgs_str
   if (k < 0 || k > 13 || n < 0 || (n > 0 && (!in || !out))) return HPXGS_E_INVALID_ARG;
   if (n == 0) return HPXGS_OK;
   k_nest2ring<<<grid_for(n), 256, 0, (cudaStream_t)s>>>(k, in, n, out);
+  note_launches(1);
   HPXGS_LAUNCH_CHECK();
   return HPXGS_OK;
 }
@@ -398,6 +434,7 @@ int hpxgs_ring2nest(int k, const int64_t* in, int64_t n, int64_t* out, hpxgs_str
   if (k < 0 || k > 13 || n < 0 || (n > 0 && (!in || !out))) return HPXGS_E_INVALID_ARG;
   if (n == 0) return HPXGS_OK;
   k_ring2nest<<<grid_for(n), 256, 0, (cudaStream_t)s>>>(k, in, n, out);
+  note_launches(1);
   HPXGS_LAUNCH_CHECK();
   return HPXGS_OK;
 }
@@ -405,6 +442,7 @@ int hpxgs_neighbours_nest(int k, const int64_t* in, int64_t n, int64_t* out, hpx
   if (k < 1 || k > 13 || n < 0 || (n > 0 && (!in || !out))) return HPXGS_E_INVALID_ARG;
   if (n == 0) return HPXGS_OK;
   k_neighbours<<<grid_for(n), 256, 0, (cudaStream_t)s>>>(k, in, n, out);
+  note_launches(1);
   HPXGS_LAUNCH_CHECK();
   return HPXGS_OK;
 }

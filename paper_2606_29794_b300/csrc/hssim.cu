@@ -194,11 +194,14 @@ int hpxgs_hssim_forward(const float* I, const float* G, const uint32_t* mask, in
   const uint32_t npix = 12u << (2 * k);
   const int nblocks = (int)((npix + kHThreads - 1) / kHThreads);
   char* w = static_cast<char*>(ws);
+  prof_begin(HPXGS_STAGE_HSSIM_FWD, s);
   k_hssim_fwd<<<nblocks, kHThreads, 0, s>>>(k, I, G, mask, reinterpret_cast<float*>(w + L.coef),
                                             reinterpret_cast<double*>(w + L.part));
   k_hssim_reduce<<<1, 256, 0, s>>>(reinterpret_cast<double*>(w + L.part), nblocks, lambda, out3,
                                    reinterpret_cast<double*>(w + L.nmask));
+  note_launches(2);
   HPXGS_LAUNCH_CHECK();
+  prof_end(HPXGS_STAGE_HSSIM_FWD, s);
   return HPXGS_OK;
 }
 
@@ -212,9 +215,12 @@ int hpxgs_hssim_backward(const float* I, const float* G, const uint32_t* mask, i
   const uint32_t npix = 12u << (2 * k);
   const int nblocks = (int)((npix + kHThreads - 1) / kHThreads);
   const char* w = static_cast<const char*>(ws);
+  prof_begin(HPXGS_STAGE_HSSIM_BWD, s);
   k_hssim_bwd<<<nblocks, kHThreads, 0, s>>>(k, I, G, mask, reinterpret_cast<const float*>(w + L.coef),
                                             reinterpret_cast<const double*>(w + L.nmask), lambda, dloss, dI);
+  note_launches(1);
   HPXGS_LAUNCH_CHECK();
+  prof_end(HPXGS_STAGE_HSSIM_BWD, s);
   return HPXGS_OK;
 }
 

@@ -65,7 +65,14 @@ constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kMaxSortBlocks = 1024;
 
 // counters block (u32 each)
-enum Counter { C_NPAIRS = 0, C_WORK_FWD = 1, C_WORK_BWD = 2, C_NSORT = 3, C_NPAIRS_HI = 4, C_COUNT = 16 };
+// (u64 counters live at u32 index 8 (n_eval) and 10 (n_contrib), 8-byte aligned)
+enum Counter { C_NPAIRS = 0, C_WORK_FWD = 1, C_WORK_BWD = 2, C_NSORT = 3, C_NPAIRS_HI = 4, C_NEVAL = 8, C_NCONTRIB = 10,
+               C_COUNT = 16 };
+
+// instrumentation (geometry.cu)
+void prof_begin(int stage, cudaStream_t s);
+void prof_end(int stage, cudaStream_t s);
+void note_launches(int n);
 
 int make_layout(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg, int64_t cap, Layout* L);
 int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,

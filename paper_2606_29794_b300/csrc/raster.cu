@@ -298,6 +298,7 @@ static int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, co
     k_sort_hist<<<G, kSortThreads, 0, s>>>(kin, n_dev, n_max, shift, nb, hist, G);
     k_scan_u32_inplace<<<1, 1024, 0, s>>>(hist, 256 * G);
     k_sort_scatter<<<G, kSortThreads, 0, s>>>(kin, vin, kout, vout, n_dev, n_max, shift, nb, hist, G);
+    note_launches(3);
     HPXGS_LAUNCH_CHECK();
     cur ^= 1;
   }
@@ -543,7 +544,8 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
                                                   const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
                                                   const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
                                                   float* __restrict__ maps, float* __restrict__ Tout,
-                                                  uint32_t* __restrict__ lastout, uint32_t* work) {
+                                                  uint32_t* __restrict__ lastout, uint32_t* work,
+                                                  unsigned long long* __restrict__ evals) {
   __shared__ float4 s_rec[BATCH][4];
   __shared__ int s_tile;
   const int tid = threadIdx.x;
@@ -565,6 +567,7 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
     uint32_t last[PPT];
     bool done[PPT], inm[PPT];
     uint32_t lp[PPT];
+    uint32_t ncontrib = 0, neval = 0;
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
       lp[q] = (lt << (2 * b)) + q * NT + tid;
@@ -592,6 +595,7 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
           Pix P;
           pixel_weight(pv[q], r0, r1, r2, r3, P);
           if (P.m <= vt.cutoff) {
+            ++ncontrib;
             const float a = fminf(vt.alpha_max, r0.w * __expf(-0.5f * P.m));
             const float w = a * T[q];
             C[q][0] += w * r3.x; C[q][1] += w * r3.y; C[q][2] += w * r3.z;
@@ -610,6 +614,7 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
       const int64_t pg = vp.pix_base + lp[q];
       if (inm[q]) {
         if (T[q] >= vt.eps_T) last[q] = rg.y - rg.x;     // ran through the whole list
+        neval += last[q];
         maps[3 * pg + 0] = C[q][0] + T[q] * vt.bg[0];
         maps[3 * pg + 1] = C[q][1] + T[q] * vt.bg[1];
         maps[3 * pg + 2] = C[q][2] + T[q] * vt.bg[2];
@@ -621,6 +626,13 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
         lastout[pg] = 0;
       }
     }
+    // per-warp totals of evaluated and contributing (pixel, entry) pairs
+    unsigned long long e64 = neval, c64 = ncontrib;
+    for (int o = 16; o > 0; o >>= 1) {
+      e64 += __shfl_xor_sync(0xffffffffu, e64, o);
+      c64 += __shfl_xor_sync(0xffffffffu, c64, o);
+    }
+    if ((tid & 31) == 0 && e64) { atomicAdd(&evals[0], e64); atomicAdd(&evals[1], c64); }
   }
 }
 
@@ -927,10 +939,12 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   HPXGS_CUDA_CHECK(cudaMemsetAsync(flags, 0, sizeof(uint32_t) * L.total_tiles, s));
   HPXGS_CUDA_CHECK(cudaMemsetAsync(counters, 0, sizeof(uint32_t) * C_COUNT, s));
   // FoV masks (kept in the workspace: the backward reads them) and tile flags
+  prof_begin(HPXGS_STAGE_MASK, s);
   for (int v = 0; v < nviews; ++v) {
     rc = launch_mask(vt->v[v], cfg->tile_level, mask_out + (vt->v[v].pix_base >> 5), flags + vt->v[v].tile_base, s);
     if (rc != HPXGS_OK) return rc;
   }
+  prof_end(HPXGS_STAGE_MASK, s);
   const int64_t PV = L.PV;
   *which_depth = 0;
   if (PV == 0) return HPXGS_OK;
@@ -939,23 +953,34 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   float* depth = at<float>(ws, L.depth);
   uint32_t* ka = at<uint32_t>(ws, L.key_a); uint32_t* kb = at<uint32_t>(ws, L.key_b);
   uint32_t* va = at<uint32_t>(ws, L.val_a); uint32_t* vb = at<uint32_t>(ws, L.val_b);
+  prof_begin(HPXGS_STAGE_PREPROCESS, s);
   k_preprocess<<<(unsigned)((PV + 255) / 256), 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va);
+  note_launches(1);
   HPXGS_LAUNCH_CHECK();
+  prof_end(HPXGS_STAGE_PREPROCESS, s);
+  prof_begin(HPXGS_STAGE_DEPTH_SORT, s);
   rc = radix_sort(ka, va, kb, vb, nullptr, (uint32_t)PV, 32, at<uint32_t>(ws, L.hist), L.sort_blocks, s, which_depth);
   if (rc != HPXGS_OK) return rc;
+  prof_end(HPXGS_STAGE_DEPTH_SORT, s);
   const uint32_t* sk = *which_depth ? kb : ka;
   const uint32_t* sv = *which_depth ? vb : va;
   uint32_t* counts = at<uint32_t>(ws, L.counts);
   uint64_t* offsets = at<uint64_t>(ws, L.offsets);
   uint64_t* part = at<uint64_t>(ws, L.scan_part);
+  prof_begin(HPXGS_STAGE_TILE_COUNT, s);
   k_tiles<false><<<(unsigned)((PV + 127) / 128), 128, 0, s>>>(*vt, rec, radii, sk, sv, flags, counts, nullptr, nullptr,
                                                              nullptr, 0, status);
+  note_launches(1);
   HPXGS_LAUNCH_CHECK();
+  prof_end(HPXGS_STAGE_TILE_COUNT, s);
   const int G = L.sort_blocks;
+  prof_begin(HPXGS_STAGE_SCAN, s);
   k_scan_part<<<G, 256, 0, s>>>(counts, PV, G, part);
   k_scan_top<<<1, 32, 0, s>>>(part, G, counters, total_out);
   k_scan_apply<<<G, 256, 0, s>>>(counts, PV, G, part, offsets);
+  note_launches(3);
   HPXGS_LAUNCH_CHECK();
+  prof_end(HPXGS_STAGE_SCAN, s);
   return HPXGS_OK;
 }
 
@@ -995,6 +1020,8 @@ int hpxgs_workspace_inspect(int32_t P, const hpxgs_view* views, int nviews, cons
   out->ranges = at<uint32_t>(w, L.ranges);
   out->n_pairs = at<uint32_t>(w, L.counters) + C_NPAIRS;
   out->accum = at<float>(w, L.accum);
+  out->n_eval = reinterpret_cast<const uint64_t*>(at<uint32_t>(w, L.counters) + C_NEVAL);
+  out->n_contrib = reinterpret_cast<const uint64_t*>(at<uint32_t>(w, L.counters) + C_NCONTRIB);
   out->total_tiles = L.total_tiles;
   return HPXGS_OK;
 }
@@ -1043,36 +1070,48 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
   if (PV > 0 && cap > 0) {
     const uint32_t* sk = which ? at<uint32_t>(ws, L.key_b) : at<uint32_t>(ws, L.key_a);
     const uint32_t* sv = which ? at<uint32_t>(ws, L.val_b) : at<uint32_t>(ws, L.val_a);
+    prof_begin(HPXGS_STAGE_TILE_EMIT, s);
     k_tiles<true><<<(unsigned)((PV + 127) / 128), 128, 0, s>>>(*vt, rec, at<float>(ws, L.radii), sk, sv, flags, nullptr,
                                                               at<uint64_t>(ws, L.offsets), pka, pva, (uint64_t)cap, status);
+    note_launches(1);
     HPXGS_LAUNCH_CHECK();
+    prof_end(HPXGS_STAGE_TILE_EMIT, s);
     int wp = 0;
+    prof_begin(HPXGS_STAGE_PAIR_SORT, s);
     rc = radix_sort(pka, pva, pkb, pvb, counters + C_NPAIRS, (uint32_t)cap, L.pair_bits, at<uint32_t>(ws, L.hist),
                     L.sort_blocks, s, &wp);
     if (rc != HPXGS_OK) { delete vt; return rc; }
+    prof_end(HPXGS_STAGE_PAIR_SORT, s);
     const uint32_t* sorted_tiles = wp ? pkb : pka;
+    prof_begin(HPXGS_STAGE_RANGES, s);
     HPXGS_CUDA_CHECK(cudaMemsetAsync(ranges, 0, sizeof(uint2) * L.total_tiles, s));
     const int64_t rblocks = std::min<int64_t>((cap + 255) / 256, 64LL * num_sms());
     k_ranges<<<(unsigned)rblocks, 256, 0, s>>>(sorted_tiles, counters + C_NPAIRS, (uint32_t)cap, ranges);
+    note_launches(1);
     HPXGS_LAUNCH_CHECK();
+    prof_end(HPXGS_STAGE_RANGES, s);
   } else {
     HPXGS_CUDA_CHECK(cudaMemsetAsync(ranges, 0, sizeof(uint2) * L.total_tiles, s));
   }
   const int passes = (L.pair_bits + 7) / 8;
   const uint32_t* ids = (passes & 1) ? pvb : pva;
   uint32_t* work = counters + C_WORK_FWD;
+  unsigned long long* evals = reinterpret_cast<unsigned long long*>(counters + C_NEVAL);
   const int b = cfg->tile_level;
+  prof_begin(HPXGS_STAGE_BLEND_FWD, s);
   if (b == 3) {
     auto fn = k_blend_fwd<64, 1, kBatchFwd>;
-    fn<<<blend_blocks((const void*)fn, 64), 64, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work);
+    fn<<<blend_blocks((const void*)fn, 64), 64, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work, evals);
   } else if (b == 4) {
     auto fn = k_blend_fwd<256, 1, kBatchFwd>;
-    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work);
+    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work, evals);
   } else {
     auto fn = k_blend_fwd<256, 4, kBatchFwd>;
-    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work);
+    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work, evals);
   }
+  note_launches(1);
   HPXGS_LAUNCH_CHECK();
+  prof_end(HPXGS_STAGE_BLEND_FWD, s);
   if (mask_bits)
     HPXGS_CUDA_CHECK(cudaMemcpyAsync(mask_bits, mask, sizeof(uint32_t) * (L.total_pix / 32), cudaMemcpyDeviceToDevice, s));
   if (radii_out && PV > 0)
@@ -1112,6 +1151,7 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   const uint32_t* mask = internal_mask(ws, L);      // written by the forward
   uint32_t* work = counters + C_WORK_BWD;
   const int b = cfg->tile_level;
+  prof_begin(HPXGS_STAGE_BLEND_BWD, s);
   if (b == 3) {
     auto fn = k_blend_bwd<64, 1, kBatchBwd>;
     fn<<<blend_blocks((const void*)fn, 64), 64, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work);
@@ -1122,10 +1162,15 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
     auto fn = k_blend_bwd<256, 4, kBatchBwd>;
     fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work);
   }
+  note_launches(1);
   HPXGS_LAUNCH_CHECK();
+  prof_end(HPXGS_STAGE_BLEND_BWD, s);
+  prof_begin(HPXGS_STAGE_PREPROCESS_BWD, s);
   k_preprocess_bwd<<<(g->P + 127) / 128, 128, 0, s>>>(*vt, *g, at<float>(ws, L.radii), accum, dmeans, dscales, drot,
                                                        dopac, dsh);
+  note_launches(1);
   HPXGS_LAUNCH_CHECK();
+  prof_end(HPXGS_STAGE_PREPROCESS_BWD, s);
   delete vt;
   return HPXGS_OK;
 }

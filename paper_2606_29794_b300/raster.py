@@ -206,7 +206,7 @@ def workspace_view(rast: Rasterizer, state) -> L.WorkspaceView:
 
 class _DevArray:
     def __init__(self, ptr, n, typestr):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (int(ptr), False),
                                          "version": 3, "strides": None}
 
 

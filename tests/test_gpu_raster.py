@@ -102,7 +102,10 @@ def test_staged_records_lists_and_maps(name, make, b):
     assert (lg[ok] == last[ok]).mean() > 0.999
     # end to end (oracle from scratch in FP64)
     full = O.render(sc, _f64view(view), cfg)
-    okf = full.amb[pix] == 0
+    # pixels whose mask decision the two sides take differently sit on the FoV
+    # boundary itself (FP64 margin < 1e-12, checked above): compare the rest
+    okf = (full.amb[pix] == 0) & (m_ref[pix] == 1)
+    assert okf.mean() > 0.995
     assert np.abs(mg - full.image[pix])[okf].max() < MAP_TOL
     # outside the mask: background, T = 1
     outside = np.nonzero(m_gpu == 0)[0]
