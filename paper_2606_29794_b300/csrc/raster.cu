@@ -222,65 +222,92 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __re
   hist[threadIdx.x * G + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Exclusive scan of len u32 entries in place (one block of 1024 threads).
+// Exclusive scan of len u32 entries in place (one block of 1024 threads), in
+// coalesced chunks of 4096 (4 consecutive entries per thread) with a running carry.
 __global__ void __launch_bounds__(1024) k_scan_u32_inplace(uint32_t* __restrict__ a, int len) {
   __shared__ uint32_t wsum[32];
-  const int per = (len + 1023) / 1024;
-  const int lo = threadIdx.x * per, hi = min(len, lo + per);
-  uint32_t s = 0;
-  for (int i = lo; i < hi; ++i) s += a[i];
-  // inclusive warp scan of s
-  uint32_t x = s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int o = 1; o < 32; o <<= 1) { uint32_t y = __shfl_up_sync(0xffffffffu, x, o); if (lane >= o) x += y; }
-  if (lane == 31) wsum[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = wsum[lane];
-    for (int o = 1; o < 32; o <<= 1) { uint32_t y = __shfl_up_sync(0xffffffffu, w, o); if (lane >= o) w += y; }
-    wsum[lane] = w;
+  uint32_t carry = 0;
+  for (int base = 0; base < len; base += 4096) {
+    const int idx = base + 4 * threadIdx.x;
+    uint32_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (idx + k < len) ? a[idx + k] : 0u;
+    const uint32_t t = v[0] + v[1] + v[2] + v[3];
+    uint32_t x = t;
+    for (int o = 1; o < 32; o <<= 1) { const uint32_t y = __shfl_up_sync(0xffffffffu, x, o); if (lane >= o) x += y; }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) { const uint32_t y = __shfl_up_sync(0xffffffffu, w, o); if (lane >= o) w += y; }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = carry + x - t + (warp > 0 ? wsum[warp - 1] : 0u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (idx + k < len) a[idx + k] = run;
+      run += v[k];
+    }
+    carry += wsum[31];
+    __syncthreads();
   }
-  __syncthreads();
-  uint32_t run = x - s + (warp > 0 ? wsum[warp - 1] : 0u);
-  for (int i = lo; i < hi; ++i) { uint32_t v = a[i]; a[i] = run; run += v; }
 }
 
+// Stable scatter of one pass. Each round ranks kRound x 256 elements (striped:
+// element t0 + it * 256 + tid), so two barriers cover 1024 elements: warp-level
+// ranks from __match_any_sync, per-(item, warp, digit) counts in shared memory,
+// then one thread per digit turns its column into running offsets.
+constexpr int kRound = 4;
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                                const uint32_t* n_ptr, uint32_t n_max, int shift, int nbits,
                                                                const uint32_t* __restrict__ hist, int G) {
   constexpr int NW = kSortThreads / 32;
-  __shared__ uint32_t base[256];
-  __shared__ uint32_t wcnt[NW][256];
-  __shared__ uint32_t woff[NW][256];
+  __shared__ uint16_t cnt[kRound][NW][256];      // 16 KB: a warp count is at most 32
+  __shared__ uint32_t off[kRound][NW][256];      // 32 KB
   const uint32_t n = n_ptr ? min(*n_ptr, n_max) : n_max;
   uint32_t begin, end;
   chunk_of(n, G, blockIdx.x, begin, end);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  base[tid] = hist[tid * G + blockIdx.x];
-  for (int w = 0; w < NW; ++w) wcnt[w][tid] = 0;
+  uint32_t run = hist[tid * G + blockIdx.x];          // this thread owns digit `tid`
+  for (int it = 0; it < kRound; ++it)
+    for (int w = 0; w < NW; ++w) cnt[it][w][tid] = 0;
   __syncthreads();
   const uint32_t mask = (1u << nbits) - 1u;
   const uint32_t lt = (1u << lane) - 1u;
-  for (uint32_t t0 = begin; t0 < end; t0 += kSortThreads) {
-    const uint32_t idx = t0 + tid;
-    const bool valid = idx < end;
-    const uint32_t key = valid ? kin[idx] : 0u;
-    const uint32_t digit = valid ? ((key >> shift) & mask) : 0xffffu;
-    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
-    const uint32_t rank = __popc(peers & lt);
-    if (valid && rank == 0) wcnt[warp][digit] = __popc(peers);
-    __syncthreads();
-    {
-      uint32_t run = base[tid];
-      for (int w = 0; w < NW; ++w) { uint32_t c = wcnt[w][tid]; woff[w][tid] = run; run += c; wcnt[w][tid] = 0; }
-      base[tid] = run;
+  for (uint32_t t0 = begin; t0 < end; t0 += kRound * kSortThreads) {
+    uint32_t key[kRound], digit[kRound], rank[kRound];
+#pragma unroll
+    for (int it = 0; it < kRound; ++it) {
+      const uint32_t idx = t0 + it * kSortThreads + tid;
+      const bool valid = idx < end;
+      key[it] = valid ? kin[idx] : 0u;
+      digit[it] = valid ? ((key[it] >> shift) & mask) : 0xffffu;
+      const uint32_t peers = __match_any_sync(0xffffffffu, digit[it]);
+      rank[it] = __popc(peers & lt);
+      if (valid && rank[it] == 0) cnt[it][warp][digit[it]] = (uint16_t)__popc(peers);
     }
     __syncthreads();
-    if (valid) {
-      const uint32_t pos = woff[warp][digit] + rank;
-      kout[pos] = key;
-      vout[pos] = vin[idx];
+#pragma unroll
+    for (int it = 0; it < kRound; ++it)
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t c = cnt[it][w][tid];
+        off[it][w][tid] = run;
+        run += c;
+        cnt[it][w][tid] = 0;
+      }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kRound; ++it) {
+      const uint32_t idx = t0 + it * kSortThreads + tid;
+      if (idx < end) {
+        const uint32_t pos = off[it][warp][digit[it]] + rank[it];
+        kout[pos] = key[it];
+        vout[pos] = vin[idx];
+      }
     }
   }
 }
@@ -326,95 +353,137 @@ __device__ __forceinline__ void ring_phi_frac(int k, int i, int j, int& num, int
   else { num = 2 * j + 2 - ((i - N + 1) & 1); den = 4 * N; }
 }
 
-template <bool EMIT>
-__device__ uint32_t enumerate_tiles(const ViewParams& vp, int kt, float3 g, float rs, const uint32_t* __restrict__ flags,
-                                    uint32_t* __restrict__ out_tile, uint32_t* __restrict__ out_id, uint64_t base,
-                                    uint64_t cap, uint32_t gid) {
-  const double Rm = fmin(kPi, (double)rs + vp.rho + 1e-7);
-  const double cosRm = cos(Rm);
-  const float cosRm32 = (float)cosRm;
-  const float Re = fminf((float)kPi, (float)Rm + 1e-5f);
-  const float cosRe = cosf(Re);
+// One warp per Gaussian: the rings of the disc are set up in parallel (one ring
+// per lane), their candidate intervals are flattened with a warp scan, and the
+// candidates are then evaluated 32 at a time, so a Gaussian that covers
+// thousands of tiles does not stall its warp-mates. Members are compacted with
+// a ballot, which keeps the emission order deterministic.
+struct DiscQ {
+  float zc, sc, omc, zmin, zmax, cosRe, cosRm32;
+  double cosRm;
+  int ilo, ihi;
+};
+
+__device__ __forceinline__ void disc_setup(const ViewParams& vp, int kt, float3 g, float rs, int lane, DiscQ& Q) {
+  double cosRm = 0.0;
+  if (lane == 0) cosRm = cos(fmin(kPi, (double)rs + vp.rho + 1e-7));   // FP64 threshold of the membership test
+  Q.cosRm = __shfl_sync(0xffffffffu, cosRm, 0);
+  Q.cosRm32 = (float)Q.cosRm;
+  const float Re = fminf((float)kPi, rs + (float)vp.rho + 1e-7f + 1e-5f);   // enumeration radius with slack
+  Q.cosRe = cosf(Re);
   const int Nt = 1 << kt;
-  const float zc = g.z;
-  const float sc = sqrtf(fmaxf(0.f, g.x * g.x + g.y * g.y));
-  const float phic = atan2f(zc, sc);
-  const float omc = atan2f(g.y, g.x);
+  Q.zc = g.z;
+  Q.sc = sqrtf(fmaxf(0.f, g.x * g.x + g.y * g.y));
+  const float phic = atan2f(Q.zc, Q.sc);
+  Q.omc = atan2f(g.y, g.x);
   const float phimin = fmaxf(-0.5f * (float)kPi, phic - Re), phimax = fminf(0.5f * (float)kPi, phic + Re);
-  const float zmin = sinf(phimin) - 1e-6f, zmax = sinf(phimax) + 1e-6f;
-  const int ilo = max(1, (int)floorf(ring_of_z(fminf(zmax, 1.f), Nt)) - 1);
-  const int ihi = min(4 * Nt - 1, (int)ceilf(ring_of_z(fmaxf(zmin, -1.f), Nt)) + 1);
-  const double3 g64 = make_double3(g.x, g.y, g.z);
-  uint32_t cnt = 0;
-  for (int i = ilo; i <= ihi; ++i) {
-    RingF rg = ring_f32(kt, i);
-    if (rg.z < zmin || rg.z > zmax) continue;
-    const float delta = sc * rg.sth;
-    int jlo = 0, jhi = -1;
-    bool full = false;
-    if (delta < 1e-6f) {
-      if (zc * rg.z >= cosRe - 1e-5f) full = true; else continue;
-    } else {
-      const float cw = (cosRe - zc * rg.z) / delta;    // Eq. ring_phi_range
-      if (cw <= -1.f) full = true;
-      else if (cw <= 1.f) {
-        const float dw = acosf(fminf(1.f, fmaxf(-1.f, cw)));
-        const float sc2 = rg.npix / (2.0f * (float)kPi);
-        jlo = (int)floorf((omc - dw - rg.phi0) * sc2) - 1;
-        jhi = (int)ceilf((omc + dw - rg.phi0) * sc2) + 1;
-        if (jhi - jlo + 1 >= rg.npix) full = true;
-      } else continue;
-    }
-    if (full) { jlo = 0; jhi = rg.npix - 1; }
-    for (int j = jlo; j <= jhi; ++j) {
-      int jj = j % rg.npix; if (jj < 0) jj += rg.npix;
-      int num, den;
-      ring_phi_frac(kt, i, jj, num, den);
-      float sp, cp;
-      sincospif((float)num / (float)den, &sp, &cp);
-      const float dot = rg.sth * (cp * g.x + sp * g.y) + rg.z * g.z;
-      bool member;
-      if (dot > cosRm32 + 1e-5f) member = true;
-      else if (dot < cosRm32 - 1e-5f) member = false;
-      else {
-        const double3 c = ringpix_vec_f64(kt, i, jj);
-        member = c.x * g64.x + c.y * g64.y + c.z * g64.z >= cosRm;
-      }
-      if (!member) continue;
-      const FaceXY fx = ring_to_fxy(kt, i, jj);
-      const uint32_t tile = fxy_to_nest(kt, fx.f, fx.x, fx.y);
-      const uint32_t gt = (uint32_t)vp.tile_base + tile;
-      if (!(flags[gt] & 1u)) continue;
-      if (EMIT) {
-        const uint64_t pos = base + cnt;
-        if (pos < cap) { out_tile[pos] = gt; out_id[pos] = gid; }
-      }
-      ++cnt;
-    }
-  }
-  return cnt;
+  Q.zmin = sinf(phimin) - 1e-6f;
+  Q.zmax = sinf(phimax) + 1e-6f;
+  Q.ilo = max(1, (int)floorf(ring_of_z(fminf(Q.zmax, 1.f), Nt)) - 1);
+  Q.ihi = min(4 * Nt - 1, (int)ceilf(ring_of_z(fmaxf(Q.zmin, -1.f), Nt)) + 1);
+}
+
+// Candidate positions [jlo, jlo + n) of ring i (Algorithm 3 with Eq. ring_phi_range).
+__device__ __forceinline__ int ring_interval(int kt, int i, const DiscQ& Q, RingF& rg, int& jlo) {
+  rg = ring_f32(kt, i);
+  jlo = 0;
+  if (rg.z < Q.zmin || rg.z > Q.zmax) return 0;
+  const float delta = Q.sc * rg.sth;
+  if (delta < 1e-6f) return (Q.zc * rg.z >= Q.cosRe - 1e-5f) ? rg.npix : 0;
+  const float cw = (Q.cosRe - Q.zc * rg.z) / delta;
+  if (cw <= -1.f) return rg.npix;
+  if (cw > 1.f) return 0;
+  const float dw = acosf(fminf(1.f, fmaxf(-1.f, cw)));
+  const float sc2 = rg.npix / (2.0f * (float)kPi);
+  // floor/ceil already take in every centre of the (slack-widened) interval
+  jlo = (int)floorf((Q.omc - dw - rg.phi0) * sc2);
+  const int jhi = (int)ceilf((Q.omc + dw - rg.phi0) * sc2);
+  if (jhi - jlo + 1 >= rg.npix) { jlo = 0; return rg.npix; }
+  return jhi - jlo + 1;
 }
 
 template <bool EMIT>
-__global__ void __launch_bounds__(128) k_tiles(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
+__global__ void __launch_bounds__(256) k_tiles(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
                                                const float* __restrict__ radii, const uint32_t* __restrict__ skeys,
                                                const uint32_t* __restrict__ svals, const uint32_t* __restrict__ flags,
                                                uint32_t* __restrict__ counts, const uint64_t* __restrict__ offsets,
                                                uint32_t* __restrict__ out_tile, uint32_t* __restrict__ out_id, uint64_t cap,
                                                int32_t* status) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
   const int64_t PV = (int64_t)vt.P * vt.nviews;
-  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j >= PV) return;
-  if (skeys[j] == 0xffffffffu) { if (!EMIT) counts[j] = 0; return; }
-  const uint32_t gid = svals[j];
-  const int v = (int)(gid / (uint32_t)vt.P);
-  const ViewParams& vp = vt.v[v];
-  const float4 r0 = rec[4 * (int64_t)gid];
-  const float3 g = make_float3(r0.x, r0.y, r0.z);
-  const uint64_t base = EMIT ? offsets[j] : 0;
-  const uint32_t n = enumerate_tiles<EMIT>(vp, vp.k - vt.b, g, radii[gid], flags, out_tile, out_id, base, cap, gid);
-  if (!EMIT) counts[j] = n;
-  else if (base + n > cap && status) atomicOr(status, HPXGS_F_CAPACITY);
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t j = blockIdx.x * wpb + (threadIdx.x >> 5); j < PV; j += (int64_t)gridDim.x * wpb) {
+    if (skeys[j] == 0xffffffffu) { if (!EMIT && lane == 0) counts[j] = 0; continue; }
+    const uint32_t gid = svals[j];
+    const int v = (int)(gid / (uint32_t)vt.P);
+    const ViewParams& vp = vt.v[v];
+    const int kt = vp.k - vt.b;
+    const float4 r0 = rec[4 * (int64_t)gid];
+    const float3 g = make_float3(r0.x, r0.y, r0.z);
+    DiscQ Q;
+    disc_setup(vp, kt, g, radii[gid], lane, Q);
+    const double3 g64 = make_double3(g.x, g.y, g.z);
+    const uint64_t base = EMIT ? offsets[j] : 0;
+    uint32_t cnt = 0;
+    for (int r0i = Q.ilo; r0i <= Q.ihi; r0i += 32) {
+      const int i = r0i + lane;
+      RingF rg; rg.z = 0.f; rg.sth = 0.f; rg.phi0 = 0.f; rg.npix = 1;
+      int jlo = 0, nc = 0;
+      if (i <= Q.ihi) nc = ring_interval(kt, i, Q, rg, jlo);
+      int inc = nc;
+      for (int o = 1; o < 32; o <<= 1) { const int y = __shfl_up_sync(FULL, inc, o); if (lane >= o) inc += y; }
+      const int total = __shfl_sync(FULL, inc, 31);
+      const int exc = inc - nc;
+      for (int q0 = 0; q0 < total; q0 += 32) {
+        const int q = q0 + lane;
+        // owner ring of candidate q: the number of leading lanes whose inclusive count is <= q
+        int pos = 0;
+        for (int step = 16; step > 0; step >>= 1) {
+          const int val = __shfl_sync(FULL, inc, pos + step - 1);
+          if (val <= q) pos += step;
+        }
+        const int o_exc = __shfl_sync(FULL, exc, pos);
+        const int o_jlo = __shfl_sync(FULL, jlo, pos);
+        const float o_z = __shfl_sync(FULL, rg.z, pos);
+        const float o_sth = __shfl_sync(FULL, rg.sth, pos);
+        const int o_np = __shfl_sync(FULL, rg.npix, pos);
+        bool member = false;
+        uint32_t gt = 0;
+        if (q < total) {
+          const int ii = r0i + pos;
+          int jj = (o_jlo + (q - o_exc)) % o_np;
+          if (jj < 0) jj += o_np;
+          int num, den;
+          ring_phi_frac(kt, ii, jj, num, den);
+          float sp, cp;
+          sincospif((float)num / (float)den, &sp, &cp);
+          const float dot = o_sth * (cp * g.x + sp * g.y) + o_z * g.z;
+          if (dot > Q.cosRm32 + 1e-5f) member = true;
+          else if (dot >= Q.cosRm32 - 1e-5f) {
+            const double3 c = ringpix_vec_f64(kt, ii, jj);
+            member = c.x * g64.x + c.y * g64.y + c.z * g64.z >= Q.cosRm;
+          }
+          if (member) {
+            const FaceXY fx = ring_to_fxy(kt, ii, jj);
+            gt = (uint32_t)vp.tile_base + fxy_to_nest(kt, fx.f, fx.x, fx.y);
+            member = flags[gt] & 1u;
+          }
+        }
+        const uint32_t bal = __ballot_sync(FULL, member);
+        if (EMIT && member) {
+          const uint64_t p = base + cnt + __popc(bal & lt);
+          if (p < cap) { out_tile[p] = gt; out_id[p] = gid; }
+        }
+        cnt += __popc(bal);
+      }
+    }
+    if (lane == 0) {
+      if (!EMIT) counts[j] = cnt;
+      else if (base + cnt > cap && status) atomicOr(status, HPXGS_F_CAPACITY);
+    }
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -720,7 +789,7 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
           const float G = __expf(-0.5f * P.m);
           const float og = r0.w * G;
           const float a = fminf(vt.alpha_max, og);
-          const float inv1ma = 1.f / (1.f - a);
+          const float inv1ma = __fdividef(1.f, 1.f - a);
           const float Tj = T[q] * inv1ma;
           const float wj = Tj * a;
           float dLda = 0.f;
@@ -968,8 +1037,8 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   uint64_t* offsets = at<uint64_t>(ws, L.offsets);
   uint64_t* part = at<uint64_t>(ws, L.scan_part);
   prof_begin(HPXGS_STAGE_TILE_COUNT, s);
-  k_tiles<false><<<(unsigned)((PV + 127) / 128), 128, 0, s>>>(*vt, rec, radii, sk, sv, flags, counts, nullptr, nullptr,
-                                                             nullptr, 0, status);
+  const unsigned tblocks = (unsigned)std::min<int64_t>((PV + 7) / 8, 32LL * num_sms());
+  k_tiles<false><<<tblocks, 256, 0, s>>>(*vt, rec, radii, sk, sv, flags, counts, nullptr, nullptr, nullptr, 0, status);
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_TILE_COUNT, s);
@@ -1071,8 +1140,9 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
     const uint32_t* sk = which ? at<uint32_t>(ws, L.key_b) : at<uint32_t>(ws, L.key_a);
     const uint32_t* sv = which ? at<uint32_t>(ws, L.val_b) : at<uint32_t>(ws, L.val_a);
     prof_begin(HPXGS_STAGE_TILE_EMIT, s);
-    k_tiles<true><<<(unsigned)((PV + 127) / 128), 128, 0, s>>>(*vt, rec, at<float>(ws, L.radii), sk, sv, flags, nullptr,
-                                                              at<uint64_t>(ws, L.offsets), pka, pva, (uint64_t)cap, status);
+    const unsigned tblocks = (unsigned)std::min<int64_t>((PV + 7) / 8, 32LL * num_sms());
+    k_tiles<true><<<tblocks, 256, 0, s>>>(*vt, rec, at<float>(ws, L.radii), sk, sv, flags, nullptr,
+                                          at<uint64_t>(ws, L.offsets), pka, pva, (uint64_t)cap, status);
     note_launches(1);
     HPXGS_LAUNCH_CHECK();
     prof_end(HPXGS_STAGE_TILE_EMIT, s);
@@ -1152,12 +1222,13 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   uint32_t* work = counters + C_WORK_BWD;
   const int b = cfg->tile_level;
   prof_begin(HPXGS_STAGE_BLEND_BWD, s);
+  // several pixels per thread: the per-entry warp reduction then covers 32 * PPT pixels
   if (b == 3) {
-    auto fn = k_blend_bwd<64, 1, kBatchBwd>;
-    fn<<<blend_blocks((const void*)fn, 64), 64, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work);
+    auto fn = k_blend_bwd<32, 2, kBatchBwd>;
+    fn<<<blend_blocks((const void*)fn, 32), 32, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work);
   } else if (b == 4) {
-    auto fn = k_blend_bwd<256, 1, kBatchBwd>;
-    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work);
+    auto fn = k_blend_bwd<64, 4, kBatchBwd>;
+    fn<<<blend_blocks((const void*)fn, 64), 64, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work);
   } else {
     auto fn = k_blend_bwd<256, 4, kBatchBwd>;
     fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work);
