@@ -179,23 +179,26 @@ __host__ __device__ __forceinline__ int floordiv(int a, int b) {   // b > 0
 __host__ __device__ __forceinline__ FaceXY ring_to_fxy(int k, int i, int j) {
   const int N = 1 << k;
   FaceXY r;
-  if (i < N) {
-    r.f = j / i; int p = j - r.f * i;
-    r.x = N - i + p; r.y = N - 1 - p;
+  if (i < N) {                                   // j < 4i: face = number of whole multiples of i
+    const int fq = (j >= i) + (j >= 2 * i) + (j >= 3 * i);
+    const int p = j - fq * i;
+    r.f = fq; r.x = N - i + p; r.y = N - 1 - p;
   } else if (i > 3 * N) {
-    int ii = 4 * N - i;
-    int fq = j / ii; int p = j - fq * ii;
+    const int ii = 4 * N - i;
+    const int fq = (j >= ii) + (j >= 2 * ii) + (j >= 3 * ii);
+    const int p = j - fq * ii;
     r.f = 8 + fq; r.x = p; r.y = ii - 1 - p;
   } else {
-    int s = (i - N + 1) & 1;
-    int a = 2 * j + 2 - s;
-    int A = floordiv(a + 3 * N - i, 2 * N), B = floordiv(3 * N - i - a, 2 * N);
+    const int s = (i - N + 1) & 1;
+    const int a = 2 * j + 2 - s;
+    // floor division by 2N = 2^(k+1): arithmetic shift
+    const int A = (a + 3 * N - i) >> (k + 1), B = (3 * N - i - a) >> (k + 1);
     int Xc, Yc;
     if (A + B >= 1) { r.f = (A - 1) & 3; Xc = 2 * A - 1; Yc = 1; }
     else if (A + B == 0) { r.f = 4 + (A & 3); Xc = 2 * A; Yc = 0; }
     else { r.f = 8 + (A & 3); Xc = 2 * A + 1; Yc = -1; }
-    r.x = (a - Xc * N + 3 * N - i - Yc * N - 1) / 2;
-    r.y = ((2 * N - i) - Yc * N - a + Xc * N + N - 1) / 2;
+    r.x = (a - Xc * N + 3 * N - i - Yc * N - 1) >> 1;
+    r.y = ((2 * N - i) - Yc * N - a + Xc * N + N - 1) >> 1;
   }
   return r;
 }

@@ -152,7 +152,7 @@ __device__ __forceinline__ void geo_compute(const ViewParams& vp, float near_pla
 __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ ViewTable vt, hpxgs_gaussians gs,
                                                     float4* __restrict__ rec, float* __restrict__ radii,
                                                     float* __restrict__ depth, uint32_t* __restrict__ keys,
-                                                    uint32_t* __restrict__ vals) {
+                                                    uint32_t* __restrict__ vals, float* __restrict__ chord2) {
   const int64_t PV = (int64_t)vt.P * vt.nviews;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= PV) return;
@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ View
   if (!G.valid) {
     keys[gid] = 0xffffffffu;
     radii[gid] = 0.f;
+    chord2[gid] = -1.f;
     rec[4 * gid + 0] = make_float4(0.f, 0.f, 1.f, 0.f);
     rec[4 * gid + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
     rec[4 * gid + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -192,6 +193,10 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ View
   rec[4 * gid + 3] = make_float4(col[0], col[1], col[2], G.qc);
   radii[gid] = G.rs;
   keys[gid] = __float_as_uint(G.r);     // r > 0: the bit pattern orders like the value
+  // m <= cutoff implies an angle <= r_s from the centre, i.e. |p - g|^2 <= 4 sin^2(r_s / 2):
+  // a pixel farther than that chord gets alpha = 0 without evaluating m (bound widened by 1e-4)
+  const float hs = sinf(0.5f * fminf(G.rs, (float)kPi));
+  chord2[gid] = 4.f * hs * hs * (1.f + 1e-4f) + 1e-12f;
 }
 
 // ----------------------------------------------------------------------------
@@ -360,15 +365,14 @@ __device__ __forceinline__ void ring_phi_frac(int k, int i, int j, int& num, int
 // a ballot, which keeps the emission order deterministic.
 struct DiscQ {
   float zc, sc, omc, zmin, zmax, cosRe, cosRm32;
-  double cosRm;
   int ilo, ihi;
 };
 
 __device__ __forceinline__ void disc_setup(const ViewParams& vp, int kt, float3 g, float rs, int lane, DiscQ& Q) {
-  double cosRm = 0.0;
-  if (lane == 0) cosRm = cos(fmin(kPi, (double)rs + vp.rho + 1e-7));   // FP64 threshold of the membership test
-  Q.cosRm = __shfl_sync(0xffffffffu, cosRm, 0);
-  Q.cosRm32 = (float)Q.cosRm;
+  (void)lane;
+  // FP32 estimate of the membership threshold; the FP64 value is formed only for
+  // candidates within 1e-5 of it
+  Q.cosRm32 = cosf(fminf((float)kPi, rs + (float)vp.rho + 1e-7f));
   const float Re = fminf((float)kPi, rs + (float)vp.rho + 1e-7f + 1e-5f);   // enumeration radius with slack
   Q.cosRe = cosf(Re);
   const int Nt = 1 << kt;
@@ -384,8 +388,13 @@ __device__ __forceinline__ void disc_setup(const ViewParams& vp, int kt, float3 
 }
 
 // Candidate positions [jlo, jlo + n) of ring i (Algorithm 3 with Eq. ring_phi_range).
-__device__ __forceinline__ int ring_interval(int kt, int i, const DiscQ& Q, RingF& rg, int& jlo) {
+// Also returns the ring's longitude as (j + off) * inv in units of pi.
+__device__ __forceinline__ int ring_interval(int kt, int i, const DiscQ& Q, RingF& rg, int& jlo, float& off, float& inv) {
   rg = ring_f32(kt, i);
+  const int N = 1 << kt;
+  if (i < N) { off = 0.5f; inv = 1.f / (float)(2 * i); }
+  else if (i > 3 * N) { off = 0.5f; inv = 1.f / (float)(2 * (4 * N - i)); }
+  else { off = 1.f - 0.5f * (float)((i - N + 1) & 1); inv = 1.f / (float)(2 * N); }
   jlo = 0;
   if (rg.z < Q.zmin || rg.z > Q.zmax) return 0;
   const float delta = Q.sc * rg.sth;
@@ -403,7 +412,7 @@ __device__ __forceinline__ int ring_interval(int kt, int i, const DiscQ& Q, Ring
 }
 
 template <bool EMIT>
-__global__ void __launch_bounds__(256) k_tiles(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
+__global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
                                                const float* __restrict__ radii, const uint32_t* __restrict__ skeys,
                                                const uint32_t* __restrict__ svals, const uint32_t* __restrict__ flags,
                                                uint32_t* __restrict__ counts, const uint64_t* __restrict__ offsets,
@@ -424,14 +433,17 @@ __global__ void __launch_bounds__(256) k_tiles(const __grid_constant__ ViewTable
     const float3 g = make_float3(r0.x, r0.y, r0.z);
     DiscQ Q;
     disc_setup(vp, kt, g, radii[gid], lane, Q);
+
     const double3 g64 = make_double3(g.x, g.y, g.z);
+    const float rs = radii[gid];
     const uint64_t base = EMIT ? offsets[j] : 0;
     uint32_t cnt = 0;
     for (int r0i = Q.ilo; r0i <= Q.ihi; r0i += 32) {
       const int i = r0i + lane;
       RingF rg; rg.z = 0.f; rg.sth = 0.f; rg.phi0 = 0.f; rg.npix = 1;
       int jlo = 0, nc = 0;
-      if (i <= Q.ihi) nc = ring_interval(kt, i, Q, rg, jlo);
+      float off = 0.f, inv = 0.f;
+      if (i <= Q.ihi) nc = ring_interval(kt, i, Q, rg, jlo, off, inv);
       int inc = nc;
       for (int o = 1; o < 32; o <<= 1) { const int y = __shfl_up_sync(FULL, inc, o); if (lane >= o) inc += y; }
       const int total = __shfl_sync(FULL, inc, 31);
@@ -449,21 +461,24 @@ __global__ void __launch_bounds__(256) k_tiles(const __grid_constant__ ViewTable
         const float o_z = __shfl_sync(FULL, rg.z, pos);
         const float o_sth = __shfl_sync(FULL, rg.sth, pos);
         const int o_np = __shfl_sync(FULL, rg.npix, pos);
+        const float o_off = __shfl_sync(FULL, off, pos);
+        const float o_inv = __shfl_sync(FULL, inv, pos);
         bool member = false;
         uint32_t gt = 0;
         if (q < total) {
           const int ii = r0i + pos;
-          int jj = (o_jlo + (q - o_exc)) % o_np;
+          int jj = o_jlo + (q - o_exc);          // within (-np, 2 np)
           if (jj < 0) jj += o_np;
-          int num, den;
-          ring_phi_frac(kt, ii, jj, num, den);
+          if (jj >= o_np) jj -= o_np;
           float sp, cp;
-          sincospif((float)num / (float)den, &sp, &cp);
+          sincospif(((float)jj + o_off) * o_inv, &sp, &cp);
           const float dot = o_sth * (cp * g.x + sp * g.y) + o_z * g.z;
           if (dot > Q.cosRm32 + 1e-5f) member = true;
           else if (dot >= Q.cosRm32 - 1e-5f) {
+            // the exact test: both sides in FP64, the threshold as the membership rule states it
+            const double cosRm = cos(fmin(kPi, (double)rs + vp.rho + 1e-7));
             const double3 c = ringpix_vec_f64(kt, ii, jj);
-            member = c.x * g64.x + c.y * g64.y + c.z * g64.z >= Q.cosRm;
+            member = c.x * g64.x + c.y * g64.y + c.z * g64.z >= cosRm;
           }
           if (member) {
             const FaceXY fx = ring_to_fxy(kt, ii, jj);
@@ -574,12 +589,14 @@ struct Pix {
   bool series;
 };
 
-__device__ __forceinline__ void pixel_weight(const float3 p, const float4 r0, const float4 r1, const float4 r2,
-                                             const float4 r3, Pix& P) {
+// Returns false (alpha = 0) when the pixel lies beyond the Gaussian's chord bound.
+__device__ __forceinline__ bool pixel_weight(const float3 p, const float4 r0, const float4 r1, const float4 r2,
+                                             const float4 r3, const float c2max, Pix& P) {
   const float dx = p.x - r0.x, dy = p.y - r0.y, dz = p.z - r0.z;
+  P.n2 = dx * dx + dy * dy + dz * dz;
+  if (P.n2 > c2max) return false;
   P.u1 = dx * r1.x + dy * r1.y + dz * r1.z;
   P.u2 = dx * r2.x + dy * r2.y + dz * r2.z;
-  P.n2 = dx * dx + dy * dy + dz * dz;
   P.s2 = P.u1 * P.u1 + P.u2 * P.u2;
   P.q = P.u1 * (r1.w * P.u1 + 2.f * r2.w * P.u2) + r3.w * P.u2 * P.u2;
   P.series = P.n2 < kSeriesN2;
@@ -589,12 +606,13 @@ __device__ __forceinline__ void pixel_weight(const float3 p, const float4 r0, co
     P.m = P.q * P.ser;
   } else {
     const float c = 1.f - 0.5f * P.n2;
-    if (P.s2 < 1e-24f) { P.ser = 0.f; P.m = (c < 0.f) ? 3.0e38f : 0.f; return; }
+    if (P.s2 < 1e-24f) { P.ser = 0.f; P.m = (c < 0.f) ? 3.0e38f : 0.f; return true; }
     const float s = sqrtf(P.s2);
     const float ratio = atan2f(s, c) / s;
     P.ser = ratio * ratio;
     P.m = P.q * P.ser;
   }
+  return true;
 }
 
 // ----------------------------------------------------------------------------
@@ -614,8 +632,9 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
                                                   const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
                                                   float* __restrict__ maps, float* __restrict__ Tout,
                                                   uint32_t* __restrict__ lastout, uint32_t* work,
-                                                  unsigned long long* __restrict__ evals) {
+                                                  unsigned long long* __restrict__ evals, const float* __restrict__ chord2) {
   __shared__ float4 s_rec[BATCH][4];
+  __shared__ float s_c2[BATCH];
   __shared__ int s_tile;
   const int tid = threadIdx.x;
   const int b = vt.b;
@@ -652,8 +671,10 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
       const int n = (int)min((uint32_t)BATCH, rg.y - bs);
       __syncthreads();
       for (int e = tid; e < n; e += NT) {
-        const float4* src = rec + 4 * (int64_t)ids[bs + e];
+        const uint32_t id = ids[bs + e];
+        const float4* src = rec + 4 * (int64_t)id;
         s_rec[e][0] = src[0]; s_rec[e][1] = src[1]; s_rec[e][2] = src[2]; s_rec[e][3] = src[3];
+        s_c2[e] = chord2[id];
       }
       __syncthreads();
 #pragma unroll
@@ -662,7 +683,7 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
         for (int e = 0; e < n; ++e) {
           const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
           Pix P;
-          pixel_weight(pv[q], r0, r1, r2, r3, P);
+          if (!pixel_weight(pv[q], r0, r1, r2, r3, s_c2[e], P)) continue;
           if (P.m <= vt.cutoff) {
             ++ncontrib;
             const float a = fminf(vt.alpha_max, r0.w * __expf(-0.5f * P.m));
@@ -720,9 +741,10 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
                                                   const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
                                                   const float* __restrict__ dmaps, const float* __restrict__ Tin,
                                                   const uint32_t* __restrict__ lastin, float* __restrict__ accum,
-                                                  uint32_t* work) {
+                                                  uint32_t* work, const float* __restrict__ chord2) {
   constexpr int NW = NT / 32;
   __shared__ float4 s_rec[BATCH][4];
+  __shared__ float s_c2[BATCH];
   __shared__ uint32_t s_id[BATCH];
   __shared__ float s_part[BATCH][NW][HPXGS_NACC];
   __shared__ int s_tile;
@@ -771,6 +793,7 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
         s_id[e] = id;
         const float4* src = rec + 4 * (int64_t)id;
         s_rec[e][0] = src[0]; s_rec[e][1] = src[1]; s_rec[e][2] = src[2]; s_rec[e][3] = src[3];
+        s_c2[e] = chord2[id];
       }
       __syncthreads();
       for (int e = n - 1; e >= 0; --e) {
@@ -784,7 +807,7 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
         for (int q = 0; q < PPT; ++q) {
           if (j >= lastp[q]) continue;
           Pix P;
-          pixel_weight(pv[q], r0, r1, r2, r3, P);
+          if (!pixel_weight(pv[q], r0, r1, r2, r3, s_c2[e], P)) continue;
           if (!(P.m <= vt.cutoff)) continue;
           const float G = __expf(-0.5f * P.m);
           const float og = r0.w * G;
@@ -1023,7 +1046,7 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   uint32_t* ka = at<uint32_t>(ws, L.key_a); uint32_t* kb = at<uint32_t>(ws, L.key_b);
   uint32_t* va = at<uint32_t>(ws, L.val_a); uint32_t* vb = at<uint32_t>(ws, L.val_b);
   prof_begin(HPXGS_STAGE_PREPROCESS, s);
-  k_preprocess<<<(unsigned)((PV + 255) / 256), 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va);
+  k_preprocess<<<(unsigned)((PV + 255) / 256), 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va, at<float>(ws, L.chord));
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_PREPROCESS, s);
@@ -1171,13 +1194,13 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
   prof_begin(HPXGS_STAGE_BLEND_FWD, s);
   if (b == 3) {
     auto fn = k_blend_fwd<64, 1, kBatchFwd>;
-    fn<<<blend_blocks((const void*)fn, 64), 64, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work, evals);
+    fn<<<blend_blocks((const void*)fn, 64), 64, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work, evals, at<float>(ws, L.chord));
   } else if (b == 4) {
     auto fn = k_blend_fwd<256, 1, kBatchFwd>;
-    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work, evals);
+    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work, evals, at<float>(ws, L.chord));
   } else {
     auto fn = k_blend_fwd<256, 4, kBatchFwd>;
-    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work, evals);
+    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work, evals, at<float>(ws, L.chord));
   }
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
@@ -1225,13 +1248,13 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   // several pixels per thread: the per-entry warp reduction then covers 32 * PPT pixels
   if (b == 3) {
     auto fn = k_blend_bwd<32, 2, kBatchBwd>;
-    fn<<<blend_blocks((const void*)fn, 32), 32, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work);
+    fn<<<blend_blocks((const void*)fn, 32), 32, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, at<float>(ws, L.chord));
   } else if (b == 4) {
     auto fn = k_blend_bwd<64, 4, kBatchBwd>;
-    fn<<<blend_blocks((const void*)fn, 64), 64, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work);
+    fn<<<blend_blocks((const void*)fn, 64), 64, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, at<float>(ws, L.chord));
   } else {
     auto fn = k_blend_bwd<256, 4, kBatchBwd>;
-    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work);
+    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, at<float>(ws, L.chord));
   }
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
