@@ -51,7 +51,7 @@ constexpr int kRecFloat4 = 4;
 
 // Workspace layout of hpxgs_forward / hpxgs_backward. All offsets 256-aligned.
 struct Layout {
-  size_t tile_flags, records, radii, chord, depth, key_a, key_b, val_a, val_b, counts, offsets, scan_part,
+  size_t tile_flags, records, radii, chord, stage, depth, key_a, key_b, val_a, val_b, counts, offsets, scan_part,
          pair_key_a, pair_key_b, pair_val_a, pair_val_b, hist, ranges, counters, accum, tile_order,
          total;
   int64_t P, PV, cap, total_tiles, total_pix;
@@ -66,7 +66,7 @@ constexpr int kMaxSortBlocks = 1024;
 
 // counters block (u32 each)
 // (u64 counters live at u32 index 8 (n_eval) and 10 (n_contrib), 8-byte aligned)
-enum Counter { C_NPAIRS = 0, C_WORK_FWD = 1, C_WORK_BWD = 2, C_NSORT = 3, C_NPAIRS_HI = 4, C_NEVAL = 8, C_NCONTRIB = 10,
+enum Counter { C_NPAIRS = 0, C_WORK_FWD = 1, C_WORK_BWD = 2, C_NSORT = 3, C_NPAIRS_HI = 4, C_STAGE = 5, C_NEVAL = 8, C_NCONTRIB = 10,
                C_COUNT = 16 };
 
 // instrumentation (geometry.cu)

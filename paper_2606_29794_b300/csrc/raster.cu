@@ -411,21 +411,44 @@ __device__ __forceinline__ int ring_interval(int kt, int i, const DiscQ& Q, Ring
   return jhi - jlo + 1;
 }
 
+// Count pass (EMIT = false): counts members and stages up to kStage member tiles
+// per Gaussian in shared memory, then copies them to a scratch list at a slot
+// taken from an atomic counter (stage[j] = slot, or ~0 when the Gaussian has more
+// members or the scratch is full). Emit pass (EMIT = true): staged Gaussians copy
+// their list to the final offset; the others run the query again and write directly.
+constexpr int kStage = 256;
+
 template <bool EMIT>
 __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
                                                const float* __restrict__ radii, const uint32_t* __restrict__ skeys,
                                                const uint32_t* __restrict__ svals, const uint32_t* __restrict__ flags,
                                                uint32_t* __restrict__ counts, const uint64_t* __restrict__ offsets,
                                                uint32_t* __restrict__ out_tile, uint32_t* __restrict__ out_id, uint64_t cap,
-                                               int32_t* status) {
+                                               int32_t* status, uint32_t* __restrict__ stage,
+                                               uint32_t* __restrict__ scratch, uint32_t* scratch_top) {
+  __shared__ uint32_t s_stage[8][kStage];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   const int64_t PV = (int64_t)vt.P * vt.nviews;
   const int64_t wpb = blockDim.x >> 5;
   for (int64_t j = blockIdx.x * wpb + (threadIdx.x >> 5); j < PV; j += (int64_t)gridDim.x * wpb) {
     if (skeys[j] == 0xffffffffu) { if (!EMIT && lane == 0) counts[j] = 0; continue; }
     const uint32_t gid = svals[j];
+    if (EMIT) {
+      const uint32_t slot = stage[j];
+      if (slot != 0xffffffffu) {                     // staged by the count pass: copy
+        const uint32_t n = counts[j];
+        const uint64_t base = offsets[j];
+        for (uint32_t e = lane; e < n; e += 32) {
+          const uint64_t p = base + e;
+          if (p < cap) { out_tile[p] = scratch[slot + e]; out_id[p] = gid; }
+        }
+        if (lane == 0 && base + n > cap && status) atomicOr(status, HPXGS_F_CAPACITY);
+        continue;
+      }
+    }
     const int v = (int)(gid / (uint32_t)vt.P);
     const ViewParams& vp = vt.v[v];
     const int kt = vp.k - vt.b;
@@ -487,16 +510,32 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
           }
         }
         const uint32_t bal = __ballot_sync(FULL, member);
-        if (EMIT && member) {
-          const uint64_t p = base + cnt + __popc(bal & lt);
-          if (p < cap) { out_tile[p] = gt; out_id[p] = gid; }
+        if (member) {
+          const uint32_t r = cnt + __popc(bal & lt);
+          if (EMIT) {
+            const uint64_t p = base + r;
+            if (p < cap) { out_tile[p] = gt; out_id[p] = gid; }
+          } else if (r < kStage) {
+            s_stage[wib][r] = gt;
+          }
         }
         cnt += __popc(bal);
       }
     }
-    if (lane == 0) {
-      if (!EMIT) counts[j] = cnt;
-      else if (base + cnt > cap && status) atomicOr(status, HPXGS_F_CAPACITY);
+    if (EMIT) {
+      if (lane == 0 && base + cnt > cap && status) atomicOr(status, HPXGS_F_CAPACITY);
+    } else {
+      uint32_t slot = 0xffffffffu;
+      if (cnt <= kStage && cnt > 0) {
+        if (lane == 0) slot = atomicAdd(scratch_top, cnt);
+        slot = __shfl_sync(FULL, slot, 0);
+        if ((uint64_t)slot + cnt > cap) slot = 0xffffffffu;     // scratch full: emit runs the query again
+        else for (uint32_t e = lane; e < cnt; e += 32) scratch[slot + e] = s_stage[wib][e];
+      } else if (cnt == 0) {
+        slot = 0u;
+      }
+      __syncwarp();
+      if (lane == 0) { counts[j] = cnt; stage[j] = slot; }
     }
   }
 }
@@ -1061,7 +1100,10 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   uint64_t* part = at<uint64_t>(ws, L.scan_part);
   prof_begin(HPXGS_STAGE_TILE_COUNT, s);
   const unsigned tblocks = (unsigned)std::min<int64_t>((PV + 7) / 8, 32LL * num_sms());
-  k_tiles<false><<<tblocks, 256, 0, s>>>(*vt, rec, radii, sk, sv, flags, counts, nullptr, nullptr, nullptr, 0, status);
+  // the count pass stages member lists in the second pair buffers (unused until the pair sort)
+  k_tiles<false><<<tblocks, 256, 0, s>>>(*vt, rec, radii, sk, sv, flags, counts, nullptr, nullptr, nullptr,
+                                         (uint64_t)L.cap, status, at<uint32_t>(ws, L.stage),
+                                         at<uint32_t>(ws, L.pair_key_b), counters + C_STAGE);
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_TILE_COUNT, s);
@@ -1164,8 +1206,9 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
     const uint32_t* sv = which ? at<uint32_t>(ws, L.val_b) : at<uint32_t>(ws, L.val_a);
     prof_begin(HPXGS_STAGE_TILE_EMIT, s);
     const unsigned tblocks = (unsigned)std::min<int64_t>((PV + 7) / 8, 32LL * num_sms());
-    k_tiles<true><<<tblocks, 256, 0, s>>>(*vt, rec, at<float>(ws, L.radii), sk, sv, flags, nullptr,
-                                          at<uint64_t>(ws, L.offsets), pka, pva, (uint64_t)cap, status);
+    k_tiles<true><<<tblocks, 256, 0, s>>>(*vt, rec, at<float>(ws, L.radii), sk, sv, flags, at<uint32_t>(ws, L.counts),
+                                          at<uint64_t>(ws, L.offsets), pka, pva, (uint64_t)cap, status,
+                                          at<uint32_t>(ws, L.stage), pkb, counters + C_STAGE);
     note_launches(1);
     HPXGS_LAUNCH_CHECK();
     prof_end(HPXGS_STAGE_TILE_EMIT, s);
