@@ -251,6 +251,20 @@ int hpxgs_hssim_backward(const float* I, const float* G, const uint32_t* mask_bi
                          const void* workspace, size_t workspace_bytes, const float* dloss, float* dI,
                          hpxgs_stream_t stream);
 
+/* ---- loss value without a workspace ----
+ * No counterpart in the paper. For callers that cannot give the library device
+ * memory (a plugin inside a host application that owns the GPU memory budget,
+ * a real-time loop that must not allocate after start-up): out3 = {loss, HSSIM,
+ * L1} as hpxgs_hssim_forward computes them, value only (no gradient). The
+ * per-block partial sums live in a fixed 1.18 MB array inside the library's
+ * device image, which every GPU that loads the library holds until exit; the
+ * call allocates nothing. Limit: k <= 10 (Nside <= 1024); larger k returns
+ * HPXGS_E_INVALID_ARG. The first call on each device looks up the array's
+ * device address (make it before any stream capture). All calls share the
+ * array: calls that overlap on the GPU race. */
+int hpxgs_hssim_loss_noalloc(const float* I, const float* G, const uint32_t* mask_bits, int k, float lambda,
+                             float* out3, hpxgs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

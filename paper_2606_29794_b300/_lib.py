@@ -88,6 +88,7 @@ _SIGS = {
     "hpxgs_hssim_workspace_size": (ctypes.c_int, [ctypes.c_int, _P(_sz)]),
     "hpxgs_hssim_forward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _f32, _vp, _sz, _vp, _vp]),
     "hpxgs_hssim_backward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _f32, _vp, _sz, _vp, _vp, _vp]),
+    "hpxgs_hssim_loss_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _f32, _vp, _vp]),
 }
 
 EXPORTS = tuple(_SIGS)
