@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile-level", type=int, default=4)
+    ap.add_argument("--fwd-ppt", type=int, default=0)
+    ap.add_argument("--bwd-ppt", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
     return ap.parse_args()
 
 
@@ -163,7 +166,8 @@ def run_ours(args, ws_n, rank, local):
     K = 16
     params = [t(sc["means"]), t(sc["scales"]), t(sc["rotations"]), t(sc["opacities"]), t(np.asarray(sc["sh"]).reshape(P_GAUSS, K, 3))]
     tparams = [t(tgt["means"]), t(tgt["scales"]), t(tgt["rotations"]), t(tgt["opacities"]), t(np.asarray(tgt["sh"]).reshape(P_GAUSS, K, 3))]
-    rast = R.Rasterizer(tile_level=args.tile_level)
+    rast = R.Rasterizer(tile_level=args.tile_level, fwd_ppt=args.fwd_ppt, bwd_ppt=args.bwd_ppt,
+                        blocks_per_sm=args.blocks_per_sm)
     rast.prepare([view])
     stream = torch.cuda.current_stream(dev)
     sptr = ctypes.c_void_p(stream.cuda_stream)

@@ -97,6 +97,12 @@ typedef struct {
   float bg[3];             /* background seen through T_final, default 0 */
   float lambda_ssim;       /* loss weight lambda (Sec. 4.1), default 0.2 */
   int32_t write_outside;   /* 1: pixels outside the FoV mask get bg, T=1, last=0; 0: inactive tiles untouched */
+  /* launch shape of the blend kernels (0 = built-in default; results do not depend on them):
+   * pixels per thread of the forward (1, 2, 4 or 8) and of the backward (1, 2, 4 or 8), and
+   * resident blocks per SM of the persistent grids (capped by occupancy). */
+  int32_t fwd_ppt;
+  int32_t bwd_ppt;
+  int32_t blocks_per_sm;
 } hpxgs_config;
 
 /* Human-readable name of a status code. */

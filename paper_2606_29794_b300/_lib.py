@@ -41,7 +41,8 @@ class View(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("tile_level", ctypes.c_int32), ("eps_T", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("cutoff_m", ctypes.c_float), ("blur_rad2", ctypes.c_float), ("near_plane", ctypes.c_float),
-                ("bg", ctypes.c_float * 3), ("lambda_ssim", ctypes.c_float), ("write_outside", ctypes.c_int32)]
+                ("bg", ctypes.c_float * 3), ("lambda_ssim", ctypes.c_float), ("write_outside", ctypes.c_int32),
+                ("fwd_ppt", ctypes.c_int32), ("bwd_ppt", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
 
 
 class WorkspaceView(ctypes.Structure):

@@ -181,9 +181,12 @@ static bool valid_view(const hpxgs_view& v, int b) {
   return true;
 }
 
+static bool valid_ppt(int v) { return v == 0 || v == 1 || v == 2 || v == 4 || v == 8; }
+
 static bool valid_cfg(const hpxgs_config* c) {
   return c && c->tile_level >= 3 && c->tile_level <= 5 && c->eps_T >= 0 && c->eps_T < 1 &&
-         c->alpha_max > 0 && c->alpha_max < 1 && c->cutoff_m > 0 && c->near_plane >= 0;
+         c->alpha_max > 0 && c->alpha_max < 1 && c->cutoff_m > 0 && c->near_plane >= 0 &&
+         valid_ppt(c->fwd_ppt) && valid_ppt(c->bwd_ppt) && c->blocks_per_sm >= 0 && c->blocks_per_sm <= 64;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -356,6 +359,9 @@ void hpxgs_config_default(hpxgs_config* c) {
   c->bg[0] = c->bg[1] = c->bg[2] = 0.0f;
   c->lambda_ssim = 0.2f;
   c->write_outside = 1;
+  c->fwd_ppt = 0;
+  c->bwd_ppt = 0;
+  c->blocks_per_sm = 0;
 }
 
 int hpxgs_nside_for_image(int kind, double W, double H, double fovx, double fovy, double* nstar, int* k,

@@ -1043,10 +1043,35 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
 template <typename T>
 static T* at(void* ws, size_t off) { return reinterpret_cast<T*>(static_cast<char*>(ws) + off); }
 
-static int blend_blocks(const void* fn, int nt) {
+static int blend_blocks(const void* fn, int nt, int want_per_sm) {
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nt, 0) != cudaSuccess || occ < 1) occ = 1;
+  if (want_per_sm > 0 && want_per_sm < occ) occ = want_per_sm;
   return occ * num_sms();
+}
+
+// Launch of a blend kernel with NT threads x PPT pixels per thread = the tile's pixels.
+template <int NT, int PPT, typename... Args>
+static void launch_fwd(int bps, cudaStream_t s, Args... args) {
+  auto fn = k_blend_fwd<NT, PPT, 128>;
+  fn<<<blend_blocks((const void*)fn, NT, bps), NT, 0, s>>>(args...);
+}
+template <int NT, int PPT, typename... Args>
+static void launch_bwd(int bps, cudaStream_t s, Args... args) {
+  auto fn = k_blend_bwd<NT, PPT, 32>;
+  fn<<<blend_blocks((const void*)fn, NT, bps), NT, 0, s>>>(args...);
+}
+
+// Pixels per thread of each kernel by tile level (the first entry is the default).
+static int pick_ppt(int b, int want, bool fwd) {
+  static const int f3[] = {1, 2}, f4[] = {1, 2, 4}, f5[] = {4, 8};
+  static const int g3[] = {2, 1}, g4[] = {4, 2, 8}, g5[] = {4, 8};
+  const int* opts; int n;
+  if (b == 3) { opts = fwd ? f3 : g3; n = 2; }
+  else if (b == 4) { opts = fwd ? f4 : g4; n = 3; }
+  else { opts = fwd ? f5 : g5; n = 2; }
+  for (int i = 0; i < n; ++i) if (opts[i] == want) return want;
+  return opts[0];
 }
 
 constexpr int kBatchFwd = 128;
@@ -1234,16 +1259,19 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
   uint32_t* work = counters + C_WORK_FWD;
   unsigned long long* evals = reinterpret_cast<unsigned long long*>(counters + C_NEVAL);
   const int b = cfg->tile_level;
+  const int bps = cfg->blocks_per_sm;
+  const float* chord = at<float>(ws, L.chord);
   prof_begin(HPXGS_STAGE_BLEND_FWD, s);
-  if (b == 3) {
-    auto fn = k_blend_fwd<64, 1, kBatchFwd>;
-    fn<<<blend_blocks((const void*)fn, 64), 64, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work, evals, at<float>(ws, L.chord));
-  } else if (b == 4) {
-    auto fn = k_blend_fwd<256, 1, kBatchFwd>;
-    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work, evals, at<float>(ws, L.chord));
-  } else {
-    auto fn = k_blend_fwd<256, 4, kBatchFwd>;
-    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, maps, T_final, last, work, evals, at<float>(ws, L.chord));
+  {
+    const int ppt = pick_ppt(b, cfg->fwd_ppt, true);
+#define FWD_ARGS bps, s, *vt, (const float4*)rec, (const uint2*)ranges, ids, (const uint32_t*)flags, (const uint32_t*)mask, maps, T_final, last, work, evals, chord
+    if (b == 3) { if (ppt == 2) launch_fwd<32, 2>(FWD_ARGS); else launch_fwd<64, 1>(FWD_ARGS); }
+    else if (b == 4) {
+      if (ppt == 2) launch_fwd<128, 2>(FWD_ARGS);
+      else if (ppt == 4) launch_fwd<64, 4>(FWD_ARGS);
+      else launch_fwd<256, 1>(FWD_ARGS);
+    } else { if (ppt == 8) launch_fwd<128, 8>(FWD_ARGS); else launch_fwd<256, 4>(FWD_ARGS); }
+#undef FWD_ARGS
   }
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
@@ -1287,17 +1315,20 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   const uint32_t* mask = internal_mask(ws, L);      // written by the forward
   uint32_t* work = counters + C_WORK_BWD;
   const int b = cfg->tile_level;
+  const int bps = cfg->blocks_per_sm;
+  const float* chord = at<float>(ws, L.chord);
   prof_begin(HPXGS_STAGE_BLEND_BWD, s);
-  // several pixels per thread: the per-entry warp reduction then covers 32 * PPT pixels
-  if (b == 3) {
-    auto fn = k_blend_bwd<32, 2, kBatchBwd>;
-    fn<<<blend_blocks((const void*)fn, 32), 32, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, at<float>(ws, L.chord));
-  } else if (b == 4) {
-    auto fn = k_blend_bwd<64, 4, kBatchBwd>;
-    fn<<<blend_blocks((const void*)fn, 64), 64, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, at<float>(ws, L.chord));
-  } else {
-    auto fn = k_blend_bwd<256, 4, kBatchBwd>;
-    fn<<<blend_blocks((const void*)fn, 256), 256, 0, s>>>(*vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, at<float>(ws, L.chord));
+  {
+    // several pixels per thread: the per-entry warp reduction then covers 32 * PPT pixels
+    const int ppt = pick_ppt(b, cfg->bwd_ppt, false);
+#define BWD_ARGS bps, s, *vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, chord
+    if (b == 3) { if (ppt == 1) launch_bwd<64, 1>(BWD_ARGS); else launch_bwd<32, 2>(BWD_ARGS); }
+    else if (b == 4) {
+      if (ppt == 2) launch_bwd<128, 2>(BWD_ARGS);
+      else if (ppt == 8) launch_bwd<32, 8>(BWD_ARGS);
+      else launch_bwd<64, 4>(BWD_ARGS);
+    } else { if (ppt == 8) launch_bwd<128, 8>(BWD_ARGS); else launch_bwd<256, 4>(BWD_ARGS); }
+#undef BWD_ARGS
   }
   note_launches(1);
   HPXGS_LAUNCH_CHECK();

@@ -64,9 +64,11 @@ class Rasterizer:
     """Holds the config and the pair capacity; each forward gets its own workspace."""
 
     def __init__(self, tile_level=4, eps_T=1e-4, alpha_max=0.99, cutoff=9.0, blur=None, near=0.2,
-                 bg=(0.0, 0.0, 0.0), lam=0.2, write_outside=1, capacity=None, headroom=1.15):
+                 bg=(0.0, 0.0, 0.0), lam=0.2, write_outside=1, capacity=None, headroom=1.15, fwd_ppt=0, bwd_ppt=0,
+                 blocks_per_sm=0):
         self.cfg = L.default_config(tile_level=tile_level, eps_T=eps_T, alpha_max=alpha_max, cutoff_m=cutoff,
-                                    blur=blur, near_plane=near, bg=bg, lam=lam, write_outside=write_outside)
+                                    blur=blur, near_plane=near, bg=bg, lam=lam, write_outside=write_outside,
+                                    fwd_ppt=fwd_ppt, bwd_ppt=bwd_ppt, blocks_per_sm=blocks_per_sm)
         self.capacity = capacity
         self.headroom = headroom
 
@@ -219,3 +221,121 @@ def device_array(ptr, n, dtype, device=None):
         return torch.empty(0, dtype=dtype, device=device or "cuda")
     view = torch.as_tensor(_DevArray(ptr, n, _TYPESTR[dtype]), device=device or "cuda")
     return view.clone()
+
+
+# ----------------------------------------------------------------------------
+# Training step under a CUDA graph
+# ----------------------------------------------------------------------------
+class GraphStep:
+    """One training step (forward render of `views`, L1 + HSSIM loss per view
+    against `targets`, loss backward, render backward) captured once into a CUDA
+    graph and replayed. Inputs live in static tensors: write new parameter values
+    or targets into `params` / `targets` in place before `replay()`.
+
+    The pair capacity is fixed at capture (from a count on the initial inputs
+    with headroom); after a replay `status` holds the device flags, and a
+    capacity overflow means the graph must be built again with more room."""
+
+    def __init__(self, params, sh_degree, views, targets, rasterizer: Rasterizer, lam=0.2, headroom=1.25):
+        self.params = [p.contiguous() for p in params]
+        self.views = list(views)
+        self.targets = targets.contiguous()
+        self.rast = rasterizer
+        self.lam = lam
+        self.sh_degree = sh_degree
+        dev = self.params[0].device
+        rasterizer.prepare(self.views)
+        g = gaussians_struct(*self.params, sh_degree)
+        cv = L.make_views(self.views)
+        need = rasterizer.count_pairs(g, cv, len(self.views), dev)
+        rasterizer.capacity = max(rasterizer.capacity or 0, int(need * headroom) + 4096)
+        self.lay = view_layout(self.views, rasterizer.cfg.tile_level)
+        self.order = [v["nside_log2"] for v in self.views]
+        # HSSIM workspaces per view (the loss is evaluated per view on its part of the packed maps)
+        self.hws = []
+        for k in self.order:
+            nb = ctypes.c_size_t()
+            L.check(L.lib().hpxgs_hssim_workspace_size(k, ctypes.byref(nb)), "hssim ws")
+            self.hws.append((torch.empty(nb.value, dtype=torch.uint8, device=dev), nb.value))
+        self.losses = torch.zeros((len(self.views), 3), dtype=torch.float32, device=dev)
+        self.dmaps = torch.zeros((self.lay.total_pix, 3), dtype=torch.float32, device=dev)
+        self.graph = None
+        self.out = None
+        self.grads = None
+        # warm up eagerly once (allocator pools, rho cache), then capture
+        self._step()
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s):
+            self._step()
+        torch.cuda.current_stream(dev).wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._step()
+        torch.cuda.synchronize()
+
+    def _step(self):
+        out, state = self.rast.forward_raw(*self.params, self.sh_degree, self.views, check_status=False)
+        st = _stream()
+        for vi, (k, base) in enumerate(zip(self.order, self.lay.pix_base)):
+            n = npix(k)
+            I = out["maps"][base:base + n]
+            G = self.targets[base:base + n]
+            m = out["mask"][base // 32:(base + n) // 32]
+            ws, nb = self.hws[vi]
+            L.check(L.lib().hpxgs_hssim_forward(_ptr(I), _ptr(G), _ptr(m), k, float(self.lam), _ptr(ws), nb,
+                                                _ptr(self.losses[vi]), ctypes.c_void_p(st)), "hssim fwd")
+            L.check(L.lib().hpxgs_hssim_backward(_ptr(I), _ptr(G), _ptr(m), k, float(self.lam), _ptr(ws), nb, None,
+                                                 _ptr(self.dmaps[base:base + n]), ctypes.c_void_p(st)), "hssim bwd")
+        self.grads = self.rast.backward_raw(state, self.dmaps)
+        self.out = out
+
+    def replay(self):
+        self.graph.replay()
+        return self.losses, self.grads
+
+    @property
+    def status(self):
+        return self.out["status"]
+
+
+# ----------------------------------------------------------------------------
+# Autotuner over the launch parameters that do not change results
+# ----------------------------------------------------------------------------
+def autotune(make_step, candidates, reps=5, warmup=2):
+    """Times `make_step(cfg_kwargs)()` for each candidate dict and returns
+    (best_kwargs, {repr(kwargs): ms}). make_step builds (and may capture) a step
+    for one candidate and returns a callable that runs it once on the current stream."""
+    timings = {}
+    best, best_ms = None, float("inf")
+    for kw in candidates:
+        try:
+            run = make_step(kw)
+        except L.HpxgsError:
+            continue
+        for _ in range(warmup):
+            run()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            run()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        timings[repr(sorted(kw.items()))] = ms
+        if ms < best_ms:
+            best, best_ms = kw, ms
+    return best, timings
+
+
+def default_candidates():
+    out = []
+    for b in (3, 4, 5):
+        for bps in (0, 2):
+            out.append(dict(tile_level=b, blocks_per_sm=bps))
+    out.append(dict(tile_level=4, fwd_ppt=2))
+    out.append(dict(tile_level=4, bwd_ppt=2))
+    return out
