@@ -277,6 +277,15 @@ int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nvi
       int rc = tile_rho(p.k, cfg->tile_level, &p.rho, stream);
       if (rc != HPXGS_OK) return rc;
     }
+    // FoV cap: every in-mask pixel lies within psi_max of the optical axis (camera +z), an
+    // active tile's centre within rho of one of them, and a listed tile's centre within
+    // r_s + rho of the Gaussian, so a Gaussian farther than psi_max + 2 rho + r_s from
+    // the axis has no listed tile and can be culled before sorting.
+    double psi_max = -1.0;
+    if (hv.cam.kind == HPXGS_CAM_PINHOLE) psi_max = std::atan(std::sqrt(p.tanx64 * p.tanx64 + p.tany64 * p.tany64));
+    else if (hv.cam.kind == HPXGS_CAM_FISHEYE) psi_max = 0.5 * kPi * std::fmax(p.wx64, p.wy64);
+    const double cull = psi_max + 2.0 * p.rho + 1e-5;
+    p.fov_cull = (need_rho && psi_max >= 0.0 && cull < kPi) ? (float)cull : -1.0f;
     tile_base += p.ntiles;
     pix_base += 12LL << (2 * p.k);
   }

@@ -163,6 +163,8 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ View
   geo_compute(vp, vt.near_plane, gs.means + 3 * (int64_t)i, gs.scales + 3 * (int64_t)i, gs.rotations + 4 * (int64_t)i, G);
   vals[gid] = (uint32_t)gid;
   depth[gid] = G.r;
+  // exact FoV-cap cull (the camera axis is the HEALPix X axis): no tile of the view can list it
+  if (G.valid && vp.fov_cull >= 0.f && G.g.x < cosf(fminf((float)kPi, vp.fov_cull + G.rs))) G.valid = false;
   if (!G.valid) {
     keys[gid] = 0xffffffffu;
     radii[gid] = 0.f;
@@ -260,60 +262,94 @@ __global__ void __launch_bounds__(1024) k_scan_u32_inplace(uint32_t* __restrict_
   }
 }
 
-// Stable scatter of one pass. Each round ranks kRound x 256 elements (striped:
-// element t0 + it * 256 + tid), so two barriers cover 1024 elements: warp-level
-// ranks from __match_any_sync, per-(item, warp, digit) counts in shared memory,
-// then one thread per digit turns its column into running offsets.
-constexpr int kRound = 4;
+// Stable scatter of one pass over the block's chunk, one 4096-element tile at a
+// time: warp w ranks the contiguous elements [w * 512, (w + 1) * 512) of the tile
+// (16 rounds of 32, ranks from __match_any_sync plus a per-warp running count
+// per digit); a digit-major scan over the warps gives each element its place in
+// the tile sorted by digit; the tile is reordered in shared memory and written
+// out so that elements of one digit go to consecutive addresses (full sectors).
+constexpr int kWarpSeg = kSortTile / (kSortThreads / 32);   // 512 elements per warp
+constexpr int kSegRounds = kWarpSeg / 32;                   // 16
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                                const uint32_t* n_ptr, uint32_t n_max, int shift, int nbits,
                                                                const uint32_t* __restrict__ hist, int G) {
   constexpr int NW = kSortThreads / 32;
-  __shared__ uint16_t cnt[kRound][NW][256];      // 16 KB: a warp count is at most 32
-  __shared__ uint32_t off[kRound][NW][256];      // 32 KB
+  __shared__ uint32_t s_key[kSortTile];        // 16 KB, tile in digit order
+  __shared__ uint32_t s_val[kSortTile];        // 16 KB
+  __shared__ uint32_t wcnt[NW][256];           // 8 KB: per-warp digit counts, then bases
+  __shared__ uint32_t dstart[257];             // tile-local start of each digit
+  __shared__ uint32_t gbase[256];              // next global position of each digit for this block
+  __shared__ uint32_t wsum[NW];
   const uint32_t n = n_ptr ? min(*n_ptr, n_max) : n_max;
   uint32_t begin, end;
   chunk_of(n, G, blockIdx.x, begin, end);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint32_t run = hist[tid * G + blockIdx.x];          // this thread owns digit `tid`
-  for (int it = 0; it < kRound; ++it)
-    for (int w = 0; w < NW; ++w) cnt[it][w][tid] = 0;
-  __syncthreads();
   const uint32_t mask = (1u << nbits) - 1u;
   const uint32_t lt = (1u << lane) - 1u;
-  for (uint32_t t0 = begin; t0 < end; t0 += kRound * kSortThreads) {
-    uint32_t key[kRound], digit[kRound], rank[kRound];
+  gbase[tid] = hist[tid * G + blockIdx.x];
+  for (uint32_t t0 = begin; t0 < end; t0 += kSortTile) {
+    // ---- phase 1: per-warp ranks
+    for (int d = lane; d < 256; d += 32) wcnt[warp][d] = 0;
+    __syncwarp();
+    uint32_t key[kSegRounds], val[kSegRounds], dr[kSegRounds];   // dr = digit << 16 | rank in warp segment
 #pragma unroll
-    for (int it = 0; it < kRound; ++it) {
-      const uint32_t idx = t0 + it * kSortThreads + tid;
+    for (int r = 0; r < kSegRounds; ++r) {
+      const uint32_t idx = t0 + warp * kWarpSeg + r * 32 + lane;
       const bool valid = idx < end;
-      key[it] = valid ? kin[idx] : 0u;
-      digit[it] = valid ? ((key[it] >> shift) & mask) : 0xffffu;
-      const uint32_t peers = __match_any_sync(0xffffffffu, digit[it]);
-      rank[it] = __popc(peers & lt);
-      if (valid && rank[it] == 0) cnt[it][warp][digit[it]] = (uint16_t)__popc(peers);
+      key[r] = valid ? kin[idx] : 0u;
+      val[r] = valid ? vin[idx] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kSegRounds; ++r) {
+      const uint32_t idx = t0 + warp * kWarpSeg + r * 32 + lane;
+      const bool valid = idx < end;
+      const uint32_t digit = valid ? ((key[r] >> shift) & mask) : 0xffffu;
+      const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+      const uint32_t before = valid ? wcnt[warp][digit] : 0u;
+      __syncwarp();
+      const uint32_t rk = __popc(peers & lt);
+      if (valid && rk == 0) wcnt[warp][digit] = before + __popc(peers);
+      __syncwarp();
+      dr[r] = (digit << 16) | (before + rk);
     }
     __syncthreads();
+    // ---- phase 2: digit-major scan over warps, then over digits
+    uint32_t tot = 0;
 #pragma unroll
-    for (int it = 0; it < kRound; ++it)
-#pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        const uint32_t c = cnt[it][w][tid];
-        off[it][w][tid] = run;
-        run += c;
-        cnt[it][w][tid] = 0;
-      }
+    for (int w = 0; w < NW; ++w) { const uint32_t c = wcnt[w][tid]; wcnt[w][tid] = tot; tot += c; }
+    uint32_t inc = tot;
+    for (int o = 1; o < 32; o <<= 1) { const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o); if (lane >= o) inc += y; }
+    if (lane == 31) wsum[warp] = inc;
     __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += wsum[w];
+    dstart[tid] = wpre + inc - tot;
+    if (tid == kSortThreads - 1) dstart[256] = wpre + inc;
+    __syncthreads();
+    // ---- phase 3: reorder the tile in shared memory
 #pragma unroll
-    for (int it = 0; it < kRound; ++it) {
-      const uint32_t idx = t0 + it * kSortThreads + tid;
-      if (idx < end) {
-        const uint32_t pos = off[it][warp][digit[it]] + rank[it];
-        kout[pos] = key[it];
-        vout[pos] = vin[idx];
+    for (int r = 0; r < kSegRounds; ++r) {
+      const uint32_t digit = dr[r] >> 16;
+      if (digit != 0xffffu) {
+        const uint32_t p = dstart[digit] + wcnt[warp][digit] + (dr[r] & 0xffffu);
+        s_key[p] = key[r];
+        s_val[p] = val[r];
       }
     }
+    __syncthreads();
+    // ---- phase 4: write runs of equal digits to consecutive global positions
+    const uint32_t m = dstart[256];
+    for (uint32_t i = tid; i < m; i += kSortThreads) {
+      const uint32_t k = s_key[i];
+      const uint32_t d = (k >> shift) & mask;
+      const uint32_t pos = gbase[d] + (i - dstart[d]);
+      kout[pos] = k;
+      vout[pos] = s_val[i];
+    }
+    __syncthreads();
+    gbase[tid] += dstart[tid + 1] - dstart[tid];
+    __syncthreads();
   }
 }
 
