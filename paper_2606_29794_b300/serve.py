@@ -52,7 +52,7 @@ class Stats:
 
 class RenderServer:
     def __init__(self, params, sh_degree, budget_bytes=8 << 30, slots=3, max_views=8, max_pixels=64 << 20,
-                 headroom=1.3, tile_level=4):
+                 headroom=1.3, tile_level=0):
         self.params = [p.contiguous() for p in params]
         self.sh_degree = sh_degree
         self.budget = int(budget_bytes)
@@ -63,13 +63,22 @@ class RenderServer:
         self.tile_level = tile_level
         self.dev = self.params[0].device
         self.g = R.gaussians_struct(*self.params, sh_degree)
-        self.cfg = L.default_config(tile_level=tile_level)
+        self.cfg_by_level = {b: L.default_config(tile_level=b) for b in (3, 4, 5)}
+        self.cfg = self.cfg_by_level[tile_level or 4]
+        self.adaptive = tile_level is None or tile_level == 0
         self.pairs_per_pixel = {}          # (k, kind) -> running max of pairs / in-mask-or-full pixel
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(slots)]
 
+    def level_for(self, views):
+        """Tile level of a batch: 5 (1024-pixel tiles) once a view reaches Nside 1024, else 4.
+        Maps do not depend on it; it trades pair count against per-tile list length."""
+        if not self.adaptive:
+            return self.tile_level
+        return 5 if max(v["nside_log2"] for v in views) >= 10 else 4
+
     # ---- memory model -------------------------------------------------------
     def _estimate_pairs(self, v):
-        key = (v["nside_log2"], v["cam"])
+        key = (v["nside_log2"], v["cam"], self.level_for([v]))
         ppx = self.pairs_per_pixel.get(key)
         if ppx is None:
             return None
@@ -79,13 +88,14 @@ class RenderServer:
         px = sum(R.npix(v["nside_log2"]) for v in views)
         ppx = n_pairs / max(px, 1)
         for v in views:
-            key = (v["nside_log2"], v["cam"])
+            key = (v["nside_log2"], v["cam"], self.level_for([v]))
             self.pairs_per_pixel[key] = max(self.pairs_per_pixel.get(key, 0.0), ppx)
 
     def _batch_bytes(self, views, cap):
         cv = L.make_views(views)
         n = ctypes.c_size_t()
-        L.check(L.lib().hpxgs_forward_workspace_size(self.g.P, cv, len(views), ctypes.byref(self.cfg), int(cap),
+        cfg = self.cfg_by_level[self.level_for(views)]
+        L.check(L.lib().hpxgs_forward_workspace_size(self.g.P, cv, len(views), ctypes.byref(cfg), int(cap),
                                                      ctypes.byref(n)), "workspace size")
         px = sum(R.npix(v["nside_log2"]) for v in views)
         return n.value + px * (12 + 4 + 4) + px // 8 + 64, cv
@@ -94,13 +104,14 @@ class RenderServer:
         """Exact pair count of a batch (synchronises): used for a request kind never seen before."""
         cv = L.make_views(views)
         ws_n = ctypes.c_size_t()
-        L.check(L.lib().hpxgs_forward_workspace_size(self.g.P, cv, len(views), ctypes.byref(self.cfg), 0,
+        cfg = self.cfg_by_level[self.level_for(views)]
+        L.check(L.lib().hpxgs_forward_workspace_size(self.g.P, cv, len(views), ctypes.byref(cfg), 0,
                                                      ctypes.byref(ws_n)), "workspace size")
         ws = torch.empty(ws_n.value, dtype=torch.uint8, device=self.dev)
         cnt = torch.zeros(1, dtype=torch.int64, device=self.dev)
         st = torch.zeros(1, dtype=torch.int32, device=self.dev)
         s = torch.cuda.current_stream(self.dev).cuda_stream
-        L.check(L.lib().hpxgs_count_pairs(ctypes.byref(self.g), cv, len(views), ctypes.byref(self.cfg),
+        L.check(L.lib().hpxgs_count_pairs(ctypes.byref(self.g), cv, len(views), ctypes.byref(cfg),
                                           ctypes.c_void_p(ws.data_ptr()), ws_n.value, ctypes.c_void_p(cnt.data_ptr()),
                                           ctypes.c_void_p(st.data_ptr()), ctypes.c_void_p(s)), "count")
         n = int(cnt.item())
@@ -110,10 +121,11 @@ class RenderServer:
     # ---- one batch ------------------------------------------------------------
     def _launch(self, views, cap, stream):
         nbytes, cv = self._batch_bytes(views, cap)
-        lay = R.view_layout(views, self.tile_level)
+        cfg = self.cfg_by_level[self.level_for(views)]
+        lay = R.view_layout(views, cfg.tile_level)
         with torch.cuda.stream(stream):
             ws_n = ctypes.c_size_t()
-            L.check(L.lib().hpxgs_forward_workspace_size(self.g.P, cv, len(views), ctypes.byref(self.cfg), int(cap),
+            L.check(L.lib().hpxgs_forward_workspace_size(self.g.P, cv, len(views), ctypes.byref(cfg), int(cap),
                                                          ctypes.byref(ws_n)), "workspace size")
             ws = torch.empty(ws_n.value, dtype=torch.uint8, device=self.dev)
             maps = torch.empty((lay.total_pix, 3), dtype=torch.float32, device=self.dev)
@@ -122,7 +134,7 @@ class RenderServer:
             mask = torch.empty(lay.total_pix // 32, dtype=torch.int32, device=self.dev)
             status = torch.zeros(1, dtype=torch.int32, device=self.dev)
             p = lambda t: ctypes.c_void_p(t.data_ptr())
-            L.check(L.lib().hpxgs_forward(ctypes.byref(self.g), cv, len(views), ctypes.byref(self.cfg), p(ws),
+            L.check(L.lib().hpxgs_forward(ctypes.byref(self.g), cv, len(views), ctypes.byref(cfg), p(ws),
                                           ws_n.value, int(cap), p(maps), p(T), p(last), p(mask), None, p(status),
                                           ctypes.c_void_p(stream.cuda_stream)), "forward")
             ev = torch.cuda.Event()
@@ -156,7 +168,7 @@ class RenderServer:
     def _workspace_pairs(self, job):
         wv = L.WorkspaceView()
         L.check(L.lib().hpxgs_workspace_inspect(self.g.P, L.make_views(job["views"]), len(job["views"]),
-                                                ctypes.byref(self.cfg), job["cap"],
+                                                ctypes.byref(self.cfg_by_level[self.level_for(job["views"])]), job["cap"],
                                                 ctypes.c_void_p(job["ws"].data_ptr()), ctypes.byref(wv)), "inspect")
         return int(R.device_array(wv.n_pairs, 1, torch.int32, self.dev).item()) & 0xffffffff
 
