@@ -965,6 +965,9 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
 // of the tangent frame, so this gives the exact derivative):
 //   d(e_i / r) = -(g (e_i . dt) + e_i (g . dt)) / r^2,  dg = (I - g g^T) dt / r.
 // ----------------------------------------------------------------------------
+// DEG is the SH degree as a compile-time constant, so the SH rows (value, basis,
+// basis gradient, per-Gaussian SH gradient) stay in registers.
+template <int DEG>
 __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ ViewTable vt, hpxgs_gaussians gs,
                                                         const float* __restrict__ radii, const float* __restrict__ accum,
                                                         float* __restrict__ dmeans, float* __restrict__ dscales,
@@ -972,12 +975,13 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
                                                         float* __restrict__ dsh) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= vt.P) return;
-  const int K = (vt.sh_degree + 1) * (vt.sh_degree + 1);
+  constexpr int K = (DEG + 1) * (DEG + 1);
   float dmu[3] = {0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dop = 0.f;
-  float dshl[48];
-  for (int c = 0; c < 3 * K; ++c) dshl[c] = 0.f;
   const float* mu = gs.means + 3 * (int64_t)i;
   const float* sh = gs.sh + (int64_t)i * K * 3;
+  float dshl[3 * K];
+#pragma unroll
+  for (int c = 0; c < 3 * K; ++c) dshl[c] = 0.f;
   for (int v = 0; v < vt.nviews; ++v) {
     const int64_t gid = (int64_t)v * vt.P + i;
     if (!(radii[gid] > 0.f)) continue;
@@ -990,18 +994,22 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
     float dx = mu[0] - vp.cam[0], dy = mu[1] - vp.cam[1], dz = mu[2] - vp.cam[2];
     const float dist = sqrtf(dx * dx + dy * dy + dz * dz), idist = 1.f / dist;
     dx *= idist; dy *= idist; dz *= idist;
-    float Y[16];
-    float3 dY[16];
-    sh_basis(vt.sh_degree, dx, dy, dz, Y, dY);
+    float Y[K];
+    float3 dY[K];
+    sh_basis(DEG, dx, dy, dz, Y, dY);
     float Lcr[3];
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
       float raw = 0.5f;
+#pragma unroll
       for (int kk = 0; kk < K; ++kk) raw += sh[3 * kk + c] * Y[kk];
       Lcr[c] = raw > 0.f ? A[c] : 0.f;
     }
     float Ld[3] = {0.f, 0.f, 0.f};
+#pragma unroll
     for (int kk = 0; kk < K; ++kk) {
       float w = 0.f;
+#pragma unroll
       for (int c = 0; c < 3; ++c) { dshl[3 * kk + c] += Y[kk] * Lcr[c]; w += Lcr[c] * sh[3 * kk + c]; }
       Ld[0] += w * dY[kk].x; Ld[1] += w * dY[kk].y; Ld[2] += w * dY[kk].z;
     }
@@ -1070,6 +1078,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
   for (int c = 0; c < 3; ++c) { dmeans[3 * (int64_t)i + c] = dmu[c]; dscales[3 * (int64_t)i + c] = ds[c]; }
   for (int c = 0; c < 4; ++c) drot[4 * (int64_t)i + c] = dq[c];
   dopac[i] = dop;
+#pragma unroll
   for (int c = 0; c < 3 * K; ++c) dsh[(int64_t)i * K * 3 + c] = dshl[c];
 }
 
@@ -1151,7 +1160,9 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_PREPROCESS, s);
   prof_begin(HPXGS_STAGE_DEPTH_SORT, s);
-  rc = radix_sort(ka, va, kb, vb, nullptr, (uint32_t)PV, 32, at<uint32_t>(ws, L.hist), L.sort_blocks, s, which_depth);
+  // a grid sized to the element count (about 4 tiles of 4096 per block): the digit scan covers 256 x G entries
+  const int Gd = (int)std::max<int64_t>(1, std::min<int64_t>(L.sort_blocks, (PV + 4 * kSortTile - 1) / (4 * kSortTile)));
+  rc = radix_sort(ka, va, kb, vb, nullptr, (uint32_t)PV, 32, at<uint32_t>(ws, L.hist), Gd, s, which_depth);
   if (rc != HPXGS_OK) return rc;
   prof_end(HPXGS_STAGE_DEPTH_SORT, s);
   const uint32_t* sk = *which_depth ? kb : ka;
@@ -1370,8 +1381,16 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_BLEND_BWD, s);
   prof_begin(HPXGS_STAGE_PREPROCESS_BWD, s);
-  k_preprocess_bwd<<<(g->P + 127) / 128, 128, 0, s>>>(*vt, *g, at<float>(ws, L.radii), accum, dmeans, dscales, drot,
-                                                       dopac, dsh);
+  {
+    const int nb = (int)((g->P + 127) / 128);
+    const float* rad = at<float>(ws, L.radii);
+    switch (g->sh_degree) {
+      case 0: k_preprocess_bwd<0><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh); break;
+      case 1: k_preprocess_bwd<1><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh); break;
+      case 2: k_preprocess_bwd<2><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh); break;
+      default: k_preprocess_bwd<3><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh); break;
+    }
+  }
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_PREPROCESS_BWD, s);
