@@ -54,6 +54,7 @@ def lib():
         _lib.or_tile_rho.restype = ctypes.c_double
         _lib.or_tile_lists.restype = ctypes.c_int64
         _lib.or_tile_lists_bruteforce.restype = ctypes.c_int64
+        _lib.or_tile_lists_subset.restype = ctypes.c_int64
         _lib.or_hssim_loss.restype = ctypes.c_double
         _lib.or_num_threads.restype = ctypes.c_int
     return _lib
@@ -270,6 +271,24 @@ def tile_lists(k, b, g, rs, valid, dbits, rho, active):
     return start, ids
 
 
+def tile_lists_subset(k, b, g, rs, valid, dbits, rho, active, tiles):
+    """Lists of the distinct tiles `tiles` only (membership definition over every
+    Gaussian, depth order); CSR over all tiles with the other lists empty."""
+    g = np.ascontiguousarray(g, np.float64); rs = np.ascontiguousarray(rs, np.float64)
+    valid = np.ascontiguousarray(valid, np.int32); dbits = np.ascontiguousarray(dbits, np.uint32)
+    active = np.ascontiguousarray(active, np.uint8)
+    sel = np.ascontiguousarray(np.unique(np.asarray(tiles, np.int64)), np.int64)
+    P = rs.size
+    nt = 12 * 4 ** (k - b)
+    start = np.empty(nt + 1, np.int64)
+    m = lib().or_tile_lists_subset(ctypes.c_int(k), ctypes.c_int(b), _i64(P), _p(g), _p(rs), _p(valid), _p(dbits),
+                                   _f64(rho), _p(active), _i64(sel.size), _p(sel), _p(start), None)
+    ids = np.empty(m, np.int64)
+    lib().or_tile_lists_subset(ctypes.c_int(k), ctypes.c_int(b), _i64(P), _p(g), _p(rs), _p(valid), _p(dbits),
+                               _f64(rho), _p(active), _i64(sel.size), _p(sel), _p(start), _p(ids))
+    return start, ids
+
+
 def tile_lists_bruteforce(k, b, g, rs, valid, rho, active):
     g = np.ascontiguousarray(g, np.float64); rs = np.ascontiguousarray(rs, np.float64)
     valid = np.ascontiguousarray(valid, np.int32); active = np.ascontiguousarray(active, np.uint8)
@@ -282,7 +301,9 @@ def tile_lists_bruteforce(k, b, g, rs, valid, rho, active):
 
 
 def composite(k, b, pre, opac, start, ids, pix, cfg: Config):
-    """Stage 3 (Algorithm 1 rendering loop) at the NESTED pixels `pix`."""
+    """Stage 3 (Algorithm 1 rendering loop) at the NESTED pixels `pix`.
+    Returns (image, T, last, amb); amb bit 0 flags a cutoff decision within
+    rounding of m = cutoff, bit 1 two contributors of nearly equal depth."""
     pix = np.ascontiguousarray(pix, np.int64)
     n = pix.size
     img = np.empty((n, 3)); T = np.empty(n); last = np.empty(n, np.int64); amb = np.empty(n, np.uint8)
@@ -306,7 +327,7 @@ class Render:
     image: np.ndarray            # (Npix, 3); outside the mask: bg
     T: np.ndarray                # (Npix,) final transmittance (1 outside the mask)
     last: np.ndarray             # (Npix,) processed entries of the tile list
-    amb: np.ndarray              # (Npix,) ambiguity flags
+    amb: np.ndarray              # (Npix,) ambiguity flags: bit 0 cutoff boundary, bit 1 depth tie
     mask: np.ndarray
     active: np.ndarray
     pre: dict

@@ -544,10 +544,15 @@ static void query_disc_ring(i64 nside_t, const double g[3], double R, std::vecto
   }
 }
 
-static bool tile_member(i64 nside_t, i64 t, const double g[3], double rs, double rho) {
-  double ct[3]; pix2vec_nest(nside_t, t, ct);
+// Membership of a Gaussian (centre g, radius r_s) in the tile with centre ct.
+static bool tile_member_at(const double ct[3], const double g[3], double rs, double rho) {
   double dt = ct[0] * g[0] + ct[1] * g[1] + ct[2] * g[2];
   return dt >= std::cos(std::min(kPi, rs + rho + 1e-7));
+}
+
+static bool tile_member(i64 nside_t, i64 t, const double g[3], double rs, double rho) {
+  double ct[3]; pix2vec_nest(nside_t, t, ct);
+  return tile_member_at(ct, g, rs, rho);
 }
 
 // Per Gaussian: the sorted set of listed tiles (RING candidates, exact test).
@@ -616,13 +621,13 @@ static void composite_pixel(double omega_p, double sphp, double cphp, const i64*
     double m = gv.conic[0] * o.d[0] * o.d[0] + 2 * gv.conic[1] * o.d[0] * o.d[1] + gv.conic[2] * o.d[1] * o.d[1];
     double Gm = std::exp(-0.5 * m);
     double a = (m > cfg.cutoff) ? 0.0 : std::min(cfg.alpha_max, gv.opac * Gm);
-    // ambiguity flags (test bookkeeping, not part of the method): the cutoff decided
-    // within 1e-5 relative while it matters, or two contributing Gaussians of
-    // nearly equal depth whose order float32 cannot settle.
+    // ambiguity flags (test bookkeeping, not part of the method): bit 0, the cutoff
+    // decided within 1e-5 relative while it matters; bit 1, two contributing
+    // Gaussians of nearly equal depth whose order float32 cannot settle.
     double cmax = std::max(gv.col[0], std::max(gv.col[1], gv.col[2]));
     if (std::fabs(m - cfg.cutoff) < 1e-5 * cfg.cutoff &&
-        T * gv.opac * std::exp(-0.5 * cfg.cutoff) * std::max(1.0, cmax) > 5e-5) amb = 1;
-    if (a > 0 && prev_a > 0 && std::fabs(gv.r - prev_r) < 2e-6 * gv.r && T * a > 5e-5) amb = 1;
+        T * gv.opac * std::exp(-0.5 * cfg.cutoff) * std::max(1.0, cmax) > 5e-5) amb |= 1;
+    if (a > 0 && prev_a > 0 && std::fabs(gv.r - prev_r) < 2e-6 * gv.r && T * a > 5e-5) amb |= 2;
     if (a > 0) { prev_r = gv.r; prev_a = a; }
     if (alphas) { alphas->push_back(a); Ts->push_back(T); Gs->push_back(Gm); }
     for (int c = 0; c < 3; ++c) C[c] += T * a * gv.col[c];
@@ -897,6 +902,38 @@ i64 or_tile_lists_bruteforce(int k, int b, i64 P, const double* g, const double*
       member[i * ntile + t] = v;
       total += v;
     }
+  return total;
+}
+
+// Lists of the chosen tiles only, by the membership definition over every
+// Gaussian, in (depth bits, id) order; every other tile gets an empty list. For
+// sampled checks of a large scene, where enumerating all tiles would be slow.
+// `sel` holds distinct tile ids. Returns the pair count; start/ids may be null.
+i64 or_tile_lists_subset(int k, int b, i64 P, const double* g, const double* rs, const int* valid,
+                         const u32* depth_bits, double rho, const u8* active, i64 nsel, const i64* sel,
+                         i64* start, i64* ids) {
+  i64 nside_t = 1LL << (k - b), ntile = 12 * nside_t * nside_t;
+  std::vector<std::vector<i64>> per(nsel);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (i64 s = 0; s < nsel; ++s) {
+    const i64 t = sel[s];
+    if (!active[t]) continue;
+    double ct[3]; pix2vec_nest(nside_t, t, ct);
+    for (i64 i = 0; i < P; ++i)
+      if (valid[i] && tile_member_at(ct, g + 3 * i, rs[i], rho)) per[s].push_back(i);
+    std::stable_sort(per[s].begin(), per[s].end(),
+                     [&](i64 a, i64 c) { return depth_bits[a] < depth_bits[c]; });   // ids ascending within a depth
+  }
+  std::vector<i64> cnt(ntile, 0);
+  for (i64 s = 0; s < nsel; ++s) cnt[sel[s]] = (i64)per[s].size();
+  i64 total = 0;
+  for (i64 t = 0; t < ntile; ++t) {
+    if (start) start[t] = total;
+    total += cnt[t];
+  }
+  if (start) start[ntile] = total;
+  if (ids && start)
+    for (i64 s = 0; s < nsel; ++s) std::copy(per[s].begin(), per[s].end(), ids + start[sel[s]]);
   return total;
 }
 

@@ -1,0 +1,181 @@
+"""Parity at the full sizes of the measured workloads, on sampled outputs.
+
+Rendering a 300k-, 1M- or 6M-Gaussian scene end to end in FP64 takes the oracle
+far longer than a test may run, but every pixel is defined by its own tile's
+list alone (Algorithm 1; with the m <= 9 cutoff the map does not depend on
+which other tiles exist). So for a seeded sample of active tiles the oracle
+builds only those lists (membership definition over every Gaussian) and
+composites a sample of their pixels. Each workload runs in the launch
+configuration the benchmark times (tile level 4, default pixels per thread):
+
+- tile lists of the sampled tiles, rebuilt by the oracle from the GPU's stored
+  FP32 (g, r_s, depth): exact, including order;
+- compositing of the sampled pixels by the oracle from the GPU's FP32 records
+  and those lists (same depth order by construction): maps and T within 2e-4,
+  the last index equal, at least 99% of pixels compared (cutoff-boundary
+  pixels excluded);
+- maps and T at the sampled pixels vs the oracle from scratch in FP64: 2e-4,
+  all ambiguous pixels excluded and counted. At these densities (1e5-1e6
+  Gaussians in depths [2, 6]) 4-6% of pixels have two contributors within 2e-6
+  relative depth, an order FP32 depths cannot settle, so the floor is 90%;
+- gradients of a loss weighting only the sampled pixels vs the oracle's backward
+  over the same pixels: 1e-3 relative.
+
+Workloads: Nside 512 fisheye 190 deg with 300k SH3 Gaussians (the training
+step); 16 views of three cameras over 1M SH3 Gaussians; Nside 2048 full sphere
+with 6M SH3 Gaussians (log-scales N(-3.5, 0.7)).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2606_29794_b300 import raster as R
+from paper_2606_29794_b300 import synth as S
+from tests.gpu_util import mask_from_words, oracle_cfg, scene_tensors
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
+
+MAP_TOL = 2e-4
+GRAD_TOL = 1e-3
+
+
+def _f64view(v):
+    v = dict(v)
+    v["W"] = np.asarray(v["W"], np.float64); v["b"] = np.asarray(v["b"], np.float64)
+    return v
+
+
+def _check_views(sc, views, rast, out, state, n_tiles, per_tile, seed):
+    """Sampled list, map and T parity for every view of one batched forward.
+    Returns per view (pixels, oracle lists (start, ids), ambiguity flags)."""
+    cfg = oracle_cfg(rast)
+    b = rast.tile_level
+    P = sc["means"].shape[0]
+    nv = len(views)
+    lay = out["layout"]
+    wv = R.workspace_view(rast, state)
+    rec = R.device_array(wv.records, nv * P * 16, torch.float32).view(nv * P, 16)
+    radii = R.device_array(wv.radii, nv * P, torch.float32)
+    depth = R.device_array(wv.depth, nv * P, torch.float32)
+    n_pairs = int(R.device_array(wv.n_pairs, 1, torch.int32).item())
+    gids = R.device_array(wv.pair_ids, n_pairs, torch.int32).cpu().numpy().astype(np.int64)
+    ranges = R.device_array(wv.ranges, 2 * lay.total_tiles, torch.int32).view(-1, 2).cpu().numpy().astype(np.int64)
+    maps = out["maps"].cpu().numpy()
+    Tg = out["T"].cpu().numpy()
+    lastg = out["last"].cpu().numpy().astype(np.int64)
+    words = out["mask"].cpu().numpy().view(np.uint32)
+    rng = np.random.default_rng(seed)
+    res = []
+    tile_base = 0
+    compared = total = staged_ok = 0
+    for v, view in enumerate(views):
+        k = view["nside_log2"]
+        N = O.npix(2 ** k)
+        base = lay.pix_base[v]
+        m_gpu = mask_from_words(words[base // 32:(base + N) // 32], N)
+        m_ref, margin = O.mask(2 ** k, view["cam"], view["fov_x"], view["fov_y"])
+        assert np.all(np.abs(margin[m_gpu != m_ref]) < 1e-12)
+        act = O.active_tiles(k, b, m_gpu)
+        cand = np.nonzero(act)[0]
+        tiles = np.sort(rng.choice(cand, min(n_tiles, cand.size), replace=False))
+        # ---- lists of the sampled tiles from the GPU's FP32 values: exact
+        sl = slice(v * P, (v + 1) * P)
+        g32 = rec[sl, 0:3].cpu().numpy().astype(np.float64)
+        rs32 = radii[sl].cpu().numpy()
+        valid = rs32 > 0
+        dbits = depth[sl].cpu().numpy().astype(np.float32).view(np.uint32).copy()
+        dbits[~valid] = 0xFFFFFFFF
+        rho = O.tile_rho(k, b)
+        st, ids_ref = O.tile_lists_subset(k, b, g32, rs32.astype(np.float64), valid.astype(np.int32), dbits, rho,
+                                          act, tiles)
+        for t in tiles:
+            lo, hi = ranges[tile_base + t]
+            got = gids[lo:hi] - v * P if hi > lo else np.zeros(0, np.int64)
+            assert np.array_equal(got, ids_ref[st[t]:st[t + 1]]), (v, t, got[:8], ids_ref[st[t]:st[t] + 8])
+        pix = []
+        for t in tiles:
+            inside = (t << (2 * b)) + np.nonzero((m_gpu & m_ref)[t << (2 * b):(t + 1) << (2 * b)])[0]
+            pix.append(rng.choice(inside, min(per_tile, inside.size), replace=False))
+        pix = np.sort(np.concatenate(pix)).astype(np.int64)
+        # ---- staged compositing from the GPU's records and lists
+        r32 = rec[sl].cpu().numpy().astype(np.float64)
+        pre_g = dict(omega=np.arctan2(r32[:, 1], r32[:, 0]), phi=np.arctan2(r32[:, 2], np.hypot(r32[:, 0], r32[:, 1])),
+                     conic=r32[:, [7, 11, 15]], col=r32[:, 12:15], r=depth[sl].cpu().numpy().astype(np.float64))
+        img, T, last, amb = O.composite(k, b, pre_g, r32[:, 3], st, ids_ref, pix, cfg)
+        ok = (amb & 1) == 0
+        staged_ok += int(ok.sum())
+        assert np.abs(maps[base + pix] - img)[ok].max() < MAP_TOL
+        assert np.abs(Tg[base + pix] - T)[ok].max() < MAP_TOL
+        assert (lastg[base + pix] == last)[ok].mean() >= 0.995
+        # ---- maps and T at sampled pixels vs the oracle from scratch
+        pre = O.preprocess(sc, _f64view(view), cfg)
+        act_ref = O.active_tiles(k, b, m_ref)
+        st2, ids2 = O.tile_lists_subset(k, b, pre["g"], pre["rs"], pre["valid"], O.depth_bits(pre["r"]), rho,
+                                        act_ref, tiles)
+        img, T, last, amb = O.composite(k, b, pre, sc["opacities"], st2, ids2, pix, cfg)
+        ok = amb == 0
+        compared += int(ok.sum()); total += ok.size
+        assert np.abs(maps[base + pix] - img)[ok].max() < MAP_TOL
+        assert np.abs(Tg[base + pix] - T)[ok].max() < MAP_TOL
+        res.append((pix, st2, ids2, amb))
+        tile_base += 12 * 4 ** (k - b)
+    assert staged_ok >= 0.99 * total, (staged_ok, total)
+    assert compared >= 0.90 * total, (compared, total)
+    return res
+
+
+def _check_grads(sc, views, rast, out, state, sampled, seed, use=None):
+    """Gradients of sum_p dI_p . I_p over the sampled, unambiguous pixels of the
+    views `use` (default all); the backward still walks every view's tiles."""
+    cfg = oracle_cfg(rast)
+    lay = out["layout"]
+    rng = np.random.default_rng(seed)
+    dmaps = np.zeros((lay.total_pix, 3), np.float32)
+    ref = None
+    for v, (view, (pix, st, ids, amb)) in enumerate(zip(views, sampled)):
+        if use is not None and v not in use:
+            continue
+        dI = rng.standard_normal((pix.size, 3)).astype(np.float32)
+        dI[amb != 0] = 0.0
+        dmaps[lay.pix_base[v] + pix] = dI
+        r = O.backward(sc, _f64view(view), cfg, dI.astype(np.float64), st, ids, pix)
+        ref = r if ref is None else {n: ref[n] + r[n] for n in ref}
+    grads = rast.backward_raw(state, torch.as_tensor(dmaps, device="cuda"))
+    torch.cuda.synchronize()
+    for name, gt in zip(["means", "scales", "rotations", "opacities", "sh"], grads):
+        g = gt.cpu().numpy().astype(np.float64).reshape(ref[name].shape)
+        r = ref[name]
+        assert np.linalg.norm(r) > 0, name
+        rel = np.linalg.norm(g - r) / np.linalg.norm(r)
+        assert rel <= GRAD_TOL, (name, rel)
+        assert np.abs(g - r).max() <= GRAD_TOL * np.abs(r).max(), (name, np.abs(g - r).max(), np.abs(r).max())
+
+
+def test_training_step_nside512_fisheye190_p300k():
+    sc = S.make_scene(300_000, 3, seed=20261205)
+    view = S.make_view(9, S.CAM_FISHEYE, 190.0)
+    rast = R.Rasterizer(tile_level=4)
+    out, state = rast.forward_raw(*scene_tensors(sc), 3, [view])
+    torch.cuda.synchronize()
+    sampled = _check_views(sc, [view], rast, out, state, n_tiles=48, per_tile=24, seed=1)
+    _check_grads(sc, [view], rast, out, state, sampled, seed=2)
+
+
+def test_sixteen_views_p1m():
+    sc = S.make_scene(1_000_000, 3, seed=20261206)
+    views = S.multiview_set(20261208)
+    rast = R.Rasterizer(tile_level=4)
+    out, state = rast.forward_raw(*scene_tensors(sc), 3, views)
+    torch.cuda.synchronize()
+    sampled = _check_views(sc, views, rast, out, state, n_tiles=6, per_tile=16, seed=3)
+    _check_grads(sc, views, rast, out, state, sampled, seed=4, use=(0, 1, 6, 12))   # pinhole x2, fisheye, full
+
+
+def test_nside2048_full_sphere_p6m():
+    sc = S.make_scene(6_000_000, 3, seed=20261213, logscale_mu=-3.5, logscale_sd=0.7)
+    view = S.make_view(11)
+    rast = R.Rasterizer(tile_level=4)
+    out, state = rast.forward_raw(*scene_tensors(sc), 3, [view])
+    torch.cuda.synchronize()
+    _check_views(sc, [view], rast, out, state, n_tiles=24, per_tile=16, seed=5)

@@ -147,6 +147,30 @@ def test_ring_query_equals_bruteforce_membership(k, b):
             assert sorted(ids[start[t]:start[t + 1]]) == list(np.nonzero(mem[:, t])[0])
 
 
+@pytest.mark.parametrize("k,b", [(5, 2), (6, 3)])
+def test_subset_lists_equal_full_lists(k, b):
+    # The per-tile builder used by the full-size sampled checks: same ids, same
+    # order as the RING-built lists on the chosen tiles, empty lists elsewhere.
+    rng = np.random.default_rng(40 + k)
+    P = 400
+    g = rng.standard_normal((P, 3)); g /= np.linalg.norm(g, axis=1, keepdims=True)
+    g[:2] = [[0, 0, 1], [0, 0, -1]]
+    rs = np.exp(rng.uniform(np.log(1e-3), np.log(1.5), P))
+    valid = (rng.random(P) > 0.1).astype(np.int32)
+    dbits = rng.integers(0, 40, P).astype(np.uint32)             # many equal depths: ties by id
+    m, _ = O.mask(1 << k, O.CAM_FISHEYE, 200.0)
+    act = O.active_tiles(k, b, m)
+    rho = O.tile_rho(k, b)
+    start, ids = O.tile_lists(k, b, g, rs, valid, dbits, rho, act)
+    nt = act.size
+    sel = np.concatenate([rng.choice(nt, 12, replace=False), [0, nt - 1], np.nonzero(act == 0)[0][:2]])
+    s2, i2 = O.tile_lists_subset(k, b, g, rs, valid, dbits, rho, act, sel)
+    for t in range(nt):
+        got = list(i2[s2[t]:s2[t + 1]])
+        want = list(ids[start[t]:start[t + 1]]) if t in set(sel.tolist()) else []
+        assert got == want
+
+
 def test_tile_rho_bounds_pixel_distance():
     for k, b in [(5, 2), (6, 4)]:
         rho = O.tile_rho(k, b)
