@@ -273,6 +273,7 @@ int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nvi
     p.tile_base = (int)tile_base;
     p.pix_base = pix_base;
     p.rho = 0;
+    p.rho32 = 0.f;
     if (need_rho) {
       int rc = tile_rho(p.k, cfg->tile_level, &p.rho, stream);
       if (rc != HPXGS_OK) return rc;
@@ -284,6 +285,7 @@ int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nvi
     double psi_max = -1.0;
     if (hv.cam.kind == HPXGS_CAM_PINHOLE) psi_max = std::atan(std::sqrt(p.tanx64 * p.tanx64 + p.tany64 * p.tany64));
     else if (hv.cam.kind == HPXGS_CAM_FISHEYE) psi_max = 0.5 * kPi * std::fmax(p.wx64, p.wy64);
+    p.rho32 = (float)p.rho;
     const double cull = psi_max + 2.0 * p.rho + 1e-5;
     p.fov_cull = (need_rho && psi_max >= 0.0 && cull < kPi) ? (float)cull : -1.0f;
     tile_base += p.ntiles;

@@ -20,6 +20,7 @@ struct ViewParams {
   float wx, wy;        // fisheye fov / 180 deg
   double tanx64, tany64, wx64, wy64;
   double rho;          // tile rho(k, b)
+  float rho32;         // (float) rho, so kernels need no FP64 conversion
   float fov_cull;      // Gaussians farther than fov_cull + r_s from the optical axis have no listed tile (< 0: none)
   float blur;          // isotropic Sigma_arc term
   int ntiles;          // 12 * 4^(k-b)

@@ -408,8 +408,8 @@ __device__ __forceinline__ void disc_setup(const ViewParams& vp, int kt, float3 
   (void)lane;
   // FP32 estimate of the membership threshold; the FP64 value is formed only for
   // candidates within 1e-5 of it
-  Q.cosRm32 = cosf(fminf((float)kPi, rs + (float)vp.rho + 1e-7f));
-  const float Re = fminf((float)kPi, rs + (float)vp.rho + 1e-7f + 1e-5f);   // enumeration radius with slack
+  Q.cosRm32 = cosf(fminf((float)kPi, rs + vp.rho32 + 1e-7f));
+  const float Re = fminf((float)kPi, rs + vp.rho32 + 1e-7f + 1e-5f);   // enumeration radius with slack
   Q.cosRe = cosf(Re);
   const int Nt = 1 << kt;
   Q.zc = g.z;
@@ -493,8 +493,8 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
     DiscQ Q;
     disc_setup(vp, kt, g, radii[gid], lane, Q);
 
-    const double3 g64 = make_double3(g.x, g.y, g.z);
     const float rs = radii[gid];
+    double cosRm = 2.0;                        // FP64 threshold, formed at this lane's first band candidate
     const uint64_t base = EMIT ? offsets[j] : 0;
     uint32_t cnt = 0;
     for (int r0i = Q.ilo; r0i <= Q.ihi; r0i += 32) {
@@ -535,9 +535,10 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
           if (dot > Q.cosRm32 + 1e-5f) member = true;
           else if (dot >= Q.cosRm32 - 1e-5f) {
             // the exact test: both sides in FP64, the threshold as the membership rule states it
-            const double cosRm = cos(fmin(kPi, (double)rs + vp.rho + 1e-7));
+            // (the FP64 pipe is slow on this part: nothing on the common path uses it)
+            if (cosRm > 1.5) cosRm = cos(fmin(kPi, (double)rs + vp.rho + 1e-7));
             const double3 c = ringpix_vec_f64(kt, ii, jj);
-            member = c.x * g64.x + c.y * g64.y + c.z * g64.z >= cosRm;
+            member = c.x * (double)g.x + c.y * (double)g.y + c.z * (double)g.z >= cosRm;
           }
           if (member) {
             const FaceXY fx = ring_to_fxy(kt, ii, jj);
