@@ -36,10 +36,6 @@ FOV = 190.0
 SEED = 20261205
 WORKLOAD = "train_step_nside512_fisheye190_P300k_sh3"
 
-# FP32 work per (pixel, list entry), counted from the kernels' inner loops
-# (FMA = 2 flops): weight evaluation 40; forward blend of a contributing entry 13;
-# backward gradient of a contributing entry 83. See DESIGN.md "Roofline".
-F_EVAL, F_BLEND, F_GRAD = 40, 13, 83
 SM_COUNT, FP32_LANES = 148, 128
 
 
@@ -174,83 +170,103 @@ def run_ours(args, ws_n, rank, local):
                         blocks_per_sm=args.blocks_per_sm)
     rast.prepare([view])
     stream = torch.cuda.current_stream(dev)
-    sptr = ctypes.c_void_p(stream.cuda_stream)
     with torch.no_grad():
-        tout, _ = rast.forward_raw(*tparams, 3, [view])
+        tout, _ = R.Rasterizer(tile_level=args.tile_level).forward_raw(*tparams, 3, [view])
     G = tout["maps"].clone()
-    # HSSIM workspace
-    nb = ctypes.c_size_t()
-    L.check(lib.hpxgs_hssim_workspace_size(K_ORDER, ctypes.byref(nb)), "hssim ws")
-    hws = torch.empty(nb.value, dtype=torch.uint8, device=dev)
-    out3 = torch.empty(3, dtype=torch.float32, device=dev)
-    dmaps = torch.empty_like(G)
-    p = lambda x: ctypes.c_void_p(x.data_ptr())
+    del tout
+    # ---------------- one training step (forward, L1 + HSSIM forward and backward, backward) as a
+    # CUDA graph; every stage's start and stop events are recorded inside the graph. Two instances
+    # alternate, so one's stage events are read while the other runs: the host never idles the GPU.
+    def new_pairs():
+        pairs = {}
+        for s in L.STAGES:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream); b.record(stream)              # torch creates the CUDA event on first record
+            pairs[s] = (a, b)
+        return pairs
 
-    def step(target):
-        out, state = rast.forward_raw(*params, 3, [view], check_status=False)
-        L.check(lib.hpxgs_hssim_forward(p(out["maps"]), p(target), p(out["mask"]), K_ORDER, 0.2, p(hws), nb.value,
-                                        p(out3), sptr), "hssim fwd")
-        L.check(lib.hpxgs_hssim_backward(p(out["maps"]), p(target), p(out["mask"]), K_ORDER, 0.2, p(hws), nb.value,
-                                         None, p(dmaps), sptr), "hssim bwd")
-        grads = rast.backward_raw(state, dmaps)
-        return out, state, grads
+    def arm(pairs):
+        for i, s in enumerate(L.STAGES):
+            a, b = pairs[s]
+            L.check(lib.hpxgs_profile_arm(i, ctypes.c_void_p(a.cuda_event), ctypes.c_void_p(b.cuda_event)), "arm")
 
-    # ---------------- warm-up (and capacity check once)
-    for _ in range(max(1, args.warmup)):
-        out, state, grads = step(G)
+    stage_pairs = [new_pairs(), new_pairs()]
+    gsteps = [R.GraphStep(params, 3, [view], G, rast, before_capture=lambda j=j: arm(stage_pairs[j])) for j in range(2)]
+    gstep = gsteps[0]
+    # ---------------- warm-up and capacity check
+    for i in range(max(1, args.warmup)):
+        gsteps[i % 2].replay()
     torch.cuda.synchronize()
-    st = int(out["status"].item())
-    if st & L.F_CAPACITY:
+    if any(int(g.status.item()) & L.F_CAPACITY for g in gsteps):
         raise RuntimeError("pair capacity exceeded after warm-up")
-    n_mask = int(np.unpackbits(out["mask"].cpu().numpy().view(np.uint8)).sum())
-    wv = R.workspace_view(rast, state)
+    n_mask = int(np.unpackbits(gstep.out["mask"].cpu().numpy().view(np.uint8)).sum())
+    wv = R.workspace_view(rast, gstep.state)
     n_pairs = int(R.device_array(wv.n_pairs, 1, torch.int32).item())
-    # ---------------- timed region (device path)
+    # ---------------- measured ALU peaks (FMA and MUFU probes at the current clocks)
+    fma_tf, ex2_t = ctypes.c_double(), ctypes.c_double()
+    L.check(lib.hpxgs_probe_alu_peak(ctypes.byref(fma_tf), ctypes.byref(ex2_t), ctypes.c_void_p(stream.cuda_stream)),
+            "alu probe")
+    # ---------------- timed region (device path: graph replays, L2 flushed before each)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)     # > 126 MB L2
-    stage_ev = {s: [] for s in L.STAGES}
-    step_ev = []
+    stage_vals = {s: [] for s in L.STAGES}
+    step_ms = []
     if ws_n > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    launches0 = lib.hpxgs_launch_count()
-    for _ in range(args.steps):
+    step_ev = []
+
+    def read_stages(j):
+        for s, (a, b) in stage_pairs[j].items():
+            try:
+                stage_vals[s].append(a.elapsed_time(b))
+            except RuntimeError:
+                pass
+
+    for k in range(args.steps):
+        j = k % 2
+        if k >= 2:                      # step k-2 used this instance: read its stage events before it runs again
+            step_ev[k - 2][1].synchronize()
+            read_stages(j)
         flush.zero_()
-        evs = {}
-        for i, s in enumerate(L.STAGES):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream); b.record(stream)       # torch creates the CUDA event on first record
-            L.check(lib.hpxgs_profile_arm(i, ctypes.c_void_p(a.cuda_event), ctypes.c_void_p(b.cuda_event)), "arm")
-            evs[s] = (a, b)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        out, state, grads = step(G)
+        gsteps[j].replay()
         e1.record(stream)
         step_ev.append((e0, e1))
-        for s in L.STAGES:
-            stage_ev[s].append(evs[s])
     torch.cuda.synchronize()
-    launches = lib.hpxgs_launch_count() - launches0
+    for k in range(max(0, args.steps - 2), args.steps):
+        read_stages(k % 2)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    launches = gstep.launches_per_replay * args.steps
     ms = sum(step_ms) / len(step_ms)
     if ws_n > 1:
         tt = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         ms = float(tt.item())
         torch.distributed.barrier()
-    stage_ms = {}
-    for s, lst in stage_ev.items():
-        vals = []
-        for a, b in lst:
-            try:
-                vals.append(a.elapsed_time(b))
-            except Exception:
-                pass
-        if vals:
-            stage_ms[s] = sum(vals) / len(vals)
+    stage_ms = {s: sum(v) / len(v) for s, v in stage_vals.items() if v and sum(v) > 0}
+    stage_source = "events recorded by the timed graph replays"
+    if not any(s in stage_ms for s in ("blend_fwd", "blend_bwd")):
+        # the graph did not record the stage events: time the stages in eager steps instead
+        stage_source = "eager steps after the timed region"
+        vals = {s: [] for s in L.STAGES}
+        for _ in range(3):
+            flush.zero_()
+            evs = {}
+            for i, s in enumerate(L.STAGES):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream); b.record(stream)
+                L.check(lib.hpxgs_profile_arm(i, ctypes.c_void_p(a.cuda_event), ctypes.c_void_p(b.cuda_event)), "arm")
+                evs[s] = (a, b)
+            gsteps[0]._step()
+            torch.cuda.synchronize()
+            for s, (a, b) in evs.items():
+                vals[s].append(a.elapsed_time(b))
+        stage_ms = {s: sum(v) / len(v) for s, v in vals.items() if v and sum(v) > 0}
     n_eval = int(R.device_array(wv.n_eval, 1, torch.int64).item())
     n_contrib = int(R.device_array(wv.n_contrib, 1, torch.int64).item())
     value = n_mask * ws_n / (ms * 1e-3) / 1e6
@@ -259,9 +275,12 @@ def run_ours(args, ws_n, rank, local):
     sm_max = float(pk.get("sm_max_mhz", 2032.0))
     alu_peak = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12        # TFLOP/s FP32 at max SM clock
     hbm = float(pk.get("hbm_gbs", 6400.0))
+    # ALU unit: a contributing (pixel, entry) pair (m <= cutoff, processed before termination)
+    f_fwd = L.FLOPS_EVAL + L.FLOPS_FWD_CONTRIB
+    f_bwd = L.FLOPS_EVAL + L.FLOPS_BWD_CONTRIB
     work = {
-        "blend_fwd": ("alu", (F_EVAL * n_eval + F_BLEND * n_contrib) / 1e12, "TFLOP/s", alu_peak),
-        "blend_bwd": ("alu", (F_EVAL * n_eval + F_GRAD * n_contrib) / 1e12, "TFLOP/s", alu_peak),
+        "blend_fwd": ("alu", f_fwd * n_contrib / 1e12, "TFLOP/s", alu_peak),
+        "blend_bwd": ("alu", f_bwd * n_contrib / 1e12, "TFLOP/s", alu_peak),
         "pair_sort": ("hbm", 20.0 * n_pairs * math.ceil(math.log2(12 * 4 ** (K_ORDER - args.tile_level)) / 8) / 1e9, "GB/s", hbm),
         "depth_sort": ("hbm", 20.0 * P_GAUSS * 4 / 1e9, "GB/s", hbm),
         "preprocess": ("hbm", (236 + 64 + 16) * P_GAUSS / 1e9, "GB/s", hbm),
@@ -278,24 +297,33 @@ def run_ours(args, ws_n, rank, local):
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": ("derived: 148 SM x 128 FP32 lanes x 2 x max SM clock" if bound == "alu"
                                 else "measured (MEASURED_PEAKS.json hbm_gbs)")}
+    if bound == "alu":
+        fe = L.FLOPS_EVAL * n_eval + (L.FLOPS_FWD_CONTRIB if dom == "blend_fwd" else L.FLOPS_BWD_CONTRIB) * n_contrib
+        roofline.update({
+            "unit_of_work": f"contributing (pixel, entry) pair, {f_fwd if dom == 'blend_fwd' else f_bwd} FP32 flops each",
+            "peak_measured_fma": round(fma_tf.value, 1), "frac_of_measured_fma": round(achieved / fma_tf.value, 4),
+            "mufu_measured_tops": round(ex2_t.value, 2),
+            "achieved_incl_rejected_evals": round(fe / 1e12 / (stage_ms[dom] * 1e-3), 3)})
     # ---------------- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
+        # the public API with host buffers: the graph copies the pinned host target in (overlapping
+        # the forward render) at every replay; the loss is read back to pinned host memory
         hostG = torch.empty(G.shape, dtype=torch.float32, pin_memory=True)
         hostG.copy_(G.cpu())
-        dG = torch.empty_like(G)
         hloss = torch.empty(1, dtype=torch.float32, pin_memory=True)
+        estep = R.GraphStep(params, 3, [view], torch.empty_like(G), R.Rasterizer(tile_level=args.tile_level),
+                            host_targets=hostG)
         for _ in range(2):
-            dG.copy_(hostG, non_blocking=True); step(dG); hloss.copy_(out3[:1], non_blocking=True)
+            estep.replay(); hloss.copy_(estep.losses[0, :1], non_blocking=True)
         torch.cuda.synchronize()
         ev = []
         for _ in range(args.steps):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            dG.copy_(hostG, non_blocking=True)
-            step(dG)
-            hloss.copy_(out3[:1], non_blocking=True)
+            estep.replay()
+            hloss.copy_(estep.losses[0, :1], non_blocking=True)
             b.record(stream)
             ev.append((a, b))
         torch.cuda.synchronize()
@@ -305,7 +333,10 @@ def run_ours(args, ws_n, rank, local):
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             e_ms = float(tt.item())
         e2e = {"value": round(n_mask * ws_n / (e_ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
-               "h2d_bytes_per_step": int(hostG.numel() * 4), "d2h_bytes_per_step": 4, "ms_per_step": round(e_ms, 4)}
+               "h2d_bytes_per_step": int(hostG.numel() * 4), "d2h_bytes_per_step": 4, "ms_per_step": round(e_ms, 4),
+               "loss_matches_device_path": bool(abs(float(hloss.item()) - float(gstep.losses[0, 0].item())) <= 1e-6)}
+        del estep
+    npix_full = 12 * 4 ** K_ORDER
     res = {
         "metric": "Mpix/s fwd+bwd at Nside 512/300k Gaussians (L1+HSSIM training step)",
         "value": round(value, 2), "unit": "Mpix/s", "n_gpus": ws_n, "steps": args.steps, "warmup": args.warmup,
@@ -313,9 +344,12 @@ def run_ours(args, ws_n, rank, local):
         "dtype": "f32", "data": "synthetic (seeded Gaussians shaped like the paper's scenes)",
         "config": {"workload": WORKLOAD, "nside": 512, "camera": "fisheye 190 deg", "in_mask_px": n_mask,
                    "gaussians": P_GAUSS, "sh_degree": 3, "tile_level": args.tile_level, "loss": "0.8 L1 + 0.2 (1-HSSIM)",
-                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{ws_n}, no collective",
+                   "l2": "flushed (256 MB write) before every timed step", "step": "CUDA graph replay",
+                   "parallelism": f"replicas x{ws_n}, no collective",
                    "pairs": n_pairs, "evals": n_eval, "contrib": n_contrib},
+        "full_grid_mpix_s": round(npix_full * ws_n / (ms * 1e-3) / 1e6, 2),
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "stage_timing": stage_source,
         "roofline": roofline,
         "clocks": clk,
         "gpu_launches": int(launches),

@@ -219,10 +219,30 @@ int hpxgs_count_pairs(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
 /* Arm a one-shot timing of `stage`: the next call that runs the stage records
  * start_event (a cudaEvent_t) on its stream right before the stage's first
  * kernel and stop_event right after its last one, then disarms. Pass NULL
- * events to disarm. Host only; the events belong to the caller. */
+ * events to disarm. Host only; the events belong to the caller. When the stream
+ * is being captured, the records become event-record nodes of the graph, so
+ * every replay records both events again. */
 int hpxgs_profile_arm(int stage, void* start_event, void* stop_event);
 /* Number of kernels this library has launched in this process. */
 uint64_t hpxgs_launch_count(void);
+/* Measured FP32 throughput of this GPU at its current clocks, the denominators
+ * of the blend kernels' roofline: dependency-free FMA chains over every SM
+ * (fma_tflops, 2 flops per FMA) and MUFU ex2 chains (ex2_tops, 1e12 ops/s).
+ * Synchronises the stream (about 20 ms of GPU time); HPXGS_E_CAPTURE inside
+ * stream capture. */
+int hpxgs_probe_alu_peak(double* fma_tflops, double* ex2_tops, hpxgs_stream_t stream);
+
+/* FP32 work of the blend kernels, counted from their inner loops (an FMA is 2
+ * flops, a MUFU op is counted apart): per evaluated (pixel, entry) pair, the
+ * offset and m = d^T conic d (chord test, tangent components, quadratic form,
+ * arc-length series); per contributing pair (m <= cutoff, before termination),
+ * alpha and compositing in the forward, and T recovery, dL/dalpha and the
+ * conic and position partials in the backward. */
+#define HPXGS_FLOPS_EVAL 40
+#define HPXGS_FLOPS_FWD_CONTRIB 13
+#define HPXGS_FLOPS_BWD_CONTRIB 83
+#define HPXGS_MUFU_FWD_CONTRIB 1   /* ex2 */
+#define HPXGS_MUFU_BWD_CONTRIB 2   /* ex2, reciprocal */
 
 /* Device pointers into a forward workspace (for inspection and tests). */
 typedef struct {

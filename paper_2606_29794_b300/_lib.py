@@ -62,6 +62,11 @@ _lib = None
 _P = ctypes.POINTER
 _vp, _i32, _i64, _sz, _f32, _f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_float, ctypes.c_double
 
+# FP32 work per (pixel, entry) pair of the blend kernels (the HPXGS_FLOPS_* and
+# HPXGS_MUFU_* values of include/hpxgs.h; a test checks they agree).
+FLOPS_EVAL, FLOPS_FWD_CONTRIB, FLOPS_BWD_CONTRIB = 40, 13, 83
+MUFU_FWD_CONTRIB, MUFU_BWD_CONTRIB = 1, 2
+
 _SIGS = {
     "hpxgs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "hpxgs_status_error": (ctypes.c_int, [_i32]),
@@ -86,6 +91,7 @@ _SIGS = {
                                                _P(WorkspaceView)]),
     "hpxgs_profile_arm": (ctypes.c_int, [ctypes.c_int, _vp, _vp]),
     "hpxgs_launch_count": (ctypes.c_uint64, []),
+    "hpxgs_probe_alu_peak": (ctypes.c_int, [_P(_f64), _P(_f64), ctypes.c_void_p]),
     "hpxgs_hssim_workspace_size": (ctypes.c_int, [ctypes.c_int, _P(_sz)]),
     "hpxgs_hssim_forward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _f32, _vp, _sz, _vp, _vp]),
     "hpxgs_hssim_backward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _f32, _vp, _sz, _vp, _vp, _vp]),

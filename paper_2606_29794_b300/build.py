@@ -7,7 +7,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["geometry.cu", "raster.cu", "hssim.cu", "hssim_noalloc.cu"]
+SOURCES = ["geometry.cu", "raster.cu", "hssim.cu", "hssim_noalloc.cu", "probe.cu"]
 HEADERS = ["hpx_math.cuh", "internal.cuh"]
 LIB = os.path.join(HERE, "libhpxgs.so")
 ROOT = os.path.dirname(HERE)

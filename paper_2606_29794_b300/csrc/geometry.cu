@@ -23,13 +23,23 @@ static std::atomic<uint64_t> g_launches{0};
 
 void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
+// In stream capture a plain record only marks a dependency; the external flag
+// makes it an event-record node that the graph performs at every replay.
+static void prof_record(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s);
+}
+
 void prof_begin(int stage, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  if (g_prof[stage][0]) cudaEventRecord(g_prof[stage][0], s);
+  if (g_prof[stage][0]) prof_record(g_prof[stage][0], s);
 }
 void prof_end(int stage, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  if (g_prof[stage][1]) cudaEventRecord(g_prof[stage][1], s);
+  if (g_prof[stage][1]) prof_record(g_prof[stage][1], s);
   g_prof[stage][0] = nullptr;
   g_prof[stage][1] = nullptr;
 }

@@ -234,9 +234,16 @@ class GraphStep:
 
     The pair capacity is fixed at capture (from a count on the initial inputs
     with headroom); after a replay `status` holds the device flags, and a
-    capacity overflow means the graph must be built again with more room."""
+    capacity overflow means the graph must be built again with more room.
+    `before_capture` (optional) runs right before the capture, e.g. to arm
+    stage events that the graph then records at every replay;
+    `launches_per_replay` is the number of library kernels in the graph.
+    With `host_targets` (a pinned host tensor shaped like `targets`) every
+    replay first copies it into `targets`, on a forked stream that overlaps the
+    forward render; the loss waits for the copy."""
 
-    def __init__(self, params, sh_degree, views, targets, rasterizer: Rasterizer, lam=0.2, headroom=1.25):
+    def __init__(self, params, sh_degree, views, targets, rasterizer: Rasterizer, lam=0.2, headroom=1.25,
+                 before_capture=None, host_targets=None):
         self.params = [p.contiguous() for p in params]
         self.views = list(views)
         self.targets = targets.contiguous()
@@ -262,6 +269,11 @@ class GraphStep:
         self.graph = None
         self.out = None
         self.grads = None
+        self.host_targets = host_targets
+        if host_targets is not None:
+            if not host_targets.is_pinned() or host_targets.shape != self.targets.shape:
+                raise ValueError("host_targets must be a pinned host tensor shaped like targets")
+            self.side = torch.cuda.Stream(device=dev)
         # warm up eagerly once (allocator pools, rho cache), then capture
         self._step()
         torch.cuda.synchronize()
@@ -272,12 +284,23 @@ class GraphStep:
         torch.cuda.current_stream(dev).wait_stream(s)
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
+        if before_capture is not None:
+            before_capture()
+        n0 = L.lib().hpxgs_launch_count()
         with torch.cuda.graph(self.graph):
             self._step()
         torch.cuda.synchronize()
+        self.launches_per_replay = int(L.lib().hpxgs_launch_count() - n0)
 
     def _step(self):
+        cur = torch.cuda.current_stream(self.targets.device)
+        if self.host_targets is not None:
+            self.side.wait_stream(cur)
+            with torch.cuda.stream(self.side):
+                self.targets.copy_(self.host_targets, non_blocking=True)
         out, state = self.rast.forward_raw(*self.params, self.sh_degree, self.views, check_status=False)
+        if self.host_targets is not None:
+            cur.wait_stream(self.side)
         st = _stream()
         for vi, (k, base) in enumerate(zip(self.order, self.lay.pix_base)):
             n = npix(k)
@@ -291,6 +314,7 @@ class GraphStep:
                                                  _ptr(self.dmaps[base:base + n]), ctypes.c_void_p(st)), "hssim bwd")
         self.grads = self.rast.backward_raw(state, self.dmaps)
         self.out = out
+        self.state = state
 
     def replay(self):
         self.graph.replay()

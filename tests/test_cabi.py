@@ -68,3 +68,11 @@ def test_host_argument_checks(lib):
                              None) == L.E_INVALID_ARG
     assert lib.hpxgs_hssim_workspace_size(2, ctypes.byref(n)) == L.E_INVALID_ARG
     assert lib.hpxgs_pix2vec_nest(20, None, 1, None, None, None) == L.E_INVALID_ARG
+
+
+def test_flop_counts_match_header():
+    text = open(HEADER).read()
+    vals = dict(re.findall(r"#define HPXGS_((?:FLOPS|MUFU)_[A-Z_]+)\s+(\d+)", text))
+    assert {k: int(v) for k, v in vals.items()} == {
+        "FLOPS_EVAL": L.FLOPS_EVAL, "FLOPS_FWD_CONTRIB": L.FLOPS_FWD_CONTRIB, "FLOPS_BWD_CONTRIB": L.FLOPS_BWD_CONTRIB,
+        "MUFU_FWD_CONTRIB": L.MUFU_FWD_CONTRIB, "MUFU_BWD_CONTRIB": L.MUFU_BWD_CONTRIB}

@@ -127,3 +127,28 @@ def test_underpredicted_capacity_is_rerun():
     n = R.npix(r["view"]["nside_log2"])
     srv.headroom = 1.3
     assert torch.equal(srv.render_batch([r["view"]])["maps"], job["maps"][base:base + n])
+
+
+def test_graph_step_with_host_targets_matches_device_targets():
+    # the copy of pinned host targets inside the graph (overlapping the forward)
+    # gives the same losses and gradients as targets already on the device
+    sc = S.make_scene(20000, 3, seed=59)
+    views = _views(4)
+    params = scene_tensors(sc)
+    lay = R.view_layout(views)
+    g = torch.Generator().manual_seed(60)
+    tgt = torch.rand((lay.total_pix, 3), generator=g)
+    host = tgt.pin_memory()
+    dev_step = R.GraphStep(params, 3, views, tgt.cuda(), R.Rasterizer())
+    host_step = R.GraphStep(params, 3, views, torch.zeros_like(tgt, device="cuda"), R.Rasterizer(), host_targets=host)
+    l1, g1 = dev_step.replay()
+    l2, g2 = host_step.replay()
+    torch.cuda.synchronize()
+    l2 = l2.clone()                                  # replay returns the graph's static buffers
+    assert torch.equal(l1, l2)
+    for a, b in zip(g1, g2):
+        assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * float(a.abs().max()) + 1e-12)
+    host.mul_(0.5)                                   # a new target written in place is picked up by the next replay
+    l3, _ = host_step.replay()
+    torch.cuda.synchronize()
+    assert not torch.equal(l3, l2)
