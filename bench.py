@@ -152,6 +152,7 @@ def run_ours(args, ws_n, rank, local):
 
     from paper_2606_29794_b300 import _lib as L
     from paper_2606_29794_b300 import raster as R
+    from paper_2606_29794_b300 import replicas as RP
     from paper_2606_29794_b300 import synth as S
 
     torch.cuda.set_device(local)
@@ -160,7 +161,7 @@ def run_ours(args, ws_n, rank, local):
     # ---------------- inputs (synthetic, seeded; each rank its own camera pose)
     sc = S.make_scene(P_GAUSS, 3, seed=SEED)
     tgt = S.perturb_scene(sc, SEED + 1)
-    rot = None if rank == 0 else S.random_rotation(np.random.default_rng(SEED + 100 + rank))
+    rot = RP.rank_rotation(rank, SEED)
     view = S.make_view(K_ORDER, S.CAM_FISHEYE, FOV, R=rot)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev)
     K = 16
@@ -242,11 +243,8 @@ def run_ours(args, ws_n, rank, local):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     launches = gstep.launches_per_replay * args.steps
-    ms = sum(step_ms) / len(step_ms)
+    ms = RP.job_time_ms(sum(step_ms) / len(step_ms))          # slowest rank
     if ws_n > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
         torch.distributed.barrier()
     stage_ms = {s: sum(v) / len(v) for s, v in stage_vals.items() if v and sum(v) > 0}
     stage_source = "events recorded by the timed graph replays"
@@ -269,7 +267,8 @@ def run_ours(args, ws_n, rank, local):
         stage_ms = {s: sum(v) / len(v) for s, v in vals.items() if v and sum(v) > 0}
     n_eval = int(R.device_array(wv.n_eval, 1, torch.int64).item())
     n_contrib = int(R.device_array(wv.n_contrib, 1, torch.int64).item())
-    value = n_mask * ws_n / (ms * 1e-3) / 1e6
+    n_job = RP.job_units(n_mask)                               # in-mask pixels of all ranks
+    value = n_job / (ms * 1e-3) / 1e6
     # ---------------- roofline of the dominant kernel
     pk = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2032.0))
@@ -327,12 +326,8 @@ def run_ours(args, ws_n, rank, local):
             b.record(stream)
             ev.append((a, b))
         torch.cuda.synchronize()
-        e_ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
-        if ws_n > 1:
-            tt = torch.tensor([e_ms], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            e_ms = float(tt.item())
-        e2e = {"value": round(n_mask * ws_n / (e_ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
+        e_ms = RP.job_time_ms(sum(a.elapsed_time(b) for a, b in ev) / len(ev))
+        e2e = {"value": round(n_job / (e_ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
                "h2d_bytes_per_step": int(hostG.numel() * 4), "d2h_bytes_per_step": 4, "ms_per_step": round(e_ms, 4),
                "loss_matches_device_path": bool(abs(float(hloss.item()) - float(gstep.losses[0, 0].item())) <= 1e-6)}
         del estep
@@ -347,7 +342,7 @@ def run_ours(args, ws_n, rank, local):
                    "l2": "flushed (256 MB write) before every timed step", "step": "CUDA graph replay",
                    "parallelism": f"replicas x{ws_n}, no collective",
                    "pairs": n_pairs, "evals": n_eval, "contrib": n_contrib},
-        "full_grid_mpix_s": round(npix_full * ws_n / (ms * 1e-3) / 1e6, 2),
+        "full_grid_mpix_s": round(RP.job_units(npix_full) / (ms * 1e-3) / 1e6, 2),
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "stage_timing": stage_source,
         "roofline": roofline,
