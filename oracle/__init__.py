@@ -402,3 +402,64 @@ def hssim_local(nside, I, G, m, qs):
     h = np.empty(qs.size)
     lib().or_hssim_local(_i64(nside), _p(I), _p(G), _p(m), _i64(qs.size), _p(qs), _p(h))
     return h
+
+
+# ---------------------------------------------------------------------------
+# Sphere <-> image resampling (Eq. camera_synthesis; Eqs. supp_image_to_healpix,
+# supp_hssim_mask; camera models of Sec. D.1)
+# ---------------------------------------------------------------------------
+
+def _cam_args(kind, W, H, fovx, fovy):
+    fovy = fovx if fovy is None else fovy
+    return ctypes.c_int(kind), _f64(W), _f64(H), _f64(fovx), _f64(fovy)
+
+
+def img_to_dir(kind, W, H, fovx, fovy, uv):
+    """P_C: image points (n, 2) -> camera directions (n, 3) and validity (D_C)."""
+    uv = np.ascontiguousarray(uv, np.float64).reshape(-1, 2)
+    d = np.empty((uv.shape[0], 3)); ok = np.empty(uv.shape[0], np.uint8)
+    lib().or_img_to_dir(*_cam_args(kind, W, H, fovx, fovy), _i64(uv.shape[0]), _p(uv), _p(d), _p(ok))
+    return d, ok
+
+
+def dir_to_img(kind, W, H, fovx, fovy, d):
+    """Pi_C^{-1}: camera directions (n, 3) -> image points (n, 2) and validity."""
+    d = np.ascontiguousarray(d, np.float64).reshape(-1, 3)
+    uv = np.empty((d.shape[0], 2)); ok = np.empty(d.shape[0], np.uint8)
+    lib().or_dir_to_img(*_cam_args(kind, W, H, fovx, fovy), _i64(d.shape[0]), _p(d), _p(uv), _p(ok))
+    return uv, ok
+
+
+def interp_weights(nside, theta, phi):
+    """Interp_H: 4 NESTED pixels and weights per (colatitude, longitude)."""
+    theta = np.ascontiguousarray(theta, np.float64).ravel()
+    phi = np.ascontiguousarray(phi, np.float64).ravel()
+    pix = np.empty((theta.size, 4), np.int64); w = np.empty((theta.size, 4))
+    lib().or_interp_weights(_i64(nside), _i64(theta.size), _p(theta), _p(phi), _p(pix), _p(w))
+    return pix, w
+
+
+def sphere_to_image(nside, hmap, kind, W, H, fovx=360.0, fovy=None):
+    """Camera image (H, W, 3) from a HEALPix map (Npix, 3) in the camera frame, and validity (H, W)."""
+    hmap = np.ascontiguousarray(hmap, np.float64).reshape(-1, 3)
+    img = np.empty((H, W, 3)); ok = np.empty((H, W), np.uint8)
+    lib().or_sphere_to_image(_i64(nside), _p(hmap), ctypes.c_int(kind), _i64(W), _i64(H), _f64(fovx),
+                             _f64(fovx if fovy is None else fovy), _p(img), _p(ok))
+    return img, ok
+
+
+def sphere_to_image_adjoint(nside, dimg, kind, W, H, fovx=360.0, fovy=None):
+    dimg = np.ascontiguousarray(dimg, np.float64).reshape(H, W, 3)
+    dmap = np.empty((12 * nside * nside, 3))
+    lib().or_sphere_to_image_adjoint(_i64(nside), _p(dimg), ctypes.c_int(kind), _i64(W), _i64(H), _f64(fovx),
+                                     _f64(fovx if fovy is None else fovy), _p(dmap))
+    return dmap
+
+
+def image_to_sphere(nside, img, kind, W, H, fovx=360.0, fovy=None):
+    """HEALPix map (Npix, 3) and mask M_C from a camera image (H, W, 3)."""
+    img = np.ascontiguousarray(img, np.float64).reshape(H, W, 3)
+    hmap = np.empty((12 * nside * nside, 3)); m = np.empty(12 * nside * nside, np.uint8)
+    lib().or_image_to_sphere(_i64(nside), _p(img), ctypes.c_int(kind), _i64(W), _i64(H), _f64(fovx),
+                             _f64(fovx if fovy is None else fovy), _p(hmap), _p(m))
+    return hmap, m

@@ -756,6 +756,150 @@ static double ssim_local(const Window& W, const double* I, const double* Gt, int
 // extern "C" entry points (called from Python through ctypes)
 // ===========================================================================
 
+// ===========================================================================
+// Sphere <-> image resampling: the rendered map to a camera image
+// (Eq. camera_synthesis) and a camera image to the HEALPix grid
+// (Eqs. supp_image_to_healpix, supp_hssim_mask), with the camera models of
+// Sec. D.1 (Eq. persp_sphere; Eqs. fish_weff, fish_sphere, imaging_region,
+// semi_axes; the omnidirectional mapping).
+// Readings (the paper names the operations, not the schemes):
+//  - image samples sit at pixel centres (i + 1/2, j + 1/2);
+//  - Interp_H is HEALPix ring-bilinear interpolation: along each of the two
+//    rings that bracket the colatitude, linear in longitude between the two
+//    pixel centres that bracket it; between the rings, linear in colatitude.
+//    Above the first ring (below the last) it runs linearly in colatitude to a
+//    pole value, the mean of that ring's 4 pixels;
+//  - the image is sampled bilinearly between pixel centres, clamped at the
+//    image edges and, for the panorama, wrapped in longitude;
+//  - each camera's formula is taken as printed (image v grows with d_y for
+//    the pinhole and fisheye; the panorama has phi = pi/2 on its top row).
+// The HEALPix map lives in the camera frame: HEALPix (X, Y, Z) = (d_z, d_x, d_y).
+// ===========================================================================
+
+struct ImgCam { int kind; double W, H, fovx, fovy; };
+
+// P_C: image point (u, v) -> unit camera direction d; false outside D_C.
+static bool img_to_dir(const ImgCam& c, double u, double v, double d[3]) {
+  if (c.kind == CAM_PINHOLE) {
+    double fx = c.W / (2.0 * std::tan(0.5 * c.fovx * kPi / 180.0));
+    double fy = c.H / (2.0 * std::tan(0.5 * c.fovy * kPi / 180.0));
+    double x = (u - 0.5 * c.W) / fx, y = (v - 0.5 * c.H) / fy;
+    double n = std::sqrt(x * x + y * y + 1.0);
+    d[0] = x / n; d[1] = y / n; d[2] = 1.0 / n;
+    return u >= 0 && u <= c.W && v >= 0 && v <= c.H;
+  }
+  if (c.kind == CAM_FISHEYE) {
+    double fx = c.W / kPi, fy = c.H / kPi;
+    double mx = (u - 0.5 * c.W) / fx, my = (v - 0.5 * c.H) / fy;
+    double rm = std::sqrt(mx * mx + my * my);
+    if (rm > 0.5 * kPi) return false;                 // outside the ellipse with a = fx pi/2, b = fy pi/2
+    double gam = std::atan2(my, mx);
+    double wx = c.fovx / 180.0, wy = c.fovy / 180.0;
+    double weff = std::sqrt(std::pow(wx * std::cos(gam), 2) + std::pow(wy * std::sin(gam), 2));
+    double psi = rm * weff;
+    d[0] = std::sin(psi) * std::cos(gam); d[1] = std::sin(psi) * std::sin(gam); d[2] = std::cos(psi);
+    return true;
+  }
+  double om = 2.0 * kPi * u / c.W - kPi, ph = 0.5 * kPi - kPi * v / c.H;
+  d[0] = std::cos(ph) * std::sin(om); d[1] = std::sin(ph); d[2] = std::cos(ph) * std::cos(om);
+  return true;
+}
+
+// Pi_C^{-1}: camera direction d -> image point (u, v); false outside D_C (the
+// same test as the FoV mask, so the resampled mask is M_C itself).
+static bool dir_to_img(const ImgCam& c, const double d[3], double& u, double& v) {
+  if (c.kind == CAM_PINHOLE) {
+    if (camera_margin(c.kind, c.fovx, c.fovy, d) < 0) return false;
+    double fx = c.W / (2.0 * std::tan(0.5 * c.fovx * kPi / 180.0));
+    double fy = c.H / (2.0 * std::tan(0.5 * c.fovy * kPi / 180.0));
+    u = 0.5 * c.W + fx * d[0] / d[2]; v = 0.5 * c.H + fy * d[1] / d[2];
+    return true;
+  }
+  if (c.kind == CAM_FISHEYE) {
+    if (camera_margin(c.kind, c.fovx, c.fovy, d) < 0) return false;
+    double psi = std::atan2(std::sqrt(d[0] * d[0] + d[1] * d[1]), d[2]);
+    double gam = std::atan2(d[1], d[0]);
+    double wx = c.fovx / 180.0, wy = c.fovy / 180.0;
+    double weff = std::sqrt(std::pow(wx * std::cos(gam), 2) + std::pow(wy * std::sin(gam), 2));
+    double rm = psi / weff;
+    u = 0.5 * c.W + (c.W / kPi) * rm * std::cos(gam); v = 0.5 * c.H + (c.H / kPi) * rm * std::sin(gam);
+    return true;
+  }
+  double om = std::atan2(d[0], d[2]), ph = std::asin(std::max(-1.0, std::min(1.0, d[1])));
+  u = c.W * (om + kPi) / (2.0 * kPi); v = c.H * (0.5 * kPi - ph) / kPi;
+  return true;
+}
+
+static double ring_theta(i64 nside, i64 i) { Ring R = ring_info(nside, i); return std::atan2(R.sth, R.z); }
+
+// NESTED index of pixel j (mod n) of ring i.
+static i64 ring_pixel_nest(i64 nside, i64 i, i64 j) {
+  Ring R = ring_info(nside, i);
+  double z, sth, phi; ring2zphi(nside, i, pmod(j, R.npix), z, sth, phi);
+  return zphi2pix_nest(nside, z, phi);
+}
+
+// The two pixels of ring i that bracket longitude phi, with linear weights.
+static void ring_bracket(i64 nside, i64 i, double phi, i64 pix[2], double w[2]) {
+  Ring R = ring_info(nside, i);
+  double t = (phi - R.phi0) * (double)R.npix / (2.0 * kPi);
+  double j0 = std::floor(t), f = t - j0;
+  pix[0] = ring_pixel_nest(nside, i, (i64)j0); pix[1] = ring_pixel_nest(nside, i, (i64)j0 + 1);
+  w[0] = 1.0 - f; w[1] = f;
+}
+
+// Interp_H weights at colatitude theta in [0, pi], longitude phi: 4 NESTED pixels
+// (a pixel may repeat) whose weights sum to 1.
+static void interp_weights(i64 nside, double theta, double phi, i64 pix[4], double w[4]) {
+  const i64 nr = 4 * nside - 1;
+  i64 lo = 0, hi = nr;                                  // last ring with theta_i <= theta (0: above ring 1)
+  while (lo < hi) { i64 mid = (lo + hi + 1) / 2; if (ring_theta(nside, mid) <= theta) lo = mid; else hi = mid - 1; }
+  const i64 ir = lo;
+  if (ir >= 1 && ir < nr) {
+    double t0 = ring_theta(nside, ir), t1 = ring_theta(nside, ir + 1);
+    double wt = (theta - t0) / (t1 - t0);
+    i64 a[2], b[2]; double wa[2], wb[2];
+    ring_bracket(nside, ir, phi, a, wa); ring_bracket(nside, ir + 1, phi, b, wb);
+    pix[0] = a[0]; pix[1] = a[1]; pix[2] = b[0]; pix[3] = b[1];
+    w[0] = (1 - wt) * wa[0]; w[1] = (1 - wt) * wa[1]; w[2] = wt * wb[0]; w[3] = wt * wb[1];
+    return;
+  }
+  // polar caps: ring 1 (or 4N-1) has 4 pixels; the pole value is their mean
+  const i64 ring = (ir == 0) ? 1 : nr;
+  double tr = ring_theta(nside, ring);
+  double wr = (ir == 0) ? theta / tr : (kPi - theta) / (kPi - tr);   // weight of the ring's bracket
+  i64 a[2]; double wa[2];
+  ring_bracket(nside, ring, phi, a, wa);
+  for (int j = 0; j < 4; ++j) { pix[j] = ring_pixel_nest(nside, ring, j); w[j] = 0.25 * (1.0 - wr); }
+  for (int q = 0; q < 2; ++q)
+    for (int j = 0; j < 4; ++j)
+      if (pix[j] == a[q]) w[j] += wr * wa[q];
+}
+
+static void dir_to_healpix_angles(const double d[3], double& theta, double& phi) {
+  const double X = d[2], Y = d[0], Z = d[1];
+  theta = std::atan2(std::sqrt(X * X + Y * Y), Z);
+  phi = std::atan2(Y, X);
+  if (phi < 0) phi += 2.0 * kPi;
+}
+
+// Bilinear image sample at (u, v): taps at pixel centres, clamped (panorama: wrapped in u).
+static void image_sample(const double* img, const ImgCam& c, double u, double v, double out[3]) {
+  const i64 W = (i64)c.W, H = (i64)c.H;
+  double x = u - 0.5, y = v - 0.5;
+  double x0 = std::floor(x), y0 = std::floor(y), fx = x - x0, fy = y - y0;
+  i64 xs[2] = {(i64)x0, (i64)x0 + 1}, ys[2] = {(i64)y0, (i64)y0 + 1};
+  for (int q = 0; q < 2; ++q) {
+    xs[q] = (c.kind == CAM_FULL) ? pmod(xs[q], W) : std::max<i64>(0, std::min<i64>(W - 1, xs[q]));
+    ys[q] = std::max<i64>(0, std::min<i64>(H - 1, ys[q]));
+  }
+  const double wx[2] = {1 - fx, fx}, wy[2] = {1 - fy, fy};
+  out[0] = out[1] = out[2] = 0;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b)
+      for (int ch = 0; ch < 3; ++ch) out[ch] += wy[a] * wx[b] * img[3 * (ys[a] * W + xs[b]) + ch];
+}
+
 extern "C" {
 
 void or_pix2vec_nest(i64 nside, i64 n, const i64* p, double* v) {
@@ -1219,6 +1363,78 @@ int or_num_threads() {
 #else
   return 1;
 #endif
+}
+
+
+// ---- resampling ----
+int or_img_to_dir(int kind, double W, double H, double fovx, double fovy, i64 n, const double* uv, double* dir,
+                  u8* valid) {
+  ImgCam c{kind, W, H, fovx, fovy};
+  for (i64 q = 0; q < n; ++q) valid[q] = img_to_dir(c, uv[2 * q], uv[2 * q + 1], dir + 3 * q);
+  return 0;
+}
+
+int or_dir_to_img(int kind, double W, double H, double fovx, double fovy, i64 n, const double* dir, double* uv,
+                  u8* valid) {
+  ImgCam c{kind, W, H, fovx, fovy};
+  for (i64 q = 0; q < n; ++q) valid[q] = dir_to_img(c, dir + 3 * q, uv[2 * q], uv[2 * q + 1]);
+  return 0;
+}
+
+void or_interp_weights(i64 nside, i64 n, const double* theta, const double* phi, i64* pix, double* w) {
+#pragma omp parallel for schedule(static)
+  for (i64 q = 0; q < n; ++q) interp_weights(nside, theta[q], phi[q], pix + 4 * q, w + 4 * q);
+}
+
+// I_C(u, v) = Interp_H(I_H, P_C(u, v)) at every pixel centre; 0 and valid = 0 outside D_C.
+void or_sphere_to_image(i64 nside, const double* map, int kind, i64 W, i64 H, double fovx, double fovy,
+                        double* img, u8* valid) {
+  ImgCam c{kind, (double)W, (double)H, fovx, fovy};
+#pragma omp parallel for schedule(static)
+  for (i64 p = 0; p < W * H; ++p) {
+    const i64 row = p / W, col = p % W;
+    double d[3];
+    img[3 * p] = img[3 * p + 1] = img[3 * p + 2] = 0;
+    valid[p] = img_to_dir(c, col + 0.5, row + 0.5, d);
+    if (!valid[p]) continue;
+    double th, ph; dir_to_healpix_angles(d, th, ph);
+    i64 pix[4]; double w[4];
+    interp_weights(nside, th, ph, pix, w);
+    for (int k = 0; k < 4; ++k)
+      for (int ch = 0; ch < 3; ++ch) img[3 * p + ch] += w[k] * map[3 * pix[k] + ch];
+  }
+}
+
+// The adjoint of or_sphere_to_image: dmap = A^T dimg (overwrites dmap).
+void or_sphere_to_image_adjoint(i64 nside, const double* dimg, int kind, i64 W, i64 H, double fovx, double fovy,
+                                double* dmap) {
+  ImgCam c{kind, (double)W, (double)H, fovx, fovy};
+  std::fill(dmap, dmap + 3 * 12 * nside * nside, 0.0);
+  for (i64 p = 0; p < W * H; ++p) {
+    const i64 row = p / W, col = p % W;
+    double d[3];
+    if (!img_to_dir(c, col + 0.5, row + 0.5, d)) continue;
+    double th, ph; dir_to_healpix_angles(d, th, ph);
+    i64 pix[4]; double w[4];
+    interp_weights(nside, th, ph, pix, w);
+    for (int k = 0; k < 4; ++k)
+      for (int ch = 0; ch < 3; ++ch) dmap[3 * pix[k] + ch] += w[k] * dimg[3 * p + ch];
+  }
+}
+
+// I_H(q) = I_C(Pi_C^{-1}(s_q)) and M_C(q) for every NESTED pixel q; 0 where M_C(q) = 0.
+void or_image_to_sphere(i64 nside, const double* img, int kind, i64 W, i64 H, double fovx, double fovy, double* map,
+                        u8* mask) {
+  ImgCam c{kind, (double)W, (double)H, fovx, fovy};
+#pragma omp parallel for schedule(static)
+  for (i64 q = 0; q < 12 * nside * nside; ++q) {
+    double v[3]; pix2vec_nest(nside, q, v);
+    const double d[3] = {v[1], v[2], v[0]};            // camera (d_x, d_y, d_z) = HEALPix (Y, Z, X)
+    double u, vv;
+    map[3 * q] = map[3 * q + 1] = map[3 * q + 2] = 0;
+    mask[q] = dir_to_img(c, d, u, vv);
+    if (mask[q]) image_sample(img, c, u, vv, map + 3 * q);
+  }
 }
 
 }  // extern "C"
