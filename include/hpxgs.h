@@ -200,6 +200,37 @@ int hpxgs_count_pairs(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
                       void* workspace, size_t workspace_bytes, uint64_t* count, int32_t* status,
                       hpxgs_stream_t stream);
 
+/* ---- sphere <-> image resampling (Eq. camera_synthesis; Eqs. supp_image_to_healpix,
+ *      supp_hssim_mask; camera models of Sec. D.1) ----
+ * Images are row-major [height, width, 3] FP32 with pixel centres at (i + 1/2, j + 1/2).
+ * HEALPix maps are NESTED [12 * 4^k, 3] FP32 in the camera frame: HEALPix (X, Y, Z)
+ * is the camera direction (d_z, d_x, d_y). Camera kinds: pinhole (FoV_x, FoV_y in
+ * (0, 180)), anisotropic equidistant fisheye (f = W / pi, H / pi, w = FoV / 180 deg,
+ * FoV in (0, 360]), panorama (HPXGS_CAM_FULL: omega = 2 pi u / W - pi, phi = pi/2 - pi v / H).
+ * The paper names the operations, not the schemes: Interp_H is HEALPix
+ * ring-bilinear interpolation (linear in longitude along the two rings that
+ * bracket the colatitude, linear in colatitude between them, and towards the
+ * mean of the first/last ring's 4 pixels above/below it); images are sampled
+ * bilinearly between pixel centres, clamped at the edges (wrapped in longitude
+ * for the panorama). Asynchronous on `stream`; HPXGS_E_INVALID_ARG for a null
+ * pointer, an order outside the stated range, a size outside [1, 65536] or a bad
+ * camera. All buffers are device memory owned by the caller. */
+
+/* I_C(u, v) = Interp_H(map, P_C(u, v)) at every pixel centre (Eq. camera_synthesis),
+ * 1 <= nside_log2 <= 13. Pixels outside the valid domain D_C get 0; `valid`
+ * ([height * width] bytes, may be NULL) gets 1 inside D_C, 0 outside. */
+int hpxgs_sphere_to_image(const float* map, int nside_log2, const hpxgs_camera* cam, int width, int height,
+                          float* image, uint8_t* valid, hpxgs_stream_t stream);
+/* The adjoint of hpxgs_sphere_to_image: dmap = A^T dimage. dmap [12 * 4^k, 3] is
+ * overwritten (zeroed, then accumulated with atomics, so the summation order varies). */
+int hpxgs_sphere_to_image_backward(const float* dimage, int nside_log2, const hpxgs_camera* cam, int width,
+                                   int height, float* dmap, hpxgs_stream_t stream);
+/* I_H(q) = I_C(Pi_C^{-1}(s_q)) for every NESTED pixel q with M_C(q) = 1, 0 elsewhere
+ * (Eq. supp_image_to_healpix), 2 <= nside_log2 <= 13; mask_bits ([12 * 4^k / 32]
+ * words, may be NULL) gets M_C (Eq. supp_hssim_mask), the same mask as hpxgs_mask_build. */
+int hpxgs_image_to_sphere(const float* image, int width, int height, const hpxgs_camera* cam, int nside_log2,
+                          float* map, uint32_t* mask_bits, hpxgs_stream_t stream);
+
 /* ---- instrumentation ---- */
 /* Stages that hpxgs_profile_arm can time. */
 #define HPXGS_STAGE_MASK 0

@@ -463,3 +463,23 @@ def image_to_sphere(nside, img, kind, W, H, fovx=360.0, fovy=None):
     lib().or_image_to_sphere(_i64(nside), _p(img), ctypes.c_int(kind), _i64(W), _i64(H), _f64(fovx),
                              _f64(fovx if fovy is None else fovy), _p(hmap), _p(m))
     return hmap, m
+
+
+def sphere_to_image_at(nside, hmap, kind, W, H, fovx, fovy, uv):
+    """sphere_to_image at image points uv (n, 2) only: values (n, 3) and validity."""
+    hmap = np.ascontiguousarray(hmap, np.float64).reshape(-1, 3)
+    uv = np.ascontiguousarray(uv, np.float64).reshape(-1, 2)
+    out = np.empty((uv.shape[0], 3)); ok = np.empty(uv.shape[0], np.uint8)
+    lib().or_sphere_to_image_at(_i64(nside), _p(hmap), ctypes.c_int(kind), _i64(W), _i64(H), _f64(fovx),
+                                _f64(fovx if fovy is None else fovy), _i64(uv.shape[0]), _p(uv), _p(out), _p(ok))
+    return out, ok
+
+
+def image_to_sphere_at(nside, img, kind, W, H, fovx, fovy, qs):
+    """image_to_sphere at NESTED pixels qs only: values (n, 3) and M_C."""
+    img = np.ascontiguousarray(img, np.float64).reshape(H, W, 3)
+    qs = np.ascontiguousarray(qs, np.int64)
+    out = np.empty((qs.size, 3)); m = np.empty(qs.size, np.uint8)
+    lib().or_image_to_sphere_at(_i64(nside), _p(img), ctypes.c_int(kind), _i64(W), _i64(H), _f64(fovx),
+                                _f64(fovx if fovy is None else fovy), _i64(qs.size), _p(qs), _p(out), _p(m))
+    return out, m

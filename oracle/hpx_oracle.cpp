@@ -1422,6 +1422,39 @@ void or_sphere_to_image_adjoint(i64 nside, const double* dimg, int kind, i64 W, 
   }
 }
 
+// or_sphere_to_image at the given image points only (for sampled checks of large images).
+void or_sphere_to_image_at(i64 nside, const double* map, int kind, i64 W, i64 H, double fovx, double fovy, i64 n,
+                           const double* uv, double* out, u8* valid) {
+  ImgCam c{kind, (double)W, (double)H, fovx, fovy};
+#pragma omp parallel for schedule(static)
+  for (i64 q = 0; q < n; ++q) {
+    double d[3];
+    out[3 * q] = out[3 * q + 1] = out[3 * q + 2] = 0;
+    valid[q] = img_to_dir(c, uv[2 * q], uv[2 * q + 1], d);
+    if (!valid[q]) continue;
+    double th, ph; dir_to_healpix_angles(d, th, ph);
+    i64 pix[4]; double w[4];
+    interp_weights(nside, th, ph, pix, w);
+    for (int k = 0; k < 4; ++k)
+      for (int ch = 0; ch < 3; ++ch) out[3 * q + ch] += w[k] * map[3 * pix[k] + ch];
+  }
+}
+
+// or_image_to_sphere at the given NESTED pixels only.
+void or_image_to_sphere_at(i64 nside, const double* img, int kind, i64 W, i64 H, double fovx, double fovy, i64 n,
+                           const i64* qs, double* out, u8* mask) {
+  ImgCam c{kind, (double)W, (double)H, fovx, fovy};
+#pragma omp parallel for schedule(static)
+  for (i64 t = 0; t < n; ++t) {
+    double v[3]; pix2vec_nest(nside, qs[t], v);
+    const double d[3] = {v[1], v[2], v[0]};
+    double u, vv;
+    out[3 * t] = out[3 * t + 1] = out[3 * t + 2] = 0;
+    mask[t] = dir_to_img(c, d, u, vv);
+    if (mask[t]) image_sample(img, c, u, vv, out + 3 * t);
+  }
+}
+
 // I_H(q) = I_C(Pi_C^{-1}(s_q)) and M_C(q) for every NESTED pixel q; 0 where M_C(q) = 0.
 void or_image_to_sphere(i64 nside, const double* img, int kind, i64 W, i64 H, double fovx, double fovy, double* map,
                         u8* mask) {

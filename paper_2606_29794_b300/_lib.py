@@ -90,6 +90,12 @@ _SIGS = {
     "hpxgs_workspace_inspect": (ctypes.c_int, [_i32, _P(View), ctypes.c_int, _P(Config), _i64, _vp,
                                                _P(WorkspaceView)]),
     "hpxgs_profile_arm": (ctypes.c_int, [ctypes.c_int, _vp, _vp]),
+    "hpxgs_sphere_to_image": (ctypes.c_int, [_vp, ctypes.c_int, _P(Camera), ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                             _vp]),
+    "hpxgs_sphere_to_image_backward": (ctypes.c_int, [_vp, ctypes.c_int, _P(Camera), ctypes.c_int, ctypes.c_int,
+                                                      _vp, _vp]),
+    "hpxgs_image_to_sphere": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _P(Camera), ctypes.c_int, _vp, _vp,
+                                             _vp]),
     "hpxgs_launch_count": (ctypes.c_uint64, []),
     "hpxgs_probe_alu_peak": (ctypes.c_int, [_P(_f64), _P(_f64), ctypes.c_void_p]),
     "hpxgs_hssim_workspace_size": (ctypes.c_int, [ctypes.c_int, _P(_sz)]),

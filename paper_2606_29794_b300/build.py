@@ -7,8 +7,8 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["geometry.cu", "raster.cu", "hssim.cu", "hssim_noalloc.cu", "probe.cu"]
-HEADERS = ["hpx_math.cuh", "internal.cuh"]
+SOURCES = ["geometry.cu", "raster.cu", "hssim.cu", "hssim_noalloc.cu", "probe.cu", "resample.cu"]
+HEADERS = ["hpx_math.cuh", "internal.cuh", "camera.cuh"]
 LIB = os.path.join(HERE, "libhpxgs.so")
 ROOT = os.path.dirname(HERE)
 

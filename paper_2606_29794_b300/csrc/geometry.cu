@@ -9,6 +9,7 @@
 
 #include "hpx_math.cuh"
 #include "internal.cuh"
+#include "camera.cuh"
 
 using namespace hpx;
 
@@ -54,35 +55,7 @@ int num_sms() {
   return n;
 }
 
-// ----------------------------------------------------------------------------
-// FoV mask. Margin >= 0 inside; the FP32 decision is re-taken in FP64 when the
-// FP32 margin is within 1e-4 of the boundary.
-// ----------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T camera_margin(int kind, T dx, T dy, T dz, T tanx, T tany, T wx, T wy) {
-  if (kind == HPXGS_CAM_PINHOLE) {
-    T mx = tanx * dz - fabs(dx), my = tany * dz - fabs(dy);
-    return mx < my ? mx : my;
-  }
-  // anisotropic equidistant fisheye: psi <= (pi/2) w_eff(gamma),
-  // w_eff = sqrt((wx cos g)^2 + (wy sin g)^2) with cos g = dx / rxy, sin g = dy / rxy
-  T rxy = sqrt(dx * dx + dy * dy);
-  T psi = atan2(rxy, dz);
-  T weff = rxy > T(0) ? sqrt(wx * wx * dx * dx + wy * wy * dy * dy) / rxy : wx;
-  return T(0.5 * kPi) * weff - psi;
-}
-
-__device__ __forceinline__ bool pixel_in_mask(const ViewParams& vp, uint32_t p) {
-  if (vp.kind == HPXGS_CAM_FULL) return true;
-  float3 h = pix2vec_f32(vp.k, p);
-  // camera direction (d_x, d_y, d_z) = HEALPix (Y, Z, X)
-  float m = camera_margin<float>(vp.kind, h.y, h.z, h.x, vp.tanx, vp.tany, vp.wx, vp.wy);
-  if (fabsf(m) > 1e-4f) return m >= 0.0f;
-  double3 hd = pix2vec_f64(vp.k, p);
-  double md = camera_margin<double>(vp.kind, hd.y, hd.z, hd.x, vp.tanx64, vp.tany64, vp.wx64, vp.wy64);
-  return md >= 0.0;
-}
-
+// FoV mask: camera_margin and pixel_in_mask live in camera.cuh.
 // One thread per pixel; a warp's 32 consecutive NESTED pixels form one mask word.
 // tile_flags (optional) gets bit 0 set for every tile with an in-mask pixel.
 __global__ void k_mask(ViewParams vp, int b, uint32_t* __restrict__ words, uint32_t* __restrict__ tile_flags) {
@@ -251,6 +224,16 @@ int make_layout(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_conf
   return HPXGS_OK;
 }
 
+void camera_params(const hpxgs_camera& cam, int k, ViewParams& p) {
+  p.k = k;
+  p.kind = cam.kind;
+  p.tanx64 = std::tan(0.5 * cam.fov_x_deg * kPi / 180.0);
+  p.tany64 = std::tan(0.5 * cam.fov_y_deg * kPi / 180.0);
+  p.wx64 = cam.fov_x_deg / 180.0;
+  p.wy64 = cam.fov_y_deg / 180.0;
+  p.tanx = (float)p.tanx64; p.tany = (float)p.tany64; p.wx = (float)p.wx64; p.wy = (float)p.wy64;
+}
+
 int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
                cudaStream_t stream, bool need_rho, ViewTable* vt) {
   if (!valid_cfg(cfg) || !views || nviews < 1 || nviews > HPXGS_MAX_VIEWS) return HPXGS_E_INVALID_ARG;
@@ -270,13 +253,7 @@ int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nvi
     for (int i = 0; i < 9; ++i) p.W[i] = hv.W[i];
     for (int i = 0; i < 3; ++i) p.b[i] = hv.b[i];
     for (int j = 0; j < 3; ++j) p.cam[j] = -(hv.W[j] * hv.b[0] + hv.W[3 + j] * hv.b[1] + hv.W[6 + j] * hv.b[2]);
-    p.k = hv.nside_log2;
-    p.kind = hv.cam.kind;
-    p.tanx64 = std::tan(0.5 * hv.cam.fov_x_deg * kPi / 180.0);
-    p.tany64 = std::tan(0.5 * hv.cam.fov_y_deg * kPi / 180.0);
-    p.wx64 = hv.cam.fov_x_deg / 180.0;
-    p.wy64 = hv.cam.fov_y_deg / 180.0;
-    p.tanx = (float)p.tanx64; p.tany = (float)p.tany64; p.wx = (float)p.wx64; p.wy = (float)p.wy64;
+    camera_params(hv.cam, hv.nside_log2, p);
     const double omega_pix = 4.0 * kPi / (12.0 * std::ldexp(1.0, 2 * p.k));
     p.blur = cfg->blur_rad2 < 0 ? (float)(0.3 * omega_pix) : cfg->blur_rad2;
     p.ntiles = 12 << (2 * (p.k - cfg->tile_level));

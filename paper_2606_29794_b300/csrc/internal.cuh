@@ -77,6 +77,8 @@ void prof_end(int stage, cudaStream_t s);
 void note_launches(int n);
 
 int make_layout(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg, int64_t cap, Layout* L);
+// Camera fields of a view (k, kind, tan(FoV/2) and FoV/180 deg in FP32 and FP64).
+void camera_params(const hpxgs_camera& cam, int k, ViewParams& p);
 int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
                cudaStream_t stream, bool need_rho, ViewTable* vt);
 int num_sms();

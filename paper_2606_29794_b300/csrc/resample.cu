@@ -1,0 +1,300 @@
+// Sphere <-> image resampling: the rendered HEALPix map to a camera image
+// (Eq. camera_synthesis) and a camera image to the HEALPix grid
+// (Eqs. supp_image_to_healpix, supp_hssim_mask), with the camera models of
+// Sec. D.1 (Eq. persp_sphere; Eqs. fish_weff, fish_sphere, imaging_region,
+// semi_axes; the omnidirectional mapping).
+//
+// The paper names the operations, not the schemes; the readings:
+//  - image samples sit at pixel centres (i + 1/2, j + 1/2);
+//  - Interp_H is HEALPix ring-bilinear interpolation: along each of the two
+//    rings that bracket the colatitude, linear in longitude between the two
+//    pixel centres that bracket it; between the rings, linear in colatitude;
+//    above the first ring (below the last) linear in colatitude to a pole
+//    value, the mean of that ring's 4 pixels;
+//  - the image is sampled bilinearly between pixel centres, clamped at the
+//    edges and, for the panorama, wrapped in longitude.
+// The map lives in the camera frame: HEALPix (X, Y, Z) = camera (d_z, d_x, d_y).
+// All three kernels are gathers or scatters bound by memory traffic: one thread
+// per output pixel, grid-stride over a grid of a few waves of the SM count.
+#include <algorithm>
+#include <cmath>
+
+#include "camera.cuh"
+#include "hpx_math.cuh"
+#include "internal.cuh"
+
+using namespace hpx;
+
+namespace hpxgs {
+namespace {
+
+constexpr int kRsThreads = 256;
+
+struct ImgCam {
+  int kind, W, H;
+  float fx, fy;      // pinhole: W / (2 tan(FoV_x / 2)), H / (2 tan(FoV_y / 2)); fisheye: W / pi, H / pi
+  float wx, wy;      // fisheye FoV / 180 deg
+};
+
+// P_C: image point (u, v) -> unit camera direction; false outside D_C.
+__device__ __forceinline__ bool img_to_dir(const ImgCam& c, float u, float v, float3& d) {
+  if (c.kind == HPXGS_CAM_FULL) {
+    float so, co, sp, cp;                         // angles in units of pi: no wide range reduction
+    sincospif(2.f * u / (float)c.W - 1.f, &so, &co);
+    sincospif(0.5f - v / (float)c.H, &sp, &cp);
+    d = make_float3(cp * so, sp, cp * co);
+    return true;
+  }
+  const float mx = (u - 0.5f * (float)c.W) / c.fx, my = (v - 0.5f * (float)c.H) / c.fy;
+  if (c.kind == HPXGS_CAM_PINHOLE) {
+    const float inv = rsqrtf(mx * mx + my * my + 1.f);
+    d = make_float3(mx * inv, my * inv, inv);
+    return true;                                  // pixel centres lie inside [0, W] x [0, H]
+  }
+  const float rm2 = mx * mx + my * my;
+  if (rm2 > 0.25f * (float)kPi * (float)kPi) return false;   // outside the ellipse a = f_x pi/2, b = f_y pi/2
+  const float rm = sqrtf(rm2);
+  if (rm == 0.f) { d = make_float3(0.f, 0.f, 1.f); return true; }
+  const float cg = mx / rm, sg = my / rm;
+  const float weff = sqrtf(c.wx * c.wx * cg * cg + c.wy * c.wy * sg * sg);
+  float sp, cp;
+  sincospif(rm * weff * (1.f / (float)kPi), &sp, &cp);
+  d = make_float3(sp * cg, sp * sg, cp);
+  return true;
+}
+
+// Pi_C^{-1} for a direction inside the camera's region: image point (u, v).
+__device__ __forceinline__ float2 dir_to_img(const ImgCam& c, float3 d) {
+  if (c.kind == HPXGS_CAM_FULL) {
+    const float om = atan2f(d.x, d.z), ph = asinf(fminf(1.f, fmaxf(-1.f, d.y)));
+    return make_float2((float)c.W * (om + (float)kPi) / (2.f * (float)kPi),
+                       (float)c.H * (0.5f * (float)kPi - ph) / (float)kPi);
+  }
+  if (c.kind == HPXGS_CAM_PINHOLE)
+    return make_float2(0.5f * (float)c.W + c.fx * d.x / d.z, 0.5f * (float)c.H + c.fy * d.y / d.z);
+  const float rxy = sqrtf(d.x * d.x + d.y * d.y);
+  if (rxy == 0.f) return make_float2(0.5f * (float)c.W, 0.5f * (float)c.H);
+  const float cg = d.x / rxy, sg = d.y / rxy;
+  const float weff = sqrtf(c.wx * c.wx * cg * cg + c.wy * c.wy * sg * sg);
+  const float rm = atan2f(rxy, d.z) / weff;
+  return make_float2(0.5f * (float)c.W + c.fx * rm * cg, 0.5f * (float)c.H + c.fy * rm * sg);
+}
+
+__device__ __forceinline__ float ring_theta(int k, int i) {
+  const RingF R = ring_f32(k, i);
+  return atan2f(R.sth, R.z);
+}
+
+// Ring i in [0, 4N - 1] with theta_i <= theta < theta_{i+1} (ring 0: the north pole),
+// from the ring's closed form in z (1 -+ z taken from sin^2 near the poles), then
+// corrected against the ring colatitudes.
+__device__ __forceinline__ int ring_above(int k, float z, float s2, float theta) {
+  const int N = 1 << k, nr = 4 * N - 1;
+  float rf;
+  if (z > 2.f / 3.f) rf = (float)N * sqrtf(3.f * s2 / (1.f + z));
+  else if (z < -2.f / 3.f) rf = 4.f * (float)N - (float)N * sqrtf(3.f * s2 / (1.f - z));
+  else rf = (float)N * (2.f - 1.5f * z);
+  int i = min(nr, max(0, (int)floorf(rf)));
+  if (i >= 1 && ring_theta(k, i) > theta) --i;
+  else if (i < nr && ring_theta(k, i + 1) <= theta) ++i;
+  return i;
+}
+
+__device__ __forceinline__ uint32_t ring_pixel_nest(int k, int i, int j, int npix) {
+  j %= npix;
+  if (j < 0) j += npix;
+  const FaceXY f = ring_to_fxy(k, i, j);
+  return fxy_to_nest(k, f.f, f.x, f.y);
+}
+
+// Interp_H weights at (theta, phi): 4 NESTED pixels (one may repeat) summing to 1.
+__device__ __forceinline__ void interp_weights(int k, float theta, float phi, float z, float s2, uint32_t pix[4],
+                                               float w[4]) {
+  const int N = 1 << k, nr = 4 * N - 1;
+  const int ir = ring_above(k, z, s2, theta);
+  struct Br { uint32_t p0, p1; float f; };
+  auto bracket = [&](int i) {
+    const RingF R = ring_f32(k, i);
+    const float t = (phi - R.phi0) * (float)R.npix * (0.5f / (float)kPi);
+    const float j0 = floorf(t);
+    return Br{ring_pixel_nest(k, i, (int)j0, R.npix), ring_pixel_nest(k, i, (int)j0 + 1, R.npix), t - j0};
+  };
+  if (ir >= 1 && ir < nr) {
+    const float t0 = ring_theta(k, ir), t1 = ring_theta(k, ir + 1);
+    const float wt = fminf(1.f, fmaxf(0.f, (theta - t0) / (t1 - t0)));
+    const Br a = bracket(ir), b = bracket(ir + 1);
+    pix[0] = a.p0; pix[1] = a.p1; pix[2] = b.p0; pix[3] = b.p1;
+    w[0] = (1.f - wt) * (1.f - a.f); w[1] = (1.f - wt) * a.f; w[2] = wt * (1.f - b.f); w[3] = wt * b.f;
+    return;
+  }
+  const int ring = ir == 0 ? 1 : nr;
+  const float tr = ring_theta(k, ring);
+  const float wr = fminf(1.f, fmaxf(0.f, ir == 0 ? theta / tr : ((float)kPi - theta) / ((float)kPi - tr)));
+  const Br a = bracket(ring);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    pix[j] = ring_pixel_nest(k, ring, j, 4);
+    w[j] = 0.25f * (1.f - wr) + (pix[j] == a.p0 ? wr * (1.f - a.f) : 0.f) + (pix[j] == a.p1 ? wr * a.f : 0.f);
+  }
+}
+
+// HEALPix angles of a camera direction: theta from atan2 (accurate at the poles).
+__device__ __forceinline__ void healpix_angles(float3 d, float& theta, float& phi, float& z, float& s2) {
+  const float X = d.z, Y = d.x;
+  z = d.y;
+  s2 = X * X + Y * Y;
+  theta = atan2f(sqrtf(s2), z);
+  phi = atan2f(Y, X);
+  if (phi < 0.f) phi += 2.f * (float)kPi;
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_sphere_to_image(const float* __restrict__ map, int k, ImgCam c,
+                                                                 float* __restrict__ img, uint8_t* __restrict__ valid) {
+  const int64_t n = (int64_t)c.W * c.H;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int row = (int)(p / c.W), col = (int)(p - (int64_t)row * c.W);
+    float3 d;
+    const bool ok = img_to_dir(c, (float)col + 0.5f, (float)row + 0.5f, d);
+    float o[3] = {0.f, 0.f, 0.f};
+    if (ok) {
+      float th, ph, z, s2;
+      healpix_angles(d, th, ph, z, s2);
+      uint32_t pix[4];
+      float w[4];
+      interp_weights(k, th, ph, z, s2, pix, w);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) o[ch] += w[q] * __ldg(map + 3 * (size_t)pix[q] + ch);
+    }
+    img[3 * p + 0] = o[0]; img[3 * p + 1] = o[1]; img[3 * p + 2] = o[2];
+    if (valid) valid[p] = ok;
+  }
+}
+
+// dmap += A^T dimg, by atomics (several image pixels share a HEALPix pixel).
+__global__ void __launch_bounds__(kRsThreads) k_sphere_to_image_bwd(const float* __restrict__ dimg, int k, ImgCam c,
+                                                                     float* __restrict__ dmap) {
+  const int64_t n = (int64_t)c.W * c.H;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int row = (int)(p / c.W), col = (int)(p - (int64_t)row * c.W);
+    float3 d;
+    if (!img_to_dir(c, (float)col + 0.5f, (float)row + 0.5f, d)) continue;
+    const float g[3] = {dimg[3 * p], dimg[3 * p + 1], dimg[3 * p + 2]};
+    if (g[0] == 0.f && g[1] == 0.f && g[2] == 0.f) continue;
+    float th, ph, z, s2;
+    healpix_angles(d, th, ph, z, s2);
+    uint32_t pix[4];
+    float w[4];
+    interp_weights(k, th, ph, z, s2, pix, w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (w[q] != 0.f)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) atomicAdd(dmap + 3 * (size_t)pix[q] + ch, w[q] * g[ch]);
+  }
+}
+
+// I_H(q) = I_C(Pi_C^{-1}(s_q)) and M_C(q) for every NESTED pixel q (0 outside M_C).
+__global__ void __launch_bounds__(kRsThreads) k_image_to_sphere(const float* __restrict__ img, ImgCam c, ViewParams vp,
+                                                                 float* __restrict__ map, uint32_t* __restrict__ words) {
+  const uint32_t npix = 12u << (2 * vp.k);                   // a multiple of 32 for k >= 2
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < npix; base += stride) {
+    const uint32_t q = base + threadIdx.x;
+    const bool inr = q < npix;
+    const bool in = inr && pixel_in_mask(vp, q);
+    float o[3] = {0.f, 0.f, 0.f};
+    if (in) {
+      const float3 h = pix2vec_f32(vp.k, q);
+      const float2 uv = dir_to_img(c, make_float3(h.y, h.z, h.x));
+      const float x = uv.x - 0.5f, y = uv.y - 0.5f;
+      const float x0 = floorf(x), y0 = floorf(y), fx = x - x0, fy = y - y0;
+      int xs[2] = {(int)x0, (int)x0 + 1}, ys[2] = {(int)y0, (int)y0 + 1};
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        if (c.kind == HPXGS_CAM_FULL) { xs[t] %= c.W; if (xs[t] < 0) xs[t] += c.W; }
+        else xs[t] = min(c.W - 1, max(0, xs[t]));
+        ys[t] = min(c.H - 1, max(0, ys[t]));
+      }
+      const float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy};
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const float* px = img + 3 * ((size_t)ys[a] * c.W + xs[b]);
+          const float ww = wy[a] * wx[b];
+          o[0] += ww * __ldg(px); o[1] += ww * __ldg(px + 1); o[2] += ww * __ldg(px + 2);
+        }
+    }
+    if (inr) { map[3 * (size_t)q] = o[0]; map[3 * (size_t)q + 1] = o[1]; map[3 * (size_t)q + 2] = o[2]; }
+    const uint32_t bits = __ballot_sync(0xffffffffu, in);
+    if (words && inr && (threadIdx.x & 31) == 0) words[q >> 5] = bits;
+  }
+}
+
+bool make_cam(const hpxgs_camera* cam, int W, int H, ImgCam& c) {
+  if (!cam || W < 1 || H < 1 || W > 65536 || H > 65536) return false;
+  c.kind = cam->kind; c.W = W; c.H = H; c.fx = c.fy = 1.f; c.wx = c.wy = 1.f;
+  if (cam->kind == HPXGS_CAM_PINHOLE) {
+    if (!(cam->fov_x_deg > 0 && cam->fov_x_deg < 180 && cam->fov_y_deg > 0 && cam->fov_y_deg < 180)) return false;
+    c.fx = (float)(W / (2.0 * std::tan(0.5 * cam->fov_x_deg * kPi / 180.0)));
+    c.fy = (float)(H / (2.0 * std::tan(0.5 * cam->fov_y_deg * kPi / 180.0)));
+  } else if (cam->kind == HPXGS_CAM_FISHEYE) {
+    if (!(cam->fov_x_deg > 0 && cam->fov_x_deg <= 360 && cam->fov_y_deg > 0 && cam->fov_y_deg <= 360)) return false;
+    c.fx = (float)(W / kPi); c.fy = (float)(H / kPi);
+    c.wx = (float)(cam->fov_x_deg / 180.0); c.wy = (float)(cam->fov_y_deg / 180.0);
+  } else if (cam->kind != HPXGS_CAM_FULL) {
+    return false;
+  }
+  return true;
+}
+
+int grid_for(int64_t n) {
+  const int64_t want = (n + kRsThreads - 1) / kRsThreads, cap = 8LL * num_sms();
+  return (int)std::max<int64_t>(1, std::min(want, cap));
+}
+
+}  // namespace
+}  // namespace hpxgs
+
+using namespace hpxgs;
+
+extern "C" int hpxgs_sphere_to_image(const float* map, int nside_log2, const hpxgs_camera* cam, int width, int height,
+                                     float* image, uint8_t* valid, hpxgs_stream_t stream) {
+  ImgCam c;
+  if (!map || !image || nside_log2 < 1 || nside_log2 > 13 || !make_cam(cam, width, height, c)) return HPXGS_E_INVALID_ARG;
+  const int64_t n = (int64_t)width * height;
+  k_sphere_to_image<<<grid_for(n), kRsThreads, 0, (cudaStream_t)stream>>>(map, nside_log2, c, image, valid);
+  note_launches(1);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+
+extern "C" int hpxgs_sphere_to_image_backward(const float* dimage, int nside_log2, const hpxgs_camera* cam, int width,
+                                              int height, float* dmap, hpxgs_stream_t stream) {
+  ImgCam c;
+  if (!dimage || !dmap || nside_log2 < 1 || nside_log2 > 13 || !make_cam(cam, width, height, c))
+    return HPXGS_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  HPXGS_CUDA_CHECK(cudaMemsetAsync(dmap, 0, sizeof(float) * 3 * (size_t)(12LL << (2 * nside_log2)), s));
+  const int64_t n = (int64_t)width * height;
+  k_sphere_to_image_bwd<<<grid_for(n), kRsThreads, 0, s>>>(dimage, nside_log2, c, dmap);
+  note_launches(1);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+
+extern "C" int hpxgs_image_to_sphere(const float* image, int width, int height, const hpxgs_camera* cam, int nside_log2,
+                                     float* map, uint32_t* mask_bits, hpxgs_stream_t stream) {
+  ImgCam c;
+  if (!image || !map || nside_log2 < 2 || nside_log2 > 13 || !make_cam(cam, width, height, c)) return HPXGS_E_INVALID_ARG;
+  ViewParams vp{};
+  camera_params(*cam, nside_log2, vp);
+  const int64_t npix = 12LL << (2 * nside_log2);
+  // the grid-stride loop keeps whole warps together: blocks of 256 over a multiple of 32 pixels
+  k_image_to_sphere<<<grid_for(npix), kRsThreads, 0, (cudaStream_t)stream>>>(image, c, vp, map, mask_bits);
+  note_launches(1);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}

@@ -1,0 +1,92 @@
+"""Sphere <-> image resampling through the C ABI (Eq. camera_synthesis;
+Eqs. supp_image_to_healpix, supp_hssim_mask): the rendered HEALPix map to a
+camera image, its adjoint, and a camera image to the HEALPix grid. Argument
+marshalling only; the work runs in libhpxgs kernels.
+
+A camera is a dict with "cam" (CAM_FULL for the panorama, CAM_PINHOLE,
+CAM_FISHEYE) and "fov_x", "fov_y" in degrees (the views of `synth` carry them).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib as L
+
+
+def _cam(cam) -> L.Camera:
+    c = L.Camera()
+    c.kind = int(cam["cam"])
+    c.fov_x_deg = float(cam.get("fov_x", 360.0))
+    fy = cam.get("fov_y")
+    c.fov_y_deg = float(c.fov_x_deg if fy is None else fy)
+    return c
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(dev):
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _f32(t):
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return t
+
+
+def sphere_to_image_raw(hmap, nside_log2, cam, width, height, with_valid=True):
+    """Image [height, width, 3] = Interp_H(hmap, P_C(u, v)) and validity [height, width] (uint8)."""
+    hmap = _f32(hmap)
+    if hmap.numel() != 3 * 12 * 4 ** nside_log2:
+        raise ValueError("map size does not match nside_log2")
+    img = torch.empty((height, width, 3), dtype=torch.float32, device=hmap.device)
+    valid = torch.empty((height, width), dtype=torch.uint8, device=hmap.device) if with_valid else None
+    c = _cam(cam)
+    L.check(L.lib().hpxgs_sphere_to_image(_ptr(hmap), nside_log2, ctypes.byref(c), width, height, _ptr(img),
+                                          _ptr(valid), _stream(hmap.device)), "sphere_to_image")
+    return img, valid
+
+
+def sphere_to_image_backward(dimage, nside_log2, cam, width, height):
+    """dL/dmap [12 * 4^k, 3] = A^T dL/dimage."""
+    dimage = _f32(dimage)
+    dmap = torch.empty((12 * 4 ** nside_log2, 3), dtype=torch.float32, device=dimage.device)
+    c = _cam(cam)
+    L.check(L.lib().hpxgs_sphere_to_image_backward(_ptr(dimage), nside_log2, ctypes.byref(c), width, height,
+                                                   _ptr(dmap), _stream(dimage.device)), "sphere_to_image_backward")
+    return dmap
+
+
+def image_to_sphere(image, cam, nside_log2, with_mask=True):
+    """HEALPix map [12 * 4^k, 3] of a camera image [height, width, 3] and the mask words of M_C."""
+    image = _f32(image)
+    height, width = image.shape[0], image.shape[1]
+    npix = 12 * 4 ** nside_log2
+    hmap = torch.empty((npix, 3), dtype=torch.float32, device=image.device)
+    words = torch.empty(npix // 32, dtype=torch.int32, device=image.device) if with_mask else None
+    c = _cam(cam)
+    L.check(L.lib().hpxgs_image_to_sphere(_ptr(image), width, height, ctypes.byref(c), nside_log2, _ptr(hmap),
+                                          _ptr(words), _stream(image.device)), "image_to_sphere")
+    return hmap, words
+
+
+class _SphereToImage(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, hmap, nside_log2, cam, width, height):
+        img, valid = sphere_to_image_raw(hmap.contiguous(), nside_log2, cam, width, height)
+        ctx.args = (nside_log2, cam, width, height)
+        ctx.mark_non_differentiable(valid)
+        return img, valid
+
+    @staticmethod
+    def backward(ctx, dimg, dvalid):
+        return sphere_to_image_backward(dimg.contiguous(), *ctx.args), None, None, None, None
+
+
+def sphere_to_image(hmap, nside_log2, cam, width, height):
+    """Differentiable in `hmap`: returns (image, valid)."""
+    return _SphereToImage.apply(hmap, nside_log2, cam, width, height)

@@ -157,3 +157,19 @@ def test_sphere_image_round_trip_is_close_at_matched_resolution():
     back, ok = O.sphere_to_image(nside, hmap, O.CAM_FULL, W, H)
     assert m.all() and ok.all()
     assert np.abs(back - img)[8:-8].max() < 0.02
+
+
+@pytest.mark.parametrize("kind,fx,fy", CAMS)
+def test_pointwise_entries_equal_whole_image_entries(kind, fx, fy):
+    nside, W, H = 8, 30, 20
+    rng = np.random.default_rng(11)
+    hmap = rng.random((12 * nside * nside, 3))
+    img, ok = O.sphere_to_image(nside, hmap, kind, W, H, fx, fy)
+    uu, vv = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    out, ok2 = O.sphere_to_image_at(nside, hmap, kind, W, H, fx, fy, np.stack([uu.ravel(), vv.ravel()], 1))
+    assert np.array_equal(ok2, ok.ravel()) and np.array_equal(out, img.reshape(-1, 3))
+    im = rng.random((H, W, 3))
+    hm, m = O.image_to_sphere(nside, im, kind, W, H, fx, fy)
+    qs = np.arange(12 * nside * nside)
+    o2, m2 = O.image_to_sphere_at(nside, im, kind, W, H, fx, fy, qs)
+    assert np.array_equal(m2, m) and np.array_equal(o2, hm)
