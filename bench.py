@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-multiview", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-resample", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=800)
     return ap.parse_args()
 
@@ -487,6 +488,46 @@ def run_large(args, dev):
     return res
 
 
+def run_resample(args, dev):
+    """Sphere <-> image resampling (Eq. camera_synthesis; Eq. supp_image_to_healpix) at matched resolutions:
+    fisheye 190 deg 1472^2 at Nside 512, pinhole 90 deg 2048^2 and a 4096 x 2048 panorama at Nside 1024.
+    Algorithmic bytes: sphere -> image writes the image (12 B/px) and validity (1 B/px) and reads the map
+    region it covers once (12 B per in-mask map pixel); the adjoint reads the image gradient and writes the
+    whole map gradient (zero fill + accumulation of the covered region); image -> sphere reads the image
+    once and writes the whole map (12 B/px) and its mask bits."""
+    import numpy as np
+    import torch
+    from paper_2606_29794_b300 import resample as RS
+    from paper_2606_29794_b300 import synth as S
+    hbm = float(peaks().get("hbm_gbs", 6400.0))
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    cases = [("fisheye190_1472x1472_nside512", {"cam": S.CAM_FISHEYE, "fov_x": 190.0, "fov_y": 190.0}, 9, 1472, 1472),
+             ("pinhole90_2048x2048_nside1024", {"cam": S.CAM_PINHOLE, "fov_x": 90.0, "fov_y": 90.0}, 10, 2048, 2048),
+             ("panorama_4096x2048_nside1024", {"cam": S.CAM_FULL, "fov_x": 360.0, "fov_y": 180.0}, 10, 4096, 2048)]
+    out = {}
+    g = torch.Generator(device=dev).manual_seed(SEED + 20)
+    for name, cam, k, W, H in cases:
+        npix = 12 * 4 ** k
+        hmap = torch.rand((npix, 3), device=dev, generator=g)
+        img = torch.rand((H, W, 3), device=dev, generator=g)
+        _, words = RS.image_to_sphere(img, cam, k)
+        n_in = int(np.unpackbits(words.cpu().numpy().view(np.uint8)).sum())
+        ops = {
+            "sphere_to_image": (lambda: RS.sphere_to_image_raw(hmap, k, cam, W, H), 13 * W * H + 12 * n_in),
+            "sphere_to_image_backward": (lambda: RS.sphere_to_image_backward(img, k, cam, W, H), 12 * W * H + 12 * npix + 12 * n_in),
+            "image_to_sphere": (lambda: RS.image_to_sphere(img, cam, k), 12 * W * H + 12 * npix + npix // 8),
+        }
+        res = {"in_mask_map_px": n_in, "image_px": W * H}
+        for op, (fn, nbytes) in ops.items():
+            for _ in range(3):
+                fn()
+            ms = _time_replays(fn, max(5, args.steps), dev, flush)
+            gbs = nbytes / (ms * 1e-3) / 1e9
+            res[op] = {"ms": round(ms, 4), "bytes": int(nbytes), "gbs": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 3)}
+        out[name] = res
+    return out
+
+
 # ----------------------------------------------------------------------------- oracle
 def oracle_sample(frac, seed=0, with_bwd=True):
     """Time the FP64 oracle on a random `frac` of the active tiles of the workload.
@@ -584,6 +625,8 @@ def main():
     if rank == 0 and ws_n == 1:
         import torch
         dev = torch.device("cuda", local)
+        if not args.no_resample:
+            res["resample"] = run_resample(args, dev)
         if not args.no_multiview:
             res["multiview"] = run_multiview(args, dev)
         if not args.no_large:
