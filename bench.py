@@ -460,16 +460,19 @@ def run_large(args, dev):
     import torch
     from paper_2606_29794_b300 import raster as R
     from paper_2606_29794_b300 import synth as S
-    torch.cuda.reset_peak_memory_stats(dev)
     sc = S.make_scene(6_000_000, 3, seed=SEED + 8, logscale_mu=-3.5, logscale_sd=0.7)
     tgt = S.perturb_scene(sc, SEED + 9)
     view = S.make_view(11)
     params = _tensors(sc, dev)
     with torch.no_grad():
-        tout, _ = R.Rasterizer().forward_raw(*_tensors(tgt, dev), 3, [view])
+        tparams = _tensors(tgt, dev)
+        tout, tstate = R.Rasterizer().forward_raw(*tparams, 3, [view])
     targets = tout["maps"].clone()
-    del tout
+    del tout, tstate, tparams
+    torch.cuda.synchronize()
     torch.cuda.empty_cache()
+    torch.cuda.reset_peak_memory_stats(dev)
+    base = torch.cuda.memory_allocated(dev)                     # scene parameters and targets
     step = R.GraphStep(params, 3, [view], targets, R.Rasterizer())
     for _ in range(max(1, args.warmup)):
         step.replay()
@@ -477,11 +480,19 @@ def run_large(args, dev):
     ms = _time_replays(step.replay, max(3, args.steps // 2), dev, flush)
     npx = 12 * 4 ** 11
     peak = torch.cuda.max_memory_allocated(dev)
+    wv = R.workspace_view(step.rast, step.state)
+    n_eval = int(R.device_array(wv.n_eval, 1, torch.int64).item())
+    n_pairs = int(R.device_array(wv.n_pairs, 1, torch.int32).item()) & 0xffffffff
     res = {"workload": "Nside 2048 full sphere (50,331,648 px), 6M SH3 Gaussians, fwd+L1/HSSIM+bwd",
            "ms_per_step": round(ms, 3), "mpix_per_s": round(npx / (ms * 1e-3) / 1e6, 1),
-           "pair_capacity": int(step.rast.capacity), "peak_gpu_bytes": int(peak),
-           "per_pixel_state_bytes": 8,
-           "blend_history_estimate_bytes": int(step.rast.capacity / 1.25 * 16),
+           "pairs": n_pairs, "pair_capacity": int(step.rast.capacity), "evals": n_eval,
+           "step_workspace_bytes": int(step.state["nb"]),
+           "peak_gpu_bytes_above_inputs": int(peak - base),
+           "peak_note": "includes the eager warm-up steps GraphStep runs before capture and the graph's own pool",
+           "per_pixel_state_bytes": 8, "per_pixel_state_total_bytes": 8 * npx,
+           "blend_history_estimate_bytes": 8 * n_eval,
+           "blend_history_note": "alpha and T per processed (pixel, entry) pair, the least a backward without "
+                                 "recomputation would keep",
            "status": int(step.status.item())}
     del step
     torch.cuda.empty_cache()
