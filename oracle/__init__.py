@@ -55,6 +55,9 @@ def lib():
         _lib.or_tile_lists.restype = ctypes.c_int64
         _lib.or_tile_lists_bruteforce.restype = ctypes.c_int64
         _lib.or_tile_lists_subset.restype = ctypes.c_int64
+        _lib.or_tile_lists_nested.restype = ctypes.c_int64
+        _lib.or_query_disc_nested.restype = ctypes.c_int64
+        _lib.or_pixrad.restype = ctypes.c_double
         _lib.or_hssim_loss.restype = ctypes.c_double
         _lib.or_num_threads.restype = ctypes.c_int
     return _lib
@@ -483,3 +486,40 @@ def image_to_sphere_at(nside, img, kind, W, H, fovx, fovy, qs):
     lib().or_image_to_sphere_at(_i64(nside), _p(img), ctypes.c_int(kind), _i64(W), _i64(H), _f64(fovx),
                                 _f64(fovx if fovy is None else fovy), _i64(qs.size), _p(qs), _p(out), _p(m))
     return out, m
+
+
+
+# ---------------------------------------------------------------------------
+# NESTED quadtree tile query (Algorithm 2)
+# ---------------------------------------------------------------------------
+
+def pixrad(o: int) -> float:
+    """PixRad(o): the largest node-centre-to-boundary angle at order o, rounded up to 2^-20."""
+    return lib().or_pixrad(ctypes.c_int(o))
+
+
+def query_disc_nested(kt, log2f, g, rs):
+    """Tiles (order kt) of one disc (unit centre g, radius rs) by Algorithm 2 with refinement 2^log2f."""
+    g = np.ascontiguousarray(g, np.float64)
+    out = np.empty(1 << 16, np.int64)
+    n = lib().or_query_disc_nested(ctypes.c_int(kt), ctypes.c_int(log2f), _p(g), _f64(rs), _p(out), _i64(out.size))
+    if n > out.size:
+        out = np.empty(n, np.int64)
+        lib().or_query_disc_nested(ctypes.c_int(kt), ctypes.c_int(log2f), _p(g), _f64(rs), _p(out), _i64(out.size))
+    return out[:n].copy()
+
+
+def tile_lists_nested(k, b, log2f, g, rs, valid, dbits, active):
+    """CSR lists like tile_lists, with Algorithm 2 (refinement 2^log2f) as the query."""
+    g = np.ascontiguousarray(g, np.float64); rs = np.ascontiguousarray(rs, np.float64)
+    valid = np.ascontiguousarray(valid, np.int32); dbits = np.ascontiguousarray(dbits, np.uint32)
+    active = np.ascontiguousarray(active, np.uint8)
+    P = rs.size
+    nt = 12 * 4 ** (k - b)
+    start = np.empty(nt + 1, np.int64)
+    m = lib().or_tile_lists_nested(ctypes.c_int(k), ctypes.c_int(b), ctypes.c_int(log2f), _i64(P), _p(g), _p(rs),
+                                   _p(valid), _p(dbits), _p(active), _p(start), None)
+    ids = np.empty(m, np.int64)
+    lib().or_tile_lists_nested(ctypes.c_int(k), ctypes.c_int(b), ctypes.c_int(log2f), _i64(P), _p(g), _p(rs),
+                               _p(valid), _p(dbits), _p(active), None, _p(ids))
+    return start, ids

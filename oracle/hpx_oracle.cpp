@@ -25,6 +25,8 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <vector>
 #ifdef _OPENMP
@@ -757,6 +759,83 @@ static double ssim_local(const Window& W, const double* I, const double* Gt, int
 // ===========================================================================
 
 // ===========================================================================
+// NESTED quadtree tile query (Algorithm 2; Sec. 3.3, "NESTED Quadtree
+// Traversal"). A depth-first search from the 12 base pixels: each node (p, o)
+// is classified by the haversine distance d from the disc centre to the node
+// centre against r_s and PixRad(o): zone 0 (d > r_s + PixRad, pruned), 3 (fully
+// inside, d + PixRad <= r_s), 2 (centre inside, d <= r_s), 1 (partial). A node of
+// zone >= 2 at or below the tile order adds its tile; otherwise it is refined
+// down to k_max = tile order + log2 f, where a zone-1 node adds its tile.
+// Reading (the paper does not define PixRad): the largest angle from a node
+// centre to its boundary over all nodes of order o, the boundary sampled at 9
+// points along each edge (corners included), rounded up to 2^-20 rad.
+// ===========================================================================
+
+static double angle_between(const double a[3], const double b[3]) {
+  const double cx = a[1] * b[2] - a[2] * b[1], cy = a[2] * b[0] - a[0] * b[2], cz = a[0] * b[1] - a[1] * b[0];
+  return std::atan2(std::sqrt(cx * cx + cy * cy + cz * cz), a[0] * b[0] + a[1] * b[1] + a[2] * b[2]);
+}
+
+static double pixrad_order(int o) {
+  static std::mutex mu;
+  static std::map<int, double> cache;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(o);
+    if (it != cache.end()) return it->second;
+  }
+  const i64 nside = 1LL << o, npix = 12 * nside * nside;
+  const double N = (double)nside;
+  double mx = 0.0;
+#pragma omp parallel for reduction(max : mx) schedule(static)
+  for (i64 p = 0; p < npix; ++p) {
+    XYF c = nest2xyf(nside, p);
+    double ctr[3]; pix2vec_nest(nside, p, ctr);
+    for (int t = 0; t <= 8; ++t) {
+      const double s = t / 8.0;
+      const double uv[4][2] = {{c.x + s, (double)c.y}, {c.x + s, c.y + 1.0}, {(double)c.x, c.y + s}, {c.x + 1.0, c.y + s}};
+      for (int e = 0; e < 4; ++e) {
+        double q[3]; face_uv2vec(c.f, uv[e][0] / N, uv[e][1] / N, q);
+        mx = std::max(mx, angle_between(ctr, q));
+      }
+    }
+  }
+  const double r = std::ceil(mx * 1048576.0) / 1048576.0;
+  std::lock_guard<std::mutex> lk(mu);
+  cache[o] = r;
+  return r;
+}
+
+static double haversine(double lon1, double lat1, double lon2, double lat2) {
+  const double a = std::sin(0.5 * (lat2 - lat1)), b = std::sin(0.5 * (lon2 - lon1));
+  const double h = a * a + std::cos(lat1) * std::cos(lat2) * b * b;
+  return 2.0 * std::asin(std::min(1.0, std::sqrt(h)));
+}
+
+// Tiles at order k touched by the disc (centre g, radius rs) with refinement down to kmax.
+static void query_disc_nested(int k, int kmax, const double g[3], double rs, std::vector<i64>& tiles) {
+  const double lon = std::atan2(g[1], g[0]), lat = std::atan2(g[2], std::sqrt(g[0] * g[0] + g[1] * g[1]));
+  struct Node { i64 p; int o; };
+  std::vector<Node> stack;
+  for (i64 p = 0; p < 12; ++p) stack.push_back({p, 0});
+  tiles.clear();
+  while (!stack.empty()) {
+    const Node nd = stack.back();
+    stack.pop_back();
+    double z, sth, ph; pix2zphi_nest(1LL << nd.o, nd.p, z, sth, ph, nullptr);
+    const double d = haversine(lon, lat, ph, std::atan2(z, sth));
+    const double pr = pixrad_order(nd.o);
+    const int zone = d > rs + pr ? 0 : (d + pr <= rs ? 3 : (d <= rs ? 2 : 1));
+    if (zone == 0) continue;
+    if (zone >= 2 && nd.o >= k) tiles.push_back(nd.p >> (2 * (nd.o - k)));
+    else if (nd.o < kmax) for (i64 c = 0; c < 4; ++c) stack.push_back({4 * nd.p + c, nd.o + 1});
+    else tiles.push_back(nd.p >> (2 * (nd.o - k)));
+  }
+  std::sort(tiles.begin(), tiles.end());
+  tiles.erase(std::unique(tiles.begin(), tiles.end()), tiles.end());
+}
+
+// ===========================================================================
 // Sphere <-> image resampling: the rendered map to a camera image
 // (Eq. camera_synthesis) and a camera image to the HEALPix grid
 // (Eqs. supp_image_to_healpix, supp_hssim_mask), with the camera models of
@@ -1468,6 +1547,51 @@ void or_image_to_sphere(i64 nside, const double* img, int kind, i64 W, i64 H, do
     mask[q] = dir_to_img(c, d, u, vv);
     if (mask[q]) image_sample(img, c, u, vv, map + 3 * q);
   }
+}
+
+
+// ---- NESTED quadtree query (Algorithm 2) ----
+double or_pixrad(int o) { return pixrad_order(o); }
+
+// Tiles (order k - b) of one disc by Algorithm 2 with refinement f; returns the count.
+i64 or_query_disc_nested(int kt, int log2f, const double* g, double rs, i64* out, i64 cap) {
+  std::vector<i64> t;
+  query_disc_nested(kt, kt + log2f, g, rs, t);
+  for (i64 i = 0; i < (i64)t.size() && i < cap; ++i) out[i] = t[i];
+  return (i64)t.size();
+}
+
+// Lists as or_tile_lists but with Algorithm 2 (refinement 2^log2f) as the query:
+// tiles without an in-mask pixel dropped, each list in (depth bits, id) order.
+i64 or_tile_lists_nested(int k, int b, int log2f, i64 P, const double* g, const double* rs, const int* valid,
+                         const u32* depth_bits, const u8* active, i64* start, i64* ids) {
+  const int kt = k - b;
+  const i64 ntile = 12LL << (2 * kt);
+  pixrad_order(kt + log2f);                                  // fill the cache before the parallel region
+  for (int o = 0; o <= kt + log2f; ++o) pixrad_order(o);
+  std::vector<std::vector<i64>> per(P);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (i64 i = 0; i < P; ++i) {
+    if (!valid[i]) continue;
+    std::vector<i64> t;
+    query_disc_nested(kt, kt + log2f, g + 3 * i, rs[i], t);
+    for (i64 x : t) if (active[x]) per[i].push_back(x);
+  }
+  struct Pair { i64 tile; u32 depth; i64 id; };
+  std::vector<Pair> pairs;
+  for (i64 i = 0; i < P; ++i) for (i64 t : per[i]) pairs.push_back({t, depth_bits[i], i});
+  std::stable_sort(pairs.begin(), pairs.end(), [](const Pair& a, const Pair& c) {
+    if (a.tile != c.tile) return a.tile < c.tile;
+    if (a.depth != c.depth) return a.depth < c.depth;
+    return a.id < c.id;
+  });
+  if (start) {
+    std::fill(start, start + ntile + 1, 0);
+    for (auto& q : pairs) start[q.tile + 1]++;
+    for (i64 t = 0; t < ntile; ++t) start[t + 1] += start[t];
+  }
+  if (ids) for (size_t q = 0; q < pairs.size(); ++q) ids[q] = pairs[q].id;
+  return (i64)pairs.size();
 }
 
 }  // extern "C"
