@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-resample", action="store_true")
+    ap.add_argument("--no-query-compare", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=800)
     return ap.parse_args()
 
@@ -539,6 +540,60 @@ def run_resample(args, dev):
     return out
 
 
+def run_query_compare(args, dev):
+    """Tile query variants on the training-step workload (Sec. 3.3): RING (Algorithm 3 at the
+    tile order, the default) against the NESTED quadtree search (Algorithm 2) refined x1, x2, x4.
+    Both list every tile the cutoff ellipse reaches, so the step computes the same maps; reported:
+    the query stages (count + emit, CUDA events) and the whole step (graph replays)."""
+    import numpy as np
+    import torch
+    from paper_2606_29794_b300 import _lib as L
+    from paper_2606_29794_b300 import raster as R
+    from paper_2606_29794_b300 import synth as S
+    lib = L.lib()
+    sc = S.make_scene(P_GAUSS, 3, seed=SEED)
+    view = S.make_view(K_ORDER, S.CAM_FISHEYE, FOV)
+    params = _tensors(sc, dev)
+    with torch.no_grad():
+        G = R.Rasterizer(tile_level=4).forward_raw(*_tensors(S.perturb_scene(sc, SEED + 1), dev), 3, [view])[0]["maps"].clone()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    modes = [("ring", dict(query=L.QUERY_RING)), ("nested_x1", dict(query=L.QUERY_NESTED, query_log2f=0)),
+             ("nested_x2", dict(query=L.QUERY_NESTED, query_log2f=1)), ("nested_x4", dict(query=L.QUERY_NESTED, query_log2f=2))]
+    out = {}
+    for name, kw in modes:
+        rast = R.Rasterizer(tile_level=4, **kw)
+        rast.prepare([view])
+        qs = []
+        for rep in range(6):
+            flush.zero_()
+            ev = {}
+            for st in ("tile_count", "tile_emit"):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream); b.record(stream)
+                L.check(lib.hpxgs_profile_arm(L.STAGES.index(st), ctypes.c_void_p(a.cuda_event), ctypes.c_void_p(b.cuda_event)), "arm")
+                ev[st] = (a, b)
+            o, _ = rast.forward_raw(*params, 3, [view])
+            torch.cuda.synchronize()
+            if rep:
+                qs.append(sum(a.elapsed_time(b) for a, b in ev.values()))
+        wv_pairs = None
+        step = R.GraphStep(params, 3, [view], G, rast)
+        for _ in range(3):
+            step.replay()
+        ms = _time_replays(step.replay, max(5, args.steps // 2), dev, flush)
+        wv = R.workspace_view(rast, step.state)
+        wv_pairs = int(R.device_array(wv.n_pairs, 1, torch.int32).item())
+        out[name] = {"query_ms": round(float(np.mean(qs)), 4), "step_ms": round(ms, 4), "pairs": wv_pairs}
+        del step
+        torch.cuda.empty_cache()
+    for name in out:
+        if name != "ring":
+            out[name]["query_time_vs_ring"] = round(out[name]["query_ms"] / out["ring"]["query_ms"], 2)
+    out["paper_claim"] = "RING about 1.7x faster than NESTED (Sec. 3.3, Table ablation: R(x4) 28.2 min vs D(x4) 49.1 min)"
+    return out
+
+
 # ----------------------------------------------------------------------------- oracle
 def oracle_sample(frac, seed=0, with_bwd=True):
     """Time the FP64 oracle on a random `frac` of the active tiles of the workload.
@@ -638,6 +693,8 @@ def main():
         dev = torch.device("cuda", local)
         if not args.no_resample:
             res["resample"] = run_resample(args, dev)
+        if not args.no_query_compare:
+            res["tile_query"] = run_query_compare(args, dev)
         if not args.no_multiview:
             res["multiview"] = run_multiview(args, dev)
         if not args.no_large:

@@ -103,7 +103,16 @@ typedef struct {
   int32_t fwd_ppt;
   int32_t bwd_ppt;
   int32_t blocks_per_sm;
+  /* tile query (Sec. 3.3): HPXGS_QUERY_RING (default; Algorithm 3 at the tile order
+   * with the exact membership test) or HPXGS_QUERY_NESTED (Algorithm 2, the
+   * quadtree search refined down to tile order + query_log2f, 0..3). Both list
+   * every tile the cutoff ellipse can reach, so the maps do not depend on it. */
+  int32_t query;
+  int32_t query_log2f;
 } hpxgs_config;
+
+#define HPXGS_QUERY_RING 0
+#define HPXGS_QUERY_NESTED 1
 
 /* Human-readable name of a status code. */
 const char* hpxgs_strerror(int code);
@@ -127,6 +136,11 @@ int hpxgs_nside_for_image(int kind, double W, double H, double fov_x_deg, double
  * SYNCHRONISES `stream` the first time a pair (k, b) is seen; returns
  * HPXGS_E_CAPTURE if that first time happens inside stream capture. */
 int hpxgs_tile_rho(int k, int b, double* rho, hpxgs_stream_t stream);
+/* PixRad(o) of the NESTED tile query (Algorithm 2), 0 <= o <= 15: the largest angle from a
+ * node centre to its boundary at order o (9 samples per edge, corners included),
+ * rounded up to 2^-20 rad. Cached per order; the first call for an order
+ * synchronises the stream and returns HPXGS_E_CAPTURE inside stream capture. */
+int hpxgs_pixrad(int o, double* out, hpxgs_stream_t stream);
 
 /* Fill the rho cache for every (view order, tile_level) pair of `views`.
  * Call once before capturing forward/backward calls into a CUDA graph. */

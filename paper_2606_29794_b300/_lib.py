@@ -42,7 +42,8 @@ class Config(ctypes.Structure):
     _fields_ = [("tile_level", ctypes.c_int32), ("eps_T", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("cutoff_m", ctypes.c_float), ("blur_rad2", ctypes.c_float), ("near_plane", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("lambda_ssim", ctypes.c_float), ("write_outside", ctypes.c_int32),
-                ("fwd_ppt", ctypes.c_int32), ("bwd_ppt", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+                ("fwd_ppt", ctypes.c_int32), ("bwd_ppt", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("query", ctypes.c_int32), ("query_log2f", ctypes.c_int32)]
 
 
 class WorkspaceView(ctypes.Structure):
@@ -65,6 +66,7 @@ _vp, _i32, _i64, _sz, _f32, _f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int
 # FP32 work per (pixel, entry) pair of the blend kernels (the HPXGS_FLOPS_* and
 # HPXGS_MUFU_* values of include/hpxgs.h; a test checks they agree).
 FLOPS_EVAL, FLOPS_FWD_CONTRIB, FLOPS_BWD_CONTRIB = 40, 13, 83
+QUERY_RING, QUERY_NESTED = 0, 1
 MUFU_FWD_CONTRIB, MUFU_BWD_CONTRIB = 1, 2
 
 _SIGS = {
@@ -73,6 +75,7 @@ _SIGS = {
     "hpxgs_config_default": (None, [_P(Config)]),
     "hpxgs_nside_for_image": (ctypes.c_int, [ctypes.c_int, _f64, _f64, _f64, _f64, _P(_f64), _P(ctypes.c_int),
                                              _P(ctypes.c_int), _P(ctypes.c_int)]),
+    "hpxgs_pixrad": (ctypes.c_int, [ctypes.c_int, _P(_f64), ctypes.c_void_p]),
     "hpxgs_tile_rho": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P(_f64), _vp]),
     "hpxgs_prepare": (ctypes.c_int, [_P(View), ctypes.c_int, _P(Config), _vp]),
     "hpxgs_mask_build": (ctypes.c_int, [_P(View), _P(Config), _vp, _vp]),

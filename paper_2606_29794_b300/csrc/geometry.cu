@@ -1,5 +1,6 @@
 // Host API basics, FoV masks (Sec. 3.1, Sec. D.1), HEALPix batch utilities,
 // the tile radius rho(k, b) and the workspace layout of the rasterizer.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <atomic>
@@ -118,6 +119,59 @@ static bool stream_capturing(cudaStream_t s) {
 // g_rho_mu, so no two calls use the word at the same time.
 static __device__ unsigned long long d_mindot;
 
+// PixRad(o): per node, the largest angle from its centre to 36 boundary points (9 per
+// edge, corners included), maximised over nodes with an atomic on the double's bits.
+static std::mutex g_pixrad_mu;
+static std::map<int, double> g_pixrad;
+static __device__ unsigned long long d_maxang;
+
+__global__ void k_pixrad_max(int o, unsigned long long* out) {
+  const uint32_t nside = 1u << o, npix = 12u * nside * nside;
+  const double iN = 1.0 / (double)nside;
+  double mx = 0.0;
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+    const FaceXY c = nest_to_fxy(o, p);
+    const double3 a = pix2vec_f64(o, p);
+    for (int t = 0; t <= 8; ++t) {
+      const double sft = t / 8.0;
+      const double uu[4] = {c.x + sft, c.x + sft, (double)c.x, c.x + 1.0};
+      const double vv[4] = {(double)c.y, c.y + 1.0, c.y + sft, c.y + sft};
+      for (int e = 0; e < 4; ++e) {
+        const double3 q = face_uv_vec_f64(c.f, uu[e] * iN, vv[e] * iN);
+        const double cx = a.y * q.z - a.z * q.y, cy = a.z * q.x - a.x * q.z, cz = a.x * q.y - a.y * q.x;
+        mx = fmax(mx, atan2(sqrt(cx * cx + cy * cy + cz * cz), a.x * q.x + a.y * q.y + a.z * q.z));
+      }
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+int pixrad(int o, double* out, cudaStream_t s) {
+  if (o < 0 || o > 15) return HPXGS_E_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_pixrad_mu);
+  auto it = g_pixrad.find(o);
+  if (it != g_pixrad.end()) { *out = it->second; return HPXGS_OK; }
+  if (stream_capturing(s)) return HPXGS_E_CAPTURE;
+  unsigned long long* dptr = nullptr;
+  HPXGS_CUDA_CHECK(cudaGetSymbolAddress((void**)&dptr, d_maxang));
+  HPXGS_CUDA_CHECK(cudaMemsetAsync(dptr, 0, sizeof(unsigned long long), s));
+  const long long npix = 12LL << (2 * o);
+  const int grid = (int)std::min<long long>((npix + 255) / 256, 8LL * num_sms());
+  k_pixrad_max<<<grid, 256, 0, s>>>(o, dptr);
+  note_launches(1);
+  HPXGS_LAUNCH_CHECK();
+  unsigned long long res = 0;
+  HPXGS_CUDA_CHECK(cudaMemcpyAsync(&res, dptr, sizeof(res), cudaMemcpyDeviceToHost, s));
+  HPXGS_CUDA_CHECK(cudaStreamSynchronize(s));
+  double mx = 0;
+  std::memcpy(&mx, &res, sizeof(mx));
+  const double r = std::ceil(mx * 1048576.0) / 1048576.0;
+  g_pixrad[o] = r;
+  *out = r;
+  return HPXGS_OK;
+}
+
 int tile_rho(int k, int b, double* rho, cudaStream_t s) {
   if (k < b || b < 0 || k > 13) return HPXGS_E_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_rho_mu);
@@ -169,7 +223,9 @@ static bool valid_ppt(int v) { return v == 0 || v == 1 || v == 2 || v == 4 || v 
 static bool valid_cfg(const hpxgs_config* c) {
   return c && c->tile_level >= 3 && c->tile_level <= 5 && c->eps_T >= 0 && c->eps_T < 1 &&
          c->alpha_max > 0 && c->alpha_max < 1 && c->cutoff_m > 0 && c->near_plane >= 0 &&
-         valid_ppt(c->fwd_ppt) && valid_ppt(c->bwd_ppt) && c->blocks_per_sm >= 0 && c->blocks_per_sm <= 64;
+         valid_ppt(c->fwd_ppt) && valid_ppt(c->bwd_ppt) && c->blocks_per_sm >= 0 && c->blocks_per_sm <= 64 &&
+         (c->query == HPXGS_QUERY_RING || c->query == HPXGS_QUERY_NESTED) && c->query_log2f >= 0 &&
+         c->query_log2f <= 3;
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -273,13 +329,38 @@ int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nvi
     if (hv.cam.kind == HPXGS_CAM_PINHOLE) psi_max = std::atan(std::sqrt(p.tanx64 * p.tanx64 + p.tany64 * p.tany64));
     else if (hv.cam.kind == HPXGS_CAM_FISHEYE) psi_max = 0.5 * kPi * std::fmax(p.wx64, p.wy64);
     p.rho32 = (float)p.rho;
-    const double cull = psi_max + 2.0 * p.rho + 1e-5;
+    // the NESTED query lists a tile from a node within r_s + PixRad(k_max) of the
+    // Gaussian, the node lies within PixRad(k_t) of the tile centre, and an in-mask
+    // pixel within rho of it: the cap grows by those radii instead of 2 rho
+    double reach = 2.0 * p.rho;
+    if (need_rho && cfg->query == HPXGS_QUERY_NESTED) {
+      double a = 0, c = 0;
+      const int kt = p.k - cfg->tile_level;
+      int rc2 = pixrad(kt, &a, stream);
+      if (rc2 == HPXGS_OK) rc2 = pixrad(kt + cfg->query_log2f, &c, stream);
+      if (rc2 != HPXGS_OK) return rc2;
+      reach = p.rho + a + c;
+    }
+    const double cull = psi_max + reach + 1e-5;
     p.fov_cull = (need_rho && psi_max >= 0.0 && cull < kPi) ? (float)cull : -1.0f;
     tile_base += p.ntiles;
     pix_base += 12LL << (2 * p.k);
   }
   vt->total_tiles = (int)tile_base;
   vt->total_pix = pix_base;
+  vt->query = cfg->query;
+  vt->log2f = cfg->query_log2f;
+  for (int o = 0; o < 16; ++o) { vt->pixrad32[o] = 0.f; vt->pixrad64[o] = 0.0; }
+  if (need_rho && cfg->query == HPXGS_QUERY_NESTED) {
+    int omax = 0;
+    for (int v = 0; v < nviews; ++v) omax = std::max(omax, views[v].nside_log2 - cfg->tile_level + cfg->query_log2f);
+    if (omax > 11) return HPXGS_E_INVALID_ARG;              // the quadtree search stops at order 11
+    for (int o = 0; o <= omax; ++o) {
+      int rc2 = pixrad(o, &vt->pixrad64[o], stream);
+      if (rc2 != HPXGS_OK) return rc2;
+      vt->pixrad32[o] = (float)vt->pixrad64[o];
+    }
+  }
   return HPXGS_OK;
 }
 
@@ -360,6 +441,8 @@ void hpxgs_config_default(hpxgs_config* c) {
   c->fwd_ppt = 0;
   c->bwd_ppt = 0;
   c->blocks_per_sm = 0;
+  c->query = HPXGS_QUERY_RING;
+  c->query_log2f = 2;
 }
 
 int hpxgs_nside_for_image(int kind, double W, double H, double fovx, double fovy, double* nstar, int* k,
@@ -390,6 +473,11 @@ int hpxgs_profile_arm(int stage, void* start_event, void* stop_event) {
 }
 
 uint64_t hpxgs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int hpxgs_pixrad(int o, double* out, hpxgs_stream_t stream) {
+  if (!out) return HPXGS_E_INVALID_ARG;
+  return pixrad(o, out, (cudaStream_t)stream);
+}
 
 int hpxgs_tile_rho(int k, int b, double* rho, hpxgs_stream_t stream) {
   if (!rho) return HPXGS_E_INVALID_ARG;

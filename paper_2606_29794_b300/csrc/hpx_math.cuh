@@ -52,6 +52,22 @@ __host__ __device__ __forceinline__ int face_jpll(int f) {
   return ((f >> 2) == 1) ? 2 * (f & 3) : 2 * (f & 3) + 1;
 }
 
+// Point of face f at continuous face coordinates (u, v) in [0, 1]^2 (x / Nside,
+// y / Nside), FP64: ring coordinate j = row + 2 - u - v (units of Nside); polar caps
+// z = +-(1 - j'^2 / 3) with j' the distance to the pole in rings, longitude
+// (pi/4)(jpll + (u - v) / j'); the belt z = (2 - j) 2/3, longitude (pi/4)(jpll + u - v).
+__device__ __forceinline__ double3 face_uv_vec_f64(int f, double u, double v) {
+  const double jr = (double)((f >> 2) + 2) - u - v;
+  double z, sth, nr;
+  if (jr < 1.0) { nr = jr; const double t = nr * nr / 3.0; z = 1.0 - t; sth = sqrt(t * (2.0 - t)); }
+  else if (jr > 3.0) { nr = 4.0 - jr; const double t = nr * nr / 3.0; z = t - 1.0; sth = sqrt(t * (2.0 - t)); }
+  else { nr = 1.0; z = (2.0 - jr) * (2.0 / 3.0); sth = sqrt((1.0 - z) * (1.0 + z)); }
+  const double phi = nr > 0.0 ? 0.25 * kPi * ((double)face_jpll(f) + (u - v) / nr) : 0.0;
+  double sp, cp;
+  sincos(phi, &sp, &cp);
+  return make_double3(sth * cp, sth * sp, z);
+}
+
 // Pixel centre of NESTED p at order k, FP32, HEALPix frame.
 __device__ __forceinline__ float3 pix2vec_f32(int k, uint32_t p) {
   const int N = 1 << k;

@@ -38,7 +38,10 @@ struct ViewTable {
   float bg[3];
   int write_outside;
   int total_tiles;
-  int pad;
+  int query;           // HPXGS_QUERY_*
+  int log2f;           // NESTED query: refinement below the tile order
+  float pixrad32[16];  // NESTED query: PixRad(o), o = 0 .. deepest order used
+  double pixrad64[16];
   int64_t total_pix;
   ViewParams v[HPXGS_MAX_VIEWS];
 };
@@ -77,6 +80,10 @@ void prof_end(int stage, cudaStream_t s);
 void note_launches(int n);
 
 int make_layout(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg, int64_t cap, Layout* L);
+// PixRad(o) of the NESTED query: the largest angle from a node centre to its
+// boundary at order o (9 samples per edge), rounded up to 2^-20; cached per order.
+// The first call for an order synchronises the stream (HPXGS_E_CAPTURE in capture).
+int pixrad(int o, double* out, cudaStream_t s);
 // Camera fields of a view (k, kind, tan(FoV/2) and FoV/180 deg in FP32 and FP64).
 void camera_params(const hpxgs_camera& cam, int k, ViewParams& p);
 int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,

@@ -653,6 +653,90 @@ __global__ void k_ranges(const uint32_t* __restrict__ tiles, const uint32_t* n_p
 }
 
 // ----------------------------------------------------------------------------
+// NESTED quadtree query (Algorithm 2): one thread per Gaussian in depth order,
+// an explicit stack of (pixel, order) nodes from the 12 base pixels down to the
+// tile order + log2 f. A node is pruned when the angle d from the Gaussian
+// centre to the node centre exceeds r_s + PixRad(o) (zone 0); a node with
+// d <= r_s (zones 2, 3) at or below the tile order adds its tile; other nodes
+// are refined, and a node left at the deepest order adds its tile (zone 1).
+// Each test is decided in FP32 and again in FP64 within 1e-5 of its threshold.
+// The nodes inside a tile are visited consecutively, so a tile added twice is
+// added twice in a row: one comparison removes repeats. The stack never holds
+// more than 12 + 3 (deepest order) <= 45 entries.
+// ----------------------------------------------------------------------------
+constexpr int kNestStack = 48;
+
+// d(node, g) <= ang, i.e. node . g >= cos(min(pi, ang)) for the unit vector g, as FP64
+// decides it. The stored centre is unit length only to FP32 rounding, and near small
+// angles that rounding moves the angle by cot(d) times as much, so both paths normalise:
+// `gn` in FP32; `graw` again in FP64 for a decision within 1e-5 of the threshold.
+__device__ __forceinline__ bool node_within(float dot, float ang32, double ang, int o, uint32_t p, float3 graw) {
+  const float c32 = cosf(fminf((float)kPi, ang32));
+  if (dot > c32 + 1e-5f) return true;
+  if (dot < c32 - 1e-5f) return false;
+  const double3 c = pix2vec_f64(o, p);
+  const double gx = graw.x, gy = graw.y, gz = graw.z;
+  const double inv = 1.0 / sqrt(gx * gx + gy * gy + gz * gz);
+  return (c.x * gx + c.y * gy + c.z * gz) * inv >= cos(fmin(kPi, ang));
+}
+
+template <bool EMIT>
+__global__ void __launch_bounds__(256) k_tiles_nested(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
+                                                      const float* __restrict__ radii, const uint32_t* __restrict__ skeys,
+                                                      const uint32_t* __restrict__ svals, const uint32_t* __restrict__ flags,
+                                                      uint32_t* __restrict__ counts, const uint64_t* __restrict__ offsets,
+                                                      uint32_t* __restrict__ out_tile, uint32_t* __restrict__ out_id,
+                                                      uint64_t cap, int32_t* status) {
+  const int64_t PV = (int64_t)vt.P * vt.nviews;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < PV; j += (int64_t)gridDim.x * blockDim.x) {
+    if (skeys[j] == 0xffffffffu) { if (!EMIT) counts[j] = 0; continue; }
+    const uint32_t gid = svals[j];
+    const ViewParams& vp = vt.v[gid / (uint32_t)vt.P];
+    const int kt = vp.k - vt.b, kmax = kt + vt.log2f;
+    const float4 r0 = rec[4 * (int64_t)gid];
+    const float3 g = make_float3(r0.x, r0.y, r0.z);
+    const float ig = rsqrtf(g.x * g.x + g.y * g.y + g.z * g.z);
+    const float3 gn = make_float3(g.x * ig, g.y * ig, g.z * ig);
+    const float rs = radii[gid];
+    const uint64_t base = EMIT ? offsets[j] : 0;
+    uint32_t stack[kNestStack];                 // (p << 4) | o; p < 12 * 4^11 < 2^26
+    int sp = 0;
+    for (int f = 11; f >= 0; --f) stack[sp++] = (uint32_t)f << 4;
+    uint32_t cnt = 0, last = 0xffffffffu;
+    while (sp > 0) {
+      const uint32_t e = stack[--sp];
+      const int o = (int)(e & 15u);
+      const uint32_t p = e >> 4;
+      const float3 c = pix2vec_f32(o, p);
+      const float dot = c.x * gn.x + c.y * gn.y + c.z * gn.z;
+      const float pr32 = vt.pixrad32[o];
+      const double pr = vt.pixrad64[o];
+      if (!node_within(dot, rs + pr32, (double)rs + pr, o, p, g)) continue;          // zone 0
+      const bool centre_in = node_within(dot, rs, (double)rs, o, p, g);            // zones 2 and 3
+      bool add = false;
+      if (centre_in && o >= kt) add = true;
+      else if (o < kmax) {
+        if (sp + 4 > kNestStack) break;       // cannot happen (see above); keeps the array in bounds
+        for (int ch = 3; ch >= 0; --ch) stack[sp++] = ((4u * p + (uint32_t)ch) << 4) | (uint32_t)(o + 1);
+      } else add = true;
+      if (!add) continue;
+      const uint32_t t = p >> (2 * (o - kt));
+      if (t == last) continue;
+      last = t;
+      const uint32_t gt = (uint32_t)vp.tile_base + t;
+      if (!(flags[gt] & 1u)) continue;
+      if (EMIT) {
+        const uint64_t q = base + cnt;
+        if (q < cap) { out_tile[q] = gt; out_id[q] = gid; }
+      }
+      ++cnt;
+    }
+    if (!EMIT) counts[j] = cnt;
+    else if (base + cnt > cap && status) atomicOr(status, HPXGS_F_CAPACITY);
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Per-pixel weight. m = d^T conic d with d = (theta / s) u, u = (delta.e1, delta.e2),
 // delta = p - g, s = |u| = sin(theta), cos(theta) = 1 - |delta|^2 / 2.
 // (theta/s)^2 = asin(s)^2 / s^2 by its Taylor series near the centre
@@ -1173,10 +1257,16 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   uint64_t* part = at<uint64_t>(ws, L.scan_part);
   prof_begin(HPXGS_STAGE_TILE_COUNT, s);
   const unsigned tblocks = (unsigned)std::min<int64_t>((PV + 7) / 8, 32LL * num_sms());
-  // the count pass stages member lists in the second pair buffers (unused until the pair sort)
-  k_tiles<false><<<tblocks, 256, 0, s>>>(*vt, rec, radii, sk, sv, flags, counts, nullptr, nullptr, nullptr,
-                                         (uint64_t)L.cap, status, at<uint32_t>(ws, L.stage),
-                                         at<uint32_t>(ws, L.pair_key_b), counters + C_STAGE);
+  if (vt->query == HPXGS_QUERY_NESTED) {
+    const unsigned nblocks = (unsigned)std::min<int64_t>((PV + 255) / 256, 32LL * num_sms());
+    k_tiles_nested<false><<<nblocks, 256, 0, s>>>(*vt, rec, radii, sk, sv, flags, counts, nullptr, nullptr, nullptr,
+                                                  (uint64_t)L.cap, status);
+  } else {
+    // the count pass stages member lists in the second pair buffers (unused until the pair sort)
+    k_tiles<false><<<tblocks, 256, 0, s>>>(*vt, rec, radii, sk, sv, flags, counts, nullptr, nullptr, nullptr,
+                                           (uint64_t)L.cap, status, at<uint32_t>(ws, L.stage),
+                                           at<uint32_t>(ws, L.pair_key_b), counters + C_STAGE);
+  }
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_TILE_COUNT, s);
@@ -1279,9 +1369,16 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
     const uint32_t* sv = which ? at<uint32_t>(ws, L.val_b) : at<uint32_t>(ws, L.val_a);
     prof_begin(HPXGS_STAGE_TILE_EMIT, s);
     const unsigned tblocks = (unsigned)std::min<int64_t>((PV + 7) / 8, 32LL * num_sms());
-    k_tiles<true><<<tblocks, 256, 0, s>>>(*vt, rec, at<float>(ws, L.radii), sk, sv, flags, at<uint32_t>(ws, L.counts),
-                                          at<uint64_t>(ws, L.offsets), pka, pva, (uint64_t)cap, status,
-                                          at<uint32_t>(ws, L.stage), pkb, counters + C_STAGE);
+    if (vt->query == HPXGS_QUERY_NESTED) {
+      const unsigned nblocks = (unsigned)std::min<int64_t>((PV + 255) / 256, 32LL * num_sms());
+      k_tiles_nested<true><<<nblocks, 256, 0, s>>>(*vt, rec, at<float>(ws, L.radii), sk, sv, flags,
+                                                   at<uint32_t>(ws, L.counts), at<uint64_t>(ws, L.offsets), pka, pva,
+                                                   (uint64_t)cap, status);
+    } else {
+      k_tiles<true><<<tblocks, 256, 0, s>>>(*vt, rec, at<float>(ws, L.radii), sk, sv, flags, at<uint32_t>(ws, L.counts),
+                                            at<uint64_t>(ws, L.offsets), pka, pva, (uint64_t)cap, status,
+                                            at<uint32_t>(ws, L.stage), pkb, counters + C_STAGE);
+    }
     note_launches(1);
     HPXGS_LAUNCH_CHECK();
     prof_end(HPXGS_STAGE_TILE_EMIT, s);
