@@ -321,6 +321,22 @@ int hpxgs_hssim_forward(const float* I, const float* G, const uint32_t* mask_bit
 int hpxgs_hssim_backward(const float* I, const float* G, const uint32_t* mask_bits, int k, float lambda,
                          const void* workspace, size_t workspace_bytes, const float* dloss, float* dI,
                          hpxgs_stream_t stream);
+/* Window table of (order k, mask): the neighbour walk and the window weights of
+ * every pixel (Sec. 4.1), which depend on the grid and the mask only, stored so
+ * that forward and backward skip them: [8][Npix] neighbour ids, [8][Npix]
+ * weights, [Npix] 1 / window sum (68 bytes per pixel, caller-owned device
+ * memory of at least hpxgs_hssim_table_size bytes). Build it once per mask; the
+ * *_table calls give the results of hpxgs_hssim_forward / _backward bit for bit
+ * when given the same mask. A mask depends on the camera's intrinsics only, so
+ * one table serves every pose of a camera. */
+int hpxgs_hssim_table_size(int k, size_t* bytes);
+int hpxgs_hssim_table_build(const uint32_t* mask_bits, int k, void* table, size_t table_bytes,
+                            hpxgs_stream_t stream);
+int hpxgs_hssim_forward_table(const float* I, const float* G, const uint32_t* mask_bits, int k, float lambda,
+                              const void* table, void* ws, size_t ws_bytes, float* out3, hpxgs_stream_t stream);
+int hpxgs_hssim_backward_table(const float* I, const float* G, const uint32_t* mask_bits, int k, float lambda,
+                               const void* table, const void* ws, size_t ws_bytes, const float* dloss, float* dI,
+                               hpxgs_stream_t stream);
 
 /* ---- loss value without a workspace ----
  * No counterpart in the paper. For callers that cannot give the library device

@@ -30,6 +30,11 @@ __device__ __forceinline__ float pair_weight(float3 a, float3 b, float inv2sig2)
   return __expf(-th * th * inv2sig2);
 }
 
+// Block partials of the loss: sum of h_q and of |I - G| in FP32 (8 warp sums of at
+// most 32 terms, added in a fixed order) and the exact in-mask count. FP64 work is
+// kept out of the per-pixel kernels (the FP64 pipe is slow on this part).
+struct HPart { float h, l1; uint32_t cnt, pad; };
+
 struct HSSIMWs {
   size_t coef, part, nmask, total;
 };
@@ -39,17 +44,37 @@ static HSSIMWs hssim_layout(int k) {
   HSSIMWs L;
   L.coef = 0;
   L.part = (sizeof(float) * 9 * npix + 255) / 256 * 256;
-  L.nmask = L.part + (sizeof(double) * 3 * nblocks + 255) / 256 * 256;
+  L.nmask = L.part + (sizeof(HPart) * nblocks + 255) / 256 * 256;   // double count, then its float copy
   L.total = L.nmask + 256;
   return L;
 }
 
+__device__ __forceinline__ void block_partials(float h, float l1, uint32_t cnt, HPart* __restrict__ part) {
+  for (int o = 16; o > 0; o >>= 1) {
+    h += __shfl_xor_sync(0xffffffffu, h, o);
+    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  __shared__ float sh[2][kHThreads / 32];
+  __shared__ uint32_t sc[kHThreads / 32];
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { sh[0][warp] = h; sh[1][warp] = l1; sc[warp] = cnt; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = 0.f, b = 0.f;
+    uint32_t c = 0;
+    for (int w2 = 0; w2 < kHThreads / 32; ++w2) { a += sh[0][w2]; b += sh[1][w2]; c += sc[w2]; }
+    part[blockIdx.x] = HPart{a, b, c, 0u};
+  }
+}
+
 __global__ void __launch_bounds__(kHThreads) k_hssim_fwd(int k, const float* __restrict__ I, const float* __restrict__ Gt,
                                                          const uint32_t* __restrict__ mask, float* __restrict__ coef,
-                                                         double* __restrict__ part) {
+                                                         HPart* __restrict__ part) {
   const uint32_t npix = 12u << (2 * k);
   const uint32_t p = blockIdx.x * kHThreads + threadIdx.x;
-  double h = 0.0, l1 = 0.0, cnt = 0.0;
+  float h = 0.f, l1 = 0.f;
+  uint32_t cnt = 0;
   if (p < npix && mbit(mask, p)) {
     const float omega = 4.f * (float)kPi / (float)npix;
     const float inv2sig2 = 1.f / (2.f * 2.25f * omega);
@@ -96,43 +121,47 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_fwd(int k, const float* __r
       l1 += fabsf(I[3 * (size_t)p + ch] - Gt[3 * (size_t)p + ch]);
     }
     h = hs / 3.f;
-    cnt = 1.0;
+    cnt = 1u;
   }
-  // block reduction in a fixed order
-  __shared__ double sh[3][kHThreads / 32];
-  for (int o = 16; o > 0; o >>= 1) {
-    h += __shfl_xor_sync(0xffffffffu, h, o);
-    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
-    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  }
-  const int warp = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) { sh[0][warp] = h; sh[1][warp] = l1; sh[2][warp] = cnt; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, b = 0, cc = 0;
-    for (int w2 = 0; w2 < kHThreads / 32; ++w2) { a += sh[0][w2]; b += sh[1][w2]; cc += sh[2][w2]; }
-    part[3 * blockIdx.x + 0] = a; part[3 * blockIdx.x + 1] = b; part[3 * blockIdx.x + 2] = cc;
-  }
+  block_partials(h, l1, cnt, part);
 }
 
-__global__ void k_hssim_reduce(const double* __restrict__ part, int nblocks, float lambda, float* out3, double* nmask) {
-  __shared__ double s[3][256];
-  double a = 0, b = 0, c = 0;
-  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) { a += part[3 * i]; b += part[3 * i + 1]; c += part[3 * i + 2]; }
-  s[0][threadIdx.x] = a; s[1][threadIdx.x] = b; s[2][threadIdx.x] = c;
+// Fixed-order sum of the block partials: per thread compensated (Kahan) FP32 sums of a
+// strided subset, then a double tree over the block's threads; the count in integers.
+constexpr int kRedThreads = 1024;
+__global__ void __launch_bounds__(kRedThreads) k_hssim_reduce(const HPart* __restrict__ part, int nblocks, float lambda,
+                                                              float* out3, double* nmask) {
+  __shared__ double s[2][kRedThreads];
+  __shared__ unsigned long long sc[kRedThreads];
+  float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
+  unsigned long long cnt = 0;
+  for (int i = threadIdx.x; i < nblocks; i += kRedThreads) {
+    const HPart q = part[i];
+    const float ya = q.h - ca, ta = sa + ya; ca = (ta - sa) - ya; sa = ta;
+    const float yb = q.l1 - cb, tb = sb + yb; cb = (tb - sb) - yb; sb = tb;
+    cnt += q.cnt;
+  }
+  s[0][threadIdx.x] = (double)sa - (double)ca;
+  s[1][threadIdx.x] = (double)sb - (double)cb;
+  sc[threadIdx.x] = cnt;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) for (int r = 0; r < 3; ++r) s[r][threadIdx.x] += s[r][threadIdx.x + o];
+  for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s[0][threadIdx.x] += s[0][threadIdx.x + o];
+      s[1][threadIdx.x] += s[1][threadIdx.x + o];
+      sc[threadIdx.x] += sc[threadIdx.x + o];
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double nm = s[2][0];
+    const double nm = (double)sc[0];
     const double hssim = nm > 0 ? s[0][0] / nm : 0.0;
     const double l1 = nm > 0 ? s[1][0] / (3.0 * nm) : 0.0;
     out3[0] = (float)((1.0 - lambda) * l1 + lambda * (1.0 - hssim));
     out3[1] = (float)hssim;
     out3[2] = (float)l1;
-    *nmask = nm;
+    nmask[0] = nm;
+    reinterpret_cast<float*>(nmask + 1)[0] = (float)nm;   // for the backward, without an FP64 conversion
   }
 }
 
@@ -144,7 +173,7 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_bwd(int k, const float* __r
   const uint32_t p = blockIdx.x * kHThreads + threadIdx.x;
   if (p >= npix) return;
   if (!mbit(mask, p)) { dI[3 * (size_t)p] = 0.f; dI[3 * (size_t)p + 1] = 0.f; dI[3 * (size_t)p + 2] = 0.f; return; }
-  const float nm = (float)*nmask;
+  const float nm = reinterpret_cast<const float*>(nmask + 1)[0];
   const float scale = (dloss ? *dloss : 1.f) / (3.f * nm);
   const float omega = 4.f * (float)kPi / (float)npix;
   const float inv2sig2 = 1.f / (2.f * 2.25f * omega);
@@ -165,6 +194,138 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_bwd(int k, const float* __r
       const float* cf = coef + 9 * (size_t)nb;
       for (int ch = 0; ch < 3; ++ch) g[ch] += e * (cf[3 * ch] + cf[3 * ch + 1] * x[ch] + cf[3 * ch + 2] * y[ch]);
     }
+  for (int ch = 0; ch < 3; ++ch) {
+    const float d = x[ch] - y[ch];
+    const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+    dI[3 * (size_t)p + ch] = scale * ((1.f - lambda) * sgn - lambda * g[ch]);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Window table: the window of a pixel depends only on the grid and the mask, not
+// on the maps, so it can be built once per (order, mask) and reused by every
+// forward and backward that uses that mask. Per pixel p, structure of arrays:
+// idx[s][p] and e[s][p] for the up to 8 in-mask neighbours in the walk order of
+// k_hssim_fwd (unused slots: idx = p, e = 0), and iZ[p] = 1 / (1 + sum e). The
+// weights come from the same pair_weight calls in the same order, and an unused
+// slot adds an exact zero, so the table kernels give the results of
+// k_hssim_fwd / k_hssim_bwd bit for bit while skipping the neighbour walk,
+// the pixel centres and the transcendental weights.
+// ----------------------------------------------------------------------------
+struct HTable {
+  uint32_t* idx;   // [8][npix]
+  float* e;        // [8][npix]
+  float* iZ;       // [npix]
+};
+static size_t htable_bytes(int k) { return (size_t)17 * 4 * (12ull << (2 * k)); }
+static HTable htable(void* t, int k) {
+  const size_t npix = 12ull << (2 * k);
+  char* b = static_cast<char*>(t);
+  return HTable{reinterpret_cast<uint32_t*>(b), reinterpret_cast<float*>(b + 32 * npix),
+                reinterpret_cast<float*>(b + 64 * npix)};
+}
+
+__global__ void __launch_bounds__(kHThreads) k_hssim_table(int k, const uint32_t* __restrict__ mask, HTable T) {
+  const uint32_t npix = 12u << (2 * k);
+  const uint32_t p = blockIdx.x * kHThreads + threadIdx.x;
+  if (p >= npix) return;
+  int n = 0;
+  float Z = 1.f;                               // the pixel itself, e_pp = 1
+  if (mbit(mask, p)) {
+    const float omega = 4.f * (float)kPi / (float)npix;
+    const float inv2sig2 = 1.f / (2.f * 2.25f * omega);
+    const float3 cq = pix2vec_f32(k, p);
+    const FaceXY c = nest_to_fxy(k, p);
+    float w[8];
+    for (int dx = -1; dx <= 1; ++dx)
+      for (int dy = -1; dy <= 1; ++dy) {
+        if (dx == 0 && dy == 0) continue;
+        const int64_t nb = neighbour_nest(k, c.f, c.x, c.y, dx, dy);
+        if (nb < 0 || !mbit(mask, (uint32_t)nb)) continue;
+        w[n] = pair_weight(cq, pix2vec_f32(k, (uint32_t)nb), inv2sig2);
+        T.idx[(size_t)n * npix + p] = (uint32_t)nb;
+        T.e[(size_t)n * npix + p] = w[n];
+        ++n;
+      }
+    for (int j = 0; j < n; ++j) Z += w[j];
+    T.iZ[p] = 1.f / Z;
+  } else {
+    T.iZ[p] = 0.f;
+  }
+  for (int j = n; j < 8; ++j) { T.idx[(size_t)j * npix + p] = p; T.e[(size_t)j * npix + p] = 0.f; }
+}
+
+__global__ void __launch_bounds__(kHThreads) k_hssim_fwd_t(int k, const float* __restrict__ I, const float* __restrict__ Gt,
+                                                           const uint32_t* __restrict__ mask, HTable T,
+                                                           float* __restrict__ coef, HPart* __restrict__ part) {
+  const uint32_t npix = 12u << (2 * k);
+  const uint32_t p = blockIdx.x * kHThreads + threadIdx.x;
+  float h = 0.f, l1 = 0.f;
+  uint32_t cnt = 0;
+  if (p < npix && mbit(mask, p)) {
+    const float iZ = T.iZ[p];
+    uint32_t q[8];
+    float e[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { q[j] = T.idx[(size_t)j * npix + p]; e[j] = T.e[(size_t)j * npix + p]; }
+    float hs = 0.f;
+    for (int ch = 0; ch < 3; ++ch) {
+      float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
+      {
+        const float wj = 1.f * iZ;
+        const float x = I[3 * (size_t)p + ch], y = Gt[3 * (size_t)p + ch];
+        mx += wj * x; my += wj * y; xx += wj * x * x; yy += wj * y * y; xy += wj * x * y;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float wj = e[j] * iZ;
+        const float x = I[3 * (size_t)q[j] + ch], y = Gt[3 * (size_t)q[j] + ch];
+        mx += wj * x; my += wj * y; xx += wj * x * x; yy += wj * y * y; xy += wj * x * y;
+      }
+      const float vx = xx - mx * mx, vy = yy - my * my, cxy = xy - mx * my;
+      const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
+      const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
+      const float iB = 1.f / (B1 * B2);
+      const float ssim = A1 * A2 * iB;
+      hs += ssim;
+      const float dmu = (2.f * my * A2 - ssim * B2 * 2.f * mx) * iB;
+      const float dvar = -ssim / B2;
+      const float dcov = 2.f * A1 * iB;
+      coef[9 * (size_t)p + 3 * ch + 0] = (dmu - 2.f * mx * dvar - my * dcov) * iZ;
+      coef[9 * (size_t)p + 3 * ch + 1] = 2.f * dvar * iZ;
+      coef[9 * (size_t)p + 3 * ch + 2] = dcov * iZ;
+      l1 += fabsf(I[3 * (size_t)p + ch] - Gt[3 * (size_t)p + ch]);
+    }
+    h = hs / 3.f;
+    cnt = 1u;
+  }
+  block_partials(h, l1, cnt, part);
+}
+
+__global__ void __launch_bounds__(kHThreads) k_hssim_bwd_t(int k, const float* __restrict__ I, const float* __restrict__ Gt,
+                                                           const uint32_t* __restrict__ mask, HTable T,
+                                                           const float* __restrict__ coef,
+                                                           const double* __restrict__ nmask, float lambda,
+                                                           const float* __restrict__ dloss, float* __restrict__ dI) {
+  const uint32_t npix = 12u << (2 * k);
+  const uint32_t p = blockIdx.x * kHThreads + threadIdx.x;
+  if (p >= npix) return;
+  if (!mbit(mask, p)) { dI[3 * (size_t)p] = 0.f; dI[3 * (size_t)p + 1] = 0.f; dI[3 * (size_t)p + 2] = 0.f; return; }
+  const float nm = reinterpret_cast<const float*>(nmask + 1)[0];
+  const float scale = (dloss ? *dloss : 1.f) / (3.f * nm);
+  float x[3], y[3], g[3];
+  for (int ch = 0; ch < 3; ++ch) {
+    x[ch] = I[3 * (size_t)p + ch]; y[ch] = Gt[3 * (size_t)p + ch];
+    const float cf0 = coef[9 * (size_t)p + 3 * ch], cf1 = coef[9 * (size_t)p + 3 * ch + 1], cf2 = coef[9 * (size_t)p + 3 * ch + 2];
+    g[ch] = cf0 + cf1 * x[ch] + cf2 * y[ch];
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t q = T.idx[(size_t)j * npix + p];
+    const float e = T.e[(size_t)j * npix + p];
+    const float* cf = coef + 9 * (size_t)q;
+    for (int ch = 0; ch < 3; ++ch) g[ch] += e * (cf[3 * ch] + cf[3 * ch + 1] * x[ch] + cf[3 * ch + 2] * y[ch]);
+  }
   for (int ch = 0; ch < 3; ++ch) {
     const float d = x[ch] - y[ch];
     const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
@@ -196,8 +357,8 @@ int hpxgs_hssim_forward(const float* I, const float* G, const uint32_t* mask, in
   char* w = static_cast<char*>(ws);
   prof_begin(HPXGS_STAGE_HSSIM_FWD, s);
   k_hssim_fwd<<<nblocks, kHThreads, 0, s>>>(k, I, G, mask, reinterpret_cast<float*>(w + L.coef),
-                                            reinterpret_cast<double*>(w + L.part));
-  k_hssim_reduce<<<1, 256, 0, s>>>(reinterpret_cast<double*>(w + L.part), nblocks, lambda, out3,
+                                            reinterpret_cast<HPart*>(w + L.part));
+  k_hssim_reduce<<<1, kRedThreads, 0, s>>>(reinterpret_cast<const HPart*>(w + L.part), nblocks, lambda, out3,
                                    reinterpret_cast<double*>(w + L.nmask));
   note_launches(2);
   HPXGS_LAUNCH_CHECK();
@@ -218,6 +379,65 @@ int hpxgs_hssim_backward(const float* I, const float* G, const uint32_t* mask, i
   prof_begin(HPXGS_STAGE_HSSIM_BWD, s);
   k_hssim_bwd<<<nblocks, kHThreads, 0, s>>>(k, I, G, mask, reinterpret_cast<const float*>(w + L.coef),
                                             reinterpret_cast<const double*>(w + L.nmask), lambda, dloss, dI);
+  note_launches(1);
+  HPXGS_LAUNCH_CHECK();
+  prof_end(HPXGS_STAGE_HSSIM_BWD, s);
+  return HPXGS_OK;
+}
+
+
+int hpxgs_hssim_table_size(int k, size_t* bytes) {
+  if (k < 3 || k > 13 || !bytes) return HPXGS_E_INVALID_ARG;
+  *bytes = htable_bytes(k);
+  return HPXGS_OK;
+}
+
+int hpxgs_hssim_table_build(const uint32_t* mask, int k, void* table, size_t table_bytes, hpxgs_stream_t stream) {
+  if (k < 3 || k > 13 || !mask || !table) return HPXGS_E_INVALID_ARG;
+  if (table_bytes < htable_bytes(k)) return HPXGS_E_WORKSPACE;
+  const uint32_t npix = 12u << (2 * k);
+  k_hssim_table<<<(npix + kHThreads - 1) / kHThreads, kHThreads, 0, (cudaStream_t)stream>>>(k, mask, htable(table, k));
+  note_launches(1);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+
+int hpxgs_hssim_forward_table(const float* I, const float* G, const uint32_t* mask, int k, float lambda,
+                              const void* table, void* ws, size_t ws_bytes, float* out3, hpxgs_stream_t stream) {
+  if (k < 3 || k > 13 || !I || !G || !mask || !table || !ws || !out3 || !(lambda >= 0.f && lambda <= 1.f))
+    return HPXGS_E_INVALID_ARG;
+  HSSIMWs L = hssim_layout(k);
+  if (ws_bytes < L.total) return HPXGS_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t npix = 12u << (2 * k);
+  const int nblocks = (int)((npix + kHThreads - 1) / kHThreads);
+  char* w = static_cast<char*>(ws);
+  prof_begin(HPXGS_STAGE_HSSIM_FWD, s);
+  k_hssim_fwd_t<<<nblocks, kHThreads, 0, s>>>(k, I, G, mask, htable(const_cast<void*>(table), k),
+                                              reinterpret_cast<float*>(w + L.coef), reinterpret_cast<HPart*>(w + L.part));
+  k_hssim_reduce<<<1, kRedThreads, 0, s>>>(reinterpret_cast<const HPart*>(w + L.part), nblocks, lambda, out3,
+                                   reinterpret_cast<double*>(w + L.nmask));
+  note_launches(2);
+  HPXGS_LAUNCH_CHECK();
+  prof_end(HPXGS_STAGE_HSSIM_FWD, s);
+  return HPXGS_OK;
+}
+
+int hpxgs_hssim_backward_table(const float* I, const float* G, const uint32_t* mask, int k, float lambda,
+                               const void* table, const void* ws, size_t ws_bytes, const float* dloss, float* dI,
+                               hpxgs_stream_t stream) {
+  if (k < 3 || k > 13 || !I || !G || !mask || !table || !ws || !dI || !(lambda >= 0.f && lambda <= 1.f))
+    return HPXGS_E_INVALID_ARG;
+  HSSIMWs L = hssim_layout(k);
+  if (ws_bytes < L.total) return HPXGS_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t npix = 12u << (2 * k);
+  const int nblocks = (int)((npix + kHThreads - 1) / kHThreads);
+  const char* w = static_cast<const char*>(ws);
+  prof_begin(HPXGS_STAGE_HSSIM_BWD, s);
+  k_hssim_bwd_t<<<nblocks, kHThreads, 0, s>>>(k, I, G, mask, htable(const_cast<void*>(table), k),
+                                              reinterpret_cast<const float*>(w + L.coef),
+                                              reinterpret_cast<const double*>(w + L.nmask), lambda, dloss, dI);
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_HSSIM_BWD, s);

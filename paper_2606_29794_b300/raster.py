@@ -275,9 +275,12 @@ class GraphStep:
             if not host_targets.is_pinned() or host_targets.shape != self.targets.shape:
                 raise ValueError("host_targets must be a pinned host tensor shaped like targets")
             self.side = torch.cuda.Stream(device=dev)
-        # warm up eagerly once (allocator pools, rho cache), then capture
+        # warm up eagerly once (allocator pools, rho cache); the HSSIM window tables come from
+        # the masks of that step (one per distinct order and camera); then capture
+        self.tables = None
         self._step()
         torch.cuda.synchronize()
+        self.tables = self._build_tables()
         s = torch.cuda.Stream(device=dev)
         s.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(s):
@@ -309,13 +312,33 @@ class GraphStep:
             G = self.targets[base:base + n]
             m = out["mask"][base // 32:(base + n) // 32]
             ws, nb = self.hws[vi]
-            L.check(L.lib().hpxgs_hssim_forward(_ptr(I), _ptr(G), _ptr(m), k, float(self.lam), _ptr(ws), nb,
-                                                _ptr(self.losses[vi]), ctypes.c_void_p(st)), "hssim fwd")
-            L.check(L.lib().hpxgs_hssim_backward(_ptr(I), _ptr(G), _ptr(m), k, float(self.lam), _ptr(ws), nb, None,
-                                                 _ptr(self.dmaps[base:base + n]), ctypes.c_void_p(st)), "hssim bwd")
+            tab = self.tables[vi] if self.tables else None
+            if tab is not None:
+                L.check(L.lib().hpxgs_hssim_forward_table(_ptr(I), _ptr(G), _ptr(m), k, float(self.lam), _ptr(tab),
+                                                          _ptr(ws), nb, _ptr(self.losses[vi]), ctypes.c_void_p(st)),
+                        "hssim fwd")
+                L.check(L.lib().hpxgs_hssim_backward_table(_ptr(I), _ptr(G), _ptr(m), k, float(self.lam), _ptr(tab),
+                                                           _ptr(ws), nb, None, _ptr(self.dmaps[base:base + n]),
+                                                           ctypes.c_void_p(st)), "hssim bwd")
+            else:
+                L.check(L.lib().hpxgs_hssim_forward(_ptr(I), _ptr(G), _ptr(m), k, float(self.lam), _ptr(ws), nb,
+                                                    _ptr(self.losses[vi]), ctypes.c_void_p(st)), "hssim fwd")
+                L.check(L.lib().hpxgs_hssim_backward(_ptr(I), _ptr(G), _ptr(m), k, float(self.lam), _ptr(ws), nb,
+                                                     None, _ptr(self.dmaps[base:base + n]), ctypes.c_void_p(st)),
+                        "hssim bwd")
         self.grads = self.rast.backward_raw(state, self.dmaps)
         self.out = out
         self.state = state
+
+    def _build_tables(self):
+        cache, per_view = {}, []
+        for vi, (v, k, base) in enumerate(zip(self.views, self.order, self.lay.pix_base)):
+            key = (k, int(v["cam"]), float(v.get("fov_x", 360.0)), float(v.get("fov_y") or v.get("fov_x", 360.0)))
+            if key not in cache:
+                m = self.out["mask"][base // 32:(base + npix(k)) // 32]
+                cache[key] = hssim_table(m, k)
+            per_view.append(cache[key])
+        return per_view
 
     def replay(self):
         self.graph.replay()
@@ -364,3 +387,14 @@ def default_candidates():
     out.append(dict(tile_level=4, fwd_ppt=2))
     out.append(dict(tile_level=4, bwd_ppt=2))
     return out
+
+
+def hssim_table(mask_words, k):
+    """HEALPix-SSIM window table of a mask (order k): neighbour ids, window weights and
+    1 / window sum per pixel, for the *_table forward and backward calls."""
+    nb = ctypes.c_size_t()
+    L.check(L.lib().hpxgs_hssim_table_size(k, ctypes.byref(nb)), "hssim table size")
+    tab = torch.empty(nb.value, dtype=torch.uint8, device=mask_words.device)
+    L.check(L.lib().hpxgs_hssim_table_build(_ptr(mask_words), k, _ptr(tab), nb.value, ctypes.c_void_p(_stream())),
+            "hssim table")
+    return tab

@@ -52,3 +52,34 @@ def test_hssim_identical_maps_is_one():
     words = _mask_words(S.make_view(k))
     loss, parts = R.hssim_loss(I, I.clone(), words, k, 0.2)
     assert abs(parts[1].item() - 1.0) < 1e-6 and abs(loss.item()) < 1e-6
+
+
+@pytest.mark.parametrize("k,kind,fov", [(5, 0, 360.0), (6, 2, 190.0), (7, 1, 90.0), (9, 2, 190.0)])
+def test_window_table_path_is_bit_identical(k, kind, fov):
+    import ctypes
+    from paper_2606_29794_b300 import _lib as L
+    rng = np.random.default_rng(k + 100)
+    n = 12 * 4 ** k
+    I = torch.tensor(rng.random((n, 3)), dtype=torch.float32, device="cuda")
+    G = torch.tensor(rng.random((n, 3)), dtype=torch.float32, device="cuda")
+    words = _mask_words(S.make_view(k, kind, fov))
+    tab = R.hssim_table(words, k)
+    nb = ctypes.c_size_t()
+    L.check(L.lib().hpxgs_hssim_workspace_size(k, ctypes.byref(nb)), "ws")
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    outs = []
+    for use_table in (False, True):
+        ws = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+        out3 = torch.empty(3, device="cuda")
+        dI = torch.empty((n, 3), device="cuda")
+        if use_table:
+            L.check(L.lib().hpxgs_hssim_forward_table(p(I), p(G), p(words), k, 0.2, p(tab), p(ws), nb.value, p(out3), s), "f")
+            L.check(L.lib().hpxgs_hssim_backward_table(p(I), p(G), p(words), k, 0.2, p(tab), p(ws), nb.value, None, p(dI), s), "b")
+        else:
+            L.check(L.lib().hpxgs_hssim_forward(p(I), p(G), p(words), k, 0.2, p(ws), nb.value, p(out3), s), "f")
+            L.check(L.lib().hpxgs_hssim_backward(p(I), p(G), p(words), k, 0.2, p(ws), nb.value, None, p(dI), s), "b")
+        torch.cuda.synchronize()
+        outs.append((out3.clone(), dI.clone()))
+    assert torch.equal(outs[0][0], outs[1][0])
+    assert torch.equal(outs[0][1], outs[1][1])
