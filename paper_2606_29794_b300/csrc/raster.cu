@@ -410,15 +410,17 @@ __device__ __forceinline__ void disc_setup(const ViewParams& vp, int kt, float3 
   // candidates within 1e-5 of it
   Q.cosRm32 = cosf(fminf((float)kPi, rs + vp.rho32 + 1e-7f));
   const float Re = fminf((float)kPi, rs + vp.rho32 + 1e-7f + 1e-5f);   // enumeration radius with slack
-  Q.cosRe = cosf(Re);
+  float sRe, cRe;
+  sincosf(Re, &sRe, &cRe);
+  Q.cosRe = cRe;
   const int Nt = 1 << kt;
   Q.zc = g.z;
   Q.sc = sqrtf(fmaxf(0.f, g.x * g.x + g.y * g.y));
-  const float phic = atan2f(Q.zc, Q.sc);
   Q.omc = atan2f(g.y, g.x);
-  const float phimin = fmaxf(-0.5f * (float)kPi, phic - Re), phimax = fminf(0.5f * (float)kPi, phic + Re);
-  Q.zmin = sinf(phimin) - 1e-6f;
-  Q.zmax = sinf(phimax) + 1e-6f;
+  // z range sin(phi_c -+ Re) = z_c cos Re -+ s_c sin Re; it reaches the north pole once
+  // Re >= the centre's colatitude (cos Re <= z_c) and the south pole once cos Re <= -z_c
+  Q.zmin = (cRe <= -Q.zc ? -1.f : Q.zc * cRe - Q.sc * sRe) - 1e-6f;
+  Q.zmax = (cRe <= Q.zc ? 1.f : Q.zc * cRe + Q.sc * sRe) + 1e-6f;
   Q.ilo = max(1, (int)floorf(ring_of_z(fminf(Q.zmax, 1.f), Nt)) - 1);
   Q.ihi = min(4 * Nt - 1, (int)ceilf(ring_of_z(fmaxf(Q.zmin, -1.f), Nt)) + 1);
 }
