@@ -271,7 +271,7 @@ int make_layout(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_conf
   L->pair_key_b = take(4 * cp);
   L->pair_val_a = take(4 * cp);
   L->pair_val_b = take(4 * cp);
-  L->hist = take(4 * 256 * (size_t)G);
+  L->hist = take(4 * (256 * (size_t)G + 256));   // per-block digit counts, then the digit bases
   L->ranges = take(8 * tiles);
   L->counters = take(4 * C_COUNT);
   L->accum = take(4 * HPXGS_NACC * pv);

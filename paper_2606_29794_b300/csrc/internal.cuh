@@ -71,7 +71,7 @@ constexpr int kMaxSortBlocks = 1024;
 
 // counters block (u32 each)
 // (u64 counters live at u32 index 8 (n_eval) and 10 (n_contrib), 8-byte aligned)
-enum Counter { C_NPAIRS = 0, C_WORK_FWD = 1, C_WORK_BWD = 2, C_NSORT = 3, C_NPAIRS_HI = 4, C_STAGE = 5, C_NEVAL = 8, C_NCONTRIB = 10,
+enum Counter { C_NPAIRS = 0, C_WORK_FWD = 1, C_WORK_BWD = 2, C_NSORT = 3, C_NPAIRS_HI = 4, C_STAGE = 5, C_NEVAL = 8, C_NCONTRIB = 10, C_SORT_TICKET = 12,
                C_COUNT = 16 };
 
 // instrumentation (geometry.cu)

@@ -229,37 +229,56 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __re
   hist[threadIdx.x * G + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Exclusive scan of len u32 entries in place (one block of 1024 threads), in
-// coalesced chunks of 4096 (4 consecutive entries per thread) with a running carry.
-__global__ void __launch_bounds__(1024) k_scan_u32_inplace(uint32_t* __restrict__ a, int len) {
-  __shared__ uint32_t wsum[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t carry = 0;
-  for (int base = 0; base < len; base += 4096) {
-    const int idx = base + 4 * threadIdx.x;
-    uint32_t v[4];
+// Digit-major exclusive scan of the per-block histograms hist[d * G + b], the order
+// a stable LSD pass needs, in one launch of one block per digit row: each block scans
+// its row in place and posts the row total; the block that finishes last (an atomic
+// ticket, nothing waits) turns the totals into digit bases in place and resets the
+// ticket. The scatter adds base[d] to the row prefix it reads.
+__global__ void __launch_bounds__(256) k_scan_digit_rows(uint32_t* __restrict__ hist, int G,
+                                                         uint32_t* __restrict__ base, uint32_t* ticket) {
+  __shared__ uint32_t wsum[8];
+  __shared__ bool s_last;
+  const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t* row = hist + (size_t)d * G;
+  // each thread owns up to 4 consecutive entries of the row (G <= 1024)
+  uint32_t v[4], t = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = (idx + k < len) ? a[idx + k] : 0u;
-    const uint32_t t = v[0] + v[1] + v[2] + v[3];
-    uint32_t x = t;
-    for (int o = 1; o < 32; o <<= 1) { const uint32_t y = __shfl_up_sync(0xffffffffu, x, o); if (lane >= o) x += y; }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t w = wsum[lane];
-      for (int o = 1; o < 32; o <<= 1) { const uint32_t y = __shfl_up_sync(0xffffffffu, w, o); if (lane >= o) w += y; }
-      wsum[lane] = w;
-    }
-    __syncthreads();
-    uint32_t run = carry + x - t + (warp > 0 ? wsum[warp - 1] : 0u);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (idx + k < len) a[idx + k] = run;
-      run += v[k];
-    }
-    carry += wsum[31];
-    __syncthreads();
+  for (int q = 0; q < 4; ++q) { const int b = 4 * tid + q; v[q] = b < G ? row[b] : 0u; t += v[q]; }
+  uint32_t x = t;
+  for (int o = 1; o < 32; o <<= 1) { const uint32_t y = __shfl_up_sync(0xffffffffu, x, o); if (lane >= o) x += y; }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < 8 ? wsum[lane] : 0u;
+    for (int o = 1; o < 8; o <<= 1) { const uint32_t y = __shfl_up_sync(0xffffffffu, w, o); if (lane >= o) w += y; }
+    if (lane < 8) wsum[lane] = w;
   }
+  __syncthreads();
+  uint32_t run = x - t + (warp > 0 ? wsum[warp - 1] : 0u);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) { const int b = 4 * tid + q; if (b < G) row[b] = run; run += v[q]; }
+  if (tid == 0) {
+    base[d] = wsum[7];                          // row total for now
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const uint32_t tot = tid < (int)gridDim.x ? *(volatile uint32_t*)&base[tid] : 0u;
+  x = tot;
+  for (int o = 1; o < 32; o <<= 1) { const uint32_t y = __shfl_up_sync(0xffffffffu, x, o); if (lane >= o) x += y; }
+  __syncthreads();
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < 8 ? wsum[lane] : 0u;
+    for (int o = 1; o < 8; o <<= 1) { const uint32_t y = __shfl_up_sync(0xffffffffu, w, o); if (lane >= o) w += y; }
+    if (lane < 8) wsum[lane] = w;
+  }
+  __syncthreads();
+  if (tid < (int)gridDim.x) base[tid] = x - tot + (warp > 0 ? wsum[warp - 1] : 0u);
+  if (tid == 0) *ticket = 0u;
 }
 
 // Stable scatter of one pass over the block's chunk, one 4096-element tile at a
@@ -273,7 +292,8 @@ constexpr int kSegRounds = kWarpSeg / 32;                   // 16
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                                const uint32_t* n_ptr, uint32_t n_max, int shift, int nbits,
-                                                               const uint32_t* __restrict__ hist, int G) {
+                                                               const uint32_t* __restrict__ hist,
+                                                               const uint32_t* __restrict__ dbase, int G) {
   constexpr int NW = kSortThreads / 32;
   __shared__ uint32_t s_key[kSortTile];        // 16 KB, tile in digit order
   __shared__ uint32_t s_val[kSortTile];        // 16 KB
@@ -287,7 +307,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t mask = (1u << nbits) - 1u;
   const uint32_t lt = (1u << lane) - 1u;
-  gbase[tid] = hist[tid * G + blockIdx.x];
+  gbase[tid] = tid <= (int)mask ? hist[tid * G + blockIdx.x] + dbase[tid] : 0u;
   for (uint32_t t0 = begin; t0 < end; t0 += kSortTile) {
     // ---- phase 1: per-warp ranks
     for (int d = lane; d < 256; d += 32) wcnt[warp][d] = 0;
@@ -355,8 +375,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* _
 
 // Sorts n (device count, capped at n_max) pairs by bits [0, bits) of the key.
 // Returns 0 if the result is in (k0, v0), 1 if in (k1, v1).
+// hist holds 256 * G per-block counts followed by 256 digit bases; ticket is a
+// zeroed counter (reset by every pass).
 static int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, const uint32_t* n_dev, uint32_t n_max,
-                      int bits, uint32_t* hist, int G, cudaStream_t s, int* which) {
+                      int bits, uint32_t* hist, int G, uint32_t* ticket, cudaStream_t s, int* which) {
   int cur = 0;
   if (n_max == 0) { *which = 0; return HPXGS_OK; }
   for (int shift = 0; shift < bits; shift += 8) {
@@ -364,8 +386,9 @@ static int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, co
     uint32_t* kin = cur ? k1 : k0; uint32_t* vin = cur ? v1 : v0;
     uint32_t* kout = cur ? k0 : k1; uint32_t* vout = cur ? v0 : v1;
     k_sort_hist<<<G, kSortThreads, 0, s>>>(kin, n_dev, n_max, shift, nb, hist, G);
-    k_scan_u32_inplace<<<1, 1024, 0, s>>>(hist, 256 * G);
-    k_sort_scatter<<<G, kSortThreads, 0, s>>>(kin, vin, kout, vout, n_dev, n_max, shift, nb, hist, G);
+    k_scan_digit_rows<<<1 << nb, 256, 0, s>>>(hist, G, hist + 256 * (size_t)G, ticket);
+    k_sort_scatter<<<G, kSortThreads, 0, s>>>(kin, vin, kout, vout, n_dev, n_max, shift, nb, hist,
+                                              hist + 256 * (size_t)G, G);
     note_launches(3);
     HPXGS_LAUNCH_CHECK();
     cur ^= 1;
@@ -1249,7 +1272,7 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   prof_begin(HPXGS_STAGE_DEPTH_SORT, s);
   // a grid sized to the element count (about 4 tiles of 4096 per block): the digit scan covers 256 x G entries
   const int Gd = (int)std::max<int64_t>(1, std::min<int64_t>(L.sort_blocks, (PV + 4 * kSortTile - 1) / (4 * kSortTile)));
-  rc = radix_sort(ka, va, kb, vb, nullptr, (uint32_t)PV, 32, at<uint32_t>(ws, L.hist), Gd, s, which_depth);
+  rc = radix_sort(ka, va, kb, vb, nullptr, (uint32_t)PV, 32, at<uint32_t>(ws, L.hist), Gd, counters + C_SORT_TICKET, s, which_depth);
   if (rc != HPXGS_OK) return rc;
   prof_end(HPXGS_STAGE_DEPTH_SORT, s);
   const uint32_t* sk = *which_depth ? kb : ka;
@@ -1387,7 +1410,7 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
     int wp = 0;
     prof_begin(HPXGS_STAGE_PAIR_SORT, s);
     rc = radix_sort(pka, pva, pkb, pvb, counters + C_NPAIRS, (uint32_t)cap, L.pair_bits, at<uint32_t>(ws, L.hist),
-                    L.sort_blocks, s, &wp);
+                    L.sort_blocks, counters + C_SORT_TICKET, s, &wp);
     if (rc != HPXGS_OK) { delete vt; return rc; }
     prof_end(HPXGS_STAGE_PAIR_SORT, s);
     const uint32_t* sorted_tiles = wp ? pkb : pka;

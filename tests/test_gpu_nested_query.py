@@ -63,12 +63,15 @@ def test_nested_lists_exact_and_maps_equal_ring(name, make, b, log2f):
     out_r, st_r = ring.forward_raw(*ts, sc["sh_degree"], [view])
     torch.cuda.synchronize()
     assert torch.equal(out_n["maps"], out_r["maps"]) and torch.equal(out_n["T"], out_r["T"])
-    g = torch.randn_like(out_r["maps"])
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    g = torch.randn(out_r["maps"].shape, device="cuda", generator=gen)
     gn = nest.backward_raw(st_n, g)
     gr = ring.backward_raw(st_r, g)
     torch.cuda.synchronize()
+    # the same contributions summed by atomics in another grouping: equal to FP32 rounding
     for a, c in zip(gn, gr):
-        assert torch.allclose(a, c, rtol=1e-4, atol=1e-6 * float(c.abs().max()) + 1e-12)
+        assert float((a - c).norm() / c.norm()) <= 1e-5
+        assert float((a - c).abs().max()) <= 1e-4 * float(c.abs().max())
 
 
 def test_training_step_workload_nested_equals_ring():
