@@ -303,13 +303,14 @@ def tile_lists_bruteforce(k, b, g, rs, valid, rho, active):
     return member
 
 
-def composite(k, b, pre, opac, start, ids, pix, cfg: Config):
+def composite(k, b, pre, opac, start, ids, pix, cfg: Config, depth=False):
     """Stage 3 (Algorithm 1 rendering loop) at the NESTED pixels `pix`.
     Returns (image, T, last, amb); amb bit 0 flags a cutoff decision within
     rounding of m = cutoff, bit 1 two contributors of nearly equal depth."""
     pix = np.ascontiguousarray(pix, np.int64)
     n = pix.size
     img = np.empty((n, 3)); T = np.empty(n); last = np.empty(n, np.int64); amb = np.empty(n, np.uint8)
+    D = np.empty(n) if depth else None
     bg = np.asarray(cfg.bg, np.float64)
     P = pre["r"].size
     lib().or_composite(ctypes.c_int(k), ctypes.c_int(b), _i64(P),
@@ -321,7 +322,9 @@ def composite(k, b, pre, opac, start, ids, pix, cfg: Config):
                        _p(np.ascontiguousarray(pre["r"], np.float64)),
                        _p(np.ascontiguousarray(start, np.int64)), _p(np.ascontiguousarray(ids, np.int64)),
                        _i64(n), _p(pix), _f64(cfg.eps_T), _f64(cfg.alpha_max),
-                       _f64(cfg.cutoff), _p(bg), _p(img), _p(T), _p(last), _p(amb))
+                       _f64(cfg.cutoff), _p(bg), _p(img), _p(T), _p(last), _p(amb), _p(D))
+    if depth:
+        return img, T, last, amb, D
     return img, T, last, amb
 
 
@@ -359,8 +362,9 @@ def render(scene, view, cfg: Config, pix=None, rho=None):
     return Render(image, T, last, amb, m, act, pre, start, ids, rho, pix)
 
 
-def backward(scene, view, cfg: Config, dLdI, start, ids, pix):
-    """Sec. 3.2 backward for one view: dL/dI at `pix` (n, 3) -> parameter gradients."""
+def backward(scene, view, cfg: Config, dLdI, start, ids, pix, dLdD=None):
+    """Sec. 3.2 backward for one view: dL/dI at `pix` (n, 3) and optionally dL/dD of the
+    inverse-depth channel at `pix` (n,) -> parameter gradients."""
     mu, s, q, o, sh, deg, P = _scene64(scene)
     k = view["nside_log2"]; b = cfg.tile_level
     nside = 1 << k
@@ -377,7 +381,8 @@ def backward(scene, view, cfg: Config, dLdI, start, ids, pix):
                       _f64(cfg.eps_T), _f64(cfg.alpha_max), _f64(cfg.cutoff), _p(bg),
                       _p(np.ascontiguousarray(start, np.int64)), _p(np.ascontiguousarray(ids, np.int64)),
                       _i64(pix.size), _p(pix), _p(dLdI), _p(out["means"]), _p(out["scales"]),
-                      _p(out["rotations"]), _p(out["opacities"]), _p(out["sh"]))
+                      _p(out["rotations"]), _p(out["opacities"]), _p(out["sh"]),
+                      _p(None if dLdD is None else np.ascontiguousarray(dLdD, np.float64).ravel()))
     return out
 
 

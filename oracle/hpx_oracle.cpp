@@ -605,14 +605,14 @@ struct GaussView {  // what compositing needs per Gaussian
   double omega, sphg, cphg, conic[3], opac, col[3], r;
 };
 
-struct PixOut { double C[3], T; i64 last; int amb; };
+struct PixOut { double C[3], T, D; i64 last; int amb; };   // D: composited inverse radial depth
 
 // Forward at one pixel; optionally records alpha, T before each entry and exp(-m/2).
 static void composite_pixel(double omega_p, double sphp, double cphp, const i64* ids, i64 n,
                             const std::vector<GaussView>& G, const Cfg& cfg, PixOut& out,
                             std::vector<double>* alphas, std::vector<double>* Ts,
                             std::vector<double>* Gs) {
-  double T = 1.0, C[3] = {0, 0, 0};
+  double T = 1.0, C[3] = {0, 0, 0}, D = 0.0;
   i64 j = 0;
   int amb = 0;
   double prev_r = -1.0, prev_a = 0.0;
@@ -633,11 +633,12 @@ static void composite_pixel(double omega_p, double sphp, double cphp, const i64*
     if (a > 0) { prev_r = gv.r; prev_a = a; }
     if (alphas) { alphas->push_back(a); Ts->push_back(T); Gs->push_back(Gm); }
     for (int c = 0; c < 3; ++c) C[c] += T * a * gv.col[c];
+    D += T * a / gv.r;                        // depth channel: inverse radial depth (Sec. 3.2)
     T *= (1.0 - a);
     if (T < cfg.eps_T) { ++j; break; }
   }
   for (int c = 0; c < 3; ++c) out.C[c] = C[c] + T * cfg.bg[c];
-  out.T = T; out.last = j; out.amb = amb;
+  out.T = T; out.D = D; out.last = j; out.amb = amb;
 }
 
 static void pixel_lonlat(i64 nside, i64 p, double& omega_p, double& sphp, double& cphp) {
@@ -1175,7 +1176,8 @@ void or_active_tiles(int k, int b, const u8* mask, u8* active) {
 void or_composite(int k, int b, i64 P, const double* omega, const double* phi, const double* conic,
                   const double* opac, const double* col, const double* r, const i64* start,
                   const i64* ids, i64 npix_q, const i64* pix, double eps_T, double alpha_max,
-                  double cutoff, const double* bg, double* img, double* Tfin, i64* last, u8* amb) {
+                  double cutoff, const double* bg, double* img, double* Tfin, i64* last, u8* amb,
+                  double* depth) {
   std::vector<GaussView> G(P);
   for (i64 i = 0; i < P; ++i) {
     G[i].omega = omega[i]; G[i].sphg = std::sin(phi[i]); G[i].cphg = std::cos(phi[i]);
@@ -1194,6 +1196,7 @@ void or_composite(int k, int b, i64 P, const double* omega, const double* phi, c
     composite_pixel(om, sp, cp, ids + start[t], start[t + 1] - start[t], G, cfg, po, nullptr, nullptr, nullptr);
     for (int c = 0; c < 3; ++c) img[3 * q + c] = po.C[c];
     Tfin[q] = po.T; last[q] = po.last; amb[q] = (u8)po.amb;
+    if (depth) depth[q] = po.D;
   }
 }
 
@@ -1205,7 +1208,7 @@ void or_backward(int k, int b, i64 P, const double* means, const double* scales,
                  double near, double blur, double eps_T, double alpha_max, double cutoff,
                  const double* bg, const i64* start, const i64* ids, i64 npix_q, const i64* pix,
                  const double* dLdI, double* dmeans, double* dscales, double* drots, double* dopac,
-                 double* dsh) {
+                 double* dsh, const double* dLdD) {
   Cfg cfg{}; cfg.near = near; cfg.blur = blur; cfg.eps_T = eps_T; cfg.alpha_max = alpha_max;
   cfg.cutoff = cutoff; for (int c = 0; c < 3; ++c) cfg.bg[c] = bg[c];
   int K = (deg + 1) * (deg + 1);
@@ -1217,8 +1220,9 @@ void or_backward(int k, int b, i64 P, const double* means, const double* scales,
     for (int c = 0; c < 3; ++c) { G[i].conic[c] = pre[i].conic[c]; G[i].col[c] = pre[i].col[c]; }
     G[i].opac = opac[i]; G[i].r = pre[i].r;
   }
-  // per-Gaussian accumulators: dcol[3], dopac, dconic[3] (a, b-unique, c), domega, dphi
-  const int NA = 9;
+  // per-Gaussian accumulators: dcol[3], dopac, dconic[3] (a, b-unique, c), domega, dphi,
+  // d(1/r) from the depth channel
+  const int NA = 10;
   i64 nside = 1LL << k;
   int nthr = 1;
 #ifdef _OPENMP
@@ -1241,8 +1245,11 @@ void or_backward(int k, int b, i64 P, const double* means, const double* scales,
     PixOut po;
     composite_pixel(om, sp, cp, L, n, G, cfg, po, &al, &Ts, &Gs);
     const double* dI = dLdI + 3 * q;
-    // colour behind entry j, including the background seen through T_final
+    // colour behind entry j, including the background seen through T_final; the depth
+    // channel has no background term
     double Sacc[3] = {po.T * cfg.bg[0], po.T * cfg.bg[1], po.T * cfg.bg[2]};
+    const double dD = dLdD ? dLdD[q] : 0.0;
+    double SD = 0.0;
     for (i64 j = po.last - 1; j >= 0; --j) {
       double a = al[j];
       if (a <= 0) continue;
@@ -1255,6 +1262,9 @@ void or_backward(int k, int b, i64 P, const double* means, const double* scales,
         dLda += dI[c] * (Tj * gv.col[c] - Sacc[c] / (1.0 - a));
         Sacc[c] += Tj * a * gv.col[c];
       }
+      A[gi * NA + 9] += Tj * a * dD;
+      dLda += dD * (Tj / gv.r - SD / (1.0 - a));
+      SD += Tj * a / gv.r;
       if (gv.opac * Gs[j] >= cfg.alpha_max) continue;   // clamped: no gradient to o, m
       A[gi * NA + 3] += dLda * Gs[j];
       double dLdm = -0.5 * dLda * gv.opac * Gs[j];
@@ -1332,7 +1342,9 @@ void or_backward(int k, int b, i64 P, const double* means, const double* scales,
     }
     double dJ[2][3][3];
     dJ_dt(o.t, dJ);
-    double Lt[3] = {0, 0, 0};
+    // depth channel: d(1/r)/dt = -t / r^3
+    const double ir3 = 1.0 / (o.r * o.r * o.r);
+    double Lt[3] = {-Ai[9] * o.t[0] * ir3, -Ai[9] * o.t[1] * ir3, -Ai[9] * o.t[2] * ir3};
     double Lmu2[2] = {Ai[7], Ai[8] + Lphi_S};
     for (int kk = 0; kk < 3; ++kk) {
       Lt[kk] += o.J[0][kk] * Lmu2[0] + o.J[1][kk] * Lmu2[1];

@@ -44,10 +44,11 @@ def quat_rot(q):
         torch.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], -2)
 
 
-def render_dense(params, view, cfg, pix, nside):
+def render_dense(params, view, cfg, pix, nside, with_depth=False):
     """params: dict of float64 tensors (means, scales, rotations, opacities, sh (P,K,3)).
 
-    Returns (colours at pix (n, 3), final transmittance (n,))."""
+    Returns (colours at pix (n, 3), final transmittance (n,)) and, with with_depth, the
+    composited inverse radial depth (n,) (Sec. 3.2: depth supervision by 1/r)."""
     W = torch.as_tensor(np.asarray(view["W"], np.float64))
     b = torch.as_tensor(np.asarray(view["b"], np.float64))
     mu, s, q, o, sh = (params[k] for k in ("means", "scales", "rotations", "opacities", "sh"))
@@ -89,7 +90,7 @@ def render_dense(params, view, cfg, pix, nside):
     key = O.depth_bits(r.detach().numpy()).astype(np.int64)
     key[~valid.numpy()] = np.iinfo(np.int64).max
     order = torch.as_tensor(np.argsort(key, kind="stable"))
-    a = a[:, order]; colo = col[order]
+    a = a[:, order]; colo = col[order]; invr = (1.0 / r)[order]
     one_minus = 1 - a
     T_ex = torch.cumprod(torch.cat([torch.ones_like(a[:, :1]), one_minus[:, :-1]], 1), 1)
     incl = (T_ex >= cfg.eps_T).to(a.dtype).detach()
@@ -97,6 +98,8 @@ def render_dense(params, view, cfg, pix, nside):
     C = w @ colo
     T_fin = torch.prod(torch.where(incl > 0, one_minus, torch.ones_like(one_minus)), 1)
     C = C + T_fin[:, None] * torch.as_tensor(np.asarray(cfg.bg, np.float64))[None, :]
+    if with_depth:
+        return C, T_fin, w @ torch.where(valid[order], invr, torch.zeros_like(invr))
     return C, T_fin
 
 
