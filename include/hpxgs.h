@@ -184,14 +184,17 @@ int hpxgs_forward_workspace_size(int32_t P, const hpxgs_view* views, int nviews,
  * Outputs (packed over views, see "pixel base"): maps [sum Npix, 3],
  * T_final [sum Npix], last [sum Npix] (number of list entries processed),
  * mask_bits [sum Npix / 32] (may be NULL), radii [nviews * P] (r_s in rad,
- * 0 when culled; may be NULL). The workspace keeps what hpxgs_backward needs;
+ * 0 when culled; may be NULL), depth_map [sum Npix] (may be NULL: the
+ * inverse-depth channel D = sum_i T_i alpha_i / r_i of Sec. 3.2's depth
+ * supervision, 0 outside the mask; it runs each tile level's default blend
+ * shape). The workspace keeps what hpxgs_backward needs;
  * do not modify it in between. If more than capacity_pairs pairs are needed,
  * HPXGS_F_CAPACITY is set in *status, the extra pairs are dropped and the
  * outputs are incomplete: grow the capacity and call again. */
 int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
                   void* workspace, size_t workspace_bytes, int64_t capacity_pairs,
                   float* maps, float* T_final, uint32_t* last, uint32_t* mask_bits, float* radii,
-                  int32_t* status, hpxgs_stream_t stream);
+                  float* depth_map, int32_t* status, hpxgs_stream_t stream);
 
 /* Backward (Sec. 3.2, Eqs. backward_lat_scale, grad_via_J_S): from dL/dmaps
  * (packed like maps) and the forward's T_final/last, walk each tile list in
@@ -200,10 +203,12 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
  * them to the parameters. Gradients are written (not accumulated): dmeans
  * [P,3], dscales [P,3], drotations [P,4] (w.r.t. the unnormalised q),
  * dopacities [P], dsh [P,K,3], summed over the views. The cull, cutoff, clamp
- * and termination sets of the forward are held fixed. */
+ * and termination sets of the forward are held fixed. dL_ddepth [sum Npix]
+ * (may be NULL) is the gradient of the inverse-depth channel; it enters through
+ * dL/dalpha and through d(1/r)/dt = -t / r^3. */
 int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
                    void* workspace, size_t workspace_bytes, int64_t capacity_pairs,
-                   const float* dL_dmaps, const float* T_final, const uint32_t* last,
+                   const float* dL_dmaps, const float* T_final, const uint32_t* last, const float* dL_ddepth,
                    float* dmeans, float* dscales, float* drotations, float* dopacities, float* dsh,
                    int32_t* status, hpxgs_stream_t stream);
 

@@ -86,9 +86,9 @@ _SIGS = {
     "hpxgs_neighbours_nest": (ctypes.c_int, [ctypes.c_int, _vp, _i64, _vp, _vp]),
     "hpxgs_forward_workspace_size": (ctypes.c_int, [_i32, _P(View), ctypes.c_int, _P(Config), _i64, _P(_sz)]),
     "hpxgs_forward": (ctypes.c_int, [_P(Gaussians), _P(View), ctypes.c_int, _P(Config), _vp, _sz, _i64, _vp, _vp, _vp,
-                                     _vp, _vp, _vp, _vp]),
+                                     _vp, _vp, _vp, _vp, _vp]),
     "hpxgs_backward": (ctypes.c_int, [_P(Gaussians), _P(View), ctypes.c_int, _P(Config), _vp, _sz, _i64, _vp, _vp,
-                                      _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+                                      _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hpxgs_count_pairs": (ctypes.c_int, [_P(Gaussians), _P(View), ctypes.c_int, _P(Config), _vp, _sz, _vp, _vp, _vp]),
     "hpxgs_workspace_inspect": (ctypes.c_int, [_i32, _P(View), ctypes.c_int, _P(Config), _i64, _vp,
                                                _P(WorkspaceView)]),

@@ -811,15 +811,20 @@ __device__ __forceinline__ int view_of_tile(const ViewTable& vt, int tile) {
   return v;
 }
 
-template <int NT, int PPT, int BATCH>
+// DEPTH adds the inverse-depth channel D = sum_i T_i alpha_i / r_i (Sec. 3.2, depth
+// supervision by 1/r): rdepth holds r per (view, Gaussian), dmap receives D per pixel.
+template <int NT, int PPT, int BATCH, bool DEPTH = false>
 __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
                                                   const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
                                                   const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
                                                   float* __restrict__ maps, float* __restrict__ Tout,
                                                   uint32_t* __restrict__ lastout, uint32_t* work,
-                                                  unsigned long long* __restrict__ evals, const float* __restrict__ chord2) {
+                                                  unsigned long long* __restrict__ evals, const float* __restrict__ chord2,
+                                                  const float* __restrict__ rdepth = nullptr,
+                                                  float* __restrict__ dmap = nullptr) {
   __shared__ float4 s_rec[BATCH][4];
   __shared__ float s_c2[BATCH];
+  __shared__ float s_invr[DEPTH ? BATCH : 1];
   __shared__ int s_tile;
   const int tid = threadIdx.x;
   const int b = vt.b;
@@ -837,6 +842,7 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
     const uint32_t* vmask = mask + (vp.pix_base >> 5);
     float3 pv[PPT];
     float C[PPT][3], T[PPT];
+    float D[DEPTH ? PPT : 1];
     uint32_t last[PPT];
     bool done[PPT], inm[PPT];
     uint32_t lp[PPT];
@@ -848,6 +854,7 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
       done[q] = !inm[q];
       pv[q] = inm[q] ? pix2vec_f32(vp.k, lp[q]) : make_float3(0.f, 0.f, 1.f);
       C[q][0] = C[q][1] = C[q][2] = 0.f;
+      if (DEPTH) D[DEPTH ? q : 0] = 0.f;
       T[q] = 1.f;
       last[q] = 0;
     }
@@ -860,6 +867,7 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
         const float4* src = rec + 4 * (int64_t)id;
         s_rec[e][0] = src[0]; s_rec[e][1] = src[1]; s_rec[e][2] = src[2]; s_rec[e][3] = src[3];
         s_c2[e] = chord2[id];
+        if (DEPTH) s_invr[e] = 1.f / rdepth[id];
       }
       __syncthreads();
 #pragma unroll
@@ -874,6 +882,7 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
             const float a = fminf(vt.alpha_max, r0.w * __expf(-0.5f * P.m));
             const float w = a * T[q];
             C[q][0] += w * r3.x; C[q][1] += w * r3.y; C[q][2] += w * r3.z;
+            if (DEPTH) D[DEPTH ? q : 0] += w * s_invr[e];
             T[q] = T[q] * (1.f - a);
             if (T[q] < vt.eps_T) { done[q] = true; last[q] = bs + e + 1 - rg.x; break; }
           }
@@ -895,10 +904,12 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
         maps[3 * pg + 2] = C[q][2] + T[q] * vt.bg[2];
         Tout[pg] = T[q];
         lastout[pg] = last[q];
+        if (DEPTH) dmap[pg] = D[DEPTH ? q : 0];
       } else if (vt.write_outside) {
         maps[3 * pg + 0] = vt.bg[0]; maps[3 * pg + 1] = vt.bg[1]; maps[3 * pg + 2] = vt.bg[2];
         Tout[pg] = 1.f;
         lastout[pg] = 0;
+        if (DEPTH) dmap[pg] = 0.f;
       }
     }
     // per-warp totals of evaluated and contributing (pixel, entry) pairs
@@ -920,18 +931,25 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
 // Accumulators per (view, Gaussian): [dcol(3), dopacity, dconic_a, dconic_b (unique
 // off-diagonal), dconic_c, d_east, d_north].
 // ----------------------------------------------------------------------------
-template <int NT, int PPT, int BATCH>
+// DEPTH adds the inverse-depth channel: ddepth is dL/dD per pixel, and the tenth
+// partial dL/d(1/r) per (view, Gaussian) goes to accum_d.
+template <int NT, int PPT, int BATCH, bool DEPTH = false>
 __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
                                                   const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
                                                   const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
                                                   const float* __restrict__ dmaps, const float* __restrict__ Tin,
                                                   const uint32_t* __restrict__ lastin, float* __restrict__ accum,
-                                                  uint32_t* work, const float* __restrict__ chord2) {
+                                                  uint32_t* work, const float* __restrict__ chord2,
+                                                  const float* __restrict__ rdepth = nullptr,
+                                                  const float* __restrict__ ddepth = nullptr,
+                                                  float* __restrict__ accum_d = nullptr) {
   constexpr int NW = NT / 32;
+  constexpr int NA = HPXGS_NACC + (DEPTH ? 1 : 0);
   __shared__ float4 s_rec[BATCH][4];
   __shared__ float s_c2[BATCH];
+  __shared__ float s_invr[DEPTH ? BATCH : 1];
   __shared__ uint32_t s_id[BATCH];
-  __shared__ float s_part[BATCH][NW][HPXGS_NACC];
+  __shared__ float s_part[BATCH][NW][NA];
   __shared__ int s_tile;
   __shared__ uint32_t s_maxlast;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -950,6 +968,7 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
     const uint32_t* vmask = mask + (vp.pix_base >> 5);
     float3 pv[PPT];
     float dI[PPT][3], S[PPT][3], T[PPT];
+    float dDp[DEPTH ? PPT : 1], SD[DEPTH ? PPT : 1];    // dL/dD and the depth behind the entry
     uint32_t lastp[PPT];
     uint32_t mylast = 0;
 #pragma unroll
@@ -964,6 +983,7 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
         dI[q][c] = inm ? dmaps[3 * pg + c] : 0.f;
         S[q][c] = T[q] * vt.bg[c];
       }
+      if (DEPTH) { dDp[DEPTH ? q : 0] = inm ? ddepth[pg] : 0.f; SD[DEPTH ? q : 0] = 0.f; }
       mylast = max(mylast, lastp[q]);
     }
     if (mylast) atomicMax(&s_maxlast, mylast);
@@ -979,14 +999,15 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
         const float4* src = rec + 4 * (int64_t)id;
         s_rec[e][0] = src[0]; s_rec[e][1] = src[1]; s_rec[e][2] = src[2]; s_rec[e][3] = src[3];
         s_c2[e] = chord2[id];
+        if (DEPTH) s_invr[e] = 1.f / rdepth[id];
       }
       __syncthreads();
       for (int e = n - 1; e >= 0; --e) {
         const uint32_t j = bs + e - rg.x;          // position in the tile list
         const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
-        float acc[HPXGS_NACC];
+        float acc[NA];
 #pragma unroll
-        for (int c = 0; c < HPXGS_NACC; ++c) acc[c] = 0.f;
+        for (int c = 0; c < NA; ++c) acc[c] = 0.f;
         bool any = false;
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
@@ -1007,6 +1028,13 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
             acc[c] += wj * dI[q][c];
             dLda += dI[q][c] * (Tj * col[c] - S[q][c] * inv1ma);
             S[q][c] += wj * col[c];
+          }
+          if (DEPTH) {
+            const int qd = DEPTH ? q : 0;
+            const float invr = s_invr[e];
+            acc[NA - 1] += wj * dDp[qd];
+            dLda += dDp[qd] * (Tj * invr - SD[qd] * inv1ma);
+            SD[qd] += wj * invr;
           }
           T[q] = Tj;
           any = true;
@@ -1042,7 +1070,7 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
         const unsigned ball = __ballot_sync(0xffffffffu, any);
         if (ball) {
 #pragma unroll
-          for (int c = 0; c < HPXGS_NACC; ++c) {
+          for (int c = 0; c < NA; ++c) {
             float x = acc[c];
             for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
             acc[c] = x;
@@ -1050,16 +1078,18 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
         }
         if (lane == 0) {
 #pragma unroll
-          for (int c = 0; c < HPXGS_NACC; ++c) s_part[e][warp][c] = ball ? acc[c] : 0.f;
+          for (int c = 0; c < NA; ++c) s_part[e][warp][c] = ball ? acc[c] : 0.f;
         }
       }
       __syncthreads();
-      for (int t = tid; t < n * HPXGS_NACC; t += NT) {
-        const int e = t / HPXGS_NACC, c = t - e * HPXGS_NACC;
+      for (int t = tid; t < n * NA; t += NT) {
+        const int e = t / NA, c = t - e * NA;
         float sum = 0.f;
 #pragma unroll
         for (int w = 0; w < NW; ++w) sum += s_part[e][w][c];
-        if (sum != 0.f) atomicAdd(&accum[(int64_t)s_id[e] * HPXGS_NACC + c], sum);
+        if (sum == 0.f) continue;
+        if (!DEPTH || c < HPXGS_NACC) atomicAdd(&accum[(int64_t)s_id[e] * HPXGS_NACC + c], sum);
+        else atomicAdd(&accum_d[s_id[e]], sum);
       }
       be = bs;
     }
@@ -1082,7 +1112,8 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
                                                         const float* __restrict__ radii, const float* __restrict__ accum,
                                                         float* __restrict__ dmeans, float* __restrict__ dscales,
                                                         float* __restrict__ drot, float* __restrict__ dopac,
-                                                        float* __restrict__ dsh) {
+                                                        float* __restrict__ dsh,
+                                                        const float* __restrict__ accum_d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= vt.P) return;
   constexpr int K = (DEG + 1) * (DEG + 1);
@@ -1171,6 +1202,10 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
     Lt[0] = -ir2 * (g1 * G.e1c.x + g2 * G.e2c.x + (h1 + h2) * G.gc.x) + ir * (A[7] * G.e1c.x + A[8] * G.e2c.x);
     Lt[1] = -ir2 * (g1 * G.e1c.y + g2 * G.e2c.y + (h1 + h2) * G.gc.y) + ir * (A[7] * G.e1c.y + A[8] * G.e2c.y);
     Lt[2] = -ir2 * (g1 * G.e1c.z + g2 * G.e2c.z + (h1 + h2) * G.gc.z) + ir * (A[7] * G.e1c.z + A[8] * G.e2c.z);
+    if (accum_d) {                                 // inverse-depth channel: d(1/r)/dt = -t / r^3 = -g_c / r^2
+      const float ad = accum_d[gid] * ir2;
+      Lt[0] -= ad * G.gc.x; Lt[1] -= ad * G.gc.y; Lt[2] -= ad * G.gc.z;
+    }
     for (int e = 0; e < 3; ++e) dmu[e] += vp.W[e] * Lt[0] + vp.W[3 + e] * Lt[1] + vp.W[6 + e] * Lt[2];
     // R(q_hat) -> q_hat -> q
     const float w = G.qn[0], x = G.qn[1], y = G.qn[2], z = G.qn[3];
@@ -1206,14 +1241,14 @@ static int blend_blocks(const void* fn, int nt, int want_per_sm) {
 }
 
 // Launch of a blend kernel with NT threads x PPT pixels per thread = the tile's pixels.
-template <int NT, int PPT, typename... Args>
+template <int NT, int PPT, bool DEPTH = false, typename... Args>
 static void launch_fwd(int bps, cudaStream_t s, Args... args) {
-  auto fn = k_blend_fwd<NT, PPT, 128>;
+  auto fn = k_blend_fwd<NT, PPT, 128, DEPTH>;
   fn<<<blend_blocks((const void*)fn, NT, bps), NT, 0, s>>>(args...);
 }
-template <int NT, int PPT, typename... Args>
+template <int NT, int PPT, bool DEPTH = false, typename... Args>
 static void launch_bwd(int bps, cudaStream_t s, Args... args) {
-  auto fn = k_blend_bwd<NT, PPT, 32>;
+  auto fn = k_blend_bwd<NT, PPT, 32, DEPTH>;
   fn<<<blend_blocks((const void*)fn, NT, bps), NT, 0, s>>>(args...);
 }
 
@@ -1368,7 +1403,7 @@ int hpxgs_count_pairs(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
 
 int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg, void* ws,
                   size_t ws_bytes, int64_t cap, float* maps, float* T_final, uint32_t* last, uint32_t* mask_bits,
-                  float* radii_out, int32_t* status, hpxgs_stream_t stream) {
+                  float* radii_out, float* depth_map, int32_t* status, hpxgs_stream_t stream) {
   if (!check_gaussians(g) || !ws || !maps || !T_final || !last) return HPXGS_E_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   Layout L;
@@ -1434,14 +1469,22 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
   prof_begin(HPXGS_STAGE_BLEND_FWD, s);
   {
     const int ppt = pick_ppt(b, cfg->fwd_ppt, true);
-#define FWD_ARGS bps, s, *vt, (const float4*)rec, (const uint2*)ranges, ids, (const uint32_t*)flags, (const uint32_t*)mask, maps, T_final, last, work, evals, chord
-    if (b == 3) { if (ppt == 2) launch_fwd<32, 2>(FWD_ARGS); else launch_fwd<64, 1>(FWD_ARGS); }
+#define FWD_BASE bps, s, *vt, (const float4*)rec, (const uint2*)ranges, ids, (const uint32_t*)flags, (const uint32_t*)mask, maps, T_final, last, work, evals, chord
+#define FWD_ARGS FWD_BASE, (const float*)nullptr, (float*)nullptr
+#define FWD_DEPTH_ARGS FWD_BASE, (const float*)at<float>(ws, L.depth), depth_map
+    if (depth_map) {                               // the depth channel runs in each level's default shape
+      if (b == 3) launch_fwd<64, 1, true>(FWD_DEPTH_ARGS);
+      else if (b == 4) launch_fwd<256, 1, true>(FWD_DEPTH_ARGS);
+      else launch_fwd<256, 4, true>(FWD_DEPTH_ARGS);
+    } else if (b == 3) { if (ppt == 2) launch_fwd<32, 2>(FWD_ARGS); else launch_fwd<64, 1>(FWD_ARGS); }
     else if (b == 4) {
       if (ppt == 2) launch_fwd<128, 2>(FWD_ARGS);
       else if (ppt == 4) launch_fwd<64, 4>(FWD_ARGS);
       else launch_fwd<256, 1>(FWD_ARGS);
     } else { if (ppt == 8) launch_fwd<128, 8>(FWD_ARGS); else launch_fwd<256, 4>(FWD_ARGS); }
+#undef FWD_DEPTH_ARGS
 #undef FWD_ARGS
+#undef FWD_BASE
   }
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
@@ -1456,8 +1499,8 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
 
 int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg, void* ws,
                    size_t ws_bytes, int64_t cap, const float* dmaps, const float* T_final, const uint32_t* last,
-                   float* dmeans, float* dscales, float* drot, float* dopac, float* dsh, int32_t* status,
-                   hpxgs_stream_t stream) {
+                   const float* ddepth, float* dmeans, float* dscales, float* drot, float* dopac, float* dsh,
+                   int32_t* status, hpxgs_stream_t stream) {
   (void)status;
   if (!check_gaussians(g) || !ws || !dmaps || !T_final || !last) return HPXGS_E_INVALID_ARG;
   if (g->P > 0 && (!dmeans || !dscales || !drot || !dopac || !dsh)) return HPXGS_E_INVALID_ARG;
@@ -1476,6 +1519,9 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   uint32_t* counters = at<uint32_t>(ws, L.counters);
   float* accum = at<float>(ws, L.accum);
   HPXGS_CUDA_CHECK(cudaMemsetAsync(accum, 0, sizeof(float) * HPXGS_NACC * PV, s));
+  float* accum_d = at<float>(ws, L.accum_d);
+  if (ddepth) HPXGS_CUDA_CHECK(cudaMemsetAsync(accum_d, 0, sizeof(float) * PV, s));
+  const float* rdepth = at<float>(ws, L.depth);
   HPXGS_CUDA_CHECK(cudaMemsetAsync(counters + C_WORK_BWD, 0, sizeof(uint32_t), s));
   const int passes = (L.pair_bits + 7) / 8;
   const uint32_t* ids = (passes & 1) ? at<uint32_t>(ws, L.pair_val_b) : at<uint32_t>(ws, L.pair_val_a);
@@ -1491,14 +1537,22 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   {
     // several pixels per thread: the per-entry warp reduction then covers 32 * PPT pixels
     const int ppt = pick_ppt(b, cfg->bwd_ppt, false);
-#define BWD_ARGS bps, s, *vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, chord
-    if (b == 3) { if (ppt == 1) launch_bwd<64, 1>(BWD_ARGS); else launch_bwd<32, 2>(BWD_ARGS); }
+#define BWD_BASE bps, s, *vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, chord
+#define BWD_ARGS BWD_BASE, (const float*)nullptr, (const float*)nullptr, (float*)nullptr
+#define BWD_DEPTH_ARGS BWD_BASE, rdepth, ddepth, accum_d
+    if (ddepth) {                                  // the depth channel runs in each level's default shape
+      if (b == 3) launch_bwd<32, 2, true>(BWD_DEPTH_ARGS);
+      else if (b == 4) launch_bwd<64, 4, true>(BWD_DEPTH_ARGS);
+      else launch_bwd<256, 4, true>(BWD_DEPTH_ARGS);
+    } else if (b == 3) { if (ppt == 1) launch_bwd<64, 1>(BWD_ARGS); else launch_bwd<32, 2>(BWD_ARGS); }
     else if (b == 4) {
       if (ppt == 2) launch_bwd<128, 2>(BWD_ARGS);
       else if (ppt == 8) launch_bwd<32, 8>(BWD_ARGS);
       else launch_bwd<64, 4>(BWD_ARGS);
     } else { if (ppt == 8) launch_bwd<128, 8>(BWD_ARGS); else launch_bwd<256, 4>(BWD_ARGS); }
+#undef BWD_DEPTH_ARGS
 #undef BWD_ARGS
+#undef BWD_BASE
   }
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
@@ -1507,11 +1561,12 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   {
     const int nb = (int)((g->P + 127) / 128);
     const float* rad = at<float>(ws, L.radii);
+    const float* acd = ddepth ? at<float>(ws, L.accum_d) : nullptr;
     switch (g->sh_degree) {
-      case 0: k_preprocess_bwd<0><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh); break;
-      case 1: k_preprocess_bwd<1><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh); break;
-      case 2: k_preprocess_bwd<2><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh); break;
-      default: k_preprocess_bwd<3><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh); break;
+      case 0: k_preprocess_bwd<0><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh, acd); break;
+      case 1: k_preprocess_bwd<1><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh, acd); break;
+      case 2: k_preprocess_bwd<2><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh, acd); break;
+      default: k_preprocess_bwd<3><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh, acd); break;
     }
   }
   note_launches(1);

@@ -96,8 +96,9 @@ class Rasterizer:
                                           _ptr(cnt), _ptr(st), ctypes.c_void_p(_stream())), "count_pairs")
         return int(cnt.item())
 
-    def forward_raw(self, means, scales, rotations, opacities, sh, sh_degree, views, check_status=True):
-        """Runs hpxgs_forward; returns a dict of outputs and the state the backward needs."""
+    def forward_raw(self, means, scales, rotations, opacities, sh, sh_degree, views, check_status=True, depth=False):
+        """Runs hpxgs_forward; returns a dict of outputs and the state the backward needs.
+        With depth=True the outputs also hold "depth", the inverse-depth channel."""
         means, scales, rotations, opacities, sh = map(_f32, (means, scales, rotations, opacities, sh))
         dev = means.device
         g = gaussians_struct(means, scales, rotations, opacities, sh, sh_degree)
@@ -115,9 +116,11 @@ class Rasterizer:
             last = torch.empty(lay.total_pix, dtype=torch.int32, device=dev)
             mask = torch.empty(lay.total_pix // 32, dtype=torch.int32, device=dev)
             radii = torch.empty((nv, g.P), dtype=torch.float32, device=dev)
+            dmap = torch.empty(lay.total_pix, dtype=torch.float32, device=dev) if depth else None
             status = torch.zeros(1, dtype=torch.int32, device=dev)
             L.check(L.lib().hpxgs_forward(ctypes.byref(g), cv, nv, ctypes.byref(self.cfg), _ptr(ws), nb, cap, _ptr(maps),
-                                          _ptr(T), _ptr(last), _ptr(mask), _ptr(radii), _ptr(status),
+                                          _ptr(T), _ptr(last), _ptr(mask), _ptr(radii),
+                                          _ptr(dmap) if depth else None, _ptr(status),
                                           ctypes.c_void_p(_stream())), "forward")
             if not check_status:
                 break
@@ -131,16 +134,22 @@ class Rasterizer:
             raise L.HpxgsError(L.E_CAPACITY, "forward")
         state = dict(ws=ws, nb=nb, cap=cap, cviews=cv, nv=nv, g=g, T=T, last=last, status=status,
                      keep=(means, scales, rotations, opacities, sh), sh_degree=sh_degree)
-        return dict(maps=maps, T=T, last=last, mask=mask, radii=radii, status=status, layout=lay), state
+        out = dict(maps=maps, T=T, last=last, mask=mask, radii=radii, status=status, layout=lay)
+        if depth:
+            out["depth"] = dmap
+        return out, state
 
-    def backward_raw(self, state, dmaps):
+    def backward_raw(self, state, dmaps, ddepth=None):
+        """Runs hpxgs_backward from dL/dmaps (and optionally dL/ddepth of the inverse-depth channel)."""
         means, scales, rotations, opacities, sh = state["keep"]
         dmaps = _f32(dmaps)
+        ddepth = _f32(ddepth) if ddepth is not None else None
         dm, ds, dq, do, dsh = (torch.empty_like(t) for t in (means, scales, rotations, opacities, sh))
         st = torch.zeros(1, dtype=torch.int32, device=means.device)
         L.check(L.lib().hpxgs_backward(ctypes.byref(state["g"]), state["cviews"], state["nv"], ctypes.byref(self.cfg),
                                        _ptr(state["ws"]), state["nb"], state["cap"], _ptr(dmaps), _ptr(state["T"]),
-                                       _ptr(state["last"]), _ptr(dm), _ptr(ds), _ptr(dq), _ptr(do), _ptr(dsh), _ptr(st),
+                                       _ptr(state["last"]), _ptr(ddepth) if ddepth is not None else None,
+                                       _ptr(dm), _ptr(ds), _ptr(dq), _ptr(do), _ptr(dsh), _ptr(st),
                                        ctypes.c_void_p(_stream())), "backward")
         return dm, ds, dq, do, dsh
 
@@ -161,12 +170,38 @@ class _RenderFn(torch.autograd.Function):
         return (*grads, None, None, None, None)
 
 
+class _RenderDepthFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, scales, rotations, opacities, sh, rast, views, sh_degree, check_status):
+        out, state = rast.forward_raw(means, scales, rotations, opacities, sh, sh_degree, views, check_status,
+                                      depth=True)
+        ctx.rast = rast
+        ctx.state = state
+        ctx.mark_non_differentiable(out["T"], out["last"], out["mask"], out["radii"])
+        return out["maps"], out["depth"], out["T"], out["last"], out["mask"], out["radii"]
+
+    @staticmethod
+    def backward(ctx, dmaps, ddepth, dT, dlast, dmask, dradii):
+        T = ctx.state["T"]
+        if dmaps is None:
+            dmaps = torch.zeros((T.shape[0], 3), dtype=torch.float32, device=T.device)
+        if ddepth is None:
+            ddepth = torch.zeros_like(T)
+        grads = ctx.rast.backward_raw(ctx.state, dmaps.contiguous(), ddepth.contiguous())
+        ctx.state = None
+        return (*grads, None, None, None, None)
+
+
 def render(means, scales, rotations, opacities, sh, views, rasterizer: Rasterizer | None = None, sh_degree=None,
-           check_status=True):
-    """Differentiable render of `views`: returns (maps, T_final, last, mask_words, radii), packed over views."""
+           check_status=True, with_depth=False):
+    """Differentiable render of `views`: returns (maps, T_final, last, mask_words, radii), packed over views;
+    with with_depth, (maps, depth, T_final, last, mask_words, radii) where depth is the inverse-depth
+    channel sum_i T_i alpha_i / r_i (Sec. 3.2), differentiable like maps."""
     rast = rasterizer or Rasterizer()
     if sh_degree is None:
         sh_degree = int(round(math.sqrt(sh.shape[1]))) - 1
+    if with_depth:
+        return _RenderDepthFn.apply(means, scales, rotations, opacities, sh, rast, views, sh_degree, check_status)
     return _RenderFn.apply(means, scales, rotations, opacities, sh, rast, views, sh_degree, check_status)
 
 

@@ -135,7 +135,7 @@ class RenderServer:
             status = torch.zeros(1, dtype=torch.int32, device=self.dev)
             p = lambda t: ctypes.c_void_p(t.data_ptr())
             L.check(L.lib().hpxgs_forward(ctypes.byref(self.g), cv, len(views), ctypes.byref(cfg), p(ws),
-                                          ws_n.value, int(cap), p(maps), p(T), p(last), p(mask), None, p(status),
+                                          ws_n.value, int(cap), p(maps), p(T), p(last), p(mask), None, None, p(status),
                                           ctypes.c_void_p(stream.cuda_stream)), "forward")
             ev = torch.cuda.Event()
             ev.record(stream)

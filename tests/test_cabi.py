@@ -65,7 +65,7 @@ def test_host_argument_checks(lib):
     # null required pointers are rejected before any launch
     g = L.Gaussians(); g.P = 10; g.sh_degree = 0
     assert lib.hpxgs_forward(ctypes.byref(g), v, 1, ctypes.byref(cfg), None, 0, 0, None, None, None, None, None, None,
-                             None) == L.E_INVALID_ARG
+                             None, None) == L.E_INVALID_ARG
     assert lib.hpxgs_hssim_workspace_size(2, ctypes.byref(n)) == L.E_INVALID_ARG
     assert lib.hpxgs_pix2vec_nest(20, None, 1, None, None, None) == L.E_INVALID_ARG
 
