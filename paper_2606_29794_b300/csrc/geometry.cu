@@ -318,9 +318,13 @@ int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nvi
     p.pix_base = pix_base;
     p.rho = 0;
     p.rho32 = 0.f;
+    p.rho_sub32 = 0.f;
     if (need_rho) {
       int rc = tile_rho(p.k, cfg->tile_level, &p.rho, stream);
+      double rs = 0;
+      if (rc == HPXGS_OK) rc = tile_rho(p.k, 2, &rs, stream);
       if (rc != HPXGS_OK) return rc;
+      p.rho_sub32 = (float)rs;
     }
     // FoV cap: every in-mask pixel lies within psi_max of the optical axis (camera +z), an
     // active tile's centre within rho of one of them, and a listed tile's centre within

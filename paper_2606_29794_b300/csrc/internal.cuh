@@ -26,7 +26,7 @@ struct ViewParams {
   int ntiles;          // 12 * 4^(k-b)
   int64_t pix_base;    // first pixel of this view in packed outputs
   int tile_base;       // first global tile id of this view
-  int pad;
+  float rho_sub32;     // rho(k, 2): 4 x 4 sub-tile centre to pixel bound (the blend's cull)
 };
 
 struct ViewTable {

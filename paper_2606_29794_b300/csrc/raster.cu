@@ -800,6 +800,61 @@ __device__ __forceinline__ bool pixel_weight(const float3 p, const float4 r0, co
   return true;
 }
 
+// Cull of (entry, 32-pixel group) pairs, taken once per staged entry. A tile's
+// pixels split into 16-pixel sub-tiles (the order-(k-2) pixels inside it) whose
+// pixel centres lie within rho_sub of the sub-tile centre p_c. For a pixel with
+// FP32 offset U that contributes (m <= cutoff), m = q(U) (theta/s)^2 with
+// (theta/s)^2 >= 1 (the series is 1 + positive terms; the atan form runs at
+// theta >= 0.2, where theta/s - 1 >= theta^2/6 dwarfs FP32 error), so the exact
+// form satisfies q(U) <= cutoff (1 + 1e-5) + g M |U|^2, with g M |U|^2 bounding
+// the FP32 rounding of q (g = 2e-6 is ~30 units of 2^-24, M = max(A, C) + |B|).
+// sqrt(q) is a norm and |U - u_c| <= rho' (rho_sub plus FP32 slack of the
+// directions and projections), so
+//   sqrt(q(u_c)) <= sqrt(cut + 2 g M (|u_c|^2 + rho'^2)) + sqrt(lambda_max) rho'
+//                <= c0 + c1 |u_c|^2   (sqrt(a^2 + x) <= a + x / (2a)).
+// A sub-tile whose centre violates that bound (with q(u_c) lowered by its own
+// rounding bound and the right side raised by 1e-5) holds no contributing pixel
+// in this kernel's own arithmetic, so skipping it leaves every output bit-identical.
+// Returns bit g set when sub-tile 2g or 2g+1 may hold a contributing pixel.
+template <int NS>
+__device__ __forceinline__ uint32_t live_groups(const float4 r0, const float4 r1, const float4 r2, const float4 r3,
+                                               const float3* __restrict__ sub, float rho_p, float sqrt_cut) {
+  const float A = r1.w, B = r2.w, C = r3.w;
+  const float h = 0.5f * (A - C);
+  const float lmax = (0.5f * (A + C) + sqrtf(h * h + B * B)) * (1.f + 1e-5f);
+  const float gM = 2e-6f * (fmaxf(A, C) + fabsf(B));
+  const float c1 = gM / sqrt_cut;
+  const float c0 = sqrt_cut + c1 * rho_p * rho_p + sqrtf(lmax) * rho_p;
+  uint32_t live = 0;
+#pragma unroll 2
+  for (int t = 0; t < NS; ++t) {
+    const float3 pc = sub[t];
+    const float dx = pc.x - r0.x, dy = pc.y - r0.y, dz = pc.z - r0.z;
+    const float u1 = dx * r1.x + dy * r1.y + dz * r1.z;
+    const float u2 = dx * r2.x + dy * r2.y + dz * r2.z;
+    const float s2 = u1 * u1 + u2 * u2;
+    const float q = u1 * (A * u1 + 2.f * B * u2) + C * u2 * u2;
+    const float rhs = c0 + c1 * s2;
+    const bool cull = q - gM * s2 > rhs * rhs * (1.f + 1e-5f);   // false for NaN: kept
+    live |= (cull ? 0u : 1u) << (t >> 1);
+  }
+  return live;
+}
+
+// Resident blocks per SM the blend kernels ask of the register allocator: the
+// group guards of the cull would otherwise grow the one- and four-pixel shapes
+// (40 and 96 registers without them) and cost them resident warps.
+constexpr int fwd_min_blocks(int nt, int ppt, bool depth) { return (ppt == 1 && nt >= 128 && !depth) ? 65536 / (nt * 40) : 1; }
+constexpr int bwd_min_blocks(int nt, int ppt, bool depth) { return (ppt <= 4 && !depth) ? 65536 / (nt * 96) : 1; }
+
+// Sub-tile centres of a tile (order k - 2 pixels) and the cull's per-view constants.
+template <int NS>
+__device__ __forceinline__ void sub_centres(const ViewParams& vp, uint32_t lt, int b, float3* sub, int tid, int nt) {
+  for (int t = tid; t < NS; t += nt) sub[t] = pix2vec_f32(vp.k - 2, (lt << (2 * (b - 2))) + (uint32_t)t);
+}
+__device__ __forceinline__ float cull_rho(const ViewParams& vp) { return vp.rho_sub32 * (1.f + 1e-5f) + 4e-6f; }
+__device__ __forceinline__ float cull_sqrt_cut(float cutoff) { return sqrtf(cutoff * (1.f + 1e-5f)) * (1.f + 1e-6f); }
+
 // ----------------------------------------------------------------------------
 // Forward compositing: persistent blocks take tiles from a counter; one thread
 // per pixel (PPT pixels per thread for 1024-pixel tiles); Gaussian records of the
@@ -814,20 +869,26 @@ __device__ __forceinline__ int view_of_tile(const ViewTable& vt, int tile) {
 // DEPTH adds the inverse-depth channel D = sum_i T_i alpha_i / r_i (Sec. 3.2, depth
 // supervision by 1/r): rdepth holds r per (view, Gaussian), dmap receives D per pixel.
 template <int NT, int PPT, int BATCH, bool DEPTH = false>
-__global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
+__global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fwd(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
                                                   const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
                                                   const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
                                                   float* __restrict__ maps, float* __restrict__ Tout,
                                                   uint32_t* __restrict__ lastout, uint32_t* work,
                                                   unsigned long long* __restrict__ evals, const float* __restrict__ chord2,
+                                                  uint32_t* __restrict__ gmask,
                                                   const float* __restrict__ rdepth = nullptr,
                                                   float* __restrict__ dmap = nullptr) {
+  constexpr int NW = NT / 32;
+  constexpr int NS = NT * PPT / 16;                 // 16-pixel sub-tiles per tile
   __shared__ float4 s_rec[BATCH][4];
   __shared__ float s_c2[BATCH];
   __shared__ float s_invr[DEPTH ? BATCH : 1];
+  __shared__ uint32_t s_gm[BATCH];                  // live 32-pixel groups per staged entry
+  __shared__ float3 s_sub[NS];
   __shared__ int s_tile;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int b = vt.b;
+  const float sqrt_cut = cull_sqrt_cut(vt.cutoff);
   for (;;) {
     if (tid == 0) s_tile = (int)atomicAdd(work, 1u);
     __syncthreads();
@@ -840,6 +901,8 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
     const bool active = flags[tile] & 1u;
     if (!active && !vt.write_outside) continue;
     const uint32_t* vmask = mask + (vp.pix_base >> 5);
+    const float rho_p = cull_rho(vp);
+    sub_centres<NS>(vp, lt, b, s_sub, tid, NT);
     float3 pv[PPT];
     float C[PPT][3], T[PPT];
     float D[DEPTH ? PPT : 1];
@@ -865,15 +928,21 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
       for (int e = tid; e < n; e += NT) {
         const uint32_t id = ids[bs + e];
         const float4* src = rec + 4 * (int64_t)id;
-        s_rec[e][0] = src[0]; s_rec[e][1] = src[1]; s_rec[e][2] = src[2]; s_rec[e][3] = src[3];
+        const float4 a0 = src[0], a1 = src[1], a2 = src[2], a3 = src[3];
+        s_rec[e][0] = a0; s_rec[e][1] = a1; s_rec[e][2] = a2; s_rec[e][3] = a3;
         s_c2[e] = chord2[id];
         if (DEPTH) s_invr[e] = 1.f / rdepth[id];
+        const uint32_t gm = live_groups<NS>(a0, a1, a2, a3, s_sub, rho_p, sqrt_cut);
+        s_gm[e] = gm;
+        gmask[bs + e] = gm;                          // for the backward pass over the same entries
       }
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
         if (done[q]) continue;
+        const int gq = q * NW + warp;
         for (int e = 0; e < n; ++e) {
+          if (!((s_gm[e] >> gq) & 1u)) continue;     // no pixel of this warp's group can contribute
           const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
           Pix P;
           if (!pixel_weight(pv[q], r0, r1, r2, r3, s_c2[e], P)) continue;
@@ -934,12 +1003,13 @@ __global__ void __launch_bounds__(NT) k_blend_fwd(const __grid_constant__ ViewTa
 // DEPTH adds the inverse-depth channel: ddepth is dL/dD per pixel, and the tenth
 // partial dL/d(1/r) per (view, Gaussian) goes to accum_d.
 template <int NT, int PPT, int BATCH, bool DEPTH = false>
-__global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
+__global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bwd(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
                                                   const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
                                                   const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
                                                   const float* __restrict__ dmaps, const float* __restrict__ Tin,
                                                   const uint32_t* __restrict__ lastin, float* __restrict__ accum,
                                                   uint32_t* work, const float* __restrict__ chord2,
+                                                  const uint32_t* __restrict__ gmask,
                                                   const float* __restrict__ rdepth = nullptr,
                                                   const float* __restrict__ ddepth = nullptr,
                                                   float* __restrict__ accum_d = nullptr) {
@@ -950,10 +1020,14 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
   __shared__ float s_invr[DEPTH ? BATCH : 1];
   __shared__ uint32_t s_id[BATCH];
   __shared__ float s_part[BATCH][NW][NA];
+  __shared__ uint32_t s_gm[BATCH];                  // live 32-pixel groups per staged entry
   __shared__ int s_tile;
   __shared__ uint32_t s_maxlast;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int b = vt.b;
+  uint32_t wgroups = 0;                             // this warp's groups q * NW + warp
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) wgroups |= 1u << (q * NW + warp);
   for (;;) {
     if (tid == 0) { s_tile = (int)atomicAdd(work, 1u); s_maxlast = 0; }
     __syncthreads();
@@ -1000,9 +1074,12 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
         s_rec[e][0] = src[0]; s_rec[e][1] = src[1]; s_rec[e][2] = src[2]; s_rec[e][3] = src[3];
         s_c2[e] = chord2[id];
         if (DEPTH) s_invr[e] = 1.f / rdepth[id];
+        s_gm[e] = gmask[bs + e];                   // the forward's cull of this entry
       }
       __syncthreads();
       for (int e = n - 1; e >= 0; --e) {
+        const uint32_t gm = s_gm[e];
+        if (!(gm & wgroups)) continue;             // no pixel of this warp can contribute: no partials
         const uint32_t j = bs + e - rg.x;          // position in the tile list
         const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
         float acc[NA];
@@ -1011,7 +1088,7 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
         bool any = false;
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
-          if (j >= lastp[q]) continue;
+          if (j >= lastp[q] || !((gm >> (q * NW + warp)) & 1u)) continue;
           Pix P;
           if (!pixel_weight(pv[q], r0, r1, r2, r3, s_c2[e], P)) continue;
           if (!(P.m <= vt.cutoff)) continue;
@@ -1084,9 +1161,15 @@ __global__ void __launch_bounds__(NT) k_blend_bwd(const __grid_constant__ ViewTa
       __syncthreads();
       for (int t = tid; t < n * NA; t += NT) {
         const int e = t / NA, c = t - e * NA;
+        const uint32_t gm = s_gm[e];
         float sum = 0.f;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) sum += s_part[e][w][c];
+        for (int w = 0; w < NW; ++w) {
+          uint32_t wg = 0;
+#pragma unroll
+          for (int q = 0; q < PPT; ++q) wg |= 1u << (q * NW + w);
+          if (gm & wg) sum += s_part[e][w][c];      // warps with no live group wrote no partials
+        }
         if (sum == 0.f) continue;
         if (!DEPTH || c < HPXGS_NACC) atomicAdd(&accum[(int64_t)s_id[e] * HPXGS_NACC + c], sum);
         else atomicAdd(&accum_d[s_id[e]], sum);
@@ -1461,6 +1544,7 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
   }
   const int passes = (L.pair_bits + 7) / 8;
   const uint32_t* ids = (passes & 1) ? pvb : pva;
+  uint32_t* gmask = (passes & 1) ? pka : pkb;        // the sort's free key buffer: per-entry cull masks
   uint32_t* work = counters + C_WORK_FWD;
   unsigned long long* evals = reinterpret_cast<unsigned long long*>(counters + C_NEVAL);
   const int b = cfg->tile_level;
@@ -1469,7 +1553,7 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
   prof_begin(HPXGS_STAGE_BLEND_FWD, s);
   {
     const int ppt = pick_ppt(b, cfg->fwd_ppt, true);
-#define FWD_BASE bps, s, *vt, (const float4*)rec, (const uint2*)ranges, ids, (const uint32_t*)flags, (const uint32_t*)mask, maps, T_final, last, work, evals, chord
+#define FWD_BASE bps, s, *vt, (const float4*)rec, (const uint2*)ranges, ids, (const uint32_t*)flags, (const uint32_t*)mask, maps, T_final, last, work, evals, chord, gmask
 #define FWD_ARGS FWD_BASE, (const float*)nullptr, (float*)nullptr
 #define FWD_DEPTH_ARGS FWD_BASE, (const float*)at<float>(ws, L.depth), depth_map
     if (depth_map) {                               // the depth channel runs in each level's default shape
@@ -1525,6 +1609,7 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   HPXGS_CUDA_CHECK(cudaMemsetAsync(counters + C_WORK_BWD, 0, sizeof(uint32_t), s));
   const int passes = (L.pair_bits + 7) / 8;
   const uint32_t* ids = (passes & 1) ? at<uint32_t>(ws, L.pair_val_b) : at<uint32_t>(ws, L.pair_val_a);
+  const uint32_t* gmask = (passes & 1) ? at<uint32_t>(ws, L.pair_key_a) : at<uint32_t>(ws, L.pair_key_b);
   const float4* rec = at<float4>(ws, L.records);
   const uint2* ranges = at<uint2>(ws, L.ranges);
   const uint32_t* flags = at<uint32_t>(ws, L.tile_flags);
@@ -1537,7 +1622,7 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   {
     // several pixels per thread: the per-entry warp reduction then covers 32 * PPT pixels
     const int ppt = pick_ppt(b, cfg->bwd_ppt, false);
-#define BWD_BASE bps, s, *vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, chord
+#define BWD_BASE bps, s, *vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, chord, gmask
 #define BWD_ARGS BWD_BASE, (const float*)nullptr, (const float*)nullptr, (float*)nullptr
 #define BWD_DEPTH_ARGS BWD_BASE, rdepth, ddepth, accum_d
     if (ddepth) {                                  // the depth channel runs in each level's default shape
