@@ -109,6 +109,11 @@ typedef struct {
    * every tile the cutoff ellipse can reach, so the maps do not depend on it. */
   int32_t query;
   int32_t query_log2f;
+  /* 1 (default): the blends skip a list entry for each group of 32 pixels that a
+   * conservative bound on its conic shows it cannot reach (m > cutoff in the
+   * kernels' own arithmetic); 0: every entry is evaluated at every pixel. The
+   * results are the same bit for bit either way. */
+  int32_t blend_cull;
 } hpxgs_config;
 
 #define HPXGS_QUERY_RING 0
@@ -307,6 +312,11 @@ typedef struct {
   const uint64_t* n_eval;      /* device scalar: (pixel, list entry) evaluations of the last forward blend */
   const uint64_t* n_contrib;   /* device scalar: of those, entries with alpha > 0 */
   int64_t total_tiles;
+  /* [n_pairs] blend cull per list entry (aligned with pair_ids): bit g set unless
+   * no pixel of the entry's tile at in-tile NESTED offsets 32g .. 32g+31 can reach
+   * m <= cutoff. Written by the forward blend for every entry it staged (at least
+   * the first max(last) entries of each active tile); read by the backward. */
+  const uint32_t* cull_masks;
 } hpxgs_workspace_view;
 int hpxgs_workspace_inspect(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
                             int64_t capacity_pairs, const void* workspace, hpxgs_workspace_view* out);

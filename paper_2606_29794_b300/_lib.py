@@ -43,14 +43,14 @@ class Config(ctypes.Structure):
                 ("cutoff_m", ctypes.c_float), ("blur_rad2", ctypes.c_float), ("near_plane", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("lambda_ssim", ctypes.c_float), ("write_outside", ctypes.c_int32),
                 ("fwd_ppt", ctypes.c_int32), ("bwd_ppt", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("query", ctypes.c_int32), ("query_log2f", ctypes.c_int32)]
+                ("query", ctypes.c_int32), ("query_log2f", ctypes.c_int32), ("blend_cull", ctypes.c_int32)]
 
 
 class WorkspaceView(ctypes.Structure):
     _fields_ = [("records", ctypes.c_void_p), ("radii", ctypes.c_void_p), ("depth", ctypes.c_void_p),
                 ("pair_tiles", ctypes.c_void_p), ("pair_ids", ctypes.c_void_p), ("ranges", ctypes.c_void_p),
                 ("n_pairs", ctypes.c_void_p), ("accum", ctypes.c_void_p), ("n_eval", ctypes.c_void_p),
-                ("n_contrib", ctypes.c_void_p), ("total_tiles", ctypes.c_int64)]
+                ("n_contrib", ctypes.c_void_p), ("total_tiles", ctypes.c_int64), ("cull_masks", ctypes.c_void_p)]
 
 
 class HpxgsError(RuntimeError):

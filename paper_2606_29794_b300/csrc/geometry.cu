@@ -225,7 +225,7 @@ static bool valid_cfg(const hpxgs_config* c) {
          c->alpha_max > 0 && c->alpha_max < 1 && c->cutoff_m > 0 && c->near_plane >= 0 &&
          valid_ppt(c->fwd_ppt) && valid_ppt(c->bwd_ppt) && c->blocks_per_sm >= 0 && c->blocks_per_sm <= 64 &&
          (c->query == HPXGS_QUERY_RING || c->query == HPXGS_QUERY_NESTED) && c->query_log2f >= 0 &&
-         c->query_log2f <= 3;
+         c->query_log2f <= 3 && (c->blend_cull == 0 || c->blend_cull == 1);
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -355,6 +355,7 @@ int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nvi
   vt->total_pix = pix_base;
   vt->query = cfg->query;
   vt->log2f = cfg->query_log2f;
+  vt->cull = cfg->blend_cull;
   for (int o = 0; o < 16; ++o) { vt->pixrad32[o] = 0.f; vt->pixrad64[o] = 0.0; }
   if (need_rho && cfg->query == HPXGS_QUERY_NESTED) {
     int omax = 0;
@@ -448,6 +449,7 @@ void hpxgs_config_default(hpxgs_config* c) {
   c->blocks_per_sm = 0;
   c->query = HPXGS_QUERY_RING;
   c->query_log2f = 2;
+  c->blend_cull = 1;
 }
 
 int hpxgs_nside_for_image(int kind, double W, double H, double fovx, double fovy, double* nstar, int* k,

@@ -40,6 +40,7 @@ struct ViewTable {
   int total_tiles;
   int query;           // HPXGS_QUERY_*
   int log2f;           // NESTED query: refinement below the tile order
+  int cull;            // 1: the blends' per-(entry, 32-pixel group) cull is on
   float pixrad32[16];  // NESTED query: PixRad(o), o = 0 .. deepest order used
   double pixrad64[16];
   int64_t total_pix;

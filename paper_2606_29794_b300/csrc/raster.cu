@@ -883,7 +883,9 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
   __shared__ float4 s_rec[BATCH][4];
   __shared__ float s_c2[BATCH];
   __shared__ float s_invr[DEPTH ? BATCH : 1];
-  __shared__ uint32_t s_gm[BATCH];                  // live 32-pixel groups per staged entry
+  constexpr int NG = NS / 2;                        // 32-pixel groups per tile
+  constexpr int BW = BATCH / 32;                    // bitmap words per batch
+  __shared__ uint32_t s_live[NG][BW];               // per group: the staged entries it may take
   __shared__ float3 s_sub[NS];
   __shared__ int s_tile;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -925,35 +927,50 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
     for (uint32_t bs = rg.x; bs < rg.y; bs += BATCH) {
       const int n = (int)min((uint32_t)BATCH, rg.y - bs);
       __syncthreads();
-      for (int e = tid; e < n; e += NT) {
-        const uint32_t id = ids[bs + e];
-        const float4* src = rec + 4 * (int64_t)id;
-        const float4 a0 = src[0], a1 = src[1], a2 = src[2], a3 = src[3];
-        s_rec[e][0] = a0; s_rec[e][1] = a1; s_rec[e][2] = a2; s_rec[e][3] = a3;
-        s_c2[e] = chord2[id];
-        if (DEPTH) s_invr[e] = 1.f / rdepth[id];
-        const uint32_t gm = live_groups<NS>(a0, a1, a2, a3, s_sub, rho_p, sqrt_cut);
-        s_gm[e] = gm;
-        gmask[bs + e] = gm;                          // for the backward pass over the same entries
+      for (int e0 = 0; e0 < n; e0 += NT) {
+        const int e = e0 + tid;
+        uint32_t gm = 0;
+        if (e < n) {
+          const uint32_t id = ids[bs + e];
+          const float4* src = rec + 4 * (int64_t)id;
+          const float4 a0 = src[0], a1 = src[1], a2 = src[2], a3 = src[3];
+          s_rec[e][0] = a0; s_rec[e][1] = a1; s_rec[e][2] = a2; s_rec[e][3] = a3;
+          s_c2[e] = chord2[id];
+          if (DEPTH) s_invr[e] = 1.f / rdepth[id];
+          gm = vt.cull ? live_groups<NS>(a0, a1, a2, a3, s_sub, rho_p, sqrt_cut) : ~0u;
+          gmask[bs + e] = gm;                        // for the backward pass over the same entries
+        }
+        if (e0 + (warp << 5) < n) {                  // this warp staged entries: one bitmap word per group
+#pragma unroll
+          for (int g = 0; g < NG; ++g) {
+            const uint32_t bl = __ballot_sync(0xffffffffu, (gm >> g) & 1u);
+            if ((tid & 31) == 0) s_live[g][(e0 >> 5) + warp] = bl;
+          }
+        }
       }
       __syncthreads();
+      const int nwords = (n + 31) >> 5;
 #pragma unroll
       for (int q = 0; q < PPT; ++q) {
-        if (done[q]) continue;
         const int gq = q * NW + warp;
-        for (int e = 0; e < n; ++e) {
-          if (!((s_gm[e] >> gq) & 1u)) continue;     // no pixel of this warp's group can contribute
-          const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
-          Pix P;
-          if (!pixel_weight(pv[q], r0, r1, r2, r3, s_c2[e], P)) continue;
-          if (P.m <= vt.cutoff) {
-            ++ncontrib;
-            const float a = fminf(vt.alpha_max, r0.w * __expf(-0.5f * P.m));
-            const float w = a * T[q];
-            C[q][0] += w * r3.x; C[q][1] += w * r3.y; C[q][2] += w * r3.z;
-            if (DEPTH) D[DEPTH ? q : 0] += w * s_invr[e];
-            T[q] = T[q] * (1.f - a);
-            if (T[q] < vt.eps_T) { done[q] = true; last[q] = bs + e + 1 - rg.x; break; }
+        // only the entries that may reach a pixel of this warp's group, in list order
+        for (int wj = 0; wj < nwords && !done[q]; ++wj) {
+          uint32_t bits = s_live[gq][wj];
+          while (bits) {
+            const int e = (wj << 5) + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
+            Pix P;
+            if (!pixel_weight(pv[q], r0, r1, r2, r3, s_c2[e], P)) continue;
+            if (P.m <= vt.cutoff) {
+              ++ncontrib;
+              const float a = fminf(vt.alpha_max, r0.w * __expf(-0.5f * P.m));
+              const float w = a * T[q];
+              C[q][0] += w * r3.x; C[q][1] += w * r3.y; C[q][2] += w * r3.z;
+              if (DEPTH) D[DEPTH ? q : 0] += w * s_invr[e];
+              T[q] = T[q] * (1.f - a);
+              if (T[q] < vt.eps_T) { done[q] = true; last[q] = bs + e + 1 - rg.x; break; }
+            }
           }
         }
       }
@@ -1020,14 +1037,13 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
   __shared__ float s_invr[DEPTH ? BATCH : 1];
   __shared__ uint32_t s_id[BATCH];
   __shared__ float s_part[BATCH][NW][NA];
+  constexpr int BW = (BATCH + 31) / 32;             // bitmap words per batch
   __shared__ uint32_t s_gm[BATCH];                  // live 32-pixel groups per staged entry
+  __shared__ uint32_t s_wlive[NW][BW];              // per warp: staged entries live in one of its groups
   __shared__ int s_tile;
   __shared__ uint32_t s_maxlast;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int b = vt.b;
-  uint32_t wgroups = 0;                             // this warp's groups q * NW + warp
-#pragma unroll
-  for (int q = 0; q < PPT; ++q) wgroups |= 1u << (q * NW + warp);
   for (;;) {
     if (tid == 0) { s_tile = (int)atomicAdd(work, 1u); s_maxlast = 0; }
     __syncthreads();
@@ -1067,95 +1083,115 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
       const uint32_t bs = (be - rg.x > (uint32_t)BATCH) ? be - BATCH : rg.x;
       const int n = (int)(be - bs);
       __syncthreads();
-      for (int e = tid; e < n; e += NT) {
-        const uint32_t id = ids[bs + e];
-        s_id[e] = id;
-        const float4* src = rec + 4 * (int64_t)id;
-        s_rec[e][0] = src[0]; s_rec[e][1] = src[1]; s_rec[e][2] = src[2]; s_rec[e][3] = src[3];
-        s_c2[e] = chord2[id];
-        if (DEPTH) s_invr[e] = 1.f / rdepth[id];
-        s_gm[e] = gmask[bs + e];                   // the forward's cull of this entry
+      for (int e0 = 0; e0 < n; e0 += NT) {
+        const int e = e0 + tid;
+        uint32_t gmv = 0;
+        if (e < n) {
+          const uint32_t id = ids[bs + e];
+          s_id[e] = id;
+          const float4* src = rec + 4 * (int64_t)id;
+          s_rec[e][0] = src[0]; s_rec[e][1] = src[1]; s_rec[e][2] = src[2]; s_rec[e][3] = src[3];
+          s_c2[e] = chord2[id];
+          if (DEPTH) s_invr[e] = 1.f / rdepth[id];
+          gmv = gmask[bs + e];                     // the forward's cull of this entry
+          s_gm[e] = gmv;
+        }
+        if (e0 + (warp << 5) < n) {                // this warp staged entries: one bitmap word per warp
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            uint32_t wg = 0;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) wg |= 1u << (q * NW + w);
+            const uint32_t bl = __ballot_sync(0xffffffffu, (gmv & wg) != 0u);
+            if (lane == 0) s_wlive[w][(e0 >> 5) + warp] = bl;
+          }
+        }
       }
       __syncthreads();
-      for (int e = n - 1; e >= 0; --e) {
-        const uint32_t gm = s_gm[e];
-        if (!(gm & wgroups)) continue;             // no pixel of this warp can contribute: no partials
-        const uint32_t j = bs + e - rg.x;          // position in the tile list
-        const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
-        float acc[NA];
+      // only the entries live in one of this warp's groups, in reverse list order (warp-uniform)
+      for (int wj = (n - 1) >> 5; wj >= 0; --wj) {
+        for (uint32_t bits = s_wlive[warp][wj]; bits;) {
+          const int i = 31 - __clz(bits);
+          bits ^= 1u << i;
+          const int e = (wj << 5) + i;
+          const uint32_t gm = s_gm[e];
+          const uint32_t j = bs + e - rg.x;          // position in the tile list
+          const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
+          float acc[NA];
 #pragma unroll
-        for (int c = 0; c < NA; ++c) acc[c] = 0.f;
-        bool any = false;
+          for (int c = 0; c < NA; ++c) acc[c] = 0.f;
+          bool any = false;
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-          if (j >= lastp[q] || !((gm >> (q * NW + warp)) & 1u)) continue;
-          Pix P;
-          if (!pixel_weight(pv[q], r0, r1, r2, r3, s_c2[e], P)) continue;
-          if (!(P.m <= vt.cutoff)) continue;
-          const float G = __expf(-0.5f * P.m);
-          const float og = r0.w * G;
-          const float a = fminf(vt.alpha_max, og);
-          const float inv1ma = __fdividef(1.f, 1.f - a);
-          const float Tj = T[q] * inv1ma;
-          const float wj = Tj * a;
-          float dLda = 0.f;
-          const float col[3] = {r3.x, r3.y, r3.z};
+          for (int q = 0; q < PPT; ++q) {
+            if (j >= lastp[q] || !((gm >> (q * NW + warp)) & 1u)) continue;
+            Pix P;
+            if (!pixel_weight(pv[q], r0, r1, r2, r3, s_c2[e], P)) continue;
+            if (!(P.m <= vt.cutoff)) continue;
+            const float G = __expf(-0.5f * P.m);
+            const float og = r0.w * G;
+            const float a = fminf(vt.alpha_max, og);
+            const float inv1ma = __fdividef(1.f, 1.f - a);
+            const float Tj = T[q] * inv1ma;
+            const float wj = Tj * a;
+            float dLda = 0.f;
+            const float col[3] = {r3.x, r3.y, r3.z};
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            acc[c] += wj * dI[q][c];
-            dLda += dI[q][c] * (Tj * col[c] - S[q][c] * inv1ma);
-            S[q][c] += wj * col[c];
+            for (int c = 0; c < 3; ++c) {
+              acc[c] += wj * dI[q][c];
+              dLda += dI[q][c] * (Tj * col[c] - S[q][c] * inv1ma);
+              S[q][c] += wj * col[c];
+            }
+            if (DEPTH) {
+              const int qd = DEPTH ? q : 0;
+              const float invr = s_invr[e];
+              acc[NA - 1] += wj * dDp[qd];
+              dLda += dDp[qd] * (Tj * invr - SD[qd] * inv1ma);
+              SD[qd] += wj * invr;
+            }
+            T[q] = Tj;
+            any = true;
+            if (og >= vt.alpha_max) continue;         // clamped: no gradient to o, m
+            acc[3] += dLda * G;
+            const float Lm = -0.5f * dLda * og;
+            const float u1 = P.u1, u2 = P.u2;
+            acc[4] += Lm * P.ser * u1 * u1;
+            acc[5] += Lm * P.ser * 2.f * u1 * u2;
+            acc[6] += Lm * P.ser * u2 * u2;
+            const float Qu1 = r1.w * u1 + r2.w * u2, Qu2 = r2.w * u1 + r3.w * u2;
+            const float c = 1.f - 0.5f * P.n2;
+            float Lu1, Lu2, Lc = 0.f;
+            if (P.series) {
+              const float s2 = P.s2;
+              const float dser = 1.f / 3.f + s2 * (16.f / 45.f + s2 * (12.f / 35.f + s2 * (512.f / 1575.f)));
+              Lu1 = Lm * (2.f * P.ser * Qu1 + 2.f * P.q * dser * u1);
+              Lu2 = Lm * (2.f * P.ser * Qu2 + 2.f * P.q * dser * u2);
+            } else {
+              const float s = sqrtf(P.s2);
+              const float ratio = sqrtf(P.ser);
+              const float th = ratio * s;
+              const float kf = (c * s - th) / (P.s2 * s);     // d(theta/s)/du_j = kf u_j
+              Lu1 = Lm * (2.f * P.ser * Qu1 + 2.f * P.q * ratio * kf * u1);
+              Lu2 = Lm * (2.f * P.ser * Qu2 + 2.f * P.q * ratio * kf * u2);
+              Lc = -2.f * Lm * P.q * ratio;                    // d(theta/s)/dc = -1/s^2... times s: -1
+            }
+            // moving g by a tangent step delta: du_i = -c delta_i, dc = u . delta
+            acc[7] += -c * Lu1 + Lc * u1;
+            acc[8] += -c * Lu2 + Lc * u2;
           }
-          if (DEPTH) {
-            const int qd = DEPTH ? q : 0;
-            const float invr = s_invr[e];
-            acc[NA - 1] += wj * dDp[qd];
-            dLda += dDp[qd] * (Tj * invr - SD[qd] * inv1ma);
-            SD[qd] += wj * invr;
-          }
-          T[q] = Tj;
-          any = true;
-          if (og >= vt.alpha_max) continue;         // clamped: no gradient to o, m
-          acc[3] += dLda * G;
-          const float Lm = -0.5f * dLda * og;
-          const float u1 = P.u1, u2 = P.u2;
-          acc[4] += Lm * P.ser * u1 * u1;
-          acc[5] += Lm * P.ser * 2.f * u1 * u2;
-          acc[6] += Lm * P.ser * u2 * u2;
-          const float Qu1 = r1.w * u1 + r2.w * u2, Qu2 = r2.w * u1 + r3.w * u2;
-          const float c = 1.f - 0.5f * P.n2;
-          float Lu1, Lu2, Lc = 0.f;
-          if (P.series) {
-            const float s2 = P.s2;
-            const float dser = 1.f / 3.f + s2 * (16.f / 45.f + s2 * (12.f / 35.f + s2 * (512.f / 1575.f)));
-            Lu1 = Lm * (2.f * P.ser * Qu1 + 2.f * P.q * dser * u1);
-            Lu2 = Lm * (2.f * P.ser * Qu2 + 2.f * P.q * dser * u2);
-          } else {
-            const float s = sqrtf(P.s2);
-            const float ratio = sqrtf(P.ser);
-            const float th = ratio * s;
-            const float kf = (c * s - th) / (P.s2 * s);     // d(theta/s)/du_j = kf u_j
-            Lu1 = Lm * (2.f * P.ser * Qu1 + 2.f * P.q * ratio * kf * u1);
-            Lu2 = Lm * (2.f * P.ser * Qu2 + 2.f * P.q * ratio * kf * u2);
-            Lc = -2.f * Lm * P.q * ratio;                    // d(theta/s)/dc = -1/s^2... times s: -1
-          }
-          // moving g by a tangent step delta: du_i = -c delta_i, dc = u . delta
-          acc[7] += -c * Lu1 + Lc * u1;
-          acc[8] += -c * Lu2 + Lc * u2;
-        }
-        // warp reduction of the 9 partials, then per-warp slot in shared memory
-        const unsigned ball = __ballot_sync(0xffffffffu, any);
-        if (ball) {
+          // warp reduction of the 9 partials, then per-warp slot in shared memory
+          const unsigned ball = __ballot_sync(0xffffffffu, any);
+          if (ball) {
 #pragma unroll
-          for (int c = 0; c < NA; ++c) {
-            float x = acc[c];
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            acc[c] = x;
+            for (int c = 0; c < NA; ++c) {
+              float x = acc[c];
+              for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+              acc[c] = x;
+            }
           }
-        }
-        if (lane == 0) {
+          if (lane == 0) {
 #pragma unroll
-          for (int c = 0; c < NA; ++c) s_part[e][warp][c] = ball ? acc[c] : 0.f;
+            for (int c = 0; c < NA; ++c) s_part[e][warp][c] = ball ? acc[c] : 0.f;
+          }
         }
       }
       __syncthreads();
@@ -1462,6 +1498,7 @@ int hpxgs_workspace_inspect(int32_t P, const hpxgs_view* views, int nviews, cons
   out->accum = at<float>(w, L.accum);
   out->n_eval = reinterpret_cast<const uint64_t*>(at<uint32_t>(w, L.counters) + C_NEVAL);
   out->n_contrib = reinterpret_cast<const uint64_t*>(at<uint32_t>(w, L.counters) + C_NCONTRIB);
+  out->cull_masks = (passes & 1) ? at<uint32_t>(w, L.pair_key_a) : at<uint32_t>(w, L.pair_key_b);
   out->total_tiles = L.total_tiles;
   return HPXGS_OK;
 }
