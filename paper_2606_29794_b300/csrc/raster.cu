@@ -767,6 +767,11 @@ __global__ void __launch_bounds__(256) k_tiles_nested(const __grid_constant__ Vi
 // (theta/s)^2 = asin(s)^2 / s^2 by its Taylor series near the centre
 // (1 + s^2/3 + 8 s^4/45 + 4 s^6/35 + 128 s^8/1575), atan2 further out.
 // ----------------------------------------------------------------------------
+// Lanes of a warp whose backward partials are summed by shuffles before they go
+// to shared memory (a power of two, 1 .. 32).
+#ifndef HPXGS_BWD_RED_LANES
+#define HPXGS_BWD_RED_LANES 8
+#endif
 constexpr float kSeriesN2 = 0.04f;      // |delta|^2 below which the series is used (theta < 0.2)
 
 struct Pix {
@@ -1036,7 +1041,9 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
   __shared__ float s_c2[BATCH];
   __shared__ float s_invr[DEPTH ? BATCH : 1];
   __shared__ uint32_t s_id[BATCH];
-  __shared__ float s_part[BATCH][NW][NA];
+  constexpr int RL = HPXGS_BWD_RED_LANES;            // lanes summed by shuffles; RL-lane partials go to shared memory
+  constexpr int NR = 32 / RL;
+  __shared__ float s_part[BATCH][NW][NR][NA];
   constexpr int BW = (BATCH + 31) / 32;             // bitmap words per batch
   __shared__ uint32_t s_gm[BATCH];                  // live 32-pixel groups per staged entry
   __shared__ uint32_t s_wlive[NW][BW];              // per warp: staged entries live in one of its groups
@@ -1178,19 +1185,21 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
             acc[7] += -c * Lu1 + Lc * u1;
             acc[8] += -c * Lu2 + Lc * u2;
           }
-          // warp reduction of the 9 partials, then per-warp slot in shared memory
+          // reduction of the 9 partials over groups of RL lanes, then one shared-memory
+          // slot per group (the block-level pass below adds the slots)
           const unsigned ball = __ballot_sync(0xffffffffu, any);
           if (ball) {
 #pragma unroll
             for (int c = 0; c < NA; ++c) {
               float x = acc[c];
-              for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+#pragma unroll
+              for (int o = RL / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
               acc[c] = x;
             }
           }
-          if (lane == 0) {
+          if ((lane & (RL - 1)) == 0) {
 #pragma unroll
-            for (int c = 0; c < NA; ++c) s_part[e][warp][c] = ball ? acc[c] : 0.f;
+            for (int c = 0; c < NA; ++c) s_part[e][warp][lane / RL][c] = ball ? acc[c] : 0.f;
           }
         }
       }
@@ -1204,7 +1213,10 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
           uint32_t wg = 0;
 #pragma unroll
           for (int q = 0; q < PPT; ++q) wg |= 1u << (q * NW + w);
-          if (gm & wg) sum += s_part[e][w][c];      // warps with no live group wrote no partials
+          if (gm & wg) {                            // warps with no live group wrote no partials
+#pragma unroll
+            for (int r = 0; r < NR; ++r) sum += s_part[e][w][r][c];
+          }
         }
         if (sum == 0.f) continue;
         if (!DEPTH || c < HPXGS_NACC) atomicAdd(&accum[(int64_t)s_id[e] * HPXGS_NACC + c], sum);
