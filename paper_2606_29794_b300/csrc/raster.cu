@@ -472,6 +472,14 @@ __device__ __forceinline__ int ring_interval(int kt, int i, const DiscQ& Q, Ring
   return jhi - jlo + 1;
 }
 
+// Half-width of the band around the FP32 threshold in which a candidate takes the
+// exact FP64 test. The FP32 dot and threshold are within 1.6e-6 of their exact
+// values: longitude folded to (-1, 1] pi (3.8e-7), sincospif's 1 ulp (0.9e-7), the
+// dot's four roundings (2.4e-7), the ring's z and sin(theta) (2.4e-7), and the
+// threshold's argument (up to 4.8e-7 at r_s + rho near pi) and cosf's 2 ulp
+// (1.2e-7). An FP32 emulation at Nside 512 with 300k Gaussians stays within 2e-7.
+constexpr float kBand32 = 3e-6f;
+
 // Count pass (EMIT = false): counts members and stages up to kStage member tiles
 // per Gaussian in shared memory, then copies them to a scratch list at a slot
 // taken from an atomic counter (stage[j] = slot, or ~0 when the Gaussian has more
@@ -554,11 +562,16 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
           int jj = o_jlo + (q - o_exc);          // within (-np, 2 np)
           if (jj < 0) jj += o_np;
           if (jj >= o_np) jj -= o_np;
+          // longitude / pi = (jj + off) inv = n / d with n = 2 (jj + off) and d = 4 / (2 inv), the
+          // ring's pixel count; folded exactly to (-1, 1] so that its FP32 rounding is at most
+          // 2^-23 in units of pi (0.5 inv = fl(1 / d))
+          int n = 2 * jj + (int)(2.f * o_off);
+          if (n > o_np) n -= 2 * o_np;
           float sp, cp;
-          sincospif(((float)jj + o_off) * o_inv, &sp, &cp);
+          sincospif((float)n * (0.5f * o_inv), &sp, &cp);
           const float dot = o_sth * (cp * g.x + sp * g.y) + o_z * g.z;
-          if (dot > Q.cosRm32 + 1e-5f) member = true;
-          else if (dot >= Q.cosRm32 - 1e-5f) {
+          if (dot > Q.cosRm32 + kBand32) member = true;
+          else if (dot >= Q.cosRm32 - kBand32) {
             // the exact test: both sides in FP64, the threshold as the membership rule states it
             // (the FP64 pipe is slow on this part: nothing on the common path uses it)
             if (cosRm > 1.5) cosRm = cos(fmin(kPi, (double)rs + vp.rho + 1e-7));
