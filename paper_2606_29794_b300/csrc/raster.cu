@@ -863,7 +863,10 @@ __device__ __forceinline__ uint32_t live_groups(const float4 r0, const float4 r1
 // group guards of the cull would otherwise grow the one- and four-pixel shapes
 // (40 and 96 registers without them) and cost them resident warps.
 constexpr int fwd_min_blocks(int nt, int ppt, bool depth) { return (ppt == 1 && nt >= 128 && !depth) ? 65536 / (nt * 40) : 1; }
-constexpr int bwd_min_blocks(int nt, int ppt, bool depth) { return (ppt <= 4 && !depth) ? 65536 / (nt * 96) : 1; }
+#ifndef HPXGS_BWD_REGS
+#define HPXGS_BWD_REGS 96
+#endif
+constexpr int bwd_min_blocks(int nt, int ppt, bool depth) { return (ppt <= 4 && !depth) ? 65536 / (nt * HPXGS_BWD_REGS) : 1; }
 
 // Sub-tile centres of a tile (order k - 2 pixels) and the cull's per-view constants.
 template <int NS>
@@ -1077,8 +1080,10 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
     const uint2 rg = ranges[tile];
     const uint32_t* vmask = mask + (vp.pix_base >> 5);
     float3 pv[PPT];
-    float dI[PPT][3], S[PPT][3], T[PPT];
-    float dDp[DEPTH ? PPT : 1], SD[DEPTH ? PPT : 1];    // dL/dD and the depth behind the entry
+    // B = dL/dI . (colour behind the entry, background included) (+ dL/dD x depth behind it), the
+    // only form in which the colour behind enters dL/dalpha, kept as one scalar per pixel
+    float dI[PPT][3], B[PPT], T[PPT];
+    float dDp[DEPTH ? PPT : 1];                         // dL/dD
     uint32_t lastp[PPT];
     uint32_t mylast = 0;
 #pragma unroll
@@ -1089,11 +1094,9 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
       lastp[q] = inm ? lastin[pg] : 0u;
       T[q] = inm ? Tin[pg] : 1.f;
       pv[q] = inm ? pix2vec_f32(vp.k, lp) : make_float3(0.f, 0.f, 1.f);
-      for (int c = 0; c < 3; ++c) {
-        dI[q][c] = inm ? dmaps[3 * pg + c] : 0.f;
-        S[q][c] = T[q] * vt.bg[c];
-      }
-      if (DEPTH) { dDp[DEPTH ? q : 0] = inm ? ddepth[pg] : 0.f; SD[DEPTH ? q : 0] = 0.f; }
+      for (int c = 0; c < 3; ++c) dI[q][c] = inm ? dmaps[3 * pg + c] : 0.f;
+      B[q] = T[q] * (dI[q][0] * vt.bg[0] + dI[q][1] * vt.bg[1] + dI[q][2] * vt.bg[2]);
+      if (DEPTH) dDp[DEPTH ? q : 0] = inm ? ddepth[pg] : 0.f;
       mylast = max(mylast, lastp[q]);
     }
     if (mylast) atomicMax(&s_maxlast, mylast);
@@ -1153,21 +1156,17 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
             const float inv1ma = __fdividef(1.f, 1.f - a);
             const float Tj = T[q] * inv1ma;
             const float wj = Tj * a;
-            float dLda = 0.f;
-            const float col[3] = {r3.x, r3.y, r3.z};
+            // A = dL/dI . colour (+ dL/dD / r); dL/da = T_j A - B / (1 - a); then B takes this entry
+            float A = dI[q][0] * r3.x + dI[q][1] * r3.y + dI[q][2] * r3.z;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              acc[c] += wj * dI[q][c];
-              dLda += dI[q][c] * (Tj * col[c] - S[q][c] * inv1ma);
-              S[q][c] += wj * col[c];
-            }
+            for (int c = 0; c < 3; ++c) acc[c] += wj * dI[q][c];
             if (DEPTH) {
               const int qd = DEPTH ? q : 0;
-              const float invr = s_invr[e];
               acc[NA - 1] += wj * dDp[qd];
-              dLda += dDp[qd] * (Tj * invr - SD[qd] * inv1ma);
-              SD[qd] += wj * invr;
+              A += dDp[qd] * s_invr[e];
             }
+            const float dLda = Tj * A - B[q] * inv1ma;
+            B[q] += wj * A;
             T[q] = Tj;
             any = true;
             if (og >= vt.alpha_max) continue;         // clamped: no gradient to o, m
