@@ -1171,31 +1171,36 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
             any = true;
             if (og >= vt.alpha_max) continue;         // clamped: no gradient to o, m
             acc[3] += dLda * G;
+            // dL/dm = Lm = -dLda o G / 2; m = q(u) ser with ser = (theta/s)^2. acc[5], acc[7] and
+            // acc[8] collect half their partials (the factor 2 is applied once per entry below).
             const float Lm = -0.5f * dLda * og;
             const float u1 = P.u1, u2 = P.u2;
-            acc[4] += Lm * P.ser * u1 * u1;
-            acc[5] += Lm * P.ser * 2.f * u1 * u2;
-            acc[6] += Lm * P.ser * u2 * u2;
+            const float Ws = Lm * P.ser;
+            const float t1 = Ws * u1;
+            acc[4] += t1 * u1;
+            acc[5] += t1 * u2;
+            acc[6] += Ws * u2 * u2;
             const float Qu1 = r1.w * u1 + r2.w * u2, Qu2 = r2.w * u1 + r3.w * u2;
             const float c = 1.f - 0.5f * P.n2;
-            float Lu1, Lu2, Lc = 0.f;
+            // dm/du_j / 2 = ser Qu_j + q (d ser / d u_j) / 2 = ser Qu_j + K u_j (K per branch below);
+            // dm/dc / 2 = Lc per unit Lm (atan form only)
+            float K, Lc = 0.f;
             if (P.series) {
               const float s2 = P.s2;
               const float dser = 1.f / 3.f + s2 * (16.f / 45.f + s2 * (12.f / 35.f + s2 * (512.f / 1575.f)));
-              Lu1 = Lm * (2.f * P.ser * Qu1 + 2.f * P.q * dser * u1);
-              Lu2 = Lm * (2.f * P.ser * Qu2 + 2.f * P.q * dser * u2);
+              K = Lm * P.q * dser;
             } else {
               const float s = sqrtf(P.s2);
               const float ratio = sqrtf(P.ser);
               const float th = ratio * s;
               const float kf = (c * s - th) / (P.s2 * s);     // d(theta/s)/du_j = kf u_j
-              Lu1 = Lm * (2.f * P.ser * Qu1 + 2.f * P.q * ratio * kf * u1);
-              Lu2 = Lm * (2.f * P.ser * Qu2 + 2.f * P.q * ratio * kf * u2);
-              Lc = -2.f * Lm * P.q * ratio;                    // d(theta/s)/dc = -1/s^2... times s: -1
+              K = Lm * P.q * ratio * kf;
+              Lc = -Lm * P.q * ratio;                          // d(theta/s)/dc = -1/s^2... times s: -1
             }
+            const float h1 = Ws * Qu1 + K * u1, h2 = Ws * Qu2 + K * u2;
             // moving g by a tangent step delta: du_i = -c delta_i, dc = u . delta
-            acc[7] += -c * Lu1 + Lc * u1;
-            acc[8] += -c * Lu2 + Lc * u2;
+            acc[7] += -c * h1 + Lc * u1;
+            acc[8] += -c * h2 + Lc * u2;
           }
           // reduction of the 9 partials over groups of RL lanes, then one shared-memory
           // slot per group (the block-level pass below adds the slots)
@@ -1211,7 +1216,8 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
           }
           if ((lane & (RL - 1)) == 0) {
 #pragma unroll
-            for (int c = 0; c < NA; ++c) s_part[e][warp][lane / RL][c] = ball ? acc[c] : 0.f;
+            for (int c = 0; c < NA; ++c)
+              s_part[e][warp][lane / RL][c] = ball ? ((c == 5 || c == 7 || c == 8) ? 2.f * acc[c] : acc[c]) : 0.f;
           }
         }
       }
