@@ -289,7 +289,7 @@ int hpxgs_probe_alu_peak(double* fma_tflops, double* ex2_tops, hpxgs_stream_t st
 
 /* FP32 work of the blend kernels, counted from their inner loops (an FMA is 2
  * flops, a MUFU op is counted apart): per evaluated (pixel, entry) pair, the
- * offset and m = d^T conic d (chord test, tangent components, quadratic form,
+ * offset and m = d^T conic d (offset and its squared chord, tangent components, quadratic form,
  * arc-length series); per contributing pair (m <= cutoff, before termination),
  * alpha and compositing in the forward, and T recovery, dL/dalpha and the
  * conic and position partials in the backward. */

@@ -257,7 +257,6 @@ int make_layout(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_conf
   L->tile_flags = take(sizeof(uint32_t) * tiles);
   L->records = take(64 * pv);
   L->radii = take(4 * pv);
-  L->chord = take(4 * pv);
   L->stage = take(4 * pv);
   L->depth = take(4 * pv);
   L->key_a = take(4 * pv);

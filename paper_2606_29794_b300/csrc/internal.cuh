@@ -57,7 +57,7 @@ constexpr int kRecFloat4 = 4;
 
 // Workspace layout of hpxgs_forward / hpxgs_backward. All offsets 256-aligned.
 struct Layout {
-  size_t tile_flags, records, radii, chord, stage, depth, key_a, key_b, val_a, val_b, counts, offsets, scan_part,
+  size_t tile_flags, records, radii, stage, depth, key_a, key_b, val_a, val_b, counts, offsets, scan_part,
          pair_key_a, pair_key_b, pair_val_a, pair_val_b, hist, ranges, counters, accum, accum_d, tile_order,
          total;
   int64_t P, PV, cap, total_tiles, total_pix;

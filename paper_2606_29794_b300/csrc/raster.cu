@@ -152,7 +152,7 @@ __device__ __forceinline__ void geo_compute(const ViewParams& vp, float near_pla
 __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ ViewTable vt, hpxgs_gaussians gs,
                                                     float4* __restrict__ rec, float* __restrict__ radii,
                                                     float* __restrict__ depth, uint32_t* __restrict__ keys,
-                                                    uint32_t* __restrict__ vals, float* __restrict__ chord2) {
+                                                    uint32_t* __restrict__ vals) {
   const int64_t PV = (int64_t)vt.P * vt.nviews;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= PV) return;
@@ -168,7 +168,6 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ View
   if (!G.valid) {
     keys[gid] = 0xffffffffu;
     radii[gid] = 0.f;
-    chord2[gid] = -1.f;
     rec[4 * gid + 0] = make_float4(0.f, 0.f, 1.f, 0.f);
     rec[4 * gid + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
     rec[4 * gid + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -195,10 +194,6 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ View
   rec[4 * gid + 3] = make_float4(col[0], col[1], col[2], G.qc);
   radii[gid] = G.rs;
   keys[gid] = __float_as_uint(G.r);     // r > 0: the bit pattern orders like the value
-  // m <= cutoff implies an angle <= r_s from the centre, i.e. |p - g|^2 <= 4 sin^2(r_s / 2):
-  // a pixel farther than that chord gets alpha = 0 without evaluating m (bound widened by 1e-4)
-  const float hs = sinf(0.5f * fminf(G.rs, (float)kPi));
-  chord2[gid] = 4.f * hs * hs * (1.f + 1e-4f) + 1e-12f;
 }
 
 // ----------------------------------------------------------------------------
@@ -792,12 +787,13 @@ struct Pix {
   bool series;
 };
 
-// Returns false (alpha = 0) when the pixel lies beyond the Gaussian's chord bound.
-__device__ __forceinline__ bool pixel_weight(const float3 p, const float4 r0, const float4 r1, const float4 r2,
-                                             const float4 r3, const float c2max, Pix& P) {
+// m of pixel p for the entry (r0, r1, r2, r3): tangent offset u, q(u), (theta/s)^2.
+// (A pixel past the Gaussian's reach gets m > cutoff; the blends' cull skips most of
+// them by groups of 32, so no per-pixel early exit is taken.)
+__device__ __forceinline__ void pixel_weight(const float3 p, const float4 r0, const float4 r1, const float4 r2,
+                                             const float4 r3, Pix& P) {
   const float dx = p.x - r0.x, dy = p.y - r0.y, dz = p.z - r0.z;
   P.n2 = dx * dx + dy * dy + dz * dz;
-  if (P.n2 > c2max) return false;
   P.u1 = dx * r1.x + dy * r1.y + dz * r1.z;
   P.u2 = dx * r2.x + dy * r2.y + dz * r2.z;
   P.s2 = P.u1 * P.u1 + P.u2 * P.u2;
@@ -809,13 +805,12 @@ __device__ __forceinline__ bool pixel_weight(const float3 p, const float4 r0, co
     P.m = P.q * P.ser;
   } else {
     const float c = 1.f - 0.5f * P.n2;
-    if (P.s2 < 1e-24f) { P.ser = 0.f; P.m = (c < 0.f) ? 3.0e38f : 0.f; return true; }
+    if (P.s2 < 1e-24f) { P.ser = 0.f; P.m = (c < 0.f) ? 3.0e38f : 0.f; return; }
     const float s = sqrtf(P.s2);
     const float ratio = atan2f(s, c) / s;
     P.ser = ratio * ratio;
     P.m = P.q * P.ser;
   }
-  return true;
 }
 
 // Cull of (entry, 32-pixel group) pairs, taken once per staged entry. A tile's
@@ -895,14 +890,12 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
                                                   const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
                                                   float* __restrict__ maps, float* __restrict__ Tout,
                                                   uint32_t* __restrict__ lastout, uint32_t* work,
-                                                  unsigned long long* __restrict__ evals, const float* __restrict__ chord2,
-                                                  uint32_t* __restrict__ gmask,
+                                                  unsigned long long* __restrict__ evals, uint32_t* __restrict__ gmask,
                                                   const float* __restrict__ rdepth = nullptr,
                                                   float* __restrict__ dmap = nullptr) {
   constexpr int NW = NT / 32;
   constexpr int NS = NT * PPT / 16;                 // 16-pixel sub-tiles per tile
   __shared__ float4 s_rec[BATCH][4];
-  __shared__ float s_c2[BATCH];
   __shared__ float s_invr[DEPTH ? BATCH : 1];
   constexpr int NG = NS / 2;                        // 32-pixel groups per tile
   constexpr int BW = BATCH / 32;                    // bitmap words per batch
@@ -956,7 +949,6 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
           const float4* src = rec + 4 * (int64_t)id;
           const float4 a0 = src[0], a1 = src[1], a2 = src[2], a3 = src[3];
           s_rec[e][0] = a0; s_rec[e][1] = a1; s_rec[e][2] = a2; s_rec[e][3] = a3;
-          s_c2[e] = chord2[id];
           if (DEPTH) s_invr[e] = 1.f / rdepth[id];
           gm = vt.cull ? live_groups<NS>(a0, a1, a2, a3, s_sub, rho_p, sqrt_cut) : ~0u;
           gmask[bs + e] = gm;                        // for the backward pass over the same entries
@@ -982,7 +974,7 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
             bits &= bits - 1u;
             const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
             Pix P;
-            if (!pixel_weight(pv[q], r0, r1, r2, r3, s_c2[e], P)) continue;
+            pixel_weight(pv[q], r0, r1, r2, r3, P);
             if (P.m <= vt.cutoff) {
               ++ncontrib;
               const float a = fminf(vt.alpha_max, r0.w * __expf(-0.5f * P.m));
@@ -1046,15 +1038,13 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
                                                   const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
                                                   const float* __restrict__ dmaps, const float* __restrict__ Tin,
                                                   const uint32_t* __restrict__ lastin, float* __restrict__ accum,
-                                                  uint32_t* work, const float* __restrict__ chord2,
-                                                  const uint32_t* __restrict__ gmask,
+                                                  uint32_t* work, const uint32_t* __restrict__ gmask,
                                                   const float* __restrict__ rdepth = nullptr,
                                                   const float* __restrict__ ddepth = nullptr,
                                                   float* __restrict__ accum_d = nullptr) {
   constexpr int NW = NT / 32;
   constexpr int NA = HPXGS_NACC + (DEPTH ? 1 : 0);
   __shared__ float4 s_rec[BATCH][4];
-  __shared__ float s_c2[BATCH];
   __shared__ float s_invr[DEPTH ? BATCH : 1];
   __shared__ uint32_t s_id[BATCH];
   constexpr int RL = HPXGS_BWD_RED_LANES;            // lanes summed by shuffles; RL-lane partials go to shared memory
@@ -1114,7 +1104,6 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
           s_id[e] = id;
           const float4* src = rec + 4 * (int64_t)id;
           s_rec[e][0] = src[0]; s_rec[e][1] = src[1]; s_rec[e][2] = src[2]; s_rec[e][3] = src[3];
-          s_c2[e] = chord2[id];
           if (DEPTH) s_invr[e] = 1.f / rdepth[id];
           gmv = gmask[bs + e];                     // the forward's cull of this entry
           s_gm[e] = gmv;
@@ -1148,7 +1137,7 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
           for (int q = 0; q < PPT; ++q) {
             if (j >= lastp[q] || !((gm >> (q * NW + warp)) & 1u)) continue;
             Pix P;
-            if (!pixel_weight(pv[q], r0, r1, r2, r3, s_c2[e], P)) continue;
+            pixel_weight(pv[q], r0, r1, r2, r3, P);
             if (!(P.m <= vt.cutoff)) continue;
             const float G = __expf(-0.5f * P.m);
             const float og = r0.w * G;
@@ -1389,10 +1378,14 @@ static int blend_blocks(const void* fn, int nt, int want_per_sm) {
   return occ * num_sms();
 }
 
+// Entries staged per batch by the forward blend (a multiple of 32).
+#ifndef HPXGS_FWD_BATCH
+#define HPXGS_FWD_BATCH 128
+#endif
 // Launch of a blend kernel with NT threads x PPT pixels per thread = the tile's pixels.
 template <int NT, int PPT, bool DEPTH = false, typename... Args>
 static void launch_fwd(int bps, cudaStream_t s, Args... args) {
-  auto fn = k_blend_fwd<NT, PPT, 128, DEPTH>;
+  auto fn = k_blend_fwd<NT, PPT, HPXGS_FWD_BATCH, DEPTH>;
   fn<<<blend_blocks((const void*)fn, NT, bps), NT, 0, s>>>(args...);
 }
 template <int NT, int PPT, bool DEPTH = false, typename... Args>
@@ -1449,7 +1442,7 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   uint32_t* ka = at<uint32_t>(ws, L.key_a); uint32_t* kb = at<uint32_t>(ws, L.key_b);
   uint32_t* va = at<uint32_t>(ws, L.val_a); uint32_t* vb = at<uint32_t>(ws, L.val_b);
   prof_begin(HPXGS_STAGE_PREPROCESS, s);
-  k_preprocess<<<(unsigned)((PV + 255) / 256), 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va, at<float>(ws, L.chord));
+  k_preprocess<<<(unsigned)((PV + 255) / 256), 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va);
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_PREPROCESS, s);
@@ -1616,11 +1609,10 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
   unsigned long long* evals = reinterpret_cast<unsigned long long*>(counters + C_NEVAL);
   const int b = cfg->tile_level;
   const int bps = cfg->blocks_per_sm;
-  const float* chord = at<float>(ws, L.chord);
   prof_begin(HPXGS_STAGE_BLEND_FWD, s);
   {
     const int ppt = pick_ppt(b, cfg->fwd_ppt, true);
-#define FWD_BASE bps, s, *vt, (const float4*)rec, (const uint2*)ranges, ids, (const uint32_t*)flags, (const uint32_t*)mask, maps, T_final, last, work, evals, chord, gmask
+#define FWD_BASE bps, s, *vt, (const float4*)rec, (const uint2*)ranges, ids, (const uint32_t*)flags, (const uint32_t*)mask, maps, T_final, last, work, evals, gmask
 #define FWD_ARGS FWD_BASE, (const float*)nullptr, (float*)nullptr
 #define FWD_DEPTH_ARGS FWD_BASE, (const float*)at<float>(ws, L.depth), depth_map
     if (depth_map) {                               // the depth channel runs in each level's default shape
@@ -1684,12 +1676,11 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   uint32_t* work = counters + C_WORK_BWD;
   const int b = cfg->tile_level;
   const int bps = cfg->blocks_per_sm;
-  const float* chord = at<float>(ws, L.chord);
   prof_begin(HPXGS_STAGE_BLEND_BWD, s);
   {
     // several pixels per thread: the per-entry warp reduction then covers 32 * PPT pixels
     const int ppt = pick_ppt(b, cfg->bwd_ppt, false);
-#define BWD_BASE bps, s, *vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, chord, gmask
+#define BWD_BASE bps, s, *vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, gmask
 #define BWD_ARGS BWD_BASE, (const float*)nullptr, (const float*)nullptr, (float*)nullptr
 #define BWD_DEPTH_ARGS BWD_BASE, rdepth, ddepth, accum_d
     if (ddepth) {                                  // the depth channel runs in each level's default shape
