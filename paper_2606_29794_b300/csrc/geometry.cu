@@ -244,9 +244,9 @@ int make_layout(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_conf
   const int64_t PV = (int64_t)P * nviews;
   if (PV >= 0xffffffffLL || tiles >= 0x7fffffffLL) return HPXGS_E_INVALID_ARG;
   L->P = P; L->PV = PV; L->cap = cap; L->total_tiles = tiles; L->total_pix = pix;
-  int G = 2 * num_sms();
-  if (G > kMaxSortBlocks) G = kMaxSortBlocks;
+  const int G = std::min(2 * num_sms(), kMaxSortBlocks);
   L->sort_blocks = G;
+  L->pair_sort_blocks = std::min(HPXGS_SORT_BPS * num_sms(), kMaxSortBlocks);
   int bits = 1;
   while ((1LL << bits) < tiles) ++bits;
   L->pair_bits = bits;
@@ -270,7 +270,7 @@ int make_layout(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_conf
   L->pair_key_b = take(4 * cp);
   L->pair_val_a = take(4 * cp);
   L->pair_val_b = take(4 * cp);
-  L->hist = take(4 * (256 * (size_t)G + 256));   // per-block digit counts, then the digit bases
+  L->hist = take(4 * (256 * (size_t)kMaxSortBlocks + 256));   // per-block digit counts, then the digit bases
   L->ranges = take(8 * tiles);
   L->counters = take(4 * C_COUNT);
   L->accum = take(4 * HPXGS_NACC * pv);

@@ -61,7 +61,8 @@ struct Layout {
          pair_key_a, pair_key_b, pair_val_a, pair_val_b, hist, ranges, counters, accum, accum_d, tile_order,
          total;
   int64_t P, PV, cap, total_tiles, total_pix;
-  int sort_blocks;
+  int sort_blocks;        // grid of the count scan
+  int pair_sort_blocks;   // grid of the pair sort
   int pair_bits;
 };
 
@@ -69,6 +70,14 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;                     // items per thread per tile
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kMaxSortBlocks = 1024;
+// Blocks per SM of the pair sort's fixed grid, and 4096-element tiles per block of
+// the depth sort's grid (build-time tunables; both grids stay within kMaxSortBlocks).
+#ifndef HPXGS_SORT_BPS
+#define HPXGS_SORT_BPS 3
+#endif
+#ifndef HPXGS_DSORT_TPB
+#define HPXGS_DSORT_TPB 1
+#endif
 
 // counters block (u32 each)
 // (u64 counters live at u32 index 8 (n_eval) and 10 (n_contrib), 8-byte aligned)

@@ -396,7 +396,7 @@ static int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, co
 // Tile query (Algorithm 3 at the tile order) and exact membership:
 // tile t is listed for Gaussian g iff t has an in-mask pixel and
 // c_t . g >= cos(min(pi, r_s + rho + 1e-7)), decided in FP32 when the margin
-// exceeds 1e-5 and in FP64 otherwise.
+// exceeds kBand32 and in FP64 otherwise.
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ float ring_of_z(float z, int Nt) {
   if (z > 2.0f / 3.0f) return Nt * sqrtf(3.0f * (1.0f - z));
@@ -1450,8 +1450,8 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_PREPROCESS, s);
   prof_begin(HPXGS_STAGE_DEPTH_SORT, s);
-  // a grid sized to the element count (about 4 tiles of 4096 per block): the digit scan covers 256 x G entries
-  const int Gd = (int)std::max<int64_t>(1, std::min<int64_t>(L.sort_blocks, (PV + 4 * kSortTile - 1) / (4 * kSortTile)));
+  // a grid sized to the element count (HPXGS_DSORT_TPB tiles of 4096 per block, at most kMaxSortBlocks)
+  const int Gd = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSortBlocks, (PV + HPXGS_DSORT_TPB * kSortTile - 1) / (HPXGS_DSORT_TPB * kSortTile)));
   rc = radix_sort(ka, va, kb, vb, nullptr, (uint32_t)PV, 32, at<uint32_t>(ws, L.hist), Gd, counters + C_SORT_TICKET, s, which_depth);
   if (rc != HPXGS_OK) return rc;
   prof_end(HPXGS_STAGE_DEPTH_SORT, s);
@@ -1591,7 +1591,7 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
     int wp = 0;
     prof_begin(HPXGS_STAGE_PAIR_SORT, s);
     rc = radix_sort(pka, pva, pkb, pvb, counters + C_NPAIRS, (uint32_t)cap, L.pair_bits, at<uint32_t>(ws, L.hist),
-                    L.sort_blocks, counters + C_SORT_TICKET, s, &wp);
+                    L.pair_sort_blocks, counters + C_SORT_TICKET, s, &wp);
     if (rc != HPXGS_OK) { delete vt; return rc; }
     prof_end(HPXGS_STAGE_PAIR_SORT, s);
     const uint32_t* sorted_tiles = wp ? pkb : pka;
