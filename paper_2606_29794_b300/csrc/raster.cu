@@ -76,6 +76,29 @@ __device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, flo
   }
 }
 
+// sum_k w_k grad Y_k(d) (the gradient formulas of sh_basis contracted with w), so
+// that no per-k gradient has to be kept.
+__device__ __forceinline__ float3 sh_grad_dot(int deg, float x, float y, float z, const float* w) {
+  float3 g = make_float3(0.f, 0.f, 0.f);
+  if (deg < 1) return g;
+  const float C1 = kSH[1], C2a = kSH[2], C2b = kSH[3], C2c = kSH[4];
+  const float C3a = kSH[5], C3b = kSH[6], C3c = kSH[7], C3d = kSH[8], C3e = kSH[9];
+  g.x = -C1 * w[3]; g.y = -C1 * w[1]; g.z = C1 * w[2];
+  if (deg < 2) return g;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  g.x += C2a * (y * w[4] - z * w[7]) - 2.f * C2b * x * w[6] + 2.f * C2c * x * w[8];
+  g.y += C2a * (x * w[4] - z * w[5]) - 2.f * C2b * y * w[6] - 2.f * C2c * y * w[8];
+  g.z += -C2a * (y * w[5] + x * w[7]) + 4.f * C2b * z * w[6];
+  if (deg < 3) return g;
+  g.x += -6.f * C3a * x * y * w[9] + C3b * y * z * w[10] + 2.f * C3c * x * y * w[11] - 6.f * C3d * x * z * w[12]
+         - C3c * (4.f * zz - 3.f * xx - yy) * w[13] + 2.f * C3e * x * z * w[14] - C3a * (3.f * xx - 3.f * yy) * w[15];
+  g.y += -C3a * (3.f * xx - 3.f * yy) * w[9] + C3b * x * z * w[10] - C3c * (4.f * zz - xx - 3.f * yy) * w[11]
+         - 6.f * C3d * y * z * w[12] + 2.f * C3c * x * y * w[13] - 2.f * C3e * y * z * w[14] + 6.f * C3a * x * y * w[15];
+  g.z += C3b * x * y * w[10] - 8.f * C3c * y * z * w[11] + C3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12]
+         - 8.f * C3c * x * z * w[13] + C3e * (xx - yy) * w[14];
+  return g;
+}
+
 __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
   R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
   R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
@@ -1246,24 +1269,40 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
 // of the tangent frame, so this gives the exact derivative):
 //   d(e_i / r) = -(g (e_i . dt) + e_i (g . dt)) / r^2,  dg = (I - g g^T) dt / r.
 // ----------------------------------------------------------------------------
-// DEG is the SH degree as a compile-time constant, so the SH rows (value, basis,
-// basis gradient, per-Gaussian SH gradient) stay in registers.
+// DEG is the SH degree as a compile-time constant. A block's SH rows are staged
+// through shared memory (coalesced in and out; rows padded to 3K + 1 floats so that
+// the per-thread rows fall in distinct banks), and the per-Gaussian SH gradient
+// accumulates there over the views.
+constexpr int kPreBwdThreads = 64;
+#ifndef HPXGS_PREBWD_MINB
+#define HPXGS_PREBWD_MINB 8
+#endif
 template <int DEG>
-__global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ ViewTable vt, hpxgs_gaussians gs,
+__global__ void __launch_bounds__(kPreBwdThreads, HPXGS_PREBWD_MINB) k_preprocess_bwd(const __grid_constant__ ViewTable vt, hpxgs_gaussians gs,
                                                         const float* __restrict__ radii, const float* __restrict__ accum,
                                                         float* __restrict__ dmeans, float* __restrict__ dscales,
                                                         float* __restrict__ drot, float* __restrict__ dopac,
                                                         float* __restrict__ dsh,
                                                         const float* __restrict__ accum_d) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= vt.P) return;
   constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int RW = 3 * K + 1;                       // padded row
+  __shared__ float s_sh[kPreBwdThreads * RW];
+  __shared__ float s_dsh[kPreBwdThreads * RW];
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * kPreBwdThreads;
+  const int nrow = min(kPreBwdThreads, vt.P - i0);
+  for (int t = tid; t < nrow * 3 * K; t += kPreBwdThreads) {
+    const int r = t / (3 * K), c = t - r * (3 * K);
+    s_sh[r * RW + c] = gs.sh[(int64_t)i0 * 3 * K + t];
+    s_dsh[r * RW + c] = 0.f;
+  }
+  __syncthreads();
+  const int i = i0 + tid;
+  if (i < vt.P) {
   float dmu[3] = {0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dop = 0.f;
   const float* mu = gs.means + 3 * (int64_t)i;
-  const float* sh = gs.sh + (int64_t)i * K * 3;
-  float dshl[3 * K];
-#pragma unroll
-  for (int c = 0; c < 3 * K; ++c) dshl[c] = 0.f;
+  const float* sh = s_sh + tid * RW;
+  float* dshl = s_dsh + tid * RW;
   for (int v = 0; v < vt.nviews; ++v) {
     const int64_t gid = (int64_t)v * vt.P + i;
     if (!(radii[gid] > 0.f)) continue;
@@ -1277,8 +1316,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
     const float dist = sqrtf(dx * dx + dy * dy + dz * dz), idist = 1.f / dist;
     dx *= idist; dy *= idist; dz *= idist;
     float Y[K];
-    float3 dY[K];
-    sh_basis(DEG, dx, dy, dz, Y, dY);
+    sh_basis(DEG, dx, dy, dz, Y, nullptr);
     float Lcr[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -1287,18 +1325,20 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
       for (int kk = 0; kk < K; ++kk) raw += sh[3 * kk + c] * Y[kk];
       Lcr[c] = raw > 0.f ? A[c] : 0.f;
     }
-    float Ld[3] = {0.f, 0.f, 0.f};
+    // dL/dsh_kc = Y_k Lcr_c; the direction gets sum_k w_k grad Y_k with w_k = sum_c Lcr_c sh_kc
+    // (Y_k is replaced by w_k in place)
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) {
       float w = 0.f;
 #pragma unroll
       for (int c = 0; c < 3; ++c) { dshl[3 * kk + c] += Y[kk] * Lcr[c]; w += Lcr[c] * sh[3 * kk + c]; }
-      Ld[0] += w * dY[kk].x; Ld[1] += w * dY[kk].y; Ld[2] += w * dY[kk].z;
+      Y[kk] = w;
     }
-    const float pd = Ld[0] * dx + Ld[1] * dy + Ld[2] * dz;
-    dmu[0] += (Ld[0] - dx * pd) * idist;
-    dmu[1] += (Ld[1] - dy * pd) * idist;
-    dmu[2] += (Ld[2] - dz * pd) * idist;
+    const float3 Ld = sh_grad_dot(DEG, dx, dy, dz, Y);
+    const float pd = Ld.x * dx + Ld.y * dy + Ld.z * dz;
+    dmu[0] += (Ld.x - dx * pd) * idist;
+    dmu[1] += (Ld.y - dy * pd) * idist;
+    dmu[2] += (Ld.z - dz * pd) * idist;
     dop += A[3];
     // conic -> Sigma_arc
     const float GQa = A[4], GQb = 0.5f * A[5], GQc = A[6];
@@ -1364,8 +1404,12 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(const __grid_constant__ 
   for (int c = 0; c < 3; ++c) { dmeans[3 * (int64_t)i + c] = dmu[c]; dscales[3 * (int64_t)i + c] = ds[c]; }
   for (int c = 0; c < 4; ++c) drot[4 * (int64_t)i + c] = dq[c];
   dopac[i] = dop;
-#pragma unroll
-  for (int c = 0; c < 3 * K; ++c) dsh[(int64_t)i * K * 3 + c] = dshl[c];
+  }
+  __syncthreads();
+  for (int t = tid; t < nrow * 3 * K; t += kPreBwdThreads) {
+    const int r = t / (3 * K), c = t - r * (3 * K);
+    dsh[(int64_t)i0 * 3 * K + t] = s_dsh[r * RW + c];
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -1705,14 +1749,14 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   prof_end(HPXGS_STAGE_BLEND_BWD, s);
   prof_begin(HPXGS_STAGE_PREPROCESS_BWD, s);
   {
-    const int nb = (int)((g->P + 127) / 128);
+    const int nb = (int)((g->P + kPreBwdThreads - 1) / kPreBwdThreads);
     const float* rad = at<float>(ws, L.radii);
     const float* acd = ddepth ? at<float>(ws, L.accum_d) : nullptr;
     switch (g->sh_degree) {
-      case 0: k_preprocess_bwd<0><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh, acd); break;
-      case 1: k_preprocess_bwd<1><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh, acd); break;
-      case 2: k_preprocess_bwd<2><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh, acd); break;
-      default: k_preprocess_bwd<3><<<nb, 128, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh, acd); break;
+      case 0: k_preprocess_bwd<0><<<nb, kPreBwdThreads, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh, acd); break;
+      case 1: k_preprocess_bwd<1><<<nb, kPreBwdThreads, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh, acd); break;
+      case 2: k_preprocess_bwd<2><<<nb, kPreBwdThreads, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh, acd); break;
+      default: k_preprocess_bwd<3><<<nb, kPreBwdThreads, 0, s>>>(*vt, *g, rad, accum, dmeans, dscales, drot, dopac, dsh, acd); break;
     }
   }
   note_launches(1);
