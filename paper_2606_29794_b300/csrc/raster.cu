@@ -504,6 +504,19 @@ constexpr float kBand32 = 3e-6f;
 // members or the scratch is full). Emit pass (EMIT = true): staged Gaussians copy
 // their list to the final offset; the others run the query again and write directly.
 constexpr int kStage = 256;
+// Gaussians a warp sets up together (one per lane) before running their queries.
+#ifndef HPXGS_TILES_BATCH
+#define HPXGS_TILES_BATCH 8
+#endif
+constexpr int kTilesBatch = HPXGS_TILES_BATCH;
+// A Gaussian's query setup as one lane leaves it for its warp.
+struct TileSet {
+  DiscQ Q;
+  float3 g;
+  float rs;
+  uint32_t gid, slot, n;
+  uint64_t base;
+};
 
 template <bool EMIT>
 __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
@@ -514,20 +527,52 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
                                                int32_t* status, uint32_t* __restrict__ stage,
                                                uint32_t* __restrict__ scratch, uint32_t* scratch_top) {
   __shared__ uint32_t s_stage[8][kStage];
+  __shared__ TileSet s_set[8][kTilesBatch];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   const int64_t PV = (int64_t)vt.P * vt.nviews;
   const int64_t wpb = blockDim.x >> 5;
-  for (int64_t j = blockIdx.x * wpb + (threadIdx.x >> 5); j < PV; j += (int64_t)gridDim.x * wpb) {
-    if (skeys[j] == 0xffffffffu) { if (!EMIT && lane == 0) counts[j] = 0; continue; }
-    const uint32_t gid = svals[j];
+  // A warp takes kTilesBatch consecutive Gaussians: lane t loads and sets up Gaussian
+  // jb + t into the warp's slot table (FoV-invisible ones are dropped here), then the
+  // warp runs the query of each in turn.
+  const int64_t nwarps = (int64_t)gridDim.x * wpb;
+  for (int64_t jb = (blockIdx.x * wpb + wib) * (int64_t)kTilesBatch; jb < PV; jb += nwarps * kTilesBatch) {
+    bool vl = false;
+    if (lane < kTilesBatch && jb + lane < PV) {
+      const int64_t jl = jb + lane;
+      if (skeys[jl] == 0xffffffffu) {
+        if (!EMIT) counts[jl] = 0;
+      } else {
+        vl = true;
+        TileSet& ts = s_set[wib][lane];
+        ts.gid = svals[jl];
+        ts.slot = EMIT ? stage[jl] : 0xffffffffu;
+        if (EMIT) { ts.n = counts[jl]; ts.base = offsets[jl]; }
+        if (!EMIT || ts.slot == 0xffffffffu) {
+          const ViewParams& vpl = vt.v[ts.gid / (uint32_t)vt.P];
+          const float4 r0 = rec[4 * (int64_t)ts.gid];
+          const float3 gl = make_float3(r0.x, r0.y, r0.z);
+          const float rsl = radii[ts.gid];
+          DiscQ Ql;
+          disc_setup(vpl, vpl.k - vt.b, gl, rsl, lane, Ql);
+          ts.g = gl; ts.rs = rsl; ts.Q = Ql;
+        }
+      }
+    }
+    const uint32_t todo0 = __ballot_sync(FULL, vl);
+    __syncwarp();
+    for (uint32_t todo = todo0; todo; todo &= todo - 1u) {
+    const int t = __ffs(todo) - 1;
+    const int64_t j = jb + t;
+    const TileSet& ts = s_set[wib][t];
+    const uint32_t gid = ts.gid;
     if (EMIT) {
-      const uint32_t slot = stage[j];
+      const uint32_t slot = ts.slot;
       if (slot != 0xffffffffu) {                     // staged by the count pass: copy
-        const uint32_t n = counts[j];
-        const uint64_t base = offsets[j];
+        const uint32_t n = ts.n;
+        const uint64_t base = ts.base;
         for (uint32_t e = lane; e < n; e += 32) {
           const uint64_t p = base + e;
           if (p < cap) { out_tile[p] = scratch[slot + e]; out_id[p] = gid; }
@@ -539,14 +584,11 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
     const int v = (int)(gid / (uint32_t)vt.P);
     const ViewParams& vp = vt.v[v];
     const int kt = vp.k - vt.b;
-    const float4 r0 = rec[4 * (int64_t)gid];
-    const float3 g = make_float3(r0.x, r0.y, r0.z);
-    DiscQ Q;
-    disc_setup(vp, kt, g, radii[gid], lane, Q);
-
-    const float rs = radii[gid];
+    const float3 g = ts.g;
+    const DiscQ Q = ts.Q;
+    const float rs = ts.rs;
     double cosRm = 2.0;                        // FP64 threshold, formed at this lane's first band candidate
-    const uint64_t base = EMIT ? offsets[j] : 0;
+    const uint64_t base = EMIT ? ts.base : 0;
     uint32_t cnt = 0;
     for (int r0i = Q.ilo; r0i <= Q.ihi; r0i += 32) {
       const int i = r0i + lane;
@@ -630,6 +672,8 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
       __syncwarp();
       if (lane == 0) { counts[j] = cnt; stage[j] = slot; }
     }
+    }
+    __syncwarp();                                    // the table is refilled by the next batch
   }
 }
 
@@ -1505,7 +1549,7 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   uint64_t* offsets = at<uint64_t>(ws, L.offsets);
   uint64_t* part = at<uint64_t>(ws, L.scan_part);
   prof_begin(HPXGS_STAGE_TILE_COUNT, s);
-  const unsigned tblocks = (unsigned)std::min<int64_t>((PV + 7) / 8, 32LL * num_sms());
+  const unsigned tblocks = (unsigned)std::min<int64_t>((PV + 8 * kTilesBatch - 1) / (8 * kTilesBatch), 32LL * num_sms());
   if (vt->query == HPXGS_QUERY_NESTED) {
     const unsigned nblocks = (unsigned)std::min<int64_t>((PV + 255) / 256, 32LL * num_sms());
     k_tiles_nested<false><<<nblocks, 256, 0, s>>>(*vt, rec, radii, sk, sv, flags, counts, nullptr, nullptr, nullptr,
@@ -1618,7 +1662,7 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
     const uint32_t* sk = which ? at<uint32_t>(ws, L.key_b) : at<uint32_t>(ws, L.key_a);
     const uint32_t* sv = which ? at<uint32_t>(ws, L.val_b) : at<uint32_t>(ws, L.val_a);
     prof_begin(HPXGS_STAGE_TILE_EMIT, s);
-    const unsigned tblocks = (unsigned)std::min<int64_t>((PV + 7) / 8, 32LL * num_sms());
+    const unsigned tblocks = (unsigned)std::min<int64_t>((PV + 8 * kTilesBatch - 1) / (8 * kTilesBatch), 32LL * num_sms());
     if (vt->query == HPXGS_QUERY_NESTED) {
       const unsigned nblocks = (unsigned)std::min<int64_t>((PV + 255) / 256, 32LL * num_sms());
       k_tiles_nested<true><<<nblocks, 256, 0, s>>>(*vt, rec, at<float>(ws, L.radii), sk, sv, flags,
