@@ -172,6 +172,7 @@ __device__ __forceinline__ void geo_compute(const ViewParams& vp, float near_pla
 // ----------------------------------------------------------------------------
 // k_preprocess: one thread per (view, Gaussian) id gid = v * P + i.
 // ----------------------------------------------------------------------------
+template <int DEG>
 __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ ViewTable vt, hpxgs_gaussians gs,
                                                     float4* __restrict__ rec, float* __restrict__ radii,
                                                     float* __restrict__ depth, uint32_t* __restrict__ keys,
@@ -201,16 +202,17 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ View
   float dx = gs.means[3 * i] - vp.cam[0], dy = gs.means[3 * i + 1] - vp.cam[1], dz = gs.means[3 * i + 2] - vp.cam[2];
   const float idist = rsqrtf(dx * dx + dy * dy + dz * dz);
   dx *= idist; dy *= idist; dz *= idist;
-  float Y[16];
-  sh_basis(vt.sh_degree, dx, dy, dz, Y, nullptr);
-  const int K = (vt.sh_degree + 1) * (vt.sh_degree + 1);
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  float Y[K];
+  sh_basis(DEG, dx, dy, dz, Y, nullptr);
   const float* sh = gs.sh + (int64_t)i * K * 3;
-  float col[3];
-  for (int c = 0; c < 3; ++c) {
-    float acc = 0.5f;
-    for (int kk = 0; kk < K; ++kk) acc += sh[3 * kk + c] * Y[kk];
-    col[c] = fmaxf(acc, 0.f);
-  }
+  float col[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+  for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) col[c] += sh[3 * kk + c] * Y[kk];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) col[c] = fmaxf(col[c], 0.f);
   rec[4 * gid + 0] = make_float4(G.g.x, G.g.y, G.g.z, gs.opacities[i]);
   rec[4 * gid + 1] = make_float4(G.e1.x, G.e1.y, G.e1.z, G.qa);
   rec[4 * gid + 2] = make_float4(G.e2.x, G.e2.y, G.e2.z, G.qb);
@@ -715,14 +717,20 @@ __global__ void __launch_bounds__(256) k_scan_part(const uint32_t* __restrict__ 
   }
 }
 
-__global__ void k_scan_top(uint64_t* part, int G, uint32_t* counters, uint64_t* total_out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  uint64_t run = 0;
-  for (int b = 0; b < G; ++b) { uint64_t v = part[b]; part[b] = run; run += v; }
-  part[G] = run;
-  counters[C_NPAIRS] = (uint32_t)(run > 0xffffffffull ? 0xffffffffull : run);
-  counters[C_NPAIRS_HI] = (uint32_t)(run >> 32);
-  if (total_out) *total_out = run;
+// One block of kMaxSortBlocks threads: exclusive scan of the G <= kMaxSortBlocks partials.
+__global__ void __launch_bounds__(kMaxSortBlocks) k_scan_top(uint64_t* part, int G, uint32_t* counters,
+                                                           uint64_t* total_out) {
+  const int t = threadIdx.x;
+  const uint64_t v = t < G ? part[t] : 0;
+  uint64_t run;
+  const uint64_t ex = block_exclusive_scan_u64(v, &run);
+  if (t < G) part[t] = ex;
+  if (t == 0) {
+    part[G] = run;
+    counters[C_NPAIRS] = (uint32_t)(run > 0xffffffffull ? 0xffffffffull : run);
+    counters[C_NPAIRS_HI] = (uint32_t)(run >> 32);
+    if (total_out) *total_out = run;
+  }
 }
 
 __global__ void __launch_bounds__(256) k_scan_apply(const uint32_t* __restrict__ c, int64_t n, int G,
@@ -1533,7 +1541,15 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   uint32_t* ka = at<uint32_t>(ws, L.key_a); uint32_t* kb = at<uint32_t>(ws, L.key_b);
   uint32_t* va = at<uint32_t>(ws, L.val_a); uint32_t* vb = at<uint32_t>(ws, L.val_b);
   prof_begin(HPXGS_STAGE_PREPROCESS, s);
-  k_preprocess<<<(unsigned)((PV + 255) / 256), 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va);
+  {
+    const unsigned nb = (unsigned)((PV + 255) / 256);
+    switch (g->sh_degree) {
+      case 0: k_preprocess<0><<<nb, 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va); break;
+      case 1: k_preprocess<1><<<nb, 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va); break;
+      case 2: k_preprocess<2><<<nb, 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va); break;
+      default: k_preprocess<3><<<nb, 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va); break;
+    }
+  }
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_PREPROCESS, s);
@@ -1566,7 +1582,7 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   const int G = L.sort_blocks;
   prof_begin(HPXGS_STAGE_SCAN, s);
   k_scan_part<<<G, 256, 0, s>>>(counts, PV, G, part);
-  k_scan_top<<<1, 32, 0, s>>>(part, G, counters, total_out);
+  k_scan_top<<<1, kMaxSortBlocks, 0, s>>>(part, G, counters, total_out);
   k_scan_apply<<<G, 256, 0, s>>>(counts, PV, G, part, offsets);
   note_launches(3);
   HPXGS_LAUNCH_CHECK();
