@@ -307,9 +307,12 @@ __global__ void __launch_bounds__(256) k_scan_digit_rows(uint32_t* __restrict__ 
 // per digit); a digit-major scan over the warps gives each element its place in
 // the tile sorted by digit; the tile is reordered in shared memory and written
 // out so that elements of one digit go to consecutive addresses (full sectors).
+#ifndef HPXGS_SCATTER_MINB
+#define HPXGS_SCATTER_MINB 4
+#endif
 constexpr int kWarpSeg = kSortTile / (kSortThreads / 32);   // 512 elements per warp
 constexpr int kSegRounds = kWarpSeg / 32;                   // 16
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+__global__ void __launch_bounds__(kSortThreads, HPXGS_SCATTER_MINB) k_sort_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                                const uint32_t* n_ptr, uint32_t n_max, int shift, int nbits,
                                                                const uint32_t* __restrict__ hist,
