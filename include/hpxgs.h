@@ -114,6 +114,11 @@ typedef struct {
    * kernels' own arithmetic); 0: every entry is evaluated at every pixel. The
    * results are the same bit for bit either way. */
   int32_t blend_cull;
+  /* 1 (default): with tile_level 5 the blends take the four order-4 quarters of each
+   * listed tile as separate units (the lists stay at order 5, about half the pairs of
+   * order 4; the blend runs in the order-4 launch shapes). 0: whole tiles. Results are
+   * the same bit for bit either way (gradients up to the order of atomic sums). */
+  int32_t blend_split;
 } hpxgs_config;
 
 #define HPXGS_QUERY_RING 0

@@ -43,7 +43,8 @@ class Config(ctypes.Structure):
                 ("cutoff_m", ctypes.c_float), ("blur_rad2", ctypes.c_float), ("near_plane", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("lambda_ssim", ctypes.c_float), ("write_outside", ctypes.c_int32),
                 ("fwd_ppt", ctypes.c_int32), ("bwd_ppt", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("query", ctypes.c_int32), ("query_log2f", ctypes.c_int32), ("blend_cull", ctypes.c_int32)]
+                ("query", ctypes.c_int32), ("query_log2f", ctypes.c_int32), ("blend_cull", ctypes.c_int32),
+                ("blend_split", ctypes.c_int32)]
 
 
 class WorkspaceView(ctypes.Structure):

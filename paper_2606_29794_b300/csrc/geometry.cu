@@ -225,7 +225,8 @@ static bool valid_cfg(const hpxgs_config* c) {
          c->alpha_max > 0 && c->alpha_max < 1 && c->cutoff_m > 0 && c->near_plane >= 0 &&
          valid_ppt(c->fwd_ppt) && valid_ppt(c->bwd_ppt) && c->blocks_per_sm >= 0 && c->blocks_per_sm <= 64 &&
          (c->query == HPXGS_QUERY_RING || c->query == HPXGS_QUERY_NESTED) && c->query_log2f >= 0 &&
-         c->query_log2f <= 3 && (c->blend_cull == 0 || c->blend_cull == 1);
+         c->query_log2f <= 3 && (c->blend_cull == 0 || c->blend_cull == 1) &&
+         (c->blend_split == 0 || c->blend_split == 1);
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -449,6 +450,7 @@ void hpxgs_config_default(hpxgs_config* c) {
   c->query = HPXGS_QUERY_RING;
   c->query_log2f = 2;
   c->blend_cull = 1;
+  c->blend_split = 1;
 }
 
 int hpxgs_nside_for_image(int kind, double W, double H, double fovx, double fovy, double* nstar, int* k,

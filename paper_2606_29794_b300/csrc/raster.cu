@@ -870,24 +870,26 @@ struct Pix {
 // them by groups of 32, so no per-pixel early exit is taken.)
 __device__ __forceinline__ void pixel_weight(const float3 p, const float4 r0, const float4 r1, const float4 r2,
                                              const float4 r3, Pix& P) {
+  // every rounding written out (fmaf, __fmul_rn), so that all launch shapes give the same bits
   const float dx = p.x - r0.x, dy = p.y - r0.y, dz = p.z - r0.z;
-  P.n2 = dx * dx + dy * dy + dz * dz;
-  P.u1 = dx * r1.x + dy * r1.y + dz * r1.z;
-  P.u2 = dx * r2.x + dy * r2.y + dz * r2.z;
-  P.s2 = P.u1 * P.u1 + P.u2 * P.u2;
-  P.q = P.u1 * (r1.w * P.u1 + 2.f * r2.w * P.u2) + r3.w * P.u2 * P.u2;
+  P.n2 = fmaf(dz, dz, fmaf(dy, dy, __fmul_rn(dx, dx)));
+  P.u1 = fmaf(dz, r1.z, fmaf(dy, r1.y, __fmul_rn(dx, r1.x)));
+  P.u2 = fmaf(dz, r2.z, fmaf(dy, r2.y, __fmul_rn(dx, r2.x)));
+  P.s2 = fmaf(P.u2, P.u2, __fmul_rn(P.u1, P.u1));
+  const float t = fmaf(r1.w, P.u1, __fmul_rn(2.f * r2.w, P.u2));
+  P.q = fmaf(__fmul_rn(r3.w, P.u2), P.u2, __fmul_rn(P.u1, t));
   P.series = P.n2 < kSeriesN2;
   if (P.series) {
     const float s2 = P.s2;
-    P.ser = 1.f + s2 * (1.f / 3.f + s2 * (8.f / 45.f + s2 * (4.f / 35.f + s2 * (128.f / 1575.f))));
-    P.m = P.q * P.ser;
+    P.ser = fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 128.f / 1575.f, 4.f / 35.f), 8.f / 45.f), 1.f / 3.f), 1.f);
+    P.m = __fmul_rn(P.q, P.ser);
   } else {
-    const float c = 1.f - 0.5f * P.n2;
+    const float c = fmaf(-0.5f, P.n2, 1.f);
     if (P.s2 < 1e-24f) { P.ser = 0.f; P.m = (c < 0.f) ? 3.0e38f : 0.f; return; }
     const float s = sqrtf(P.s2);
     const float ratio = atan2f(s, c) / s;
-    P.ser = ratio * ratio;
-    P.m = P.q * P.ser;
+    P.ser = __fmul_rn(ratio, ratio);
+    P.m = __fmul_rn(P.q, P.ser);
   }
 }
 
@@ -967,7 +969,7 @@ __device__ __forceinline__ int view_of_tile(const ViewTable& vt, int tile) {
 
 // DEPTH adds the inverse-depth channel D = sum_i T_i alpha_i / r_i (Sec. 3.2, depth
 // supervision by 1/r): rdepth holds r per (view, Gaussian), dmap receives D per pixel.
-template <int NT, int PPT, int BATCH, bool DEPTH = false>
+template <int NT, int PPT, int BATCH, bool DEPTH = false, bool SPLIT = false>
 __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fwd(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
                                                   const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
                                                   const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
@@ -986,17 +988,20 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
   __shared__ float3 s_sub[NS];
   __shared__ int s_tile;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int b = vt.b;
+  const int b = SPLIT ? vt.b - 1 : vt.b;            // order of a blend unit below k
+  const int nunits = SPLIT ? 4 * vt.total_tiles : vt.total_tiles;
   const float sqrt_cut = cull_sqrt_cut(vt.cutoff);
   for (;;) {
     if (tid == 0) s_tile = (int)atomicAdd(work, 1u);
     __syncthreads();
-    const int tile = s_tile;
+    const int unit = s_tile;
     __syncthreads();
-    if (tile >= vt.total_tiles) break;
+    if (unit >= nunits) break;
+    const int tile = SPLIT ? unit >> 2 : unit;       // SPLIT: unit = one quarter of a listed tile
     const int v = view_of_tile(vt, tile);
     const ViewParams& vp = vt.v[v];
-    const uint32_t lt = (uint32_t)(tile - vp.tile_base);
+    const uint32_t lt = SPLIT ? (((uint32_t)(tile - vp.tile_base) << 2) | (uint32_t)(unit & 3))
+                              : (uint32_t)(tile - vp.tile_base);
     const bool active = flags[tile] & 1u;
     if (!active && !vt.write_outside) continue;
     const uint32_t* vmask = mask + (vp.pix_base >> 5);
@@ -1020,7 +1025,14 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
       T[q] = 1.f;
       last[q] = 0;
     }
-    const uint2 rg = active ? ranges[tile] : make_uint2(0, 0);
+    bool unit_active = active;
+    if (SPLIT) {                                     // a quarter with no in-mask pixel stages nothing
+      int any = 0;
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) any |= inm[q];
+      unit_active = __syncthreads_or(any) != 0;
+    }
+    const uint2 rg = unit_active ? ranges[tile] : make_uint2(0, 0);
     for (uint32_t bs = rg.x; bs < rg.y; bs += BATCH) {
       const int n = (int)min((uint32_t)BATCH, rg.y - bs);
       __syncthreads();
@@ -1033,8 +1045,10 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
           const float4 a0 = src[0], a1 = src[1], a2 = src[2], a3 = src[3];
           s_rec[e][0] = a0; s_rec[e][1] = a1; s_rec[e][2] = a2; s_rec[e][3] = a3;
           if (DEPTH) s_invr[e] = 1.f / rdepth[id];
-          gm = vt.cull ? live_groups<NS>(a0, a1, a2, a3, s_sub, rho_p, sqrt_cut) : ~0u;
-          gmask[bs + e] = gm;                        // for the backward pass over the same entries
+          gm = vt.cull ? live_groups<NS>(a0, a1, a2, a3, s_sub, rho_p, sqrt_cut) : (NG == 32 ? ~0u : (1u << NG) - 1u);
+          // for the backward pass over the same entries (SPLIT: one byte of the entry's word per quarter)
+          if (SPLIT) reinterpret_cast<uint8_t*>(gmask)[4 * (size_t)(bs + e) + (unit & 3)] = (uint8_t)gm;
+          else gmask[bs + e] = gm;
         }
         if (e0 + (warp << 5) < n) {                  // this warp staged entries: one bitmap word per group
 #pragma unroll
@@ -1060,11 +1074,11 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
             pixel_weight(pv[q], r0, r1, r2, r3, P);
             if (P.m <= vt.cutoff) {
               ++ncontrib;
-              const float a = fminf(vt.alpha_max, r0.w * __expf(-0.5f * P.m));
-              const float w = a * T[q];
-              C[q][0] += w * r3.x; C[q][1] += w * r3.y; C[q][2] += w * r3.z;
-              if (DEPTH) D[DEPTH ? q : 0] += w * s_invr[e];
-              T[q] = T[q] * (1.f - a);
+              const float a = fminf(vt.alpha_max, __fmul_rn(r0.w, __expf(-0.5f * P.m)));
+              const float w = __fmul_rn(a, T[q]);
+              C[q][0] = fmaf(w, r3.x, C[q][0]); C[q][1] = fmaf(w, r3.y, C[q][1]); C[q][2] = fmaf(w, r3.z, C[q][2]);
+              if (DEPTH) D[DEPTH ? q : 0] = fmaf(w, s_invr[e], D[DEPTH ? q : 0]);
+              T[q] = __fmul_rn(T[q], 1.f - a);
               if (T[q] < vt.eps_T) { done[q] = true; last[q] = bs + e + 1 - rg.x; break; }
             }
           }
@@ -1081,9 +1095,9 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
       if (inm[q]) {
         if (T[q] >= vt.eps_T) last[q] = rg.y - rg.x;     // ran through the whole list
         neval += last[q];
-        maps[3 * pg + 0] = C[q][0] + T[q] * vt.bg[0];
-        maps[3 * pg + 1] = C[q][1] + T[q] * vt.bg[1];
-        maps[3 * pg + 2] = C[q][2] + T[q] * vt.bg[2];
+        maps[3 * pg + 0] = fmaf(T[q], vt.bg[0], C[q][0]);
+        maps[3 * pg + 1] = fmaf(T[q], vt.bg[1], C[q][1]);
+        maps[3 * pg + 2] = fmaf(T[q], vt.bg[2], C[q][2]);
         Tout[pg] = T[q];
         lastout[pg] = last[q];
         if (DEPTH) dmap[pg] = D[DEPTH ? q : 0];
@@ -1115,7 +1129,7 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
 // ----------------------------------------------------------------------------
 // DEPTH adds the inverse-depth channel: ddepth is dL/dD per pixel, and the tenth
 // partial dL/d(1/r) per (view, Gaussian) goes to accum_d.
-template <int NT, int PPT, int BATCH, bool DEPTH = false>
+template <int NT, int PPT, int BATCH, bool DEPTH = false, bool SPLIT = false>
 __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bwd(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
                                                   const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
                                                   const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
@@ -1139,17 +1153,20 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
   __shared__ int s_tile;
   __shared__ uint32_t s_maxlast;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int b = vt.b;
+  const int b = SPLIT ? vt.b - 1 : vt.b;            // order of a blend unit below k
+  const int nunits = SPLIT ? 4 * vt.total_tiles : vt.total_tiles;
   for (;;) {
     if (tid == 0) { s_tile = (int)atomicAdd(work, 1u); s_maxlast = 0; }
     __syncthreads();
-    const int tile = s_tile;
-    if (tile >= vt.total_tiles) break;
+    const int unit = s_tile;
+    if (unit >= nunits) break;
+    const int tile = SPLIT ? unit >> 2 : unit;       // SPLIT: unit = one quarter of a listed tile
     const bool active = flags[tile] & 1u;
     if (!active) { __syncthreads(); continue; }
     const int v = view_of_tile(vt, tile);
     const ViewParams& vp = vt.v[v];
-    const uint32_t lt = (uint32_t)(tile - vp.tile_base);
+    const uint32_t lt = SPLIT ? (((uint32_t)(tile - vp.tile_base) << 2) | (uint32_t)(unit & 3))
+                              : (uint32_t)(tile - vp.tile_base);
     const uint2 rg = ranges[tile];
     const uint32_t* vmask = mask + (vp.pix_base >> 5);
     float3 pv[PPT];
@@ -1188,7 +1205,8 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
           const float4* src = rec + 4 * (int64_t)id;
           s_rec[e][0] = src[0]; s_rec[e][1] = src[1]; s_rec[e][2] = src[2]; s_rec[e][3] = src[3];
           if (DEPTH) s_invr[e] = 1.f / rdepth[id];
-          gmv = gmask[bs + e];                     // the forward's cull of this entry
+          gmv = SPLIT ? (uint32_t)reinterpret_cast<const uint8_t*>(gmask)[4 * (size_t)(bs + e) + (unit & 3)]
+                      : gmask[bs + e];             // the forward's cull of this entry
           s_gm[e] = gmv;
         }
         if (e0 + (warp << 5) < n) {                // this warp staged entries: one bitmap word per warp
@@ -1487,14 +1505,14 @@ static int blend_blocks(const void* fn, int nt, int want_per_sm) {
 #define HPXGS_FWD_BATCH 128
 #endif
 // Launch of a blend kernel with NT threads x PPT pixels per thread = the tile's pixels.
-template <int NT, int PPT, bool DEPTH = false, typename... Args>
+template <int NT, int PPT, bool DEPTH = false, bool SPLIT = false, typename... Args>
 static void launch_fwd(int bps, cudaStream_t s, Args... args) {
-  auto fn = k_blend_fwd<NT, PPT, HPXGS_FWD_BATCH, DEPTH>;
+  auto fn = k_blend_fwd<NT, PPT, HPXGS_FWD_BATCH, DEPTH, SPLIT>;
   fn<<<blend_blocks((const void*)fn, NT, bps), NT, 0, s>>>(args...);
 }
-template <int NT, int PPT, bool DEPTH = false, typename... Args>
+template <int NT, int PPT, bool DEPTH = false, bool SPLIT = false, typename... Args>
 static void launch_bwd(int bps, cudaStream_t s, Args... args) {
-  auto fn = k_blend_bwd<NT, PPT, 32, DEPTH>;
+  auto fn = k_blend_bwd<NT, PPT, 32, DEPTH, SPLIT>;
   fn<<<blend_blocks((const void*)fn, NT, bps), NT, 0, s>>>(args...);
 }
 
@@ -1720,6 +1738,7 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
   uint32_t* work = counters + C_WORK_FWD;
   unsigned long long* evals = reinterpret_cast<unsigned long long*>(counters + C_NEVAL);
   const int b = cfg->tile_level;
+  const bool split = b == 5 && cfg->blend_split;   // quarters of order-5 tiles as blend units
   const int bps = cfg->blocks_per_sm;
   prof_begin(HPXGS_STAGE_BLEND_FWD, s);
   {
@@ -1727,7 +1746,12 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
 #define FWD_BASE bps, s, *vt, (const float4*)rec, (const uint2*)ranges, ids, (const uint32_t*)flags, (const uint32_t*)mask, maps, T_final, last, work, evals, gmask
 #define FWD_ARGS FWD_BASE, (const float*)nullptr, (float*)nullptr
 #define FWD_DEPTH_ARGS FWD_BASE, (const float*)at<float>(ws, L.depth), depth_map
-    if (depth_map) {                               // the depth channel runs in each level's default shape
+    if (split) {                                   // order-5 lists, quarters blended in the order-4 shapes
+      if (depth_map) launch_fwd<256, 1, true, true>(FWD_DEPTH_ARGS);
+      else if (pick_ppt(4, cfg->fwd_ppt, true) == 2) launch_fwd<128, 2, false, true>(FWD_ARGS);
+      else if (pick_ppt(4, cfg->fwd_ppt, true) == 4) launch_fwd<64, 4, false, true>(FWD_ARGS);
+      else launch_fwd<256, 1, false, true>(FWD_ARGS);
+    } else if (depth_map) {                        // the depth channel runs in each level's default shape
       if (b == 3) launch_fwd<64, 1, true>(FWD_DEPTH_ARGS);
       else if (b == 4) launch_fwd<256, 1, true>(FWD_DEPTH_ARGS);
       else launch_fwd<256, 4, true>(FWD_DEPTH_ARGS);
@@ -1787,6 +1811,7 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   const uint32_t* mask = internal_mask(ws, L);      // written by the forward
   uint32_t* work = counters + C_WORK_BWD;
   const int b = cfg->tile_level;
+  const bool split = b == 5 && cfg->blend_split;   // quarters of order-5 tiles as blend units
   const int bps = cfg->blocks_per_sm;
   prof_begin(HPXGS_STAGE_BLEND_BWD, s);
   {
@@ -1795,7 +1820,12 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
 #define BWD_BASE bps, s, *vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, gmask
 #define BWD_ARGS BWD_BASE, (const float*)nullptr, (const float*)nullptr, (float*)nullptr
 #define BWD_DEPTH_ARGS BWD_BASE, rdepth, ddepth, accum_d
-    if (ddepth) {                                  // the depth channel runs in each level's default shape
+    if (split) {                                   // order-5 lists, quarters blended in the order-4 shapes
+      if (ddepth) launch_bwd<64, 4, true, true>(BWD_DEPTH_ARGS);
+      else if (pick_ppt(4, cfg->bwd_ppt, false) == 2) launch_bwd<128, 2, false, true>(BWD_ARGS);
+      else if (pick_ppt(4, cfg->bwd_ppt, false) == 8) launch_bwd<32, 8, false, true>(BWD_ARGS);
+      else launch_bwd<64, 4, false, true>(BWD_ARGS);
+    } else if (ddepth) {                           // the depth channel runs in each level's default shape
       if (b == 3) launch_bwd<32, 2, true>(BWD_DEPTH_ARGS);
       else if (b == 4) launch_bwd<64, 4, true>(BWD_DEPTH_ARGS);
       else launch_bwd<256, 4, true>(BWD_DEPTH_ARGS);

@@ -65,11 +65,11 @@ class Rasterizer:
 
     def __init__(self, tile_level=4, eps_T=1e-4, alpha_max=0.99, cutoff=9.0, blur=None, near=0.2,
                  bg=(0.0, 0.0, 0.0), lam=0.2, write_outside=1, capacity=None, headroom=1.15, fwd_ppt=0, bwd_ppt=0,
-                 blocks_per_sm=0, query=0, query_log2f=2, blend_cull=1):
+                 blocks_per_sm=0, query=0, query_log2f=2, blend_cull=1, blend_split=1):
         self.cfg = L.default_config(tile_level=tile_level, eps_T=eps_T, alpha_max=alpha_max, cutoff_m=cutoff,
                                     blur=blur, near_plane=near, bg=bg, lam=lam, write_outside=write_outside,
                                     fwd_ppt=fwd_ppt, bwd_ppt=bwd_ppt, blocks_per_sm=blocks_per_sm, query=query,
-                                    query_log2f=query_log2f, blend_cull=blend_cull)
+                                    query_log2f=query_log2f, blend_cull=blend_cull, blend_split=blend_split)
         self.capacity = capacity
         self.headroom = headroom
 
