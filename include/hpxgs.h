@@ -314,7 +314,8 @@ typedef struct {
   const uint32_t* ranges;      /* [total_tiles, 2] start/end into pair_ids */
   const uint32_t* n_pairs;     /* device scalar: pairs needed (may exceed capacity) */
   const float* accum;          /* [nviews*P, HPXGS_NACC] backward partials (after hpxgs_backward) */
-  const uint64_t* n_eval;      /* device scalar: (pixel, list entry) evaluations of the last forward blend */
+  const uint64_t* n_eval;      /* device scalar: (pixel, list entry) pairs up to each pixel's termination in the
+                                  last forward blend (the blend cull skips most of those that cannot contribute) */
   const uint64_t* n_contrib;   /* device scalar: of those, entries with alpha > 0 */
   int64_t total_tiles;
   /* [n_pairs] blend cull per list entry (aligned with pair_ids): bit g set unless

@@ -6,7 +6,9 @@ list alone (Algorithm 1; with the m <= 9 cutoff the map does not depend on
 which other tiles exist). So for a seeded sample of active tiles the oracle
 builds only those lists (membership definition over every Gaussian) and
 composites a sample of their pixels. Each workload runs in the launch
-configuration the benchmark times (tile level 4, default pixels per thread):
+configuration the benchmark times (order-5 lists blended by 16 x 16 quarters for
+the training step and the Nside 2048 step, tile level 4 for the 16 views; default
+pixels per thread):
 
 - tile lists of the sampled tiles, rebuilt by the oracle from the GPU's stored
   FP32 (g, r_s, depth): exact, including order;
@@ -155,7 +157,7 @@ def _check_grads(sc, views, rast, out, state, sampled, seed, use=None):
 def test_training_step_nside512_fisheye190_p300k():
     sc = S.make_scene(300_000, 3, seed=20261205)
     view = S.make_view(9, S.CAM_FISHEYE, 190.0)
-    rast = R.Rasterizer(tile_level=4)
+    rast = R.Rasterizer(tile_level=5)
     out, state = rast.forward_raw(*scene_tensors(sc), 3, [view])
     torch.cuda.synchronize()
     sampled = _check_views(sc, [view], rast, out, state, n_tiles=48, per_tile=24, seed=1)
@@ -175,7 +177,7 @@ def test_sixteen_views_p1m():
 def test_nside2048_full_sphere_p6m():
     sc = S.make_scene(6_000_000, 3, seed=20261213, logscale_mu=-3.5, logscale_sd=0.7)
     view = S.make_view(11)
-    rast = R.Rasterizer(tile_level=4)
+    rast = R.Rasterizer(tile_level=5)
     out, state = rast.forward_raw(*scene_tensors(sc), 3, [view])
     torch.cuda.synchronize()
     _check_views(sc, [view], rast, out, state, n_tiles=24, per_tile=16, seed=5)
