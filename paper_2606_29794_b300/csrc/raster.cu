@@ -172,16 +172,28 @@ __device__ __forceinline__ void geo_compute(const ViewParams& vp, float near_pla
 // ----------------------------------------------------------------------------
 // k_preprocess: one thread per (view, Gaussian) id gid = v * P + i.
 // ----------------------------------------------------------------------------
+// Grid (P / kPreThreads, views): a block's SH rows are one contiguous span, loaded
+// coalesced into shared memory (rows padded to 3K + 1 floats).
+constexpr int kPreThreads = 128;
 template <int DEG>
-__global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ ViewTable vt, hpxgs_gaussians gs,
+__global__ void __launch_bounds__(kPreThreads) k_preprocess(const __grid_constant__ ViewTable vt, hpxgs_gaussians gs,
                                                     float4* __restrict__ rec, float* __restrict__ radii,
                                                     float* __restrict__ depth, uint32_t* __restrict__ keys,
                                                     uint32_t* __restrict__ vals) {
-  const int64_t PV = (int64_t)vt.P * vt.nviews;
-  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= PV) return;
-  const int v = (int)(gid / vt.P);
-  const int i = (int)(gid - (int64_t)v * vt.P);
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int RW = 3 * K + 1;
+  __shared__ float s_sh[kPreThreads * RW];
+  const int v = blockIdx.y;
+  const int i0 = blockIdx.x * kPreThreads;
+  const int nrow = min(kPreThreads, vt.P - i0);
+  for (int t = threadIdx.x; t < nrow * 3 * K; t += kPreThreads) {
+    const int r = t / (3 * K), c = t - r * (3 * K);
+    s_sh[r * RW + c] = gs.sh[(int64_t)i0 * 3 * K + t];
+  }
+  __syncthreads();
+  const int i = i0 + threadIdx.x;
+  if (i >= vt.P) return;
+  const int64_t gid = (int64_t)v * vt.P + i;
   const ViewParams& vp = vt.v[v];
   Geo G;
   geo_compute(vp, vt.near_plane, gs.means + 3 * (int64_t)i, gs.scales + 3 * (int64_t)i, gs.rotations + 4 * (int64_t)i, G);
@@ -202,10 +214,9 @@ __global__ void __launch_bounds__(256) k_preprocess(const __grid_constant__ View
   float dx = gs.means[3 * i] - vp.cam[0], dy = gs.means[3 * i + 1] - vp.cam[1], dz = gs.means[3 * i + 2] - vp.cam[2];
   const float idist = rsqrtf(dx * dx + dy * dy + dz * dz);
   dx *= idist; dy *= idist; dz *= idist;
-  constexpr int K = (DEG + 1) * (DEG + 1);
   float Y[K];
   sh_basis(DEG, dx, dy, dz, Y, nullptr);
-  const float* sh = gs.sh + (int64_t)i * K * 3;
+  const float* sh = s_sh + threadIdx.x * RW;
   float col[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
   for (int kk = 0; kk < K; ++kk)
@@ -1565,12 +1576,12 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   uint32_t* va = at<uint32_t>(ws, L.val_a); uint32_t* vb = at<uint32_t>(ws, L.val_b);
   prof_begin(HPXGS_STAGE_PREPROCESS, s);
   {
-    const unsigned nb = (unsigned)((PV + 255) / 256);
+    const dim3 nb((unsigned)((g->P + kPreThreads - 1) / kPreThreads), (unsigned)nviews);
     switch (g->sh_degree) {
-      case 0: k_preprocess<0><<<nb, 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va); break;
-      case 1: k_preprocess<1><<<nb, 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va); break;
-      case 2: k_preprocess<2><<<nb, 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va); break;
-      default: k_preprocess<3><<<nb, 256, 0, s>>>(*vt, *g, rec, radii, depth, ka, va); break;
+      case 0: k_preprocess<0><<<nb, kPreThreads, 0, s>>>(*vt, *g, rec, radii, depth, ka, va); break;
+      case 1: k_preprocess<1><<<nb, kPreThreads, 0, s>>>(*vt, *g, rec, radii, depth, ka, va); break;
+      case 2: k_preprocess<2><<<nb, kPreThreads, 0, s>>>(*vt, *g, rec, radii, depth, ka, va); break;
+      default: k_preprocess<3><<<nb, kPreThreads, 0, s>>>(*vt, *g, rec, radii, depth, ka, va); break;
     }
   }
   note_launches(1);
