@@ -99,6 +99,24 @@ def test_mask_bits_match_oracle(k, kind, fx, fy):
     assert np.all(np.abs(margin[bad]) < 1e-12), (bad[:10], margin[bad[:10]])
 
 
+@pytest.mark.parametrize("k,kind,fx,fy", [(6, 0, 360, 360), (9, 2, 190, 190), (8, 1, 90, 90), (9, 1, 60, 100),
+                                          (7, 2, 220, 180), (10, 2, 180, 180), (4, 2, 200, 200), (9, 1, 120, 100)])
+def test_forward_mask_equals_per_pixel_mask(k, kind, fx, fy):
+    # the forward builds the mask by 16-pixel sub-tiles (whole sub-tiles decided at their centre
+    # when the margin bound allows); it must equal the per-pixel mask of hpxgs_mask_build bit for bit
+    import numpy as np
+    from tests.gpu_util import scene_tensors
+    view = S.make_view(k, kind, fx, fy)
+    rast = R.Rasterizer(tile_level=min(4, k))
+    cv = L.make_views([view])
+    words = torch.empty(12 * 4 ** k // 32, dtype=torch.int32, device="cuda")
+    L.check(L.lib().hpxgs_mask_build(cv, ctypes.byref(rast.cfg), _p(words), _s()), "mask")
+    sc = S.make_scene(500, 0, seed=7)
+    out, _ = rast.forward_raw(*scene_tensors(sc), 0, [view])
+    torch.cuda.synchronize()
+    assert torch.equal(out["mask"], words)
+
+
 @pytest.mark.parametrize("k,b", [(6, 3), (9, 4), (11, 4), (10, 5)])
 def test_tile_rho_matches_oracle(k, b):
     rho = ctypes.c_double()
