@@ -91,7 +91,11 @@ typedef struct {
   int32_t tile_level;      /* b: tiles are NESTED blocks of 4^b pixels (B = 2^b); 3..5, default 4 */
   float eps_T;             /* early termination T < eps_T (Algorithm 1), default 1e-4 */
   float alpha_max;         /* alpha clamp, default 0.99 */
-  float cutoff_m;          /* alpha = 0 where d^T conic d > cutoff_m (3-sigma ellipse), default 9 */
+  float cutoff_m;          /* alpha = 0 where d^T conic d > cutoff_m (3-sigma ellipse), default 9.
+                            * INFINITY gives the literal tile semantics of the paper's ablation
+                            * (Sec. 3.3): every listed Gaussian contributes at every pixel of its
+                            * listed tiles (the lists keep their 3-sigma radius r_s), so the image
+                            * depends on the tile query. */
   float blur_rad2;         /* isotropic term added to Sigma_arc; < 0 selects 0.3 * Omega_pix (default) */
   float near_plane;        /* Gaussians with radial depth r <= near_plane are culled, default 0.2 */
   float bg[3];             /* background seen through T_final, default 0 */

@@ -44,11 +44,13 @@ def quat_rot(q):
         torch.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], -2)
 
 
-def render_dense(params, view, cfg, pix, nside, with_depth=False):
+def render_dense(params, view, cfg, pix, nside, with_depth=False, members=None):
     """params: dict of float64 tensors (means, scales, rotations, opacities, sh (P,K,3)).
 
     Returns (colours at pix (n, 3), final transmittance (n,)) and, with with_depth, the
-    composited inverse radial depth (n,) (Sec. 3.2: depth supervision by 1/r)."""
+    composited inverse radial depth (n,) (Sec. 3.2: depth supervision by 1/r).
+    members (optional, (n, P) bool): Gaussian i may contribute to pixel n only where set
+    (the tile lists of the literal semantics, where the cutoff no longer decides)."""
     W = torch.as_tensor(np.asarray(view["W"], np.float64))
     b = torch.as_tensor(np.asarray(view["b"], np.float64))
     mu, s, q, o, sh = (params[k] for k in ("means", "scales", "rotations", "opacities", "sh"))
@@ -85,7 +87,10 @@ def render_dense(params, view, cfg, pix, nside, with_depth=False):
     dx, dy = fac * u1, fac * u2
     m = Q[None, :, 0, 0] * dx * dx + 2 * Q[None, :, 0, 1] * dx * dy + Q[None, :, 1, 1] * dy * dy
     a = torch.clamp(o[None, :] * torch.exp(-0.5 * m), max=cfg.alpha_max)
-    a = torch.where((m <= cfg.cutoff) & valid[None, :], a, torch.zeros_like(a))
+    keep = (m <= cfg.cutoff) & valid[None, :]
+    if members is not None:
+        keep = keep & torch.as_tensor(members)
+    a = torch.where(keep, a, torch.zeros_like(a))
     # global order by (float32 depth bits, index)
     key = O.depth_bits(r.detach().numpy()).astype(np.int64)
     key[~valid.numpy()] = np.iinfo(np.int64).max

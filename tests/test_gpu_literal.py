@@ -1,0 +1,126 @@
+"""GPU parity of the paper's literal tile semantics (Sec. 3.3 ablation) against the FP64 oracle.
+
+Every Gaussian listed for a tile contributes at every pixel of the tile, with no
+m <= 9 cutoff (config cutoff_m = infinity; the lists keep their 3-sigma radius,
+and the blend cull, whose bound grows with the cutoff, skips nothing). The image
+then depends on the tile query:
+
+- maps, T and last composited by the oracle from the GPU's FP32 records over the
+  GPU's own lists (RING at tile levels 4 and 5 split, NESTED x1 and x2): within 2e-4;
+- RING end to end against the oracle's FP64 render with an infinite cutoff;
+- gradients of a map loss within 1e-3 relative (RING);
+- RING and NESTED images differ under the literal semantics (they are equal under the
+  cutoff semantics, tests/test_gpu_nested_query.py).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2606_29794_b300 import _lib as L
+from paper_2606_29794_b300 import raster as R
+from paper_2606_29794_b300 import synth as S
+from tests.gpu_util import mask_from_words, oracle_cfg, scene_tensors
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
+
+TOL = 2e-4
+
+
+def _f64view(v):
+    return dict(v, W=np.asarray(v["W"], np.float64), b=np.asarray(v["b"], np.float64))
+
+
+def _scene_view():
+    return S.make_scene(2500, 3, seed=71), S.make_view(7, S.CAM_FISHEYE, 190.0)
+
+
+def _gpu_records(rast, state, P):
+    wv = R.workspace_view(rast, state)
+    rec = R.device_array(wv.records, P * 16, torch.float32).view(P, 16).cpu().numpy().astype(np.float64)
+    depth = R.device_array(wv.depth, P, torch.float32).cpu().numpy().astype(np.float64)
+    radii = R.device_array(wv.radii, P, torch.float32).cpu().numpy()
+    return rec, depth, radii
+
+
+@pytest.mark.parametrize("name,kw", [("ring_b4", dict(tile_level=4)), ("ring_b5_split", dict(tile_level=5)),
+                                     ("nested_x1", dict(tile_level=4, query=L.QUERY_NESTED, query_log2f=0)),
+                                     ("nested_x2", dict(tile_level=4, query=L.QUERY_NESTED, query_log2f=1))],
+                         ids=lambda x: x if isinstance(x, str) else "")
+def test_literal_staged_parity(name, kw):
+    sc, view = _scene_view()
+    k = view["nside_log2"]
+    b = kw["tile_level"]
+    P = sc["means"].shape[0]
+    rast = R.Rasterizer(cutoff=math.inf, **kw)
+    cfg = oracle_cfg(rast)
+    assert math.isinf(cfg.cutoff)
+    out, state = rast.forward_raw(*scene_tensors(sc), sc["sh_degree"], [view])
+    torch.cuda.synchronize()
+    m_gpu = mask_from_words(out["mask"].cpu().numpy().view(np.uint32), O.npix(2 ** k))
+    pix = np.nonzero(m_gpu)[0].astype(np.int64)
+    rec, depth, radii = _gpu_records(rast, state, P)
+    valid = radii > 0
+    dbits = depth.astype(np.float32).view(np.uint32).copy()
+    dbits[~valid] = 0xFFFFFFFF
+    act = O.active_tiles(k, b, m_gpu)
+    if kw.get("query", 0) == L.QUERY_NESTED:
+        st, ids = O.tile_lists_nested(k, b, kw["query_log2f"], rec[:, 0:3], radii.astype(np.float64),
+                                      valid.astype(np.int32), dbits, act)
+    else:
+        st, ids = O.tile_lists(k, b, rec[:, 0:3], radii.astype(np.float64), valid.astype(np.int32), dbits,
+                               O.tile_rho(k, b), act)
+    pre_g = dict(omega=np.arctan2(rec[:, 1], rec[:, 0]), phi=np.arctan2(rec[:, 2], np.hypot(rec[:, 0], rec[:, 1])),
+                 conic=rec[:, [7, 11, 15]], col=rec[:, 12:15], r=depth)
+    img, T, last, amb = O.composite(k, b, pre_g, rec[:, 3], st, ids, pix, cfg)
+    ok = amb == 0
+    assert ok.mean() > 0.99
+    maps = out["maps"].cpu().numpy().astype(np.float64)
+    assert np.abs(maps[pix] - img)[ok].max() < TOL
+    assert np.abs(out["T"].cpu().numpy()[pix] - T)[ok].max() < TOL
+    gl = out["last"].cpu().numpy().astype(np.int64)[pix]
+    assert (gl[ok] == last[ok]).mean() > 0.99
+
+
+def test_literal_end_to_end_and_gradients():
+    sc, view = _scene_view()
+    k = view["nside_log2"]
+    rast = R.Rasterizer(tile_level=4, cutoff=math.inf)
+    cfg = oracle_cfg(rast)
+    ts = scene_tensors(sc)
+    out, _ = rast.forward_raw(*ts, sc["sh_degree"], [view])
+    torch.cuda.synchronize()
+    m_gpu = mask_from_words(out["mask"].cpu().numpy().view(np.uint32), O.npix(2 ** k))
+    pix = np.nonzero(m_gpu)[0].astype(np.int64)
+    full = O.render(sc, _f64view(view), cfg)
+    ok = full.amb[pix] == 0
+    assert ok.mean() > 0.99
+    assert np.abs(out["maps"].cpu().numpy()[pix] - full.image[pix])[ok].max() < TOL
+    rng = np.random.default_rng(5)
+    dI = rng.standard_normal((pix.size, 3)) * ok[:, None]
+    ps = [t.clone().requires_grad_(True) for t in ts]
+    maps, *_ = R.render(*ps, [view], rasterizer=R.Rasterizer(tile_level=4, cutoff=math.inf), sh_degree=sc["sh_degree"])
+    gI = np.zeros((O.npix(2 ** k), 3), np.float32)
+    gI[pix] = dI
+    (maps * torch.as_tensor(gI, device="cuda")).sum().backward()
+    ref = O.backward(sc, _f64view(view), cfg, dI, full.start, full.ids, pix)
+    for t, nm in zip(ps, ["means", "scales", "rotations", "opacities", "sh"]):
+        g = t.grad.cpu().numpy().astype(np.float64).reshape(ref[nm].shape)
+        r = ref[nm]
+        assert np.linalg.norm(g - r) <= 1e-3 * np.linalg.norm(r), nm
+        assert np.abs(g - r).max() <= 1e-3 * np.abs(r).max() + 1e-12, nm
+
+
+def test_literal_image_depends_on_query():
+    sc, view = _scene_view()
+    ts = scene_tensors(sc)
+    outs = {}
+    for cut in (9.0, math.inf):
+        for q, f in ((L.QUERY_RING, 2), (L.QUERY_NESTED, 1)):
+            out, _ = R.Rasterizer(tile_level=4, cutoff=cut, query=q, query_log2f=f).forward_raw(*ts, 3, [view])
+            outs[(cut, q)] = out["maps"]
+    torch.cuda.synchronize()
+    assert torch.equal(outs[(9.0, L.QUERY_RING)], outs[(9.0, L.QUERY_NESTED)])
+    assert float((outs[(math.inf, L.QUERY_RING)] - outs[(math.inf, L.QUERY_NESTED)]).abs().max()) > 1e-5
