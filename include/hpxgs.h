@@ -226,6 +226,29 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
                    float* dmeans, float* dscales, float* drotations, float* dopacities, float* dsh,
                    int32_t* status, hpxgs_stream_t stream);
 
+/* Radian-space density-control statistics (Sec. 4.2), after hpxgs_backward on the same
+ * workspace (same g->P, views, cfg, capacity). For every (view, Gaussian) the Gaussian is
+ * visible in (listed for at least one active tile of the view), updates the caller's
+ * per-Gaussian buffers [P] in place:
+ *   rs_max[i]      <- max(rs_max[i], r_s)                       (angular radius, rad)
+ *   grad_accum[i]  += |(dL/domega, dL/dphi)|                     (rad^-1 units of the loss)
+ *   vis_count[i]   += 1
+ * dL/domega, dL/dphi: the gradient of the loss with respect to the centre's longitude and
+ * latitude through the pixel offsets, with the conic held in the local (east, north) frame
+ * (the radian-space counterpart of the screen-space mean gradient; a reading: the paper
+ * does not spell out the angular gradient). From the backward's partials: dL/dphi is the
+ * north partial; dL/domega = cos(phi) (east partial) + sin(phi) (2 b (L_c - L_a) + (a - c) L_b),
+ * the second term the turn of the local frame against the transported one. angular (may
+ * be NULL) receives (dL/domega, dL/dphi) per (view, Gaussian), [nviews * P, 2], 0 where
+ * not visible. rs_max entries must be non-negative (zero-initialised by the caller: the
+ * maximum compares float bit patterns). All buffers device memory; asynchronous on the
+ * stream. Errors: HPXGS_E_INVALID_ARG for null buffers, HPXGS_E_WORKSPACE for a workspace
+ * smaller than the layout. */
+int hpxgs_density_stats(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+                        const void* workspace, size_t workspace_bytes, int64_t capacity_pairs,
+                        float* rs_max, float* grad_accum, uint32_t* vis_count, float* angular,
+                        hpxgs_stream_t stream);
+
 /* Steps 1-3 of hpxgs_forward without emission: writes the total number of
  * (Gaussian, tile) pairs the views need to *count (device uint64). Used to
  * size capacity and for memory-based admission. */

@@ -362,9 +362,11 @@ def render(scene, view, cfg: Config, pix=None, rho=None):
     return Render(image, T, last, amb, m, act, pre, start, ids, rho, pix)
 
 
-def backward(scene, view, cfg: Config, dLdI, start, ids, pix, dLdD=None):
+def backward(scene, view, cfg: Config, dLdI, start, ids, pix, dLdD=None, angular=False):
     """Sec. 3.2 backward for one view: dL/dI at `pix` (n, 3) and optionally dL/dD of the
-    inverse-depth channel at `pix` (n,) -> parameter gradients."""
+    inverse-depth channel at `pix` (n,) -> parameter gradients. With angular=True, out["angular"]
+    (P, 2) holds dL/domega and dL/dphi of each centre through the pixel offsets with the conic held
+    in the local (east, north) frame: the statistic of radian-space density control (Sec. 4.2)."""
     mu, s, q, o, sh, deg, P = _scene64(scene)
     k = view["nside_log2"]; b = cfg.tile_level
     nside = 1 << k
@@ -375,6 +377,8 @@ def backward(scene, view, cfg: Config, dLdI, start, ids, pix, dLdD=None):
     K = (deg + 1) ** 2
     out = dict(means=np.empty((P, 3)), scales=np.empty((P, 3)), rotations=np.empty((P, 4)),
                opacities=np.empty(P), sh=np.empty((P, K, 3)))
+    if angular:
+        out["angular"] = np.empty((P, 2))
     bg = np.asarray(cfg.bg, np.float64)
     lib().or_backward(ctypes.c_int(k), ctypes.c_int(b), _i64(P), _p(mu), _p(s), _p(q), _p(o), _p(sh),
                       ctypes.c_int(deg), _p(W), _p(bv), _f64(cfg.near), _f64(cfg.blur_for(nside)),
@@ -382,8 +386,18 @@ def backward(scene, view, cfg: Config, dLdI, start, ids, pix, dLdD=None):
                       _p(np.ascontiguousarray(start, np.int64)), _p(np.ascontiguousarray(ids, np.int64)),
                       _i64(pix.size), _p(pix), _p(dLdI), _p(out["means"]), _p(out["scales"]),
                       _p(out["rotations"]), _p(out["opacities"]), _p(out["sh"]),
-                      _p(None if dLdD is None else np.ascontiguousarray(dLdD, np.float64).ravel()))
+                      _p(None if dLdD is None else np.ascontiguousarray(dLdD, np.float64).ravel()),
+                      _p(out["angular"]) if angular else None)
     return out
+
+
+def density_stats_update(rs_max, grad_acc, count, rs, angular, valid):
+    """Radian-space density statistics of one view (Sec. 4.2), updated in place for the visible
+    Gaussians: r_s,max <- max(r_s,max, r_s); grad_acc += |(dL/domega, dL/dphi)|; count += 1."""
+    v = np.asarray(valid).astype(bool)
+    rs_max[v] = np.maximum(rs_max[v], np.asarray(rs)[v])
+    grad_acc[v] += np.hypot(angular[v, 0], angular[v, 1])
+    count[v] += 1
 
 
 # ---------------------------------------------------------------------------

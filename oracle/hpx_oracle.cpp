@@ -1208,7 +1208,7 @@ void or_backward(int k, int b, i64 P, const double* means, const double* scales,
                  double near, double blur, double eps_T, double alpha_max, double cutoff,
                  const double* bg, const i64* start, const i64* ids, i64 npix_q, const i64* pix,
                  const double* dLdI, double* dmeans, double* dscales, double* drots, double* dopac,
-                 double* dsh, const double* dLdD) {
+                 double* dsh, const double* dLdD, double* dang) {
   Cfg cfg{}; cfg.near = near; cfg.blur = blur; cfg.eps_T = eps_T; cfg.alpha_max = alpha_max;
   cfg.cutoff = cutoff; for (int c = 0; c < 3; ++c) cfg.bg[c] = bg[c];
   int K = (deg + 1) * (deg + 1);
@@ -1294,9 +1294,13 @@ void or_backward(int k, int b, i64 P, const double* means, const double* scales,
     for (int c = 0; c < 4; ++c) dq[c] = 0;
     for (int c = 0; c < K * 3; ++c) dshi[c] = 0;
     dopac[i] = 0;
+    if (dang) { dang[2 * i] = 0; dang[2 * i + 1] = 0; }
     const Pre& o = pre[i];
     if (!o.valid) continue;
     const double* Ai = tot.data() + i * NA;
+    // the angular gradient of density control (Sec. 4.2, radian-space density control; reading): dL/domega
+    // and dL/dphi of the centre through the pixel offsets, the conic held in the local (east, north) frame
+    if (dang) { dang[2 * i] = Ai[7]; dang[2 * i + 1] = Ai[8]; }
     // colour -> SH (clamped channels give no gradient)
     double dcr[3];
     for (int c = 0; c < 3; ++c) dcr[c] = o.craw[c] > 0 ? Ai[c] : 0.0;

@@ -91,6 +91,8 @@ _SIGS = {
     "hpxgs_backward": (ctypes.c_int, [_P(Gaussians), _P(View), ctypes.c_int, _P(Config), _vp, _sz, _i64, _vp, _vp,
                                       _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hpxgs_count_pairs": (ctypes.c_int, [_P(Gaussians), _P(View), ctypes.c_int, _P(Config), _vp, _sz, _vp, _vp, _vp]),
+    "hpxgs_density_stats": (ctypes.c_int, [_i32, _P(View), ctypes.c_int, _P(Config), _vp, _sz, _i64, _vp, _vp, _vp,
+                                           _vp, _vp]),
     "hpxgs_workspace_inspect": (ctypes.c_int, [_i32, _P(View), ctypes.c_int, _P(Config), _i64, _vp,
                                                _P(WorkspaceView)]),
     "hpxgs_profile_arm": (ctypes.c_int, [ctypes.c_int, _vp, _vp]),

@@ -1499,6 +1499,45 @@ __global__ void __launch_bounds__(kPreBwdThreads, HPXGS_PREBWD_MINB) k_preproces
 }
 
 // ----------------------------------------------------------------------------
+// Radian-space density statistics (Sec. 4.2): one thread per (view, Gaussian).
+// The blend backward's partials hold dL/d(east, north displacement) with the conic
+// held in the parallel-transported frame (accum 7, 8) and dL/d(conic a, b, c)
+// (accum 4-6). Moving the centre east by d omega turns the local (east, north)
+// frame against the transported one by sin(phi) d omega, so with the conic held in
+// the local frame dL/domega = cos(phi) L_E + sin(phi) (2 b (L_c - L_a) + (a - c) L_b)
+// and dL/dphi = L_N.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_density_stats(int64_t PV, int P, const uint32_t* __restrict__ skeys,
+                                                       const uint32_t* __restrict__ svals, const uint32_t* __restrict__ counts,
+                                                       const float4* __restrict__ rec,
+                                                       const float* __restrict__ radii, const float* __restrict__ accum,
+                                                       float* __restrict__ rs_max, float* __restrict__ grad_accum,
+                                                       uint32_t* __restrict__ vis_count, float* __restrict__ angular) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // depth-sorted position
+  if (j >= PV) return;
+  const uint32_t gid = svals[j];
+  // visible: listed for at least one active tile of its view
+  const bool vis = skeys[j] != 0xffffffffu && counts[j] > 0u;
+  float dw = 0.f, dp = 0.f;
+  if (vis) {
+    const float rs = radii[gid];
+    const float4 r0 = rec[4 * (int64_t)gid], r1 = rec[4 * (int64_t)gid + 1], r2 = rec[4 * (int64_t)gid + 2],
+                 r3 = rec[4 * (int64_t)gid + 3];
+    const float* A = accum + (int64_t)gid * HPXGS_NACC;
+    const float a = r1.w, b = r2.w, c = r3.w;
+    const float sphi = r0.z, cphi = sqrtf(r0.x * r0.x + r0.y * r0.y);
+    const float La = 2.f * b * (A[6] - A[4]) + (a - c) * A[5];
+    dw = cphi * A[7] + sphi * La;
+    dp = A[8];
+    const uint32_t i = gid % (uint32_t)P;
+    atomicMax(reinterpret_cast<int*>(rs_max) + i, __float_as_int(rs));   // rs > 0: int order = float order
+    atomicAdd(grad_accum + i, sqrtf(dw * dw + dp * dp));
+    atomicAdd(vis_count + i, 1u);
+  }
+  if (angular) { angular[2 * (int64_t)gid] = dw; angular[2 * (int64_t)gid + 1] = dp; }
+}
+
+// ----------------------------------------------------------------------------
 // Host side
 // ----------------------------------------------------------------------------
 template <typename T>
@@ -1869,6 +1908,29 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_PREPROCESS_BWD, s);
   delete vt;
+  return HPXGS_OK;
+}
+
+int hpxgs_density_stats(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+                        const void* ws, size_t ws_bytes, int64_t cap, float* rs_max, float* grad_accum,
+                        uint32_t* vis_count, float* angular, hpxgs_stream_t stream) {
+  if (!ws || !rs_max || !grad_accum || !vis_count || P < 0) return HPXGS_E_INVALID_ARG;
+  Layout L;
+  int rc = make_layout(P, views, nviews, cfg, cap, &L);
+  if (rc != HPXGS_OK) return rc;
+  size_t need = 0;
+  hpxgs_forward_workspace_size(P, views, nviews, cfg, cap, &need);
+  if (ws_bytes < need) return HPXGS_E_WORKSPACE;
+  if (L.PV == 0) return HPXGS_OK;
+  void* w = const_cast<void*>(ws);
+  cudaStream_t s = (cudaStream_t)stream;
+  // the 32-bit depth sort takes an even number of passes: its result is in the first key/value buffers
+  k_density_stats<<<(unsigned)((L.PV + 255) / 256), 256, 0, s>>>(L.PV, P, at<uint32_t>(w, L.key_a), at<uint32_t>(w, L.val_a),
+                                                               at<uint32_t>(w, L.counts), at<float4>(w, L.records),
+                                                               at<float>(w, L.radii), at<float>(w, L.accum), rs_max,
+                                                               grad_accum, vis_count, angular);
+  note_launches(1);
+  HPXGS_LAUNCH_CHECK();
   return HPXGS_OK;
 }
 

@@ -153,6 +153,19 @@ class Rasterizer:
                                        ctypes.c_void_p(_stream())), "backward")
         return dm, ds, dq, do, dsh
 
+    def density_stats(self, state, rs_max, grad_accum, vis_count, angular=None):
+        """Radian-space density statistics (Sec. 4.2) after backward_raw on `state`: updates the
+        per-Gaussian buffers rs_max (float32 [P]), grad_accum (float32 [P]) and vis_count (int32 [P])
+        in place over the visible (view, Gaussian) pairs; angular (float32 [views, P, 2] or None)
+        receives dL/domega, dL/dphi per pair."""
+        for t in (rs_max, grad_accum, vis_count):
+            assert t.is_cuda and t.is_contiguous() and t.numel() == state["g"].P
+        L.check(L.lib().hpxgs_density_stats(state["g"].P, state["cviews"], state["nv"], ctypes.byref(self.cfg),
+                                            _ptr(state["ws"]), state["nb"], state["cap"], _ptr(rs_max),
+                                            _ptr(grad_accum), _ptr(vis_count),
+                                            _ptr(angular) if angular is not None else None,
+                                            ctypes.c_void_p(_stream())), "density_stats")
+
 
 class _RenderFn(torch.autograd.Function):
     @staticmethod
