@@ -54,7 +54,7 @@ typedef struct CUstream_st* hpxgs_stream_t; /* a cudaStream_t (0 = legacy defaul
 
 /* ---- cameras (Sec. 3.1, Sec. D.1) ---- */
 #define HPXGS_CAM_FULL 0     /* omnidirectional: every pixel is valid */
-#define HPXGS_CAM_PINHOLE 1  /* Eq. persp_sphere; valid iff d_z > 0, |d_x/d_z| <= tan(fov_x/2), |d_y/d_z| <= tan(fov_y/2) */
+#define HPXGS_CAM_PINHOLE 1  /* Eq. persp_sphere; valid iff -t_x (1 + ppx) <= d_x/d_z <= t_x (1 - ppx), likewise y, t = tan(fov/2) */
 #define HPXGS_CAM_FISHEYE 2  /* anisotropic equidistant, Eqs. fish_weff..semi_axes; valid iff psi <= (pi/2) w_eff(gamma), w = fov/180 deg */
 
 #define HPXGS_MAX_VIEWS 64
@@ -73,8 +73,14 @@ typedef struct {
 
 typedef struct {
   int32_t kind;            /* HPXGS_CAM_* */
-  float fov_x_deg;         /* full horizontal FoV, degrees */
+  float fov_x_deg;         /* full horizontal FoV, degrees (pinhole: of the centred frustum, 2 atan(W / 2 f_x)) */
   float fov_y_deg;         /* full vertical FoV, degrees */
+  /* Pinhole principal point (Eq. persp_sphere) as an offset from the image centre in
+   * half-image units: c_x = (W/2)(1 + ppx), c_y = (H/2)(1 + ppy), |ppx|, |ppy| < 1, so the
+   * frustum is asymmetric: d_x/d_z in [-tan(fov_x/2)(1 + ppx), tan(fov_x/2)(1 - ppx)].
+   * Must be 0 for the fisheye (the paper fixes its principal point at the centre) and
+   * the full sphere. Zero-initialised structs give the centred camera. */
+  float ppx, ppy;
 } hpxgs_camera;
 
 /* One view V = [W | b] (Sec. 3.2) rendered at HEALPix order nside_log2. */

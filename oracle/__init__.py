@@ -157,13 +157,15 @@ def neighbours_nest(nside, p):
 # Cameras (Sec. 3.1; Sec. D.1)
 # ---------------------------------------------------------------------------
 
-def mask(nside, kind, fov_x=360.0, fov_y=None):
-    """FoV mask M_C(p) over all NESTED pixels (uint8) and the FP64 decision margin."""
+def mask(nside, kind, fov_x=360.0, fov_y=None, pp=(0.0, 0.0)):
+    """FoV mask M_C(p) over all NESTED pixels (uint8) and the FP64 decision margin. pp: the
+    pinhole principal point's offset from the image centre in half-image units."""
     fov_y = fov_x if fov_y is None else fov_y
     n = npix(nside)
     m = np.empty(n, np.uint8)
     mg = np.empty(n, np.float64)
-    lib().or_mask(_i64(nside), ctypes.c_int(kind), _f64(fov_x), _f64(fov_y), _p(m), _p(mg))
+    lib().or_mask(_i64(nside), ctypes.c_int(kind), _f64(fov_x), _f64(fov_y), _f64(pp[0]), _f64(pp[1]), _p(m),
+                  _p(mg))
     return m, mg
 
 
@@ -347,7 +349,7 @@ def render(scene, view, cfg: Config, pix=None, rho=None):
     """Forward render of one view end to end in FP64 (Algorithm 1)."""
     k = view["nside_log2"]; b = cfg.tile_level
     nside = 1 << k
-    m, _ = mask(nside, view["cam"], view.get("fov_x", 360.0), view.get("fov_y"))
+    m, _ = mask(nside, view["cam"], view.get("fov_x", 360.0), view.get("fov_y"), view.get("pp", (0.0, 0.0)))
     act = active_tiles(k, b, m)
     pre = preprocess(scene, view, cfg)
     rho = tile_rho(k, b) if rho is None else rho
@@ -431,24 +433,31 @@ def hssim_local(nside, I, G, m, qs):
 # supp_hssim_mask; camera models of Sec. D.1)
 # ---------------------------------------------------------------------------
 
-def _cam_args(kind, W, H, fovx, fovy):
+def _cam_args(kind, W, H, fovx, fovy, pp=(0.0, 0.0)):
     fovy = fovx if fovy is None else fovy
-    return ctypes.c_int(kind), _f64(W), _f64(H), _f64(fovx), _f64(fovy)
+    return ctypes.c_int(kind), _f64(W), _f64(H), _f64(fovx), _f64(fovy), _f64(pp[0]), _f64(pp[1])
 
 
-def img_to_dir(kind, W, H, fovx, fovy, uv):
+def _fov_pp(fovx, fovy, pp):
+    return _f64(fovx), _f64(fovx if fovy is None else fovy), _f64(pp[0]), _f64(pp[1])
+
+
+# The camera arguments: kind, image size W x H, FoV in degrees and, for the pinhole, the
+# principal point's offset pp from the image centre in half-image units.
+
+def img_to_dir(kind, W, H, fovx, fovy, uv, pp=(0.0, 0.0)):
     """P_C: image points (n, 2) -> camera directions (n, 3) and validity (D_C)."""
     uv = np.ascontiguousarray(uv, np.float64).reshape(-1, 2)
     d = np.empty((uv.shape[0], 3)); ok = np.empty(uv.shape[0], np.uint8)
-    lib().or_img_to_dir(*_cam_args(kind, W, H, fovx, fovy), _i64(uv.shape[0]), _p(uv), _p(d), _p(ok))
+    lib().or_img_to_dir(*_cam_args(kind, W, H, fovx, fovy, pp), _i64(uv.shape[0]), _p(uv), _p(d), _p(ok))
     return d, ok
 
 
-def dir_to_img(kind, W, H, fovx, fovy, d):
+def dir_to_img(kind, W, H, fovx, fovy, d, pp=(0.0, 0.0)):
     """Pi_C^{-1}: camera directions (n, 3) -> image points (n, 2) and validity."""
     d = np.ascontiguousarray(d, np.float64).reshape(-1, 3)
     uv = np.empty((d.shape[0], 2)); ok = np.empty(d.shape[0], np.uint8)
-    lib().or_dir_to_img(*_cam_args(kind, W, H, fovx, fovy), _i64(d.shape[0]), _p(d), _p(uv), _p(ok))
+    lib().or_dir_to_img(*_cam_args(kind, W, H, fovx, fovy, pp), _i64(d.shape[0]), _p(d), _p(uv), _p(ok))
     return uv, ok
 
 
@@ -461,49 +470,49 @@ def interp_weights(nside, theta, phi):
     return pix, w
 
 
-def sphere_to_image(nside, hmap, kind, W, H, fovx=360.0, fovy=None):
+def sphere_to_image(nside, hmap, kind, W, H, fovx=360.0, fovy=None, pp=(0.0, 0.0)):
     """Camera image (H, W, 3) from a HEALPix map (Npix, 3) in the camera frame, and validity (H, W)."""
     hmap = np.ascontiguousarray(hmap, np.float64).reshape(-1, 3)
     img = np.empty((H, W, 3)); ok = np.empty((H, W), np.uint8)
-    lib().or_sphere_to_image(_i64(nside), _p(hmap), ctypes.c_int(kind), _i64(W), _i64(H), _f64(fovx),
-                             _f64(fovx if fovy is None else fovy), _p(img), _p(ok))
+    lib().or_sphere_to_image(_i64(nside), _p(hmap), ctypes.c_int(kind), _i64(W), _i64(H),
+                             *_fov_pp(fovx, fovy, pp), _p(img), _p(ok))
     return img, ok
 
 
-def sphere_to_image_adjoint(nside, dimg, kind, W, H, fovx=360.0, fovy=None):
+def sphere_to_image_adjoint(nside, dimg, kind, W, H, fovx=360.0, fovy=None, pp=(0.0, 0.0)):
     dimg = np.ascontiguousarray(dimg, np.float64).reshape(H, W, 3)
     dmap = np.empty((12 * nside * nside, 3))
-    lib().or_sphere_to_image_adjoint(_i64(nside), _p(dimg), ctypes.c_int(kind), _i64(W), _i64(H), _f64(fovx),
-                                     _f64(fovx if fovy is None else fovy), _p(dmap))
+    lib().or_sphere_to_image_adjoint(_i64(nside), _p(dimg), ctypes.c_int(kind), _i64(W), _i64(H),
+                                     *_fov_pp(fovx, fovy, pp), _p(dmap))
     return dmap
 
 
-def image_to_sphere(nside, img, kind, W, H, fovx=360.0, fovy=None):
+def image_to_sphere(nside, img, kind, W, H, fovx=360.0, fovy=None, pp=(0.0, 0.0)):
     """HEALPix map (Npix, 3) and mask M_C from a camera image (H, W, 3)."""
     img = np.ascontiguousarray(img, np.float64).reshape(H, W, 3)
     hmap = np.empty((12 * nside * nside, 3)); m = np.empty(12 * nside * nside, np.uint8)
-    lib().or_image_to_sphere(_i64(nside), _p(img), ctypes.c_int(kind), _i64(W), _i64(H), _f64(fovx),
-                             _f64(fovx if fovy is None else fovy), _p(hmap), _p(m))
+    lib().or_image_to_sphere(_i64(nside), _p(img), ctypes.c_int(kind), _i64(W), _i64(H),
+                             *_fov_pp(fovx, fovy, pp), _p(hmap), _p(m))
     return hmap, m
 
 
-def sphere_to_image_at(nside, hmap, kind, W, H, fovx, fovy, uv):
+def sphere_to_image_at(nside, hmap, kind, W, H, fovx, fovy, uv, pp=(0.0, 0.0)):
     """sphere_to_image at image points uv (n, 2) only: values (n, 3) and validity."""
     hmap = np.ascontiguousarray(hmap, np.float64).reshape(-1, 3)
     uv = np.ascontiguousarray(uv, np.float64).reshape(-1, 2)
     out = np.empty((uv.shape[0], 3)); ok = np.empty(uv.shape[0], np.uint8)
-    lib().or_sphere_to_image_at(_i64(nside), _p(hmap), ctypes.c_int(kind), _i64(W), _i64(H), _f64(fovx),
-                                _f64(fovx if fovy is None else fovy), _i64(uv.shape[0]), _p(uv), _p(out), _p(ok))
+    lib().or_sphere_to_image_at(_i64(nside), _p(hmap), ctypes.c_int(kind), _i64(W), _i64(H),
+                                *_fov_pp(fovx, fovy, pp), _i64(uv.shape[0]), _p(uv), _p(out), _p(ok))
     return out, ok
 
 
-def image_to_sphere_at(nside, img, kind, W, H, fovx, fovy, qs):
+def image_to_sphere_at(nside, img, kind, W, H, fovx, fovy, qs, pp=(0.0, 0.0)):
     """image_to_sphere at NESTED pixels qs only: values (n, 3) and M_C."""
     img = np.ascontiguousarray(img, np.float64).reshape(H, W, 3)
     qs = np.ascontiguousarray(qs, np.int64)
     out = np.empty((qs.size, 3)); m = np.empty(qs.size, np.uint8)
-    lib().or_image_to_sphere_at(_i64(nside), _p(img), ctypes.c_int(kind), _i64(W), _i64(H), _f64(fovx),
-                                _f64(fovx if fovy is None else fovy), _i64(qs.size), _p(qs), _p(out), _p(m))
+    lib().or_image_to_sphere_at(_i64(nside), _p(img), ctypes.c_int(kind), _i64(W), _i64(H),
+                                *_fov_pp(fovx, fovy, pp), _i64(qs.size), _p(qs), _p(out), _p(m))
     return out, m
 
 

@@ -263,16 +263,22 @@ static int neighbours_nest(i64 nside, i64 p, i64 out[8]) {
 enum { CAM_FULL = 0, CAM_PINHOLE = 1, CAM_FISHEYE = 2 };
 
 // Signed margin of direction d (camera frame) against the camera's valid region:
-// >= 0 inside. Pinhole: d_z > 0 and |d_x/d_z| <= tan(FoV_x/2), |d_y/d_z| <= tan(FoV_y/2)
-// (Eq. persp_sphere with the image domain [0,W) x [0,H)). Fisheye: incident angle
+// >= 0 inside. Pinhole (Eq. persp_sphere): d_z > 0 and the image point
+// u = c_x + f_x d_x/d_z, v = c_y + f_y d_y/d_z inside [0,W] x [0,H], with
+// f_x = W / (2 tan(FoV_x/2)) and the principal point c_x = (W/2)(1 + ppx),
+// c_y = (H/2)(1 + ppy); in units of d_z: min(d_x - lo_x d_z, hi_x d_z - d_x, ...)
+// with lo_x = -c_x / f_x, hi_x = (W - c_x) / f_x. Fisheye: incident angle
 // psi <= (pi/2) w_eff(gamma) (Eqs. fish_weff, imaging_region, semi_axes).
-static double camera_margin(int kind, double fovx_deg, double fovy_deg, const double d[3]) {
+static double camera_margin(int kind, double fovx_deg, double fovy_deg, double ppx, double ppy, const double d[3]) {
   if (kind == CAM_FULL) return 1.0;
   if (kind == CAM_PINHOLE) {
     double tx = std::tan(0.5 * fovx_deg * kPi / 180.0), ty = std::tan(0.5 * fovy_deg * kPi / 180.0);
     if (d[2] <= 0) return -1.0;
-    double mx = tx * d[2] - std::fabs(d[0]);
-    double my = ty * d[2] - std::fabs(d[1]);
+    // c_x / f_x = tan(FoV_x/2)(1 + ppx), (W - c_x) / f_x = tan(FoV_x/2)(1 - ppx)
+    double lox = -tx * (1.0 + ppx), hix = tx * (1.0 - ppx);
+    double loy = -ty * (1.0 + ppy), hiy = ty * (1.0 - ppy);
+    double mx = std::min(d[0] - lox * d[2], hix * d[2] - d[0]);
+    double my = std::min(d[1] - loy * d[2], hiy * d[2] - d[1]);
     return std::min(mx, my);
   }
   double wx = fovx_deg / 180.0, wy = fovy_deg / 180.0;
@@ -856,14 +862,14 @@ static void query_disc_nested(int k, int kmax, const double g[3], double rs, std
 // The HEALPix map lives in the camera frame: HEALPix (X, Y, Z) = (d_z, d_x, d_y).
 // ===========================================================================
 
-struct ImgCam { int kind; double W, H, fovx, fovy; };
+struct ImgCam { int kind; double W, H, fovx, fovy, ppx, ppy; };   // pp: pinhole principal point offset
 
 // P_C: image point (u, v) -> unit camera direction d; false outside D_C.
 static bool img_to_dir(const ImgCam& c, double u, double v, double d[3]) {
   if (c.kind == CAM_PINHOLE) {
     double fx = c.W / (2.0 * std::tan(0.5 * c.fovx * kPi / 180.0));
     double fy = c.H / (2.0 * std::tan(0.5 * c.fovy * kPi / 180.0));
-    double x = (u - 0.5 * c.W) / fx, y = (v - 0.5 * c.H) / fy;
+    double x = (u - 0.5 * c.W * (1.0 + c.ppx)) / fx, y = (v - 0.5 * c.H * (1.0 + c.ppy)) / fy;
     double n = std::sqrt(x * x + y * y + 1.0);
     d[0] = x / n; d[1] = y / n; d[2] = 1.0 / n;
     return u >= 0 && u <= c.W && v >= 0 && v <= c.H;
@@ -889,14 +895,14 @@ static bool img_to_dir(const ImgCam& c, double u, double v, double d[3]) {
 // same test as the FoV mask, so the resampled mask is M_C itself).
 static bool dir_to_img(const ImgCam& c, const double d[3], double& u, double& v) {
   if (c.kind == CAM_PINHOLE) {
-    if (camera_margin(c.kind, c.fovx, c.fovy, d) < 0) return false;
+    if (camera_margin(c.kind, c.fovx, c.fovy, c.ppx, c.ppy, d) < 0) return false;
     double fx = c.W / (2.0 * std::tan(0.5 * c.fovx * kPi / 180.0));
     double fy = c.H / (2.0 * std::tan(0.5 * c.fovy * kPi / 180.0));
-    u = 0.5 * c.W + fx * d[0] / d[2]; v = 0.5 * c.H + fy * d[1] / d[2];
+    u = 0.5 * c.W * (1.0 + c.ppx) + fx * d[0] / d[2]; v = 0.5 * c.H * (1.0 + c.ppy) + fy * d[1] / d[2];
     return true;
   }
   if (c.kind == CAM_FISHEYE) {
-    if (camera_margin(c.kind, c.fovx, c.fovy, d) < 0) return false;
+    if (camera_margin(c.kind, c.fovx, c.fovy, 0.0, 0.0, d) < 0) return false;
     double psi = std::atan2(std::sqrt(d[0] * d[0] + d[1] * d[1]), d[2]);
     double gam = std::atan2(d[1], d[0]);
     double wx = c.fovx / 180.0, wy = c.fovy / 180.0;
@@ -1035,13 +1041,13 @@ void or_neighbours_nest(i64 nside, i64 n, const i64* p, i64* out, int* cnt) {
 }
 
 // FoV mask M_C(p) = 1[(omega_p, phi_p) in R_C] and its signed margin.
-void or_mask(i64 nside, int kind, double fovx, double fovy, u8* mask, double* margin) {
+void or_mask(i64 nside, int kind, double fovx, double fovy, double ppx, double ppy, u8* mask, double* margin) {
   i64 npix = 12 * nside * nside;
 #pragma omp parallel for schedule(static)
   for (i64 p = 0; p < npix; ++p) {
     double v[3]; pix2vec_nest(nside, p, v);
     double d[3] = {v[1], v[2], v[0]};   // camera direction from the HEALPix vector
-    double mg = camera_margin(kind, fovx, fovy, d);
+    double mg = camera_margin(kind, fovx, fovy, ppx, ppy, d);
     mask[p] = mg >= 0 ? 1 : 0;
     if (margin) margin[p] = mg;
   }
@@ -1462,16 +1468,18 @@ int or_num_threads() {
 
 
 // ---- resampling ----
-int or_img_to_dir(int kind, double W, double H, double fovx, double fovy, i64 n, const double* uv, double* dir,
+int or_img_to_dir(int kind, double W, double H, double fovx, double fovy,
+                  double ppx, double ppy, i64 n, const double* uv, double* dir,
                   u8* valid) {
-  ImgCam c{kind, W, H, fovx, fovy};
+  ImgCam c{kind, W, H, fovx, fovy, ppx, ppy};
   for (i64 q = 0; q < n; ++q) valid[q] = img_to_dir(c, uv[2 * q], uv[2 * q + 1], dir + 3 * q);
   return 0;
 }
 
-int or_dir_to_img(int kind, double W, double H, double fovx, double fovy, i64 n, const double* dir, double* uv,
+int or_dir_to_img(int kind, double W, double H, double fovx, double fovy,
+                  double ppx, double ppy, i64 n, const double* dir, double* uv,
                   u8* valid) {
-  ImgCam c{kind, W, H, fovx, fovy};
+  ImgCam c{kind, W, H, fovx, fovy, ppx, ppy};
   for (i64 q = 0; q < n; ++q) valid[q] = dir_to_img(c, dir + 3 * q, uv[2 * q], uv[2 * q + 1]);
   return 0;
 }
@@ -1483,8 +1491,9 @@ void or_interp_weights(i64 nside, i64 n, const double* theta, const double* phi,
 
 // I_C(u, v) = Interp_H(I_H, P_C(u, v)) at every pixel centre; 0 and valid = 0 outside D_C.
 void or_sphere_to_image(i64 nside, const double* map, int kind, i64 W, i64 H, double fovx, double fovy,
+                        double ppx, double ppy,
                         double* img, u8* valid) {
-  ImgCam c{kind, (double)W, (double)H, fovx, fovy};
+  ImgCam c{kind, (double)W, (double)H, fovx, fovy, ppx, ppy};
 #pragma omp parallel for schedule(static)
   for (i64 p = 0; p < W * H; ++p) {
     const i64 row = p / W, col = p % W;
@@ -1502,8 +1511,9 @@ void or_sphere_to_image(i64 nside, const double* map, int kind, i64 W, i64 H, do
 
 // The adjoint of or_sphere_to_image: dmap = A^T dimg (overwrites dmap).
 void or_sphere_to_image_adjoint(i64 nside, const double* dimg, int kind, i64 W, i64 H, double fovx, double fovy,
+                                double ppx, double ppy,
                                 double* dmap) {
-  ImgCam c{kind, (double)W, (double)H, fovx, fovy};
+  ImgCam c{kind, (double)W, (double)H, fovx, fovy, ppx, ppy};
   std::fill(dmap, dmap + 3 * 12 * nside * nside, 0.0);
   for (i64 p = 0; p < W * H; ++p) {
     const i64 row = p / W, col = p % W;
@@ -1518,9 +1528,10 @@ void or_sphere_to_image_adjoint(i64 nside, const double* dimg, int kind, i64 W, 
 }
 
 // or_sphere_to_image at the given image points only (for sampled checks of large images).
-void or_sphere_to_image_at(i64 nside, const double* map, int kind, i64 W, i64 H, double fovx, double fovy, i64 n,
+void or_sphere_to_image_at(i64 nside, const double* map, int kind, i64 W, i64 H, double fovx, double fovy,
+                           double ppx, double ppy, i64 n,
                            const double* uv, double* out, u8* valid) {
-  ImgCam c{kind, (double)W, (double)H, fovx, fovy};
+  ImgCam c{kind, (double)W, (double)H, fovx, fovy, ppx, ppy};
 #pragma omp parallel for schedule(static)
   for (i64 q = 0; q < n; ++q) {
     double d[3];
@@ -1536,9 +1547,10 @@ void or_sphere_to_image_at(i64 nside, const double* map, int kind, i64 W, i64 H,
 }
 
 // or_image_to_sphere at the given NESTED pixels only.
-void or_image_to_sphere_at(i64 nside, const double* img, int kind, i64 W, i64 H, double fovx, double fovy, i64 n,
+void or_image_to_sphere_at(i64 nside, const double* img, int kind, i64 W, i64 H, double fovx, double fovy,
+                           double ppx, double ppy, i64 n,
                            const i64* qs, double* out, u8* mask) {
-  ImgCam c{kind, (double)W, (double)H, fovx, fovy};
+  ImgCam c{kind, (double)W, (double)H, fovx, fovy, ppx, ppy};
 #pragma omp parallel for schedule(static)
   for (i64 t = 0; t < n; ++t) {
     double v[3]; pix2vec_nest(nside, qs[t], v);
@@ -1551,9 +1563,10 @@ void or_image_to_sphere_at(i64 nside, const double* img, int kind, i64 W, i64 H,
 }
 
 // I_H(q) = I_C(Pi_C^{-1}(s_q)) and M_C(q) for every NESTED pixel q; 0 where M_C(q) = 0.
-void or_image_to_sphere(i64 nside, const double* img, int kind, i64 W, i64 H, double fovx, double fovy, double* map,
+void or_image_to_sphere(i64 nside, const double* img, int kind, i64 W, i64 H, double fovx, double fovy,
+                        double ppx, double ppy, double* map,
                         u8* mask) {
-  ImgCam c{kind, (double)W, (double)H, fovx, fovy};
+  ImgCam c{kind, (double)W, (double)H, fovx, fovy, ppx, ppy};
 #pragma omp parallel for schedule(static)
   for (i64 q = 0; q < 12 * nside * nside; ++q) {
     double v[3]; pix2vec_nest(nside, q, v);

@@ -30,7 +30,8 @@ class Gaussians(ctypes.Structure):
 
 
 class Camera(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("fov_x_deg", ctypes.c_float), ("fov_y_deg", ctypes.c_float)]
+    _fields_ = [("kind", ctypes.c_int32), ("fov_x_deg", ctypes.c_float), ("fov_y_deg", ctypes.c_float),
+                ("ppx", ctypes.c_float), ("ppy", ctypes.c_float)]
 
 
 class View(ctypes.Structure):
@@ -171,4 +172,5 @@ def make_views(views) -> ctypes.Array:
         arr[i].cam.kind = int(v.get("cam", CAM_FULL))
         arr[i].cam.fov_x_deg = float(v.get("fov_x", 360.0))
         arr[i].cam.fov_y_deg = float(v.get("fov_y", v.get("fov_x", 360.0)))
+        arr[i].cam.ppx, arr[i].cam.ppy = (float(x) for x in v.get("pp", (0.0, 0.0)))
     return arr

@@ -204,12 +204,19 @@ int tile_rho(int k, int b, double* rho, cudaStream_t s) {
 // ----------------------------------------------------------------------------
 // View table and workspace layout
 // ----------------------------------------------------------------------------
+// Pinhole: FoV in (0, 180) and the principal point strictly inside the image; the
+// other cameras have a centred principal point.
+bool valid_camera(const hpxgs_camera& c) {
+  const bool pp_in = std::fabs(c.ppx) < 1.f && std::fabs(c.ppy) < 1.f;   // false for NaN
+  if (c.kind == HPXGS_CAM_PINHOLE)
+    return c.fov_x_deg > 0 && c.fov_x_deg < 180 && c.fov_y_deg > 0 && c.fov_y_deg < 180 && pp_in;
+  return c.ppx == 0.f && c.ppy == 0.f;
+}
+
 static bool valid_view(const hpxgs_view& v, int b) {
   if (v.nside_log2 < b || v.nside_log2 > 13) return false;
   if (v.cam.kind < 0 || v.cam.kind > 2) return false;
-  if (v.cam.kind == HPXGS_CAM_PINHOLE &&
-      !(v.cam.fov_x_deg > 0 && v.cam.fov_x_deg < 180 && v.cam.fov_y_deg > 0 && v.cam.fov_y_deg < 180))
-    return false;
+  if (!valid_camera(v.cam)) return false;
   if (v.cam.kind == HPXGS_CAM_FISHEYE &&
       !(v.cam.fov_x_deg > 0 && v.cam.fov_x_deg <= 360 && v.cam.fov_y_deg > 0 && v.cam.fov_y_deg <= 360))
     return false;
@@ -284,11 +291,14 @@ int make_layout(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_conf
 void camera_params(const hpxgs_camera& cam, int k, ViewParams& p) {
   p.k = k;
   p.kind = cam.kind;
-  p.tanx64 = std::tan(0.5 * cam.fov_x_deg * kPi / 180.0);
-  p.tany64 = std::tan(0.5 * cam.fov_y_deg * kPi / 180.0);
+  // u in [0, W] with x = (u - c_x) / f_x, c_x = (W/2)(1 + ppx), W / (2 f_x) = tan(fov_x / 2)
+  const double tx = std::tan(0.5 * cam.fov_x_deg * kPi / 180.0), ty = std::tan(0.5 * cam.fov_y_deg * kPi / 180.0);
+  p.xlo64 = -tx * (1.0 + (double)cam.ppx); p.xhi64 = tx * (1.0 - (double)cam.ppx);
+  p.ylo64 = -ty * (1.0 + (double)cam.ppy); p.yhi64 = ty * (1.0 - (double)cam.ppy);
   p.wx64 = cam.fov_x_deg / 180.0;
   p.wy64 = cam.fov_y_deg / 180.0;
-  p.tanx = (float)p.tanx64; p.tany = (float)p.tany64; p.wx = (float)p.wx64; p.wy = (float)p.wy64;
+  p.xlo = (float)p.xlo64; p.xhi = (float)p.xhi64; p.ylo = (float)p.ylo64; p.yhi = (float)p.yhi64;
+  p.wx = (float)p.wx64; p.wy = (float)p.wy64;
 }
 
 int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
@@ -331,7 +341,10 @@ int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nvi
     // r_s + rho of the Gaussian, so a Gaussian farther than psi_max + 2 rho + r_s from
     // the axis has no listed tile and can be culled before sorting.
     double psi_max = -1.0;
-    if (hv.cam.kind == HPXGS_CAM_PINHOLE) psi_max = std::atan(std::sqrt(p.tanx64 * p.tanx64 + p.tany64 * p.tany64));
+    if (hv.cam.kind == HPXGS_CAM_PINHOLE) {
+      const double ex = std::fmax(-p.xlo64, p.xhi64), ey = std::fmax(-p.ylo64, p.yhi64);   // farthest frustum corner
+      psi_max = std::atan(std::sqrt(ex * ex + ey * ey));
+    }
     else if (hv.cam.kind == HPXGS_CAM_FISHEYE) psi_max = 0.5 * kPi * std::fmax(p.wx64, p.wy64);
     p.rho32 = (float)p.rho;
     // the NESTED query lists a tile from a node within r_s + PixRad(k_max) of the

@@ -16,9 +16,9 @@ struct ViewParams {
   float cam[3];        // camera centre -W^T b (world)
   int k;               // HEALPix order of the view
   int kind;            // HPXGS_CAM_*
-  float tanx, tany;    // pinhole tan(fov/2)
+  float xlo, xhi, ylo, yhi;   // pinhole frustum: xlo <= d_x / d_z <= xhi, ylo <= d_y / d_z <= yhi
   float wx, wy;        // fisheye fov / 180 deg
-  double tanx64, tany64, wx64, wy64;
+  double xlo64, xhi64, ylo64, yhi64, wx64, wy64;
   double rho;          // tile rho(k, b)
   float rho32;         // (float) rho, so kernels need no FP64 conversion
   float fov_cull;      // Gaussians farther than fov_cull + r_s from the optical axis have no listed tile (< 0: none)
@@ -96,6 +96,7 @@ int make_layout(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_conf
 int pixrad(int o, double* out, cudaStream_t s);
 // Camera fields of a view (k, kind, tan(FoV/2) and FoV/180 deg in FP32 and FP64).
 void camera_params(const hpxgs_camera& cam, int k, ViewParams& p);
+bool valid_camera(const hpxgs_camera& cam);
 int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
                cudaStream_t stream, bool need_rho, ViewTable* vt);
 int num_sms();

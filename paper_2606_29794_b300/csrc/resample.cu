@@ -33,6 +33,7 @@ constexpr int kRsThreads = 256;
 struct ImgCam {
   int kind, W, H;
   float fx, fy;      // pinhole: W / (2 tan(FoV_x / 2)), H / (2 tan(FoV_y / 2)); fisheye: W / pi, H / pi
+  float cx, cy;      // principal point: pinhole (W/2)(1 + ppx), (H/2)(1 + ppy); fisheye and panorama W/2, H/2
   float wx, wy;      // fisheye FoV / 180 deg
 };
 
@@ -45,7 +46,7 @@ __device__ __forceinline__ bool img_to_dir(const ImgCam& c, float u, float v, fl
     d = make_float3(cp * so, sp, cp * co);
     return true;
   }
-  const float mx = (u - 0.5f * (float)c.W) / c.fx, my = (v - 0.5f * (float)c.H) / c.fy;
+  const float mx = (u - c.cx) / c.fx, my = (v - c.cy) / c.fy;
   if (c.kind == HPXGS_CAM_PINHOLE) {
     const float inv = rsqrtf(mx * mx + my * my + 1.f);
     d = make_float3(mx * inv, my * inv, inv);
@@ -71,13 +72,13 @@ __device__ __forceinline__ float2 dir_to_img(const ImgCam& c, float3 d) {
                        (float)c.H * (0.5f * (float)kPi - ph) / (float)kPi);
   }
   if (c.kind == HPXGS_CAM_PINHOLE)
-    return make_float2(0.5f * (float)c.W + c.fx * d.x / d.z, 0.5f * (float)c.H + c.fy * d.y / d.z);
+    return make_float2(c.cx + c.fx * d.x / d.z, c.cy + c.fy * d.y / d.z);
   const float rxy = sqrtf(d.x * d.x + d.y * d.y);
-  if (rxy == 0.f) return make_float2(0.5f * (float)c.W, 0.5f * (float)c.H);
+  if (rxy == 0.f) return make_float2(c.cx, c.cy);
   const float cg = d.x / rxy, sg = d.y / rxy;
   const float weff = sqrtf(c.wx * c.wx * cg * cg + c.wy * c.wy * sg * sg);
   const float rm = atan2f(rxy, d.z) / weff;
-  return make_float2(0.5f * (float)c.W + c.fx * rm * cg, 0.5f * (float)c.H + c.fy * rm * sg);
+  return make_float2(c.cx + c.fx * rm * cg, c.cy + c.fy * rm * sg);
 }
 
 __device__ __forceinline__ float ring_theta(int k, int i) {
@@ -236,10 +237,12 @@ __global__ void __launch_bounds__(kRsThreads) k_image_to_sphere(const float* __r
 bool make_cam(const hpxgs_camera* cam, int W, int H, ImgCam& c) {
   if (!cam || W < 1 || H < 1 || W > 65536 || H > 65536) return false;
   c.kind = cam->kind; c.W = W; c.H = H; c.fx = c.fy = 1.f; c.wx = c.wy = 1.f;
+  c.cx = (float)(0.5 * W); c.cy = (float)(0.5 * H);
+  if (!valid_camera(*cam)) return false;
   if (cam->kind == HPXGS_CAM_PINHOLE) {
-    if (!(cam->fov_x_deg > 0 && cam->fov_x_deg < 180 && cam->fov_y_deg > 0 && cam->fov_y_deg < 180)) return false;
     c.fx = (float)(W / (2.0 * std::tan(0.5 * cam->fov_x_deg * kPi / 180.0)));
     c.fy = (float)(H / (2.0 * std::tan(0.5 * cam->fov_y_deg * kPi / 180.0)));
+    c.cx = (float)(0.5 * W * (1.0 + (double)cam->ppx)); c.cy = (float)(0.5 * H * (1.0 + (double)cam->ppy));
   } else if (cam->kind == HPXGS_CAM_FISHEYE) {
     if (!(cam->fov_x_deg > 0 && cam->fov_x_deg <= 360 && cam->fov_y_deg > 0 && cam->fov_y_deg <= 360)) return false;
     c.fx = (float)(W / kPi); c.fy = (float)(H / kPi);

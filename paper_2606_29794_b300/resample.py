@@ -4,7 +4,9 @@ camera image, its adjoint, and a camera image to the HEALPix grid. Argument
 marshalling only; the work runs in libhpxgs kernels.
 
 A camera is a dict with "cam" (CAM_FULL for the panorama, CAM_PINHOLE,
-CAM_FISHEYE) and "fov_x", "fov_y" in degrees (the views of `synth` carry them).
+CAM_FISHEYE) and "fov_x", "fov_y" in degrees, and for the pinhole optionally "pp",
+the principal point's offset from the image centre in half-image units (the views of
+`synth` carry them).
 """
 from __future__ import annotations
 
@@ -21,6 +23,7 @@ def _cam(cam) -> L.Camera:
     c.fov_x_deg = float(cam.get("fov_x", 360.0))
     fy = cam.get("fov_y")
     c.fov_y_deg = float(c.fov_x_deg if fy is None else fy)
+    c.ppx, c.ppy = (float(x) for x in cam.get("pp", (0.0, 0.0)))
     return c
 
 

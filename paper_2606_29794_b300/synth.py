@@ -74,22 +74,24 @@ def random_rotation(rng) -> np.ndarray:
 
 
 def make_view(nside_log2: int, cam: int = CAM_FULL, fov_x: float = 360.0, fov_y: float | None = None,
-              R: np.ndarray | None = None, position=(0.0, 0.0, 0.0)) -> dict:
-    """World-to-camera view V = [W | b] with W = R (rotation) and b = -R c (camera centre c)."""
+              R: np.ndarray | None = None, position=(0.0, 0.0, 0.0), pp=(0.0, 0.0)) -> dict:
+    """World-to-camera view V = [W | b] with W = R (rotation) and b = -R c (camera centre c).
+    pp: a pinhole's principal point offset from the image centre, in half-image units
+    (c_x = (W/2)(1 + pp[0]), c_y = (H/2)(1 + pp[1]))."""
     W = np.eye(3) if R is None else np.asarray(R, np.float64)
     c = np.asarray(position, np.float64)
     b = -W @ c
     return dict(W=np.ascontiguousarray(W, np.float32), b=np.ascontiguousarray(b, np.float32),
                 nside_log2=int(nside_log2), cam=int(cam), fov_x=float(fov_x),
-                fov_y=float(fov_x if fov_y is None else fov_y))
+                fov_y=float(fov_x if fov_y is None else fov_y), pp=(float(pp[0]), float(pp[1])))
 
 
-def random_pose_view(rng, nside_log2, cam, fov_x, fov_y=None, radius=1.0) -> dict:
+def random_pose_view(rng, nside_log2, cam, fov_x, fov_y=None, radius=1.0, pp=(0.0, 0.0)) -> dict:
     R = random_rotation(rng)
     d = rng.standard_normal(3)
     d /= np.linalg.norm(d)
     pos = d * radius * np.cbrt(rng.random())
-    return make_view(nside_log2, cam, fov_x, fov_y, R, pos)
+    return make_view(nside_log2, cam, fov_x, fov_y, R, pos, pp)
 
 
 def multiview_set(seed: int) -> list:

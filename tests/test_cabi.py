@@ -60,6 +60,12 @@ def test_host_argument_checks(lib):
     assert lib.hpxgs_forward_workspace_size(1000, vb, 1, ctypes.byref(cfg), 10000, ctypes.byref(n)) == L.E_INVALID_ARG
     vp = L.make_views([dict(W=[1, 0, 0, 0, 1, 0, 0, 0, 1], b=[0, 0, 0], nside_log2=6, cam=1, fov_x=200.0)])
     assert lib.hpxgs_forward_workspace_size(1000, vp, 1, ctypes.byref(cfg), 10000, ctypes.byref(n)) == L.E_INVALID_ARG
+    # principal point: inside the image for the pinhole, centred for the fisheye and the full sphere
+    I3 = [1, 0, 0, 0, 1, 0, 0, 0, 1]
+    for cam, pp, rc in [(1, (0.5, -0.9), 0), (1, (1.0, 0.0), L.E_INVALID_ARG), (1, (0.0, float("nan")), L.E_INVALID_ARG),
+                        (2, (0.1, 0.0), L.E_INVALID_ARG), (0, (0.0, 0.2), L.E_INVALID_ARG), (2, (0.0, 0.0), 0)]:
+        vv = L.make_views([dict(W=I3, b=[0, 0, 0], nside_log2=6, cam=cam, fov_x=90.0, pp=pp)])
+        assert lib.hpxgs_forward_workspace_size(1000, vv, 1, ctypes.byref(cfg), 10000, ctypes.byref(n)) == rc, (cam, pp)
     assert lib.hpxgs_forward_workspace_size(1000, v, 1, ctypes.byref(cfg), -5, ctypes.byref(n)) == L.E_INVALID_ARG
     assert lib.hpxgs_forward_workspace_size(1000, v, 0, ctypes.byref(cfg), 10, ctypes.byref(n)) == L.E_INVALID_ARG
     # null required pointers are rejected before any launch

@@ -117,6 +117,29 @@ def test_forward_mask_equals_per_pixel_mask(k, kind, fx, fy):
     assert torch.equal(out["mask"], words)
 
 
+@pytest.mark.parametrize("k,fx,fy,pp", [(8, 90.0, 70.0, (0.3, -0.45)), (9, 60.0, 100.0, (-0.7, 0.2)),
+                                        (7, 120.0, 80.0, (0.9, 0.9))])
+def test_off_centre_pinhole_mask_matches_oracle(k, fx, fy, pp):
+    # principal point (W/2)(1 + ppx), (H/2)(1 + ppy): an asymmetric frustum; the per-pixel
+    # mask equals the oracle's except on the boundary itself, and the forward's mask equals it
+    from tests.gpu_util import scene_tensors
+    view = S.make_view(k, S.CAM_PINHOLE, fx, fy, pp=pp)
+    rast = R.Rasterizer(tile_level=4)
+    cv = L.make_views([view])
+    words = torch.empty(12 * 4 ** k // 32, dtype=torch.int32, device="cuda")
+    L.check(L.lib().hpxgs_mask_build(cv, ctypes.byref(rast.cfg), _p(words), _s()), "mask")
+    out, _ = rast.forward_raw(*scene_tensors(S.make_scene(500, 0, seed=8)), 0, [view])
+    torch.cuda.synchronize()
+    w = words.cpu().numpy().view(np.uint32)
+    bits = ((w[:, None] >> np.arange(32, dtype=np.uint32)) & 1).astype(np.uint8).reshape(-1)
+    ref, margin = O.mask(2 ** k, S.CAM_PINHOLE, fx, fy, pp=pp)
+    bad = np.nonzero(bits != ref)[0]
+    assert np.all(np.abs(margin[bad]) < 1e-12), (bad[:10], margin[bad[:10]])
+    centred, _ = O.mask(2 ** k, S.CAM_PINHOLE, fx, fy)
+    assert (bits != centred).sum() > 100                  # the offset moves the frustum
+    assert torch.equal(out["mask"], words)
+
+
 @pytest.mark.parametrize("k,b", [(6, 3), (9, 4), (11, 4), (10, 5)])
 def test_tile_rho_matches_oracle(k, b):
     rho = ctypes.c_double()

@@ -48,6 +48,9 @@ CASES = [
     ("pinhole_rot", lambda: (S.make_scene(2500, 3, seed=6),
                              S.random_pose_view(np.random.default_rng(2), 7, S.CAM_PINHOLE, 90.0, 70.0)), 3),
     ("full_b5", lambda: (S.make_scene(2500, 0, seed=7, logscale_mu=-2.0), S.make_view(7)), 5),
+    ("pinhole_off_centre", lambda: (S.make_scene(2500, 3, seed=8),
+                                    S.random_pose_view(np.random.default_rng(12), 7, S.CAM_PINHOLE, 100.0, 75.0,
+                                                       pp=(0.35, -0.5))), 4),
 ]
 
 
@@ -76,7 +79,7 @@ def test_staged_records_lists_and_maps(name, make, b):
     assert np.abs(conic_gpu[valid] - pre["conic"][valid]).max() <= 0 + (2e-4 * scale).max()
     # ---- mask and active tiles
     m_gpu = mask_from_words(out["mask"].cpu().numpy().view(np.uint32), O.npix(2 ** k))
-    m_ref, margin = O.mask(2 ** k, view["cam"], view["fov_x"], view["fov_y"])
+    m_ref, margin = O.mask(2 ** k, view["cam"], view["fov_x"], view["fov_y"], view.get("pp", (0.0, 0.0)))
     assert np.all(np.abs(margin[m_gpu != m_ref]) < 1e-12)
     act = O.active_tiles(k, b, m_gpu)
     # ---- stage 2: tile lists from the GPU's stored FP32 values, exact
@@ -212,3 +215,9 @@ def test_gradients_pinhole_b3():
     sc = S.make_scene(3000, 3, seed=42)
     view = S.random_pose_view(np.random.default_rng(10), 7, S.CAM_PINHOLE, 80.0, 100.0, 0.5)
     _grad_check(sc, view, 3, 2)
+
+
+def test_gradients_off_centre_pinhole():
+    sc = S.make_scene(3000, 3, seed=43)
+    view = S.random_pose_view(np.random.default_rng(11), 7, S.CAM_PINHOLE, 90.0, 70.0, 0.5, pp=(-0.6, 0.4))
+    _grad_check(sc, view, 4, 3)

@@ -38,12 +38,13 @@ def tol_s2i(k):
 
 def tol_i2s(W, H):
     return 1e-6 + 2e-7 * max(W, H)
-CAMS = [(O.CAM_PINHOLE, 90.0, 70.0), (O.CAM_FISHEYE, 190.0, 190.0), (O.CAM_FISHEYE, 200.0, 170.0),
-        (O.CAM_FULL, 360.0, 180.0)]
+Z = (0.0, 0.0)
+CAMS = [(O.CAM_PINHOLE, 90.0, 70.0, Z), (O.CAM_PINHOLE, 90.0, 70.0, (0.3, -0.45)), (O.CAM_FISHEYE, 190.0, 190.0, Z),
+        (O.CAM_FISHEYE, 200.0, 170.0, Z), (O.CAM_FULL, 360.0, 180.0, Z)]
 
 
-def _cam(kind, fx, fy):
-    return {"cam": kind, "fov_x": fx, "fov_y": fy}
+def _cam(kind, fx, fy, pp=Z):
+    return {"cam": kind, "fov_x": fx, "fov_y": fy, "pp": pp}
 
 
 def _fisheye_edge(kind, W, H, uv):
@@ -55,14 +56,14 @@ def _fisheye_edge(kind, W, H, uv):
     return np.abs(np.hypot(mx, my) - math.pi / 2) < 1e-5
 
 
-@pytest.mark.parametrize("kind,fx,fy", CAMS)
-def test_sphere_to_image(kind, fx, fy):
+@pytest.mark.parametrize("kind,fx,fy,pp", CAMS)
+def test_sphere_to_image(kind, fx, fy, pp):
     k, W, H = 6, 160, 120
     rng = np.random.default_rng(kind + 10)
     hmap = rng.random((12 * 4 ** k, 3))
     img, ok = RS.sphere_to_image_raw(torch.as_tensor(hmap, dtype=torch.float32, device="cuda"), k,
-                                     _cam(kind, fx, fy), W, H)
-    ref, ok_ref = O.sphere_to_image(2 ** k, hmap, kind, W, H, fx, fy)
+                                     _cam(kind, fx, fy, pp), W, H)
+    ref, ok_ref = O.sphere_to_image(2 ** k, hmap, kind, W, H, fx, fy, pp=pp)
     uu, vv = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
     edge = _fisheye_edge(kind, W, H, np.stack([uu.ravel(), vv.ravel()], 1)).reshape(H, W)
     okg = ok.cpu().numpy()
@@ -73,18 +74,19 @@ def test_sphere_to_image(kind, fx, fy):
     assert np.all(img.cpu().numpy()[okg == 0] == 0)
 
 
-@pytest.mark.parametrize("kind,fx,fy", CAMS)
-def test_sphere_to_image_adjoint(kind, fx, fy):
+@pytest.mark.parametrize("kind,fx,fy,pp", CAMS)
+def test_sphere_to_image_adjoint(kind, fx, fy, pp):
     k, W, H = 5, 96, 64
     rng = np.random.default_rng(kind + 20)
     y = rng.standard_normal((H, W, 3))
     dmap = RS.sphere_to_image_backward(torch.as_tensor(y, dtype=torch.float32, device="cuda"), k,
-                                       _cam(kind, fx, fy), W, H).cpu().numpy().astype(np.float64)
-    ref = O.sphere_to_image_adjoint(2 ** k, y, kind, W, H, fx, fy)
+                                       _cam(kind, fx, fy, pp), W, H).cpu().numpy().astype(np.float64)
+    ref = O.sphere_to_image_adjoint(2 ** k, y, kind, W, H, fx, fy, pp=pp)
     assert np.abs(dmap - ref).max() < tol_s2i(k) * np.abs(ref).max() * 4
     # <A x, y> = <x, A^T y> with the GPU's forward and backward
     x = rng.standard_normal((12 * 4 ** k, 3))
-    Ax, ok = RS.sphere_to_image_raw(torch.as_tensor(x, dtype=torch.float32, device="cuda"), k, _cam(kind, fx, fy), W, H)
+    Ax, ok = RS.sphere_to_image_raw(torch.as_tensor(x, dtype=torch.float32, device="cuda"), k, _cam(kind, fx, fy, pp),
+                                    W, H)
     lhs = (Ax.cpu().numpy().astype(np.float64) * y).sum()
     rhs = (x * dmap).sum()
     assert abs(lhs - rhs) < 1e-5 * np.abs(Ax.cpu().numpy() * y).sum()
@@ -101,45 +103,45 @@ def test_autograd_through_sphere_to_image():
     assert torch.allclose(hmap.grad, want)
 
 
-@pytest.mark.parametrize("kind,fx,fy", CAMS)
-def test_image_to_sphere(kind, fx, fy):
+@pytest.mark.parametrize("kind,fx,fy,pp", CAMS)
+def test_image_to_sphere(kind, fx, fy, pp):
     k, W, H = 6, 150, 100
     rng = np.random.default_rng(kind + 30)
     img = rng.random((H, W, 3))
-    hm, words = RS.image_to_sphere(torch.as_tensor(img, dtype=torch.float32, device="cuda"), _cam(kind, fx, fy), k)
+    hm, words = RS.image_to_sphere(torch.as_tensor(img, dtype=torch.float32, device="cuda"), _cam(kind, fx, fy, pp), k)
     n = 12 * 4 ** k
     m = mask_from_words(words.cpu().numpy().view(np.uint32), n)
     # the mask is M_C of the FoV mask kernel, bit for bit
     fov = torch.empty(n // 32, dtype=torch.int32, device="cuda")
     v = L.make_views([{"W": np.eye(3, dtype=np.float32), "b": np.zeros(3, np.float32), "nside_log2": k,
-                       "cam": kind, "fov_x": fx, "fov_y": fy}])
+                       "cam": kind, "fov_x": fx, "fov_y": fy, "pp": pp}])
     cfg = L.default_config()
     L.check(L.lib().hpxgs_mask_build(v, ctypes.byref(cfg), ctypes.c_void_p(fov.data_ptr()),
                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)), "mask")
     torch.cuda.synchronize()
     assert np.array_equal(m, mask_from_words(fov.cpu().numpy().view(np.uint32), n))
-    ref, m_ref = O.image_to_sphere(2 ** k, img, kind, W, H, fx, fy)
-    _, margin = O.mask(2 ** k, kind, fx, fy)
+    ref, m_ref = O.image_to_sphere(2 ** k, img, kind, W, H, fx, fy, pp=pp)
+    _, margin = O.mask(2 ** k, kind, fx, fy, pp=pp)
     assert np.all(np.abs(margin[m != m_ref]) < 1e-12)
     both = (m == 1) & (m_ref == 1)
     assert np.abs(hm.cpu().numpy()[both] - ref[both]).max() < tol_i2s(W, H)
     assert np.all(hm.cpu().numpy()[m == 0] == 0)
 
 
-BENCH_CASES = [(O.CAM_FISHEYE, 190.0, 190.0, 9, 1472, 1472), (O.CAM_PINHOLE, 90.0, 90.0, 10, 2048, 2048),
-               (O.CAM_FULL, 360.0, 180.0, 10, 4096, 2048)]
+BENCH_CASES = [(O.CAM_FISHEYE, 190.0, 190.0, Z, 9, 1472, 1472), (O.CAM_PINHOLE, 90.0, 90.0, Z, 10, 2048, 2048),
+               (O.CAM_PINHOLE, 90.0, 90.0, (0.25, 0.1), 10, 2048, 1536), (O.CAM_FULL, 360.0, 180.0, Z, 10, 4096, 2048)]
 
 
-@pytest.mark.parametrize("kind,fx,fy,k,W,H", BENCH_CASES)
-def test_bench_sizes_sampled(kind, fx, fy, k, W, H):
+@pytest.mark.parametrize("kind,fx,fy,pp,k,W,H", BENCH_CASES)
+def test_bench_sizes_sampled(kind, fx, fy, pp, k, W, H):
     rng = np.random.default_rng(W + k)
     n = 12 * 4 ** k
     hmap = rng.random((n, 3)).astype(np.float32)
-    cam = _cam(kind, fx, fy)
+    cam = _cam(kind, fx, fy, pp)
     img, ok = RS.sphere_to_image_raw(torch.as_tensor(hmap, device="cuda"), k, cam, W, H)
     sel = rng.choice(W * H, 20000, replace=False)
     uv = np.stack([sel % W + 0.5, sel // W + 0.5], 1)
-    ref, ok_ref = O.sphere_to_image_at(2 ** k, hmap.astype(np.float64), kind, W, H, fx, fy, uv)
+    ref, ok_ref = O.sphere_to_image_at(2 ** k, hmap.astype(np.float64), kind, W, H, fx, fy, uv, pp=pp)
     okg = ok.cpu().numpy().ravel()[sel]
     edge = _fisheye_edge(kind, W, H, uv)
     assert np.array_equal(okg[~edge], ok_ref[~edge])
@@ -149,9 +151,9 @@ def test_bench_sizes_sampled(kind, fx, fy, k, W, H):
     im = rng.random((H, W, 3)).astype(np.float32)
     hm, words = RS.image_to_sphere(torch.as_tensor(im, device="cuda"), cam, k)
     qs = rng.choice(n, 20000, replace=False)
-    ref2, m2 = O.image_to_sphere_at(2 ** k, im.astype(np.float64), kind, W, H, fx, fy, qs)
+    ref2, m2 = O.image_to_sphere_at(2 ** k, im.astype(np.float64), kind, W, H, fx, fy, qs, pp=pp)
     m = mask_from_words(words.cpu().numpy().view(np.uint32), n)[qs]
-    _, margin = O.mask(2 ** k, kind, fx, fy)
+    _, margin = O.mask(2 ** k, kind, fx, fy, pp=pp)
     assert np.all(np.abs(margin[qs][m != m2]) < 1e-12)
     both = (m == 1) & (m2 == 1)
     assert np.abs(hm.cpu().numpy()[qs][both] - ref2[both]).max() < tol_i2s(W, H)

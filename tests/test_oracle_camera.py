@@ -24,6 +24,51 @@ def test_pinhole_mask_solid_angle(fx, fy):
     assert abs(m.mean() - om / (4 * np.pi)) < 2e-3
 
 
+def _rect_solid_angle(x1, x2, y1, y2):
+    """Solid angle, seen from the origin, of the rectangle [x1, x2] x [y1, y2] on the plane z = 1:
+    F(x, y) = atan(x y / sqrt(1 + x^2 + y^2)) is the solid angle of [0, x] x [0, y] (signed), and
+    the rectangle is F(x2, y2) - F(x1, y2) - F(x2, y1) + F(x1, y1)."""
+    F = lambda x, y: np.arctan(x * y / np.sqrt(1 + x * x + y * y))
+    return F(x2, y2) - F(x1, y2) - F(x2, y1) + F(x1, y1)
+
+
+def test_rect_solid_angle_closed_form_reduces_to_the_centred_pinhole():
+    for fx, fy in [(90.0, 90.0), (60.0, 100.0)]:
+        tx, ty = np.tan(np.radians(fx / 2)), np.tan(np.radians(fy / 2))
+        om = 4 * np.arcsin(np.sin(np.radians(fx / 2)) * np.sin(np.radians(fy / 2)))
+        assert np.isclose(_rect_solid_angle(-tx, tx, -ty, ty), om, rtol=1e-12)
+
+
+@pytest.mark.parametrize("fx,fy,pp", [(90.0, 70.0, (0.3, -0.45)), (60.0, 100.0, (-0.7, 0.2)),
+                                      (120.0, 80.0, (0.9, 0.9))])
+def test_off_centre_pinhole_mask_solid_angle(fx, fy, pp):
+    # principal point c = (W/2)(1 + pp): the frustum spans d_x/d_z in [-t_x(1 + ppx), t_x(1 - ppx)]
+    nside = 256
+    m, _ = O.mask(nside, O.CAM_PINHOLE, fx, fy, pp=pp)
+    tx, ty = np.tan(np.radians(fx / 2)), np.tan(np.radians(fy / 2))
+    om = _rect_solid_angle(-tx * (1 + pp[0]), tx * (1 - pp[0]), -ty * (1 + pp[1]), ty * (1 - pp[1]))
+    assert abs(m.mean() - om / (4 * np.pi)) < 2e-3
+
+
+def test_off_centre_pinhole_mask_containment_and_mirror():
+    nside = 64
+    fx, fy, pp = 90.0, 70.0, (0.3, -0.45)
+    tx, ty = np.tan(np.radians(fx / 2)), np.tan(np.radians(fy / 2))
+    m, mg = O.mask(nside, O.CAM_PINHOLE, fx, fy, pp=pp)
+    fov = lambda t: 2 * np.degrees(np.arctan(t))
+    inner, _ = O.mask(nside, O.CAM_PINHOLE, fov(tx * (1 - abs(pp[0]))), fov(ty * (1 - abs(pp[1]))))
+    outer, _ = O.mask(nside, O.CAM_PINHOLE, fov(tx * (1 + abs(pp[0]))), fov(ty * (1 + abs(pp[1]))))
+    assert np.all(m >= inner) and np.all(m <= outer) and inner.sum() < m.sum() < outer.sum()
+    # mirroring d_x (HEALPix Y -> -Y) maps the mask at ppx to the mask at -ppx
+    v = O.pix2vec_nest(nside, np.arange(O.npix(nside)))
+    mirror = O.vec2pix_nest(nside, v * np.array([1.0, -1.0, 1.0]))
+    m_neg, _ = O.mask(nside, O.CAM_PINHOLE, fx, fy, pp=(-pp[0], pp[1]))
+    far = np.abs(mg) > 1e-12
+    assert np.array_equal(m_neg[mirror][far], m[far])
+    # pp = 0 is the centred camera
+    assert np.array_equal(O.mask(nside, O.CAM_PINHOLE, fx, fy, pp=(0.0, 0.0))[0], O.mask(nside, O.CAM_PINHOLE, fx, fy)[0])
+
+
 @pytest.mark.parametrize("fov", [120.0, 180.0, 190.0, 220.0])
 def test_fisheye_mask_solid_angle(fov):
     nside = 256

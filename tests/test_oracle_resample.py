@@ -14,8 +14,9 @@ import pytest
 
 import oracle as O
 
-CAMS = [(O.CAM_PINHOLE, 90.0, 70.0), (O.CAM_FISHEYE, 190.0, 190.0), (O.CAM_FISHEYE, 200.0, 170.0),
-        (O.CAM_FULL, 360.0, 180.0)]
+Z = (0.0, 0.0)
+CAMS = [(O.CAM_PINHOLE, 90.0, 70.0, Z), (O.CAM_PINHOLE, 90.0, 70.0, (0.3, -0.45)), (O.CAM_FISHEYE, 190.0, 190.0, Z),
+        (O.CAM_FISHEYE, 200.0, 170.0, Z), (O.CAM_FULL, 360.0, 180.0, Z)]
 
 
 def _ring_thetas(nside):
@@ -93,54 +94,65 @@ def test_camera_closed_forms():
         assert ok.tolist() == [1, 1, 0]
         assert np.allclose(d[0], [math.sin(math.pi / 2 * wx), 0, math.cos(math.pi / 2 * wx)])
         assert np.allclose(d[1], [0, math.sin(math.pi / 2 * wy), math.cos(math.pi / 2 * wy)])
+    # off-centre pinhole (Eq. persp_sphere with c_x = (W/2)(1 + ppx), c_y = (H/2)(1 + ppy)): the
+    # principal point -> optical axis; corner (0, 0) -> x = -c_x / f_x; corner (W, H) -> (W - c_x) / f_x
+    ppx, ppy = 0.3, -0.45
+    cx, cy = W / 2 * (1 + ppx), H / 2 * (1 + ppy)
+    fpx, fpy = W / (2 * math.tan(math.radians(45.0))), H / (2 * math.tan(math.radians(35.0)))
+    d, ok = O.img_to_dir(O.CAM_PINHOLE, W, H, 90.0, 70.0, [[cx, cy], [0.0, 0.0], [W, H]], pp=(ppx, ppy))
+    assert ok.all() and np.allclose(d[0], [0, 0, 1])
+    for dd, (u, v) in zip(d[1:], [(0.0, 0.0), (W, H)]):
+        c = np.array([(u - cx) / fpx, (v - cy) / fpy, 1.0])
+        assert np.allclose(dd, c / np.linalg.norm(c))
+    assert np.isclose(d[1, 0] / d[1, 2], -1.3) and np.isclose(d[2, 0] / d[2, 2], 0.7)      # tan 45 = 1
     # panorama: centre -> forward; left edge -> backward; top row -> +y (phi = pi/2)
     d, ok = O.img_to_dir(O.CAM_FULL, W, H, 360.0, 180.0, [[W / 2, H / 2], [0.0, H / 2], [W / 2, 0.0]])
     assert np.allclose(d, [[0, 0, 1], [0, 0, -1], [0, 1, 0]], atol=1e-12)
 
 
-@pytest.mark.parametrize("kind,fx,fy", CAMS)
-def test_camera_round_trip(kind, fx, fy):
+@pytest.mark.parametrize("kind,fx,fy,pp", CAMS)
+def test_camera_round_trip(kind, fx, fy, pp):
     W, H = 96, 72
     rng = np.random.default_rng(kind)
     uv = np.stack([rng.uniform(0, W, 2000), rng.uniform(0, H, 2000)], 1)
-    d, ok = O.img_to_dir(kind, W, H, fx, fy, uv)
-    uv2, ok2 = O.dir_to_img(kind, W, H, fx, fy, d[ok == 1])
+    d, ok = O.img_to_dir(kind, W, H, fx, fy, uv, pp=pp)
+    uv2, ok2 = O.dir_to_img(kind, W, H, fx, fy, d[ok == 1], pp=pp)
     assert ok2.all()
     assert np.allclose(uv2, uv[ok == 1], atol=1e-9)
     assert np.allclose(np.linalg.norm(d[ok == 1], axis=1), 1.0)
 
 
-@pytest.mark.parametrize("kind,fx,fy", CAMS)
-def test_resampled_mask_is_the_fov_mask(kind, fx, fy):
+@pytest.mark.parametrize("kind,fx,fy,pp", CAMS)
+def test_resampled_mask_is_the_fov_mask(kind, fx, fy, pp):
     nside = 16
-    m_ref, _ = O.mask(nside, kind, fx, fy)
-    _, m = O.image_to_sphere(nside, np.zeros((40, 50, 3)), kind, 50, 40, fx, fy)
+    m_ref, _ = O.mask(nside, kind, fx, fy, pp=pp)
+    _, m = O.image_to_sphere(nside, np.zeros((40, 50, 3)), kind, 50, 40, fx, fy, pp=pp)
     assert np.array_equal(m, m_ref)
 
 
-@pytest.mark.parametrize("kind,fx,fy", CAMS)
-def test_adjoint_identity(kind, fx, fy):
+@pytest.mark.parametrize("kind,fx,fy,pp", CAMS)
+def test_adjoint_identity(kind, fx, fy, pp):
     nside, W, H = 8, 40, 30
     rng = np.random.default_rng(7)
     x = rng.standard_normal((12 * nside * nside, 3))
     y = rng.standard_normal((H, W, 3))
-    Ax, ok = O.sphere_to_image(nside, x, kind, W, H, fx, fy)
-    Aty = O.sphere_to_image_adjoint(nside, y, kind, W, H, fx, fy)
+    Ax, ok = O.sphere_to_image(nside, x, kind, W, H, fx, fy, pp=pp)
+    Aty = O.sphere_to_image_adjoint(nside, y, kind, W, H, fx, fy, pp=pp)
     assert ok.any()
     assert abs((Ax * y).sum() - (x * Aty).sum()) < 1e-9 * np.abs(Ax * y).sum()
 
 
-@pytest.mark.parametrize("kind,fx,fy", CAMS)
-def test_linear_image_is_sampled_exactly(kind, fx, fy):
+@pytest.mark.parametrize("kind,fx,fy,pp", CAMS)
+def test_linear_image_is_sampled_exactly(kind, fx, fy, pp):
     # bilinear sampling reproduces an image linear in (u, v) at interior points
     nside, W, H = 32, 80, 60
     uu, vv = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
     img = np.stack([0.1 + 0.01 * uu, 0.2 - 0.005 * vv, 0.003 * uu + 0.004 * vv], -1)
-    hmap, m = O.image_to_sphere(nside, img, kind, W, H, fx, fy)
+    hmap, m = O.image_to_sphere(nside, img, kind, W, H, fx, fy, pp=pp)
     thq, phq = O.pix2ang_nest(nside, np.arange(12 * nside * nside))
     v = np.stack([np.sin(thq) * np.cos(phq), np.sin(thq) * np.sin(phq), np.cos(thq)], 1)
     d = v[:, [1, 2, 0]]                                     # camera (d_x, d_y, d_z) = HEALPix (Y, Z, X)
-    uv, ok = O.dir_to_img(kind, W, H, fx, fy, d)
+    uv, ok = O.dir_to_img(kind, W, H, fx, fy, d, pp=pp)
     inner = (ok == 1) & (uv[:, 0] > 0.5) & (uv[:, 0] < W - 0.5) & (uv[:, 1] > 0.5) & (uv[:, 1] < H - 0.5)
     assert inner.sum() > 100
     u, w = uv[inner, 0], uv[inner, 1]
@@ -159,17 +171,17 @@ def test_sphere_image_round_trip_is_close_at_matched_resolution():
     assert np.abs(back - img)[8:-8].max() < 0.02
 
 
-@pytest.mark.parametrize("kind,fx,fy", CAMS)
-def test_pointwise_entries_equal_whole_image_entries(kind, fx, fy):
+@pytest.mark.parametrize("kind,fx,fy,pp", CAMS)
+def test_pointwise_entries_equal_whole_image_entries(kind, fx, fy, pp):
     nside, W, H = 8, 30, 20
     rng = np.random.default_rng(11)
     hmap = rng.random((12 * nside * nside, 3))
-    img, ok = O.sphere_to_image(nside, hmap, kind, W, H, fx, fy)
+    img, ok = O.sphere_to_image(nside, hmap, kind, W, H, fx, fy, pp=pp)
     uu, vv = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
-    out, ok2 = O.sphere_to_image_at(nside, hmap, kind, W, H, fx, fy, np.stack([uu.ravel(), vv.ravel()], 1))
+    out, ok2 = O.sphere_to_image_at(nside, hmap, kind, W, H, fx, fy, np.stack([uu.ravel(), vv.ravel()], 1), pp=pp)
     assert np.array_equal(ok2, ok.ravel()) and np.array_equal(out, img.reshape(-1, 3))
     im = rng.random((H, W, 3))
-    hm, m = O.image_to_sphere(nside, im, kind, W, H, fx, fy)
+    hm, m = O.image_to_sphere(nside, im, kind, W, H, fx, fy, pp=pp)
     qs = np.arange(12 * nside * nside)
-    o2, m2 = O.image_to_sphere_at(nside, im, kind, W, H, fx, fy, qs)
+    o2, m2 = O.image_to_sphere_at(nside, im, kind, W, H, fx, fy, qs, pp=pp)
     assert np.array_equal(m2, m) and np.array_equal(o2, hm)
