@@ -196,7 +196,15 @@ def run_ours(args, ws_n, rank, local):
             L.check(lib.hpxgs_profile_arm(i, ctypes.c_void_p(a.cuda_event), ctypes.c_void_p(b.cuda_event)), "arm")
 
     stage_pairs = [new_pairs(), new_pairs()]
-    gsteps = [R.GraphStep(params, 3, [view], G, rast, before_capture=lambda j=j: arm(stage_pairs[j])) for j in range(2)]
+    gsteps = []
+    for j in range(2):
+        gsteps.append(R.GraphStep(params, 3, [view], G, rast, before_capture=lambda j=j: arm(stage_pairs[j])))
+        # stages the captured step does not run are still armed: drop them and disarm, so that
+        # later eager steps cannot record into this instance's events
+        for i, s in enumerate(L.STAGES):
+            if lib.hpxgs_profile_armed(i) == 1:
+                stage_pairs[j].pop(s)
+                L.check(lib.hpxgs_profile_arm(i, None, None), "disarm")
     gstep = gsteps[0]
     # ---------------- warm-up and capacity check
     for i in range(max(1, args.warmup)):
@@ -266,7 +274,10 @@ def run_ours(args, ws_n, rank, local):
                 evs[s] = (a, b)
             gsteps[0]._step()
             torch.cuda.synchronize()
-            for s, (a, b) in evs.items():
+            for i, (s, (a, b)) in enumerate(evs.items()):
+                if lib.hpxgs_profile_armed(i) == 1:           # the step does not run this stage
+                    L.check(lib.hpxgs_profile_arm(i, None, None), "disarm")
+                    continue
                 vals[s].append(a.elapsed_time(b))
         stage_ms = {s: sum(v) / len(v) for s, v in vals.items() if v and sum(v) > 0}
     n_eval = int(R.device_array(wv.n_eval, 1, torch.int64).item())

@@ -232,6 +232,32 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
                    float* dmeans, float* dscales, float* drotations, float* dopacities, float* dsh,
                    int32_t* status, hpxgs_stream_t stream);
 
+/* The L1 + HSSIM loss gradient of one view, for hpxgs_backward_hssim. All device memory. */
+typedef struct {
+  const float* maps;       /* I: the view's rendered maps [Npix, 3] (its slice of hpxgs_forward's maps) */
+  const float* targets;    /* G: the view's targets [Npix, 3] */
+  const void* table;       /* window table of the view's order and mask (hpxgs_hssim_table_build) */
+  const void* hssim_ws;    /* HSSIM workspace that hpxgs_hssim_forward_table filled for I, G this step */
+  const float* dloss;      /* dL/dloss of the view (one float), or NULL for 1 */
+} hpxgs_loss_view;
+
+/* hpxgs_backward for the training loss of Sec. 4.1 (Eq. supp_hssim_eval), with the HSSIM
+ * backward folded into the backward blend: each pixel's dL/dI is formed where the blend
+ * reads it, from the view's window table and the coefficients its HSSIM forward stored,
+ * instead of being written to and read from a dL/dmaps buffer. The result equals
+ * hpxgs_hssim_backward_table per view (same lambda, dloss) followed by hpxgs_backward
+ * with the packed dL/dmaps, up to the order of the atomic sums. Preconditions: the
+ * forward on the same workspace, then hpxgs_hssim_forward_table for every view, on the
+ * same stream. No inverse-depth channel (use hpxgs_backward with dL_ddepth); each tile
+ * level runs its default blend shape (cfg->bwd_ppt is not used). loss_views [nviews];
+ * lambda in [0, 1]; views need nside_log2 >= 3. Errors: HPXGS_E_INVALID_ARG for null or
+ * out-of-range arguments, HPXGS_E_WORKSPACE for a workspace smaller than the layout. */
+int hpxgs_backward_hssim(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+                         void* workspace, size_t workspace_bytes, int64_t capacity_pairs,
+                         const hpxgs_loss_view* loss_views, float lambda, const float* T_final,
+                         const uint32_t* last, float* dmeans, float* dscales, float* drotations,
+                         float* dopacities, float* dsh, int32_t* status, hpxgs_stream_t stream);
+
 /* Radian-space density-control statistics (Sec. 4.2), after hpxgs_backward on the same
  * workspace (same g->P, views, cfg, capacity). For every (view, Gaussian) the Gaussian is
  * visible in (listed for at least one active tile of the view), updates the caller's
@@ -316,6 +342,10 @@ int hpxgs_image_to_sphere(const float* image, int width, int height, const hpxgs
  * is being captured, the records become event-record nodes of the graph, so
  * every replay records both events again. */
 int hpxgs_profile_arm(int stage, void* start_event, void* stop_event);
+/* 1 if `stage` is still armed (no call has run it since hpxgs_profile_arm), 0 if not,
+ * HPXGS_E_INVALID_ARG for an unknown stage. After a captured step, the stages still
+ * armed are the ones the graph does not record. */
+int hpxgs_profile_armed(int stage);
 /* Number of kernels this library has launched in this process. */
 uint64_t hpxgs_launch_count(void);
 /* Measured FP32 throughput of this GPU at its current clocks, the denominators

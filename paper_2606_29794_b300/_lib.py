@@ -39,6 +39,11 @@ class View(ctypes.Structure):
                 ("cam", Camera)]
 
 
+class LossView(ctypes.Structure):
+    _fields_ = [("maps", ctypes.c_void_p), ("targets", ctypes.c_void_p), ("table", ctypes.c_void_p),
+                ("hssim_ws", ctypes.c_void_p), ("dloss", ctypes.c_void_p)]
+
+
 class Config(ctypes.Structure):
     _fields_ = [("tile_level", ctypes.c_int32), ("eps_T", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("cutoff_m", ctypes.c_float), ("blur_rad2", ctypes.c_float), ("near_plane", ctypes.c_float),
@@ -91,12 +96,15 @@ _SIGS = {
                                      _vp, _vp, _vp, _vp, _vp]),
     "hpxgs_backward": (ctypes.c_int, [_P(Gaussians), _P(View), ctypes.c_int, _P(Config), _vp, _sz, _i64, _vp, _vp,
                                       _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "hpxgs_backward_hssim": (ctypes.c_int, [_P(Gaussians), _P(View), ctypes.c_int, _P(Config), _vp, _sz, _i64,
+                                            _P(LossView), _f32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "hpxgs_count_pairs": (ctypes.c_int, [_P(Gaussians), _P(View), ctypes.c_int, _P(Config), _vp, _sz, _vp, _vp, _vp]),
     "hpxgs_density_stats": (ctypes.c_int, [_i32, _P(View), ctypes.c_int, _P(Config), _vp, _sz, _i64, _vp, _vp, _vp,
                                            _vp, _vp]),
     "hpxgs_workspace_inspect": (ctypes.c_int, [_i32, _P(View), ctypes.c_int, _P(Config), _i64, _vp,
                                                _P(WorkspaceView)]),
     "hpxgs_profile_arm": (ctypes.c_int, [ctypes.c_int, _vp, _vp]),
+    "hpxgs_profile_armed": (ctypes.c_int, [ctypes.c_int]),
     "hpxgs_sphere_to_image": (ctypes.c_int, [_vp, ctypes.c_int, _P(Camera), ctypes.c_int, ctypes.c_int, _vp, _vp,
                                              _vp]),
     "hpxgs_sphere_to_image_backward": (ctypes.c_int, [_vp, ctypes.c_int, _P(Camera), ctypes.c_int, ctypes.c_int,

@@ -493,6 +493,12 @@ int hpxgs_profile_arm(int stage, void* start_event, void* stop_event) {
   return HPXGS_OK;
 }
 
+int hpxgs_profile_armed(int stage) {
+  if (stage < 0 || stage >= HPXGS_NUM_STAGES) return HPXGS_E_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  return (g_prof[stage][0] || g_prof[stage][1]) ? 1 : 0;
+}
+
 uint64_t hpxgs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int hpxgs_pixrad(int o, double* out, hpxgs_stream_t stream) {

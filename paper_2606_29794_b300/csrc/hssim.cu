@@ -12,6 +12,7 @@
 // k_hssim_reduce: fixed-order sum of the block partials -> {loss, HSSIM, L1}.
 // k_hssim_bwd: per pixel, gather over the windows that contain it.
 #include "hpx_math.cuh"
+#include "hssim_grad.cuh"
 #include "internal.cuh"
 
 using namespace hpx;
@@ -313,24 +314,23 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_bwd_t(int k, const float* _
   if (!mbit(mask, p)) { dI[3 * (size_t)p] = 0.f; dI[3 * (size_t)p + 1] = 0.f; dI[3 * (size_t)p + 2] = 0.f; return; }
   const float nm = reinterpret_cast<const float*>(nmask + 1)[0];
   const float scale = (dloss ? *dloss : 1.f) / (3.f * nm);
-  float x[3], y[3], g[3];
-  for (int ch = 0; ch < 3; ++ch) {
-    x[ch] = I[3 * (size_t)p + ch]; y[ch] = Gt[3 * (size_t)p + ch];
-    const float cf0 = coef[9 * (size_t)p + 3 * ch], cf1 = coef[9 * (size_t)p + 3 * ch + 1], cf2 = coef[9 * (size_t)p + 3 * ch + 2];
-    g[ch] = cf0 + cf1 * x[ch] + cf2 * y[ch];
-  }
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const uint32_t q = T.idx[(size_t)j * npix + p];
-    const float e = T.e[(size_t)j * npix + p];
-    const float* cf = coef + 9 * (size_t)q;
-    for (int ch = 0; ch < 3; ++ch) g[ch] += e * (cf[3 * ch] + cf[3 * ch + 1] * x[ch] + cf[3 * ch + 2] * y[ch]);
-  }
-  for (int ch = 0; ch < 3; ++ch) {
-    const float d = x[ch] - y[ch];
-    const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-    dI[3 * (size_t)p + ch] = scale * ((1.f - lambda) * sgn - lambda * g[ch]);
-  }
+  float g[3];
+  hssim_pixel_grad(p, npix, I, Gt, T.idx, T.e, coef, scale, lambda, g);
+  for (int ch = 0; ch < 3; ++ch) dI[3 * (size_t)p + ch] = g[ch];
+}
+
+// The buffers the per-pixel gradient of one view reads: the window table's slot
+// arrays and, in the HSSIM workspace the forward wrote, the coefficients and the
+// float copy of the in-mask count.
+void hssim_bind(int k, const void* table, const void* ws, LossView* out) {
+  const HTable T = htable(const_cast<void*>(table), k);
+  const HSSIMWs L = hssim_layout(k);
+  const char* w = static_cast<const char*>(ws);
+  out->idx = T.idx;
+  out->e = T.e;
+  out->coef = reinterpret_cast<const float*>(w + L.coef);
+  out->nm = reinterpret_cast<const float*>(w + L.nmask + sizeof(double));
+  out->npix = (uint32_t)(12u << (2 * k));
 }
 
 }  // namespace hpxgs

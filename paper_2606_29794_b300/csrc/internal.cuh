@@ -47,6 +47,24 @@ struct ViewTable {
   ViewParams v[HPXGS_MAX_VIEWS];
 };
 
+// Inputs of the per-pixel L1 + HSSIM gradient of each view, read by the backward
+// blend of hpxgs_backward_hssim in place of a dL/dI map (kernel parameter space).
+struct LossView {
+  const float* I;          // rendered maps of the view [npix, 3]
+  const float* G;          // targets [npix, 3]
+  const uint32_t* idx;     // window table slots [8][npix]
+  const float* e;          // window table weights [8][npix]
+  const float* coef;       // per-window gradient coefficients [npix, 9] (HSSIM forward)
+  const float* nm;         // float in-mask count (HSSIM forward)
+  const float* dloss;      // dL/dloss of the view, or null for 1
+  uint32_t npix;
+};
+struct LossViews {
+  float lambda;
+  LossView v[HPXGS_MAX_VIEWS];
+};
+struct NoLossViews { float lambda; };
+
 // One record per (view, Gaussian): 4 x float4 = 64 bytes.
 //   r0 = (g.x, g.y, g.z, opacity)     g: unit direction of the centre, HEALPix frame
 //   r1 = (e1.x, e1.y, e1.z, conic_a)  e1: east tangent (increasing longitude)
@@ -100,6 +118,7 @@ bool valid_camera(const hpxgs_camera& cam);
 int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
                cudaStream_t stream, bool need_rho, ViewTable* vt);
 int num_sms();
+void hssim_bind(int k, const void* table, const void* ws, LossView* out);
 
 }  // namespace hpxgs
 

@@ -20,8 +20,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "hpx_math.cuh"
+#include "hssim_grad.cuh"
 #include "internal.cuh"
 
 using namespace hpx;
@@ -1140,16 +1142,20 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
 // ----------------------------------------------------------------------------
 // DEPTH adds the inverse-depth channel: ddepth is dL/dD per pixel, and the tenth
 // partial dL/d(1/r) per (view, Gaussian) goes to accum_d.
-template <int NT, int PPT, int BATCH, bool DEPTH = false, bool SPLIT = false>
+// LOSS takes dL/dI of each pixel from the L1 + HSSIM gradient of its view
+// (hssim_pixel_grad over the view's window table and the HSSIM forward's
+// coefficients) instead of a dL/dI map: the HSSIM backward runs in this prologue.
+template <int NT, int PPT, int BATCH, bool DEPTH = false, bool SPLIT = false, bool LOSS = false>
 __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bwd(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
                                                   const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
                                                   const uint32_t* __restrict__ flags, const uint32_t* __restrict__ mask,
                                                   const float* __restrict__ dmaps, const float* __restrict__ Tin,
                                                   const uint32_t* __restrict__ lastin, float* __restrict__ accum,
                                                   uint32_t* work, const uint32_t* __restrict__ gmask,
-                                                  const float* __restrict__ rdepth = nullptr,
-                                                  const float* __restrict__ ddepth = nullptr,
-                                                  float* __restrict__ accum_d = nullptr) {
+                                                  const float* __restrict__ rdepth,
+                                                  const float* __restrict__ ddepth,
+                                                  float* __restrict__ accum_d,
+                                                  const __grid_constant__ std::conditional_t<LOSS, LossViews, NoLossViews> lv) {
   constexpr int NW = NT / 32;
   constexpr int NA = HPXGS_NACC + (DEPTH ? 1 : 0);
   __shared__ float4 s_rec[BATCH][4];
@@ -1195,7 +1201,17 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
       lastp[q] = inm ? lastin[pg] : 0u;
       T[q] = inm ? Tin[pg] : 1.f;
       pv[q] = inm ? pix2vec_f32(vp.k, lp) : make_float3(0.f, 0.f, 1.f);
-      for (int c = 0; c < 3; ++c) dI[q][c] = inm ? dmaps[3 * pg + c] : 0.f;
+      if constexpr (LOSS) {
+        if (inm) {
+          const LossView& lw = lv.v[v];
+          const float scale = (lw.dloss ? *lw.dloss : 1.f) / (3.f * *lw.nm);
+          hssim_pixel_grad(lp, lw.npix, lw.I, lw.G, lw.idx, lw.e, lw.coef, scale, lv.lambda, dI[q]);
+        } else {
+          dI[q][0] = 0.f; dI[q][1] = 0.f; dI[q][2] = 0.f;
+        }
+      } else {
+        for (int c = 0; c < 3; ++c) dI[q][c] = inm ? dmaps[3 * pg + c] : 0.f;
+      }
       B[q] = T[q] * (dI[q][0] * vt.bg[0] + dI[q][1] * vt.bg[1] + dI[q][2] * vt.bg[2]);
       if (DEPTH) dDp[DEPTH ? q : 0] = inm ? ddepth[pg] : 0.f;
       mylast = max(mylast, lastp[q]);
@@ -1560,9 +1576,9 @@ static void launch_fwd(int bps, cudaStream_t s, Args... args) {
   auto fn = k_blend_fwd<NT, PPT, HPXGS_FWD_BATCH, DEPTH, SPLIT>;
   fn<<<blend_blocks((const void*)fn, NT, bps), NT, 0, s>>>(args...);
 }
-template <int NT, int PPT, bool DEPTH = false, bool SPLIT = false, typename... Args>
+template <int NT, int PPT, bool DEPTH = false, bool SPLIT = false, bool LOSS = false, typename... Args>
 static void launch_bwd(int bps, cudaStream_t s, Args... args) {
-  auto fn = k_blend_bwd<NT, PPT, 32, DEPTH, SPLIT>;
+  auto fn = k_blend_bwd<NT, PPT, 32, DEPTH, SPLIT, LOSS>;
   fn<<<blend_blocks((const void*)fn, NT, bps), NT, 0, s>>>(args...);
 }
 
@@ -1826,12 +1842,14 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
   return HPXGS_OK;
 }
 
-int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg, void* ws,
-                   size_t ws_bytes, int64_t cap, const float* dmaps, const float* T_final, const uint32_t* last,
-                   const float* ddepth, float* dmeans, float* dscales, float* drot, float* dopac, float* dsh,
-                   int32_t* status, hpxgs_stream_t stream) {
-  (void)status;
-  if (!check_gaussians(g) || !ws || !dmaps || !T_final || !last) return HPXGS_E_INVALID_ARG;
+}  // extern "C"
+
+// hpxgs_backward with dL/dI from a map (dmaps) or, with lv, from the views' L1 + HSSIM gradient.
+static int backward_impl(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+                         void* ws, size_t ws_bytes, int64_t cap, const float* dmaps, const LossViews* lv,
+                         const float* T_final, const uint32_t* last, const float* ddepth, float* dmeans,
+                         float* dscales, float* drot, float* dopac, float* dsh, hpxgs_stream_t stream) {
+  if (!check_gaussians(g) || !ws || !(dmaps || lv) || !T_final || !last) return HPXGS_E_INVALID_ARG;
   if (g->P > 0 && (!dmeans || !dscales || !drot || !dopac || !dsh)) return HPXGS_E_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   Layout L;
@@ -1868,9 +1886,15 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
     // several pixels per thread: the per-entry warp reduction then covers 32 * PPT pixels
     const int ppt = pick_ppt(b, cfg->bwd_ppt, false);
 #define BWD_BASE bps, s, *vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, gmask
-#define BWD_ARGS BWD_BASE, (const float*)nullptr, (const float*)nullptr, (float*)nullptr
-#define BWD_DEPTH_ARGS BWD_BASE, rdepth, ddepth, accum_d
-    if (split) {                                   // order-5 lists, quarters blended in the order-4 shapes
+#define BWD_ARGS BWD_BASE, (const float*)nullptr, (const float*)nullptr, (float*)nullptr, NoLossViews{0.f}
+#define BWD_DEPTH_ARGS BWD_BASE, rdepth, ddepth, accum_d, NoLossViews{0.f}
+#define BWD_LOSS_ARGS BWD_BASE, (const float*)nullptr, (const float*)nullptr, (float*)nullptr, *lv
+    if (lv) {                                      // each level's default shape
+      if (split) launch_bwd<64, 4, false, true, true>(BWD_LOSS_ARGS);
+      else if (b == 3) launch_bwd<32, 2, false, false, true>(BWD_LOSS_ARGS);
+      else if (b == 4) launch_bwd<64, 4, false, false, true>(BWD_LOSS_ARGS);
+      else launch_bwd<256, 4, false, false, true>(BWD_LOSS_ARGS);
+    } else if (split) {                                   // order-5 lists, quarters blended in the order-4 shapes
       if (ddepth) launch_bwd<64, 4, true, true>(BWD_DEPTH_ARGS);
       else if (pick_ppt(4, cfg->bwd_ppt, false) == 2) launch_bwd<128, 2, false, true>(BWD_ARGS);
       else if (pick_ppt(4, cfg->bwd_ppt, false) == 8) launch_bwd<32, 8, false, true>(BWD_ARGS);
@@ -1885,6 +1909,7 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
       else if (ppt == 8) launch_bwd<32, 8>(BWD_ARGS);
       else launch_bwd<64, 4>(BWD_ARGS);
     } else { if (ppt == 8) launch_bwd<128, 8>(BWD_ARGS); else launch_bwd<256, 4>(BWD_ARGS); }
+#undef BWD_LOSS_ARGS
 #undef BWD_DEPTH_ARGS
 #undef BWD_ARGS
 #undef BWD_BASE
@@ -1909,6 +1934,43 @@ int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews
   prof_end(HPXGS_STAGE_PREPROCESS_BWD, s);
   delete vt;
   return HPXGS_OK;
+}
+
+extern "C" {
+
+int hpxgs_backward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg, void* ws,
+                   size_t ws_bytes, int64_t cap, const float* dmaps, const float* T_final, const uint32_t* last,
+                   const float* ddepth, float* dmeans, float* dscales, float* drot, float* dopac, float* dsh,
+                   int32_t* status, hpxgs_stream_t stream) {
+  (void)status;
+  if (!dmaps) return HPXGS_E_INVALID_ARG;
+  return backward_impl(g, views, nviews, cfg, ws, ws_bytes, cap, dmaps, nullptr, T_final, last, ddepth, dmeans,
+                       dscales, drot, dopac, dsh, stream);
+}
+
+int hpxgs_backward_hssim(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,
+                         void* ws, size_t ws_bytes, int64_t cap, const hpxgs_loss_view* loss_views, float lambda,
+                         const float* T_final, const uint32_t* last, float* dmeans, float* dscales, float* drot,
+                         float* dopac, float* dsh, int32_t* status, hpxgs_stream_t stream) {
+  (void)status;
+  if (!loss_views || !views || nviews < 1 || nviews > HPXGS_MAX_VIEWS || !(lambda >= 0.f && lambda <= 1.f))
+    return HPXGS_E_INVALID_ARG;
+  LossViews* lv = new LossViews;
+  std::memset(lv, 0, sizeof(*lv));
+  lv->lambda = lambda;
+  for (int v = 0; v < nviews; ++v) {
+    const hpxgs_loss_view& l = loss_views[v];
+    const int k = views[v].nside_log2;
+    if (!l.maps || !l.targets || !l.table || !l.hssim_ws || k < 3 || k > 13) { delete lv; return HPXGS_E_INVALID_ARG; }
+    hssim_bind(k, l.table, l.hssim_ws, &lv->v[v]);
+    lv->v[v].I = l.maps;
+    lv->v[v].G = l.targets;
+    lv->v[v].dloss = l.dloss;
+  }
+  const int rc = backward_impl(g, views, nviews, cfg, ws, ws_bytes, cap, nullptr, lv, T_final, last, nullptr, dmeans,
+                               dscales, drot, dopac, dsh, stream);
+  delete lv;
+  return rc;
 }
 
 int hpxgs_density_stats(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_config* cfg,

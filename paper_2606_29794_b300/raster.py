@@ -153,6 +153,25 @@ class Rasterizer:
                                        ctypes.c_void_p(_stream())), "backward")
         return dm, ds, dq, do, dsh
 
+    def backward_hssim_raw(self, state, loss_views, lam):
+        """Runs hpxgs_backward_hssim: the backward of the L1 + HSSIM loss of every view, with each
+        pixel's dL/dI formed inside the backward blend. loss_views: one (maps, targets, table,
+        hssim_ws, dloss or None) per view, after hpxgs_hssim_forward_table on the same stream."""
+        means, scales, rotations, opacities, sh = state["keep"]
+        lv = (L.LossView * len(loss_views))()
+        for i, (I, G, tab, hws, dl) in enumerate(loss_views):
+            lv[i].maps, lv[i].targets = I.data_ptr(), G.data_ptr()
+            lv[i].table, lv[i].hssim_ws = tab.data_ptr(), hws.data_ptr()
+            lv[i].dloss = dl.data_ptr() if dl is not None else None
+        dm, ds, dq, do, dsh = (torch.empty_like(t) for t in (means, scales, rotations, opacities, sh))
+        st = torch.zeros(1, dtype=torch.int32, device=means.device)
+        L.check(L.lib().hpxgs_backward_hssim(ctypes.byref(state["g"]), state["cviews"], state["nv"],
+                                             ctypes.byref(self.cfg), _ptr(state["ws"]), state["nb"], state["cap"], lv,
+                                             float(lam), _ptr(state["T"]), _ptr(state["last"]), _ptr(dm), _ptr(ds),
+                                             _ptr(dq), _ptr(do), _ptr(dsh), _ptr(st), ctypes.c_void_p(_stream())),
+                "backward_hssim")
+        return dm, ds, dq, do, dsh
+
     def density_stats(self, state, rs_max, grad_accum, vis_count, angular=None):
         """Radian-space density statistics (Sec. 4.2) after backward_raw on `state`: updates the
         per-Gaussian buffers rs_max (float32 [P]), grad_accum (float32 [P]) and vis_count (int32 [P])
@@ -289,15 +308,19 @@ class GraphStep:
     `launches_per_replay` is the number of library kernels in the graph.
     With `host_targets` (a pinned host tensor shaped like `targets`) every
     replay first copies it into `targets`, on a forked stream that overlaps the
-    forward render; the loss waits for the copy."""
+    forward render; the loss waits for the copy.
+    With `fused` (the default) the loss backward runs inside the render backward
+    (hpxgs_backward_hssim): each pixel's dL/dI is formed where the backward blend reads
+    it instead of going through a dL/dmaps buffer."""
 
     def __init__(self, params, sh_degree, views, targets, rasterizer: Rasterizer, lam=0.2, headroom=1.25,
-                 before_capture=None, host_targets=None):
+                 before_capture=None, host_targets=None, fused=True):
         self.params = [p.contiguous() for p in params]
         self.views = list(views)
         self.targets = targets.contiguous()
         self.rast = rasterizer
         self.lam = lam
+        self.fused = fused
         self.sh_degree = sh_degree
         dev = self.params[0].device
         rasterizer.prepare(self.views)
@@ -354,6 +377,8 @@ class GraphStep:
         if self.host_targets is not None:
             cur.wait_stream(self.side)
         st = _stream()
+        fused = self.fused and self.tables is not None
+        loss_views = []
         for vi, (k, base) in enumerate(zip(self.order, self.lay.pix_base)):
             n = npix(k)
             I = out["maps"][base:base + n]
@@ -365,6 +390,9 @@ class GraphStep:
                 L.check(L.lib().hpxgs_hssim_forward_table(_ptr(I), _ptr(G), _ptr(m), k, float(self.lam), _ptr(tab),
                                                           _ptr(ws), nb, _ptr(self.losses[vi]), ctypes.c_void_p(st)),
                         "hssim fwd")
+                if fused:
+                    loss_views.append((I, G, tab, ws, None))
+                    continue
                 L.check(L.lib().hpxgs_hssim_backward_table(_ptr(I), _ptr(G), _ptr(m), k, float(self.lam), _ptr(tab),
                                                            _ptr(ws), nb, None, _ptr(self.dmaps[base:base + n]),
                                                            ctypes.c_void_p(st)), "hssim bwd")
@@ -374,14 +402,18 @@ class GraphStep:
                 L.check(L.lib().hpxgs_hssim_backward(_ptr(I), _ptr(G), _ptr(m), k, float(self.lam), _ptr(ws), nb,
                                                      None, _ptr(self.dmaps[base:base + n]), ctypes.c_void_p(st)),
                         "hssim bwd")
-        self.grads = self.rast.backward_raw(state, self.dmaps)
+        if fused:
+            self.grads = self.rast.backward_hssim_raw(state, loss_views, self.lam)
+        else:
+            self.grads = self.rast.backward_raw(state, self.dmaps)
         self.out = out
         self.state = state
 
     def _build_tables(self):
         cache, per_view = {}, []
         for vi, (v, k, base) in enumerate(zip(self.views, self.order, self.lay.pix_base)):
-            key = (k, int(v["cam"]), float(v.get("fov_x", 360.0)), float(v.get("fov_y") or v.get("fov_x", 360.0)))
+            key = (k, int(v["cam"]), float(v.get("fov_x", 360.0)), float(v.get("fov_y") or v.get("fov_x", 360.0)),
+                   tuple(float(x) for x in v.get("pp", (0.0, 0.0))))
             if key not in cache:
                 m = self.out["mask"][base // 32:(base + npix(k)) // 32]
                 cache[key] = hssim_table(m, k)

@@ -68,6 +68,14 @@ def test_host_argument_checks(lib):
         assert lib.hpxgs_forward_workspace_size(1000, vv, 1, ctypes.byref(cfg), 10000, ctypes.byref(n)) == rc, (cam, pp)
     assert lib.hpxgs_forward_workspace_size(1000, v, 1, ctypes.byref(cfg), -5, ctypes.byref(n)) == L.E_INVALID_ARG
     assert lib.hpxgs_forward_workspace_size(1000, v, 0, ctypes.byref(cfg), 10, ctypes.byref(n)) == L.E_INVALID_ARG
+    # the fused loss backward checks its loss views and lambda before any launch
+    g0 = L.Gaussians(); g0.P = 0; g0.sh_degree = 0
+    lv = (L.LossView * 1)()
+    args = lambda lvs, lam: (ctypes.byref(g0), v, 1, ctypes.byref(cfg), ctypes.c_void_p(8), 1 << 20, 100, lvs, lam,
+                             ctypes.c_void_p(8), ctypes.c_void_p(8), None, None, None, None, None, None, None)
+    assert lib.hpxgs_backward_hssim(*args(None, 0.2)) == L.E_INVALID_ARG
+    assert lib.hpxgs_backward_hssim(*args(lv, 0.2)) == L.E_INVALID_ARG          # null maps / table / workspace
+    assert lib.hpxgs_backward_hssim(*args(lv, 1.5)) == L.E_INVALID_ARG
     # null required pointers are rejected before any launch
     g = L.Gaussians(); g.P = 10; g.sh_degree = 0
     assert lib.hpxgs_forward(ctypes.byref(g), v, 1, ctypes.byref(cfg), None, 0, 0, None, None, None, None, None, None,

@@ -154,3 +154,67 @@ def test_graph_step_with_host_targets_matches_device_targets():
     l3, _ = host_step.replay()
     torch.cuda.synchronize()
     assert not torch.equal(l3, l2)
+
+
+@pytest.mark.parametrize("tile_level,views", [(5, "fisheye"), (4, "mixed"), (3, "fisheye")])
+def test_fused_loss_backward_equals_two_pass(tile_level, views):
+    # hpxgs_backward_hssim (dL/dI formed inside the backward blend) against the HSSIM
+    # backward writing dL/dmaps followed by hpxgs_backward: same losses, gradients equal
+    # up to the order of the atomic sums
+    sc = S.make_scene(20000, 3, seed=61)
+    vs = [S.make_view(7, S.CAM_FISHEYE, 190.0)] if views == "fisheye" else _views(5)
+    params = scene_tensors(sc)
+    lay = R.view_layout(vs)
+    g = torch.Generator().manual_seed(62)
+    tgt = torch.rand((lay.total_pix, 3), generator=g).cuda()
+    res = []
+    for fused in (True, False):
+        st = R.GraphStep(params, 3, vs, tgt, R.Rasterizer(tile_level=tile_level), fused=fused)
+        losses, grads = st.replay()
+        torch.cuda.synchronize()
+        assert int(st.status.item()) == 0
+        res.append((losses.clone(), [x.clone() for x in grads], st.launches_per_replay))
+    (l1, g1, n1), (l0, g0, n0) = res
+    assert torch.equal(l1, l0)
+    assert n1 == n0 - len(vs)                          # one HSSIM backward launch fewer per view
+    for a, b in zip(g1, g0):
+        assert float((a - b).norm()) <= 1e-4 * float(b.norm()) + 1e-12
+        assert float((a - b).abs().max()) <= 1e-3 * float(b.abs().max()) + 1e-12
+
+
+def test_fused_loss_backward_direct_with_dloss():
+    # the C ABI call with a per-view dL/dloss against the two-pass path with the same scale
+    import ctypes
+    from paper_2606_29794_b300 import _lib as L
+    sc = S.make_scene(15000, 3, seed=63)
+    vs = _views(6)
+    params = scene_tensors(sc)
+    lay = R.view_layout(vs)
+    tgt = torch.rand((lay.total_pix, 3), generator=torch.Generator().manual_seed(64)).cuda()
+    rast = R.Rasterizer()
+    out, state = rast.forward_raw(*params, 3, vs)
+    dl = torch.tensor([0.5, 2.0, 1.25], device="cuda")
+    dmaps = torch.zeros((lay.total_pix, 3), device="cuda")
+    loss_views = []
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for vi, (v, base) in enumerate(zip(vs, lay.pix_base)):
+        k = v["nside_log2"]
+        n = R.npix(k)
+        I, G = out["maps"][base:base + n], tgt[base:base + n]
+        m = out["mask"][base // 32:(base + n) // 32]
+        tab = R.hssim_table(m, k)
+        nb = ctypes.c_size_t()
+        L.check(L.lib().hpxgs_hssim_workspace_size(k, ctypes.byref(nb)), "ws")
+        ws = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+        l3 = torch.empty(3, device="cuda")
+        p = lambda t: ctypes.c_void_p(t.data_ptr())
+        L.check(L.lib().hpxgs_hssim_forward_table(p(I), p(G), p(m), k, 0.2, p(tab), p(ws), nb.value, p(l3), s), "f")
+        L.check(L.lib().hpxgs_hssim_backward_table(p(I), p(G), p(m), k, 0.2, p(tab), p(ws), nb.value, p(dl[vi:vi + 1]),
+                                                   p(dmaps[base:base + n]), s), "b")
+        loss_views.append((I, G, tab, ws, dl[vi:vi + 1]))
+    ref = rast.backward_raw(state, dmaps)
+    got = rast.backward_hssim_raw(state, loss_views, 0.2)
+    torch.cuda.synchronize()
+    for a, b in zip(got, ref):
+        assert float((a - b).norm()) <= 1e-4 * float(b.norm()) + 1e-12
+        assert float((a - b).abs().max()) <= 1e-3 * float(b.abs().max()) + 1e-12
