@@ -50,7 +50,8 @@ static HSSIMWs hssim_layout(int k) {
   return L;
 }
 
-__device__ __forceinline__ void block_partials(float h, float l1, uint32_t cnt, HPart* __restrict__ part) {
+__device__ __forceinline__ void block_partials(float h, float l1, uint32_t cnt, HPart* __restrict__ part,
+                                               uint32_t slot) {
   for (int o = 16; o > 0; o >>= 1) {
     h += __shfl_xor_sync(0xffffffffu, h, o);
     l1 += __shfl_xor_sync(0xffffffffu, l1, o);
@@ -65,7 +66,7 @@ __device__ __forceinline__ void block_partials(float h, float l1, uint32_t cnt, 
     float a = 0.f, b = 0.f;
     uint32_t c = 0;
     for (int w2 = 0; w2 < kHThreads / 32; ++w2) { a += sh[0][w2]; b += sh[1][w2]; c += sc[w2]; }
-    part[blockIdx.x] = HPart{a, b, c, 0u};
+    part[slot] = HPart{a, b, c, 0u};
   }
 }
 
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_fwd(int k, const float* __r
     h = hs / 3.f;
     cnt = 1u;
   }
-  block_partials(h, l1, cnt, part);
+  block_partials(h, l1, cnt, part, blockIdx.x);
 }
 
 // Fixed-order sum of the block partials: per thread compensated (Kahan) FP32 sums of a
@@ -260,7 +261,11 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_fwd_t(int k, const float* _
                                                            const uint32_t* __restrict__ mask, HTable T,
                                                            float* __restrict__ coef, HPart* __restrict__ part) {
   const uint32_t npix = 12u << (2 * k);
-  const uint32_t p = blockIdx.x * kHThreads + threadIdx.x;
+  // pixel ranges in decreasing order: the backward blend that follows walks its units upwards
+  // from pixel 0, so the table rows, maps and coefficients it gathers first are the ones this
+  // kernel touched last (still in L2). Each range keeps its own partial slot (same loss bits).
+  const uint32_t blk = gridDim.x - 1u - blockIdx.x;
+  const uint32_t p = blk * kHThreads + threadIdx.x;
   float h = 0.f, l1 = 0.f;
   uint32_t cnt = 0;
   if (p < npix && mbit(mask, p)) {
@@ -300,7 +305,7 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_fwd_t(int k, const float* _
     h = hs / 3.f;
     cnt = 1u;
   }
-  block_partials(h, l1, cnt, part);
+  block_partials(h, l1, cnt, part, blk);
 }
 
 __global__ void __launch_bounds__(kHThreads) k_hssim_bwd_t(int k, const float* __restrict__ I, const float* __restrict__ Gt,
