@@ -1393,25 +1393,39 @@ __global__ void __launch_bounds__(kPreBwdThreads, HPXGS_PREBWD_MINB) k_preproces
   const int tid = threadIdx.x;
   const int i0 = blockIdx.x * kPreBwdThreads;
   const int nrow = min(kPreBwdThreads, vt.P - i0);
+  const int i = i0 + tid;
+  const bool own = i < vt.P;
+  // this thread's parameters and its first view's radius and partials, issued before the
+  // block's SH rows so that their latencies overlap
+  float mu[3] = {0.f, 0.f, 0.f}, scl[3] = {1.f, 1.f, 1.f}, rq[4] = {1.f, 0.f, 0.f, 0.f};
+  float rad = 0.f, A[HPXGS_NACC];
+  for (int c = 0; c < HPXGS_NACC; ++c) A[c] = 0.f;
+  if (own) {
+    for (int c = 0; c < 3; ++c) { mu[c] = gs.means[3 * (int64_t)i + c]; scl[c] = gs.scales[3 * (int64_t)i + c]; }
+    for (int c = 0; c < 4; ++c) rq[c] = gs.rotations[4 * (int64_t)i + c];
+    rad = radii[i];
+    for (int c = 0; c < HPXGS_NACC; ++c) A[c] = accum[(int64_t)i * HPXGS_NACC + c];
+  }
   for (int t = tid; t < nrow * 3 * K; t += kPreBwdThreads) {
     const int r = t / (3 * K), c = t - r * (3 * K);
     s_sh[r * RW + c] = gs.sh[(int64_t)i0 * 3 * K + t];
     s_dsh[r * RW + c] = 0.f;
   }
   __syncthreads();
-  const int i = i0 + tid;
-  if (i < vt.P) {
+  if (own) {
   float dmu[3] = {0.f, 0.f, 0.f}, ds[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f}, dop = 0.f;
-  const float* mu = gs.means + 3 * (int64_t)i;
   const float* sh = s_sh + tid * RW;
   float* dshl = s_dsh + tid * RW;
   for (int v = 0; v < vt.nviews; ++v) {
     const int64_t gid = (int64_t)v * vt.P + i;
-    if (!(radii[gid] > 0.f)) continue;
+    if (v > 0) {                                   // the view's radius and partials together
+      rad = radii[gid];
+      for (int c = 0; c < HPXGS_NACC; ++c) A[c] = accum[gid * HPXGS_NACC + c];
+    }
+    if (!(rad > 0.f)) continue;
     const ViewParams& vp = vt.v[v];
-    const float* A = accum + gid * HPXGS_NACC;
     Geo G;
-    geo_compute(vp, vt.near_plane, mu, gs.scales + 3 * (int64_t)i, gs.rotations + 4 * (int64_t)i, G);
+    geo_compute(vp, vt.near_plane, mu, scl, rq, G);
     if (!G.valid) continue;
     // colour -> SH and the viewing direction
     float dx = mu[0] - vp.cam[0], dy = mu[1] - vp.cam[1], dz = mu[2] - vp.cam[2];
