@@ -207,12 +207,14 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_bwd(int k, const float* __r
 // Window table: the window of a pixel depends only on the grid and the mask, not
 // on the maps, so it can be built once per (order, mask) and reused by every
 // forward and backward that uses that mask. Per pixel p, structure of arrays:
-// idx[s][p] and e[s][p] for the up to 8 in-mask neighbours in the walk order of
-// k_hssim_fwd (unused slots: idx = p, e = 0), and iZ[p] = 1 / (1 + sum e). The
-// weights come from the same pair_weight calls in the same order, and an unused
-// slot adds an exact zero, so the table kernels give the results of
-// k_hssim_fwd / k_hssim_bwd bit for bit while skipping the neighbour walk,
-// the pixel centres and the transcendental weights.
+// e[s][p], the weight towards walk direction s (window_dx/dy), 0 where that
+// neighbour is missing or outside the mask; idx[s][p], that neighbour (p where the
+// weight is 0), which the forward reads only on a face's edges (elsewhere the
+// interleaved-bit step gives it) and the gradient gathers read everywhere; and
+// iZ[p] = 1 / (1 + sum e). A zero-weight slot adds an exact zero. The weights come from the same
+// pair_weight calls in the same order and a zero weight is skipped, so the table
+// kernels give the results of k_hssim_fwd / k_hssim_bwd bit for bit while skipping
+// the neighbour walk, the pixel centres and the transcendental weights.
 // ----------------------------------------------------------------------------
 struct HTable {
   uint32_t* idx;   // [8][npix]
@@ -231,30 +233,23 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_table(int k, const uint32_t
   const uint32_t npix = 12u << (2 * k);
   const uint32_t p = blockIdx.x * kHThreads + threadIdx.x;
   if (p >= npix) return;
-  int n = 0;
   float Z = 1.f;                               // the pixel itself, e_pp = 1
-  if (mbit(mask, p)) {
-    const float omega = 4.f * (float)kPi / (float)npix;
-    const float inv2sig2 = 1.f / (2.f * 2.25f * omega);
-    const float3 cq = pix2vec_f32(k, p);
-    const FaceXY c = nest_to_fxy(k, p);
-    float w[8];
-    for (int dx = -1; dx <= 1; ++dx)
-      for (int dy = -1; dy <= 1; ++dy) {
-        if (dx == 0 && dy == 0) continue;
-        const int64_t nb = neighbour_nest(k, c.f, c.x, c.y, dx, dy);
-        if (nb < 0 || !mbit(mask, (uint32_t)nb)) continue;
-        w[n] = pair_weight(cq, pix2vec_f32(k, (uint32_t)nb), inv2sig2);
-        T.idx[(size_t)n * npix + p] = (uint32_t)nb;
-        T.e[(size_t)n * npix + p] = w[n];
-        ++n;
-      }
-    for (int j = 0; j < n; ++j) Z += w[j];
-    T.iZ[p] = 1.f / Z;
-  } else {
-    T.iZ[p] = 0.f;
+  const bool in = mbit(mask, p);
+  const FaceXY c = nest_to_fxy(k, p);
+  const float omega = 4.f * (float)kPi / (float)npix;
+  const float inv2sig2 = 1.f / (2.f * 2.25f * omega);
+  const float3 cq = pix2vec_f32(k, p);
+  for (int s = 0; s < 8; ++s) {                // the walk order: dx = -1, 0, 1, then dy
+    const int64_t nb = neighbour_nest(k, c.f, c.x, c.y, window_dx(s), window_dy(s));
+    float w = 0.f;
+    if (in && nb >= 0 && mbit(mask, (uint32_t)nb)) {
+      w = pair_weight(cq, pix2vec_f32(k, (uint32_t)nb), inv2sig2);
+      Z += w;
+    }
+    T.idx[(size_t)s * npix + p] = w != 0.f ? (uint32_t)nb : p;
+    T.e[(size_t)s * npix + p] = w;
   }
-  for (int j = n; j < 8; ++j) { T.idx[(size_t)j * npix + p] = p; T.e[(size_t)j * npix + p] = 0.f; }
+  T.iZ[p] = in ? 1.f / Z : 0.f;
 }
 
 __global__ void __launch_bounds__(kHThreads) k_hssim_fwd_t(int k, const float* __restrict__ I, const float* __restrict__ Gt,
@@ -270,10 +265,14 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_fwd_t(int k, const float* _
   uint32_t cnt = 0;
   if (p < npix && mbit(mask, p)) {
     const float iZ = T.iZ[p];
+    const WinStep wst(k, p);
     uint32_t q[8];
     float e[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) { q[j] = T.idx[(size_t)j * npix + p]; e[j] = T.e[(size_t)j * npix + p]; }
+    for (int j = 0; j < 8; ++j) {
+      e[j] = T.e[(size_t)j * npix + p];
+      q[j] = wst.interior ? wst.at(j) : T.idx[(size_t)j * npix + p];
+    }
     float hs = 0.f;
     for (int ch = 0; ch < 3; ++ch) {
       float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
@@ -284,6 +283,7 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_fwd_t(int k, const float* _
       }
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
+        if (e[j] == 0.f) continue;
         const float wj = e[j] * iZ;
         const float x = I[3 * (size_t)q[j] + ch], y = Gt[3 * (size_t)q[j] + ch];
         mx += wj * x; my += wj * y; xx += wj * x * x; yy += wj * y * y; xy += wj * x * y;

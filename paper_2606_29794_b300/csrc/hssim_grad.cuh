@@ -7,11 +7,42 @@
 
 namespace hpxgs {
 
-// Window-table gradient at in-mask pixel p of a map with npix pixels:
-//   g_c = cf(p) + sum_s e_s(p) cf(idx_s(p)),  cf(q) = alpha_c(q) + beta_c(q) x_c(p) + gamma_c(q) y_c(p)
+// Window directions (dx, dy) in the order of the neighbour walk (dx = -1, 0, 1, then dy):
+// slot s of the window table belongs to direction s.
+__host__ __device__ __forceinline__ int window_dx(int s) { return s < 3 ? -1 : (s < 5 ? 0 : 1); }
+__host__ __device__ __forceinline__ int window_dy(int s) { return (s == 0 || s == 3 || s == 5) ? -1 : ((s == 1 || s == 6) ? 0 : 1); }
+
+// Neighbours of a pixel away from its face's edges, on the interleaved bits of the NESTED
+// index (x in the even bits, y in the odd ones): with MX the x bits and MY the y bits,
+// x + 1 = ((q | MY) + 1) & MX (the carry runs through the y gaps) and x - 1 = ((q & MX) - 1) & MX.
+// `interior` is false on the face's edges, where the table's ids are used instead
+// (the HSSIM forward takes this step; the backward gathers read the ids).
+struct WinStep {
+  uint32_t MX, MY, qx, qy, face;
+  bool interior;
+  __device__ __forceinline__ WinStep(int k, uint32_t p) {
+    const uint32_t fm = (1u << (2 * k)) - 1u;
+    MX = 0x55555555u & fm;
+    MY = MX << 1;
+    qx = p & MX;
+    qy = p & MY;
+    face = p & ~fm;
+    interior = qx != 0u && qx != MX && qy != 0u && qy != MY;
+  }
+  __device__ __forceinline__ uint32_t at(int s) const {
+    const int dx = window_dx(s), dy = window_dy(s);
+    const uint32_t nx = dx > 0 ? (((qx | MY) + 1u) & MX) : (dx < 0 ? ((qx - 1u) & MX) : qx);
+    const uint32_t ny = dy > 0 ? (((qy | MX) + 1u) & MY) : (dy < 0 ? ((qy - 1u) & MY) : qy);
+    return face | nx | ny;
+  }
+};
+
+// Window-table gradient at in-mask pixel p of an order-k map with npix pixels:
+//   g_c = cf(p) + sum_s e_s(p) cf(n_s(p)),  cf(q) = alpha_c(q) + beta_c(q) x_c(p) + gamma_c(q) y_c(p)
 // (coefficients of the forward per window, divided by its weight sum), then
 //   dL/dI_c(p) = scale ((1 - lambda) sign(x_c - y_c) - lambda g_c),  scale = dL/dloss / (3 |M|).
-// idx/e are the table's slot arrays [8][npix] (unused slots: idx = p, e = 0).
+// idx/e are the table's arrays [8][npix] by walk direction; where that neighbour is missing
+// or outside the mask, e = 0 and idx = p, so the term adds an exact zero.
 __device__ __forceinline__ void hssim_pixel_grad(uint32_t p, uint32_t npix, const float* __restrict__ I,
                                                  const float* __restrict__ Gt, const uint32_t* __restrict__ idx,
                                                  const float* __restrict__ e, const float* __restrict__ coef,

@@ -52,8 +52,8 @@ struct ViewTable {
 struct LossView {
   const float* I;          // rendered maps of the view [npix, 3]
   const float* G;          // targets [npix, 3]
-  const uint32_t* idx;     // window table slots [8][npix]
-  const float* e;          // window table weights [8][npix]
+  const uint32_t* idx;     // window table neighbours [8][npix] by walk direction
+  const float* e;          // window table weights [8][npix] by walk direction
   const float* coef;       // per-window gradient coefficients [npix, 9] (HSSIM forward)
   const float* nm;         // float in-mask count (HSSIM forward)
   const float* dloss;      // dL/dloss of the view, or null for 1
