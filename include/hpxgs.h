@@ -407,8 +407,10 @@ int hpxgs_hssim_backward(const float* I, const float* G, const uint32_t* mask_bi
                          hpxgs_stream_t stream);
 /* Window table of (order k, mask): the neighbour walk and the window weights of
  * every pixel (Sec. 4.1), which depend on the grid and the mask only, stored so
- * that forward and backward skip them: [8][Npix] neighbour ids, [8][Npix]
- * weights, [Npix] 1 / window sum (68 bytes per pixel, caller-owned device
+ * that forward and backward skip them: [8][Npix] neighbour ids and [8][Npix]
+ * weights by neighbour direction (weight 0 and the pixel's own id where that
+ * neighbour is missing or outside the mask), [Npix] 1 / window sum (68 bytes per
+ * pixel, caller-owned device
  * memory of at least hpxgs_hssim_table_size bytes). Build it once per mask; the
  * *_table calls give the results of hpxgs_hssim_forward / _backward bit for bit
  * when given the same mask. A mask depends on the camera's intrinsics only, so
