@@ -40,6 +40,21 @@ def test_strerror_and_status(lib):
     assert lib.hpxgs_status_error(0) == 0
 
 
+def test_profile_arm_and_armed(lib):
+    # arming records the events at the stage's next run; a stage that never ran stays armed
+    # (host-side bookkeeping only: no event is recorded without a launch)
+    st = L.STAGES.index("hssim_bwd")
+    assert lib.hpxgs_profile_armed(st) in (0, 1)
+    assert lib.hpxgs_profile_arm(st, ctypes.c_void_p(0x10), ctypes.c_void_p(0x20)) == 0
+    try:                                   # placeholder handles: never leave them armed
+        assert lib.hpxgs_profile_armed(st) == 1
+    finally:
+        assert lib.hpxgs_profile_arm(st, None, None) == 0
+    assert lib.hpxgs_profile_armed(st) == 0
+    assert lib.hpxgs_profile_armed(len(L.STAGES)) == L.E_INVALID_ARG
+    assert lib.hpxgs_profile_armed(-1) == L.E_INVALID_ARG
+
+
 def test_adaptive_nside(lib):
     ns = ctypes.c_double(); k = ctypes.c_int(); kl = ctypes.c_int(); kh = ctypes.c_int()
     assert lib.hpxgs_nside_for_image(0, 6080, 3040, 360, 360, ctypes.byref(ns), ctypes.byref(k), ctypes.byref(kl),
