@@ -1608,6 +1608,8 @@ static int pick_ppt(int b, int want, bool fwd) {
   return opts[0];
 }
 
+constexpr int kBatchFwd = 128;
+constexpr int kBatchBwd = 32;
 
 static bool check_gaussians(const hpxgs_gaussians* g) {
   if (!g || g->P < 0 || g->sh_degree < 0 || g->sh_degree > 3) return false;
