@@ -177,6 +177,12 @@ int hpxgs_mask_build(const hpxgs_view* view, const hpxgs_config* cfg, uint32_t* 
 int hpxgs_pix2vec_nest(int k, const int64_t* pix, int64_t n, float* vec32, double* vec64, hpxgs_stream_t stream);
 /* NESTED pixel containing each direction (FP64 input, need not be normalised). */
 int hpxgs_vec2pix_nest(int k, const double* vec, int64_t n, int64_t* pix, hpxgs_stream_t stream);
+/* Pixel centre angles of NESTED pixels (Sec. 3.1): colatitude theta in [0, pi] and longitude
+ * phi in [0, 2 pi) of the HEALPix frame, FP64. */
+int hpxgs_pix2ang_nest(int k, const int64_t* pix, int64_t n, double* theta, double* phi, hpxgs_stream_t stream);
+/* NESTED pixel containing the direction (theta, phi) (FP64; the vec2pix construction of
+ * the unit vector (sin theta cos phi, sin theta sin phi, cos theta)). */
+int hpxgs_ang2pix_nest(int k, const double* theta, const double* phi, int64_t n, int64_t* pix, hpxgs_stream_t stream);
 /* NESTED <-> RING index conversion. */
 int hpxgs_nest2ring(int k, const int64_t* in, int64_t n, int64_t* out, hpxgs_stream_t stream);
 int hpxgs_ring2nest(int k, const int64_t* in, int64_t n, int64_t* out, hpxgs_stream_t stream);

@@ -88,6 +88,8 @@ _SIGS = {
     "hpxgs_mask_build": (ctypes.c_int, [_P(View), _P(Config), _vp, _vp]),
     "hpxgs_pix2vec_nest": (ctypes.c_int, [ctypes.c_int, _vp, _i64, _vp, _vp, _vp]),
     "hpxgs_vec2pix_nest": (ctypes.c_int, [ctypes.c_int, _vp, _i64, _vp, _vp]),
+    "hpxgs_pix2ang_nest": (ctypes.c_int, [ctypes.c_int, _vp, _i64, _vp, _vp, _vp]),
+    "hpxgs_ang2pix_nest": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _i64, _vp, _vp]),
     "hpxgs_nest2ring": (ctypes.c_int, [ctypes.c_int, _vp, _i64, _vp, _vp]),
     "hpxgs_ring2nest": (ctypes.c_int, [ctypes.c_int, _vp, _i64, _vp, _vp]),
     "hpxgs_neighbours_nest": (ctypes.c_int, [ctypes.c_int, _vp, _i64, _vp, _vp]),

@@ -398,6 +398,24 @@ __global__ void k_vec2pix(int k, const double* v, int64_t n, int64_t* pix) {
   if (i >= n) return;
   pix[i] = vec2pix_f64(k, make_double3(v[3 * i], v[3 * i + 1], v[3 * i + 2]));
 }
+// Angles of a direction: colatitude theta = atan2(sqrt(x^2 + y^2), z), longitude
+// phi = atan2(y, x) in [0, 2 pi) (HEALPix frame).
+__global__ void k_pix2ang(int k, const int64_t* pix, int64_t n, double* theta, double* phi) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double3 a = pix2vec_f64(k, (uint32_t)pix[i]);
+  theta[i] = atan2(sqrt(a.x * a.x + a.y * a.y), a.z);
+  double ph = atan2(a.y, a.x);
+  phi[i] = ph < 0.0 ? ph + 2.0 * kPi : ph;
+}
+__global__ void k_ang2pix(int k, const double* theta, const double* phi, int64_t n, int64_t* pix) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double st, ct, sp, cp;
+  sincos(theta[i], &st, &ct);
+  sincos(phi[i], &sp, &cp);
+  pix[i] = vec2pix_f64(k, make_double3(st * cp, st * sp, ct));
+}
 __global__ void k_nest2ring(int k, const int64_t* in, int64_t n, int64_t* out) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) out[i] = nest2ring(k, (uint32_t)in[i]);
@@ -539,6 +557,22 @@ int hpxgs_vec2pix_nest(int k, const double* v, int64_t n, int64_t* pix, hpxgs_st
   if (k < 0 || k > 13 || n < 0 || (n > 0 && (!v || !pix))) return HPXGS_E_INVALID_ARG;
   if (n == 0) return HPXGS_OK;
   k_vec2pix<<<grid_for(n), 256, 0, (cudaStream_t)s>>>(k, v, n, pix);
+  note_launches(1);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+int hpxgs_pix2ang_nest(int k, const int64_t* pix, int64_t n, double* theta, double* phi, hpxgs_stream_t s) {
+  if (k < 0 || k > 13 || n < 0 || (n > 0 && (!pix || !theta || !phi))) return HPXGS_E_INVALID_ARG;
+  if (n == 0) return HPXGS_OK;
+  k_pix2ang<<<grid_for(n), 256, 0, (cudaStream_t)s>>>(k, pix, n, theta, phi);
+  note_launches(1);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+int hpxgs_ang2pix_nest(int k, const double* theta, const double* phi, int64_t n, int64_t* pix, hpxgs_stream_t s) {
+  if (k < 0 || k > 13 || n < 0 || (n > 0 && (!theta || !phi || !pix))) return HPXGS_E_INVALID_ARG;
+  if (n == 0) return HPXGS_OK;
+  k_ang2pix<<<grid_for(n), 256, 0, (cudaStream_t)s>>>(k, theta, phi, n, pix);
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
   return HPXGS_OK;

@@ -26,6 +26,35 @@ def _p(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+@pytest.mark.parametrize("k", [0, 3, 9, 13])
+def test_pix2ang_and_ang2pix_match_oracle(k):
+    nside = 2 ** k
+    n = min(12 * nside * nside, 200_000)
+    rng = np.random.default_rng(k + 40)
+    pix = np.sort(rng.choice(12 * nside * nside, n, replace=False)).astype(np.int64)
+    pg = torch.as_tensor(pix, device="cuda")
+    th = torch.empty(n, dtype=torch.float64, device="cuda")
+    ph = torch.empty(n, dtype=torch.float64, device="cuda")
+    L.check(L.lib().hpxgs_pix2ang_nest(k, _p(pg), n, _p(th), _p(ph), _s()), "pix2ang")
+    back = torch.empty(n, dtype=torch.int64, device="cuda")
+    L.check(L.lib().hpxgs_ang2pix_nest(k, _p(th), _p(ph), n, _p(back), _s()), "ang2pix")
+    # random directions
+    u = rng.random(n)
+    t2 = np.arccos(1 - 2 * u)
+    p2 = rng.random(n) * 2 * np.pi
+    got = torch.empty(n, dtype=torch.int64, device="cuda")
+    t2g, p2g = torch.as_tensor(t2, device="cuda"), torch.as_tensor(p2, device="cuda")   # held until the kernel ran
+    L.check(L.lib().hpxgs_ang2pix_nest(k, _p(t2g), _p(p2g), n, _p(got), _s()), "ang2pix random")
+    torch.cuda.synchronize()
+    tr, pr = O.pix2ang_nest(nside, pix)
+    assert np.abs(th.cpu().numpy() - tr).max() < 1e-12
+    dphi = np.abs(np.angle(np.exp(1j * (ph.cpu().numpy() - pr))))     # longitude modulo 2 pi
+    assert dphi.max() < 1e-12
+    assert np.all((ph.cpu().numpy() >= 0) & (ph.cpu().numpy() < 2 * np.pi))
+    assert np.array_equal(back.cpu().numpy(), pix)                     # centres map to their pixel
+    assert np.array_equal(got.cpu().numpy(), O.ang2pix_nest(nside, t2, p2))
+
+
 @pytest.mark.parametrize("k", [0, 1, 3, 6, 9, 11])
 def test_pix2vec_and_roundtrip(k):
     n = 12 * 4 ** k
