@@ -267,6 +267,65 @@ def hssim_loss(I, G, mask_words, k, lam=0.2):
     return _HSSIMFn.apply(I, G, mask_words, k, lam)
 
 
+class _RenderLossFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, scales, rotations, opacities, sh, targets, rast, views, sh_degree, lam):
+        out, state = rast.forward_raw(means, scales, rotations, opacities, sh, sh_degree, views)
+        lay = view_layout(views, rast.cfg.tile_level)
+        G = _f32(targets)
+        parts = torch.empty((len(views), 3), dtype=torch.float32, device=means.device)
+        loss_views = []
+        for vi, (v, base) in enumerate(zip(views, lay.pix_base)):
+            k = v["nside_log2"]
+            n = npix(k)
+            I, Gv = out["maps"][base:base + n], G[base:base + n]
+            m = out["mask"][base // 32:(base + n) // 32]
+            tab = _window_table(rast, v, m)
+            nb = ctypes.c_size_t()
+            L.check(L.lib().hpxgs_hssim_workspace_size(k, ctypes.byref(nb)), "hssim workspace")
+            ws = torch.empty(nb.value, dtype=torch.uint8, device=means.device)
+            L.check(L.lib().hpxgs_hssim_forward_table(_ptr(I), _ptr(Gv), _ptr(m), k, float(lam), _ptr(tab), _ptr(ws),
+                                                      nb.value, _ptr(parts[vi]), ctypes.c_void_p(_stream())),
+                    "hssim forward")
+            loss_views.append((I, Gv, tab, ws))
+        ctx.rast, ctx.state, ctx.loss_views, ctx.lam = rast, state, loss_views, lam
+        ctx.mark_non_differentiable(parts)
+        return parts[:, 0].sum(), parts
+
+    @staticmethod
+    def backward(ctx, gloss, gparts):
+        dev = ctx.state["T"].device
+        dl = _f32(gloss.reshape(1)) if gloss is not None else torch.ones(1, device=dev)
+        grads = ctx.rast.backward_hssim_raw(ctx.state, [(I, G, tab, ws, dl) for I, G, tab, ws in ctx.loss_views],
+                                            ctx.lam)
+        ctx.state, ctx.loss_views = None, None
+        return (*grads, None, None, None, None, None)
+
+
+def _window_table(rast: Rasterizer, view, mask_words):
+    """HSSIM window table of a view's order and mask; a mask depends on the camera's
+    intrinsics only, so tables are kept per (order, camera) on the rasterizer."""
+    key = (int(view["nside_log2"]), int(view.get("cam", L.CAM_FULL)), float(view.get("fov_x", 360.0)),
+           float(view.get("fov_y") or view.get("fov_x", 360.0)), tuple(float(x) for x in view.get("pp", (0.0, 0.0))))
+    cache = rast.__dict__.setdefault("_tables", {})
+    if key not in cache:
+        cache[key] = hssim_table(mask_words, key[0])
+    return cache[key]
+
+
+def render_loss(means, scales, rotations, opacities, sh, views, targets, rasterizer: Rasterizer | None = None,
+                sh_degree=None, lam=0.2):
+    """The training loss of Sec. 4.1 summed over `views`: sum_v (1 - lam) L1_v + lam (1 - HSSIM_v)
+    against `targets` (packed like the maps), with the render and loss backward in one pass
+    (hpxgs_backward_hssim: each pixel's dL/dI is formed inside the backward blend). Returns
+    (loss, per-view [loss, HSSIM, L1]); the same values and gradients as render + hssim_loss
+    per view, up to the order of the atomic sums."""
+    rast = rasterizer or Rasterizer()
+    if sh_degree is None:
+        sh_degree = int(round(math.sqrt(sh.shape[1]))) - 1
+    return _RenderLossFn.apply(means, scales, rotations, opacities, sh, targets, rast, list(views), sh_degree, lam)
+
+
 def workspace_view(rast: Rasterizer, state) -> L.WorkspaceView:
     out = L.WorkspaceView()
     L.check(L.lib().hpxgs_workspace_inspect(state["g"].P, state["cviews"], state["nv"], ctypes.byref(rast.cfg),

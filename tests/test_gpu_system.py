@@ -218,3 +218,32 @@ def test_fused_loss_backward_direct_with_dloss():
     for a, b in zip(got, ref):
         assert float((a - b).norm()) <= 1e-4 * float(b.norm()) + 1e-12
         assert float((a - b).abs().max()) <= 1e-3 * float(b.abs().max()) + 1e-12
+
+
+def test_render_loss_autograd_equals_render_then_loss():
+    # the one-pass autograd loss (hpxgs_backward_hssim) against render + hssim_loss per view,
+    # summed; a scaled loss scales the gradients
+    sc = S.make_scene(20000, 3, seed=65)
+    vs = _views(7)
+    lay = R.view_layout(vs)
+    tgt = torch.rand((lay.total_pix, 3), generator=torch.Generator().manual_seed(66)).cuda()
+    base = scene_tensors(sc)
+    ps = [p.clone().requires_grad_(True) for p in base]
+    rast = R.Rasterizer()
+    loss, parts = R.render_loss(*ps, vs, tgt, rasterizer=rast, sh_degree=3)
+    (2.5 * loss).backward()
+    g_fused = [p.grad.clone() for p in ps]
+    qs = [p.clone().requires_grad_(True) for p in base]
+    maps, T, last, mask, radii = R.render(*qs, vs, rasterizer=R.Rasterizer(), sh_degree=3)
+    total = 0
+    for vi, (v, b0) in enumerate(zip(vs, lay.pix_base)):
+        n = R.npix(v["nside_log2"])
+        lv, pv = R.hssim_loss(maps[b0:b0 + n], tgt[b0:b0 + n], mask[b0 // 32:(b0 + n) // 32], v["nside_log2"], 0.2)
+        assert torch.equal(pv, parts[vi])                      # table and direct HSSIM forward agree bit for bit
+        total = total + lv
+    assert torch.allclose(total, loss, rtol=1e-6, atol=0)
+    (2.5 * total).backward()
+    for a, q in zip(g_fused, qs):
+        c = q.grad
+        assert float((a - c).double().norm()) <= 1e-4 * float(c.double().norm()) + 1e-12
+        assert float((a - c).abs().max()) <= 1e-3 * float(c.abs().max()) + 1e-12
