@@ -1,0 +1,130 @@
+"""Host-side policy of the continuous-batching server, on the CPU.
+
+RenderServer.run admits waiting requests in arrival order into batches bounded by
+views, pixels and the memory budget, keeps up to `slots` batches in flight, and
+renders a batch again when its tile lists overflowed the predicted capacity. Here
+the device work is replaced by fakes (a launch returns a completion event that
+fires after a fixed time and a status word that reports an overflow whenever the
+capacity is below the true pair count), so the admission, memory accounting and
+re-run logic run as they do on the GPU. The memory model itself (workspace sizes)
+is the library's host-side size query.
+"""
+import time
+
+import pytest
+import torch
+
+from paper_2606_29794_b300 import _lib as L
+from paper_2606_29794_b300 import raster as R
+from paper_2606_29794_b300 import serve as SV
+from paper_2606_29794_b300 import synth as S
+
+
+class _Event:
+    def __init__(self, seconds):
+        self.t = time.perf_counter() + seconds
+
+    def query(self):
+        return time.perf_counter() >= self.t
+
+
+def _px(views):
+    return sum(R.npix(v["nside_log2"]) for v in views)
+
+
+def _server(budget, slots=3, max_views=4, max_pixels=64 << 20, ppx=2.0, first_count=1.0, run_s=2e-3):
+    """A RenderServer without a device: the scene has 100k Gaussians, a view of n pixels
+    really lists ppx * n pairs, and the first count of a request kind reports
+    first_count times that."""
+    srv = object.__new__(SV.RenderServer)
+    srv.sh_degree, srv.budget, srv.slots = 0, int(budget), slots
+    srv.max_views, srv.max_pixels, srv.headroom = max_views, max_pixels, 1.3
+    srv.tile_level, srv.adaptive = 0, True
+    srv.cfg_by_level = {b: L.default_config(tile_level=b) for b in (3, 4, 5)}
+    srv.cfg = srv.cfg_by_level[4]
+    srv.pairs_per_pixel = {}
+    srv.streams = [None] * slots
+    g = L.Gaussians()
+    g.P, g.sh_degree = 100_000, 0
+    srv.g = g
+    log = {"launches": []}
+
+    def count(views):
+        n = int(ppx * _px(views) * first_count)
+        srv._learn(views, n)
+        return n
+
+    def launch(views, cap, stream):
+        nb, _ = srv._batch_bytes(views, cap)
+        need = int(ppx * _px(views))
+        status = torch.tensor([L.F_CAPACITY if cap < need else 0], dtype=torch.int32)
+        log["launches"].append(dict(n=len(views), px=_px(views), cap=cap, need=need, bytes=nb))
+        return dict(views=views, cap=cap, status=status, event=_Event(run_s), bytes=nb,
+                    layout=R.view_layout(views, srv.cfg_by_level[srv.level_for(views)].tile_level))
+
+    srv._count = count
+    srv._launch = launch
+    srv._workspace_pairs = lambda job: int(ppx * _px(job["views"]))
+    return srv, log
+
+
+@pytest.fixture(autouse=True)
+def _no_device_sync(monkeypatch):
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+
+
+def _requests(n=40, rate=4000.0, seed=3, nsides=(5, 6, 7)):
+    return S.request_stream(n, rate_hz=rate, seed=seed, nside_choices=nsides)
+
+
+def test_batches_respect_views_pixels_and_budget():
+    reqs = _requests()
+    srv, log = _server(budget=256 << 20, max_views=4, max_pixels=150_000)
+    stats, results = srv.run(reqs, keep_outputs=True)
+    s = stats.summary()
+    assert s["served"] == len(reqs) and s["reruns"] == 0
+    assert sorted(results) == sorted(r["id"] for r in reqs)          # every request answered once
+    assert all(b["n"] <= 4 for b in log["launches"])
+    # a batch grows past one view only while its pixels stay within the limit
+    assert all(b["px"] <= 150_000 or b["n"] == 1 for b in log["launches"])
+    assert s["peak_budget_bytes"] <= 256 << 20
+    assert s["mean_batch"] > 1.0                                        # arrivals faster than service batch up
+    # the predicted capacity (learned density x headroom) covers every launch here
+    assert all(b["cap"] >= b["need"] for b in log["launches"])
+
+
+def test_plain_mode_serves_one_request_per_launch():
+    reqs = _requests(n=12)
+    srv, log = _server(budget=256 << 20)
+    stats, _ = srv.run(reqs, plain=True)
+    assert stats.summary()["served"] == 12
+    assert stats.summary()["mean_batch"] == 1.0
+    assert all(b["n"] == 1 for b in log["launches"])
+
+
+def test_tight_budget_admits_one_batch_at_a_time():
+    reqs = _requests(n=10, nsides=(7,))                                 # equal sizes: two never fit
+    srv, log = _server(budget=1 << 30)
+    one = max(srv._batch_bytes([r["view"]], int(2.0 * R.npix(r["view"]["nside_log2"]) * 1.3) + 4096)[0]
+              for r in reqs)
+    srv.budget = int(one * 1.05)                                         # room for any one request, not two
+    stats, _ = srv.run(reqs)
+    s = stats.summary()
+    assert s["served"] == 10
+    assert s["peak_budget_bytes"] <= srv.budget
+    assert all(b["n"] == 1 for b in log["launches"])
+
+
+def test_underpredicted_capacity_is_rendered_again_and_learned():
+    # the first count of each kind reports a third of the true pairs: the first batches of a
+    # kind overflow, are rendered again with the exact count, and later batches fit
+    reqs = _requests(n=30, seed=5)
+    srv, log = _server(budget=256 << 20, first_count=1.0 / 3.0)
+    stats, results = srv.run(reqs, keep_outputs=True)
+    s = stats.summary()
+    assert s["served"] == 30 and len(results) == 30
+    assert s["reruns"] > 0
+    over = [i for i, b in enumerate(log["launches"]) if b["cap"] < b["need"]]
+    assert over and over[-1] < len(log["launches"]) - 1                 # the last launches fit
+    for key, ppx in srv.pairs_per_pixel.items():
+        assert ppx >= 2.0 - 1e-9                                         # learned up to the true density
