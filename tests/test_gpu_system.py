@@ -156,8 +156,9 @@ def test_graph_step_with_host_targets_matches_device_targets():
     assert not torch.equal(l3, l2)
 
 
-@pytest.mark.parametrize("tile_level,views", [(5, "fisheye"), (4, "mixed"), (3, "fisheye")])
-def test_fused_loss_backward_equals_two_pass(tile_level, views):
+@pytest.mark.parametrize("tile_level,views,split", [(5, "fisheye", 1), (5, "fisheye", 0), (4, "mixed", 1),
+                                                    (3, "fisheye", 1)])
+def test_fused_loss_backward_equals_two_pass(tile_level, views, split):
     # hpxgs_backward_hssim (dL/dI formed inside the backward blend) against the HSSIM
     # backward writing dL/dmaps followed by hpxgs_backward: same losses, gradients equal
     # up to the order of the atomic sums
@@ -169,7 +170,7 @@ def test_fused_loss_backward_equals_two_pass(tile_level, views):
     tgt = torch.rand((lay.total_pix, 3), generator=g).cuda()
     res = []
     for fused in (True, False):
-        st = R.GraphStep(params, 3, vs, tgt, R.Rasterizer(tile_level=tile_level), fused=fused)
+        st = R.GraphStep(params, 3, vs, tgt, R.Rasterizer(tile_level=tile_level, blend_split=split), fused=fused)
         losses, grads = st.replay()
         torch.cuda.synchronize()
         assert int(st.status.item()) == 0
