@@ -303,3 +303,34 @@ def test_literal_semantics_equals_dense_over_tile_members(b, kind, fov):
     # the semantics differ: contributions beyond the 3-sigma ellipse change some pixels
     R9 = O.render(sc, v, O.Config(tile_level=b))
     assert np.abs(R9.image[R.pix] - R.image[R.pix]).max() > 1e-6
+
+
+def _quat_mul(a, b):
+    """Hamilton product of (w, x, y, z) quaternions, rows of a with rows of b: R(a b) = R(a) R(b)."""
+    w1, v1 = a[..., :1], a[..., 1:]
+    w2, v2 = b[..., :1], b[..., 1:]
+    return np.concatenate([w1 * w2 - (v1 * v2).sum(-1, keepdims=True), w1 * v2 + w2 * v1 + np.cross(v1, v2)], -1)
+
+
+@pytest.mark.parametrize("kind,fov", [(O.CAM_FISHEYE, 190.0), (O.CAM_PINHOLE, 90.0)])
+def test_joint_rotation_of_scene_and_camera_leaves_the_map_unchanged(kind, fov):
+    # the map lives in the camera frame: turning every Gaussian (position and orientation) and the
+    # camera by the same world rotation Q (W' = W Q^T, b' = b) changes nothing the camera sees.
+    # SH degree 0 (a colour that does not depend on the world direction). A wrong frame anywhere in
+    # the view transform, the quaternion-to-rotation map or the covariance projection breaks it.
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(41 + kind)
+    sc = S.make_scene(300, 0, seed=42 + kind, r_min=1.5, r_max=4.0, logscale_mu=-2.0)
+    v = _f64view(S.random_pose_view(rng, 5, kind, fov, fov, radius=0.3))
+    Q = S.random_rotation(rng)
+    qQ = np.roll(Rotation.from_matrix(Q).as_quat(), 1)               # (x, y, z, w) -> (w, x, y, z)
+    sc2 = dict(sc, means=sc["means"] @ Q.T, rotations=_quat_mul(np.broadcast_to(qQ, sc["rotations"].shape),
+                                                                  np.asarray(sc["rotations"], np.float64)))
+    v2 = dict(v, W=v["W"] @ Q.T)
+    cfg = O.Config(tile_level=3)
+    R1, R2 = O.render(sc, v, cfg), O.render(sc2, v2, cfg)
+    assert np.array_equal(R1.mask, R2.mask)
+    ok = (R1.amb == 0) & (R2.amb == 0)
+    assert ok[R1.pix].mean() > 0.99 and (R1.T[R1.pix] < 1).mean() > 0.2       # a non-trivial image
+    assert np.abs(R1.image - R2.image)[ok].max() < 1e-10
+    assert np.abs(R1.T - R2.T)[ok].max() < 1e-10
