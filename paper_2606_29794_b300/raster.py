@@ -158,6 +158,8 @@ class Rasterizer:
         pixel's dL/dI formed inside the backward blend. loss_views: one (maps, targets, table,
         hssim_ws, dloss or None) per view, after hpxgs_hssim_forward_table on the same stream."""
         means, scales, rotations, opacities, sh = state["keep"]
+        if len(loss_views) != state["nv"]:
+            raise ValueError(f"one loss view per rendered view: got {len(loss_views)} for {state['nv']}")
         lv = (L.LossView * len(loss_views))()
         for i, (I, G, tab, hws, dl) in enumerate(loss_views):
             lv[i].maps, lv[i].targets = I.data_ptr(), G.data_ptr()

@@ -105,3 +105,12 @@ def test_flop_counts_match_header():
     assert {k: int(v) for k, v in vals.items()} == {
         "FLOPS_EVAL": L.FLOPS_EVAL, "FLOPS_FWD_CONTRIB": L.FLOPS_FWD_CONTRIB, "FLOPS_BWD_CONTRIB": L.FLOPS_BWD_CONTRIB,
         "MUFU_FWD_CONTRIB": L.MUFU_FWD_CONTRIB, "MUFU_BWD_CONTRIB": L.MUFU_BWD_CONTRIB}
+
+
+def test_fused_backward_binding_wants_one_loss_view_per_view():
+    # checked on the host before the library is called (the library reads nviews entries)
+    from paper_2606_29794_b300 import raster as R
+    rast = R.Rasterizer.__new__(R.Rasterizer)
+    state = {"keep": [None] * 5, "nv": 2}
+    with pytest.raises(ValueError):
+        rast.backward_hssim_raw(state, [("I", "G", "tab", "ws", None)], 0.2)
