@@ -36,6 +36,19 @@ def npix(k: int) -> int:
 
 
 def gaussians_struct(means, scales, rotations, opacities, sh, sh_degree) -> L.Gaussians:
+    """The scene as the C ABI's struct of device pointers, after checking that every tensor is a
+    contiguous float32 CUDA tensor on one device with the shapes the kernels index: means, scales
+    [P, 3], rotations [P, 4], opacities [P] (or [P, 1]), sh [P, (sh_degree + 1)^2, 3]."""
+    P = int(means.shape[0]) if means.dim() == 2 else -1
+    K = (int(sh_degree) + 1) ** 2
+    want = [(means, (P, 3)), (scales, (P, 3)), (rotations, (P, 4)), (sh, (P, K, 3))]
+    ok = 0 <= int(sh_degree) <= 3 and P >= 0 and opacities.numel() == P and opacities.dim() in (1, 2)
+    for t, shape in want + [(opacities, tuple(opacities.shape))]:
+        ok = ok and tuple(t.shape) == shape and t.dtype == torch.float32 and t.is_cuda and t.is_contiguous() \
+            and t.device == means.device
+    if not ok:
+        raise ValueError("gaussians: expected contiguous float32 CUDA tensors on one device: means, scales [P, 3], "
+                         "rotations [P, 4], opacities [P], sh [P, (sh_degree + 1)^2, 3], 0 <= sh_degree <= 3")
     g = L.Gaussians()
     g.means, g.scales, g.rotations = means.data_ptr(), scales.data_ptr(), rotations.data_ptr()
     g.opacities, g.sh = opacities.data_ptr(), sh.data_ptr()
@@ -144,6 +157,9 @@ class Rasterizer:
         means, scales, rotations, opacities, sh = state["keep"]
         dmaps = _f32(dmaps)
         ddepth = _f32(ddepth) if ddepth is not None else None
+        npx = state["T"].numel()
+        if dmaps.numel() != 3 * npx or (ddepth is not None and ddepth.numel() != npx):
+            raise ValueError(f"backward: dL/dmaps needs {3 * npx} values and dL/ddepth {npx}")
         dm, ds, dq, do, dsh = (torch.empty_like(t) for t in (means, scales, rotations, opacities, sh))
         st = torch.zeros(1, dtype=torch.int32, device=means.device)
         L.check(L.lib().hpxgs_backward(ctypes.byref(state["g"]), state["cviews"], state["nv"], ctypes.byref(self.cfg),
@@ -179,8 +195,13 @@ class Rasterizer:
         per-Gaussian buffers rs_max (float32 [P]), grad_accum (float32 [P]) and vis_count (int32 [P])
         in place over the visible (view, Gaussian) pairs; angular (float32 [views, P, 2] or None)
         receives dL/domega, dL/dphi per pair."""
-        for t in (rs_max, grad_accum, vis_count):
-            assert t.is_cuda and t.is_contiguous() and t.numel() == state["g"].P
+        P, nv = state["g"].P, state["nv"]
+        for t, dt in ((rs_max, torch.float32), (grad_accum, torch.float32), (vis_count, torch.int32)):
+            if not (t.is_cuda and t.is_contiguous() and t.dtype == dt and t.numel() == P):
+                raise ValueError(f"density_stats: expected a contiguous CUDA {dt} tensor of {P} elements")
+        if angular is not None and not (angular.is_cuda and angular.is_contiguous() and angular.dtype == torch.float32
+                                        and angular.numel() == 2 * nv * P):
+            raise ValueError(f"density_stats: angular must be a contiguous CUDA float32 tensor of {2 * nv * P} elements")
         L.check(L.lib().hpxgs_density_stats(state["g"].P, state["cviews"], state["nv"], ctypes.byref(self.cfg),
                                             _ptr(state["ws"]), state["nb"], state["cap"], _ptr(rs_max),
                                             _ptr(grad_accum), _ptr(vis_count),

@@ -57,6 +57,8 @@ def sphere_to_image_raw(hmap, nside_log2, cam, width, height, with_valid=True):
 def sphere_to_image_backward(dimage, nside_log2, cam, width, height):
     """dL/dmap [12 * 4^k, 3] = A^T dL/dimage."""
     dimage = _f32(dimage)
+    if dimage.numel() != 3 * width * height:
+        raise ValueError("dimage size does not match width x height x 3")
     dmap = torch.empty((12 * 4 ** nside_log2, 3), dtype=torch.float32, device=dimage.device)
     c = _cam(cam)
     L.check(L.lib().hpxgs_sphere_to_image_backward(_ptr(dimage), nside_log2, ctypes.byref(c), width, height,
@@ -67,6 +69,8 @@ def sphere_to_image_backward(dimage, nside_log2, cam, width, height):
 def image_to_sphere(image, cam, nside_log2, with_mask=True):
     """HEALPix map [12 * 4^k, 3] of a camera image [height, width, 3] and the mask words of M_C."""
     image = _f32(image)
+    if image.dim() != 3 or image.shape[2] != 3:
+        raise ValueError("expected an image of shape [height, width, 3]")
     height, width = image.shape[0], image.shape[1]
     npix = 12 * 4 ** nside_log2
     hmap = torch.empty((npix, 3), dtype=torch.float32, device=image.device)
