@@ -5,6 +5,7 @@ import os
 import re
 
 import pytest
+import torch
 
 from paper_2606_29794_b300 import _lib as L
 from paper_2606_29794_b300 import build as B
@@ -114,3 +115,26 @@ def test_fused_backward_binding_wants_one_loss_view_per_view():
     state = {"keep": [None] * 5, "nv": 2}
     with pytest.raises(ValueError):
         rast.backward_hssim_raw(state, [("I", "G", "tab", "ws", None)], 0.2)
+
+
+def test_density_stats_binding_checks_buffers():
+    from paper_2606_29794_b300 import raster as R
+    rast = R.Rasterizer.__new__(R.Rasterizer)
+    g = L.Gaussians()
+    g.P = 4
+    state = {"g": g, "nv": 2}
+    cpu = torch.zeros(4)
+    with pytest.raises(ValueError):
+        rast.density_stats(state, cpu, cpu, cpu.int())          # host tensors are refused
+
+
+def test_scene_tensors_are_validated_before_any_launch():
+    from paper_2606_29794_b300 import raster as R
+    P = 8
+    t = lambda *s: torch.zeros(*s)
+    with pytest.raises(ValueError):                              # host tensors
+        R.gaussians_struct(t(P, 3), t(P, 3), t(P, 4), t(P), t(P, 16, 3), 3)
+    with pytest.raises(ValueError):                              # SH rows do not match the degree
+        R.gaussians_struct(t(P, 3), t(P, 3), t(P, 4), t(P), t(P, 9, 3), 3)
+    with pytest.raises(ValueError):                              # degree out of range
+        R.gaussians_struct(t(P, 3), t(P, 3), t(P, 4), t(P), t(P, 25, 3), 4)
