@@ -434,13 +434,17 @@ int hpxgs_hssim_backward_table(const float* I, const float* G, const uint32_t* m
  * No counterpart in the paper. For callers that cannot give the library device
  * memory (a plugin inside a host application that owns the GPU memory budget,
  * a real-time loop that must not allocate after start-up): out3 = {loss, HSSIM,
- * L1} as hpxgs_hssim_forward computes them, value only (no gradient). The
- * per-block partial sums live in a fixed 1.18 MB array inside the library's
- * device image, which every GPU that loads the library holds until exit; the
- * call allocates nothing. Limit: k <= 10 (Nside <= 1024); larger k returns
- * HPXGS_E_INVALID_ARG. The first call on each device looks up the array's
- * device address (make it before any stream capture). All calls share the
- * array: calls that overlap on the GPU race. */
+ * L1}, value only (no gradient). Per pixel it runs the same window and SSIM
+ * arithmetic as hpxgs_hssim_forward; only the block sums are added differently,
+ * and the two agree within 2e-6. The per-block partial sums live in a fixed
+ * 1.18 MB array inside the library's device image, which every GPU that loads
+ * the library holds until exit; the call allocates nothing. Limit: k <= 10
+ * (Nside <= 1024); larger k returns HPXGS_E_INVALID_ARG. A call outside stream
+ * capture looks up the array's device address on the current device and caches
+ * it; a call inside capture uses that cache and returns HPXGS_E_CAPTURE if the
+ * device has none, so make a first call on each device (and again after a
+ * cudaDeviceReset) before capturing. All calls share the array: calls that
+ * overlap on the GPU race. */
 int hpxgs_hssim_loss_noalloc(const float* I, const float* G, const uint32_t* mask_bits, int k, float lambda,
                              float* out3, hpxgs_stream_t stream);
 

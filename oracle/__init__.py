@@ -34,10 +34,11 @@ CAM_FULL, CAM_PINHOLE, CAM_FISHEYE = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (-O2, OpenMP, IEEE double; no fast-math)."""
+    """Compile the oracle with g++ (-O2, OpenMP, IEEE double: no fast-math and no contraction
+    of a multiply and an add into one rounding)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC", _SRC, "-o", tmp]
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", _SRC, "-o", tmp]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
     return _LIB
@@ -60,6 +61,7 @@ def lib():
         _lib.or_pixrad.restype = ctypes.c_double
         _lib.or_hssim_loss.restype = ctypes.c_double
         _lib.or_num_threads.restype = ctypes.c_int
+        _lib.or_max_leaves.restype = ctypes.c_int
     return _lib
 
 
@@ -305,24 +307,33 @@ def tile_lists_bruteforce(k, b, g, rs, valid, rho, active):
     return member
 
 
+def _composite_inputs(pre, opac, start, ids):
+    return [np.ascontiguousarray(pre["omega"], np.float64), np.ascontiguousarray(pre["phi"], np.float64),
+            np.ascontiguousarray(pre["conic"], np.float64), np.ascontiguousarray(opac, np.float64),
+            np.ascontiguousarray(pre["col"], np.float64), np.ascontiguousarray(pre["r"], np.float64),
+            np.ascontiguousarray(start, np.int64), np.ascontiguousarray(ids, np.int64)]
+
+
+# Flags of composite / render (test bookkeeping, not the method): decisions an FP32
+# rasterizer may take the other way, because the FP64 value lies within a narrow band
+# of its threshold (m <= cutoff within 2e-5 relative; T < eps within 1e-4 relative).
+AMB_CUTOFF = 1       # a cutoff decision in its band: composite_variants holds both outcomes
+AMB_TERM = 2         # a termination decision in its band: likewise
+AMB_UNRESOLVED = 4   # more band decisions than the variants follow: not comparable
+
+
 def composite(k, b, pre, opac, start, ids, pix, cfg: Config, depth=False):
     """Stage 3 (Algorithm 1 rendering loop) at the NESTED pixels `pix`.
-    Returns (image, T, last, amb); amb bit 0 flags a cutoff decision within
-    rounding of m = cutoff, bit 1 two contributors of nearly equal depth."""
+    Returns (image, T, last, amb) with the FP64 outcome of every decision; amb holds the
+    AMB_* flags of decisions single precision may take the other way."""
     pix = np.ascontiguousarray(pix, np.int64)
     n = pix.size
     img = np.empty((n, 3)); T = np.empty(n); last = np.empty(n, np.int64); amb = np.empty(n, np.uint8)
     D = np.empty(n) if depth else None
     bg = np.asarray(cfg.bg, np.float64)
     P = pre["r"].size
-    lib().or_composite(ctypes.c_int(k), ctypes.c_int(b), _i64(P),
-                       _p(np.ascontiguousarray(pre["omega"], np.float64)),
-                       _p(np.ascontiguousarray(pre["phi"], np.float64)),
-                       _p(np.ascontiguousarray(pre["conic"], np.float64)),
-                       _p(np.ascontiguousarray(opac, np.float64)),
-                       _p(np.ascontiguousarray(pre["col"], np.float64)),
-                       _p(np.ascontiguousarray(pre["r"], np.float64)),
-                       _p(np.ascontiguousarray(start, np.int64)), _p(np.ascontiguousarray(ids, np.int64)),
+    args = _composite_inputs(pre, opac, start, ids)
+    lib().or_composite(ctypes.c_int(k), ctypes.c_int(b), _i64(P), *[_p(a) for a in args],
                        _i64(n), _p(pix), _f64(cfg.eps_T), _f64(cfg.alpha_max),
                        _f64(cfg.cutoff), _p(bg), _p(img), _p(T), _p(last), _p(amb), _p(D))
     if depth:
@@ -330,12 +341,34 @@ def composite(k, b, pre, opac, start, ids, pix, cfg: Config, depth=False):
     return img, T, last, amb
 
 
+def max_leaves() -> int:
+    return lib().or_max_leaves()
+
+
+def composite_variants(k, b, pre, opac, start, ids, pix, cfg: Config):
+    """Every result the rendering loop can give at `pix` when each decision within its FP32
+    band takes either outcome (see AMB_*): dict with n (leaves per pixel), image (n, L, 3),
+    T (n, L), last (n, L), D (n, L); leaf 0 is composite's FP64 result, slots past n[q]
+    repeat it."""
+    pix = np.ascontiguousarray(pix, np.int64)
+    n = pix.size
+    L = max_leaves()
+    out = dict(n=np.empty(n, np.int32), image=np.empty((n, L, 3)), T=np.empty((n, L)),
+               last=np.empty((n, L), np.int64), D=np.empty((n, L)))
+    bg = np.asarray(cfg.bg, np.float64)
+    args = _composite_inputs(pre, opac, start, ids)
+    lib().or_composite_variants(ctypes.c_int(k), ctypes.c_int(b), _i64(pre["r"].size), *[_p(a) for a in args],
+                                _i64(n), _p(pix), _f64(cfg.eps_T), _f64(cfg.alpha_max), _f64(cfg.cutoff), _p(bg),
+                                _p(out["n"]), _p(out["image"]), _p(out["T"]), _p(out["last"]), _p(out["D"]))
+    return out
+
+
 @dataclass
 class Render:
     image: np.ndarray            # (Npix, 3); outside the mask: bg
     T: np.ndarray                # (Npix,) final transmittance (1 outside the mask)
     last: np.ndarray             # (Npix,) processed entries of the tile list
-    amb: np.ndarray              # (Npix,) ambiguity flags: bit 0 cutoff boundary, bit 1 depth tie
+    amb: np.ndarray              # (Npix,) AMB_* flags of FP32-undecidable decisions
     mask: np.ndarray
     active: np.ndarray
     pre: dict

@@ -611,7 +611,7 @@ struct GaussView {  // what compositing needs per Gaussian
   double omega, sphg, cphg, conic[3], opac, col[3], r;
 };
 
-struct PixOut { double C[3], T, D; i64 last; int amb; };   // D: composited inverse radial depth
+struct PixOut { double C[3], T, D; i64 last; };   // D: composited inverse radial depth
 
 // Forward at one pixel; optionally records alpha, T before each entry and exp(-m/2).
 static void composite_pixel(double omega_p, double sphp, double cphp, const i64* ids, i64 n,
@@ -620,8 +620,6 @@ static void composite_pixel(double omega_p, double sphp, double cphp, const i64*
                             std::vector<double>* Gs) {
   double T = 1.0, C[3] = {0, 0, 0}, D = 0.0;
   i64 j = 0;
-  int amb = 0;
-  double prev_r = -1.0, prev_a = 0.0;
   for (; j < n; ++j) {
     const GaussView& gv = G[ids[j]];
     Offset o;
@@ -629,14 +627,6 @@ static void composite_pixel(double omega_p, double sphp, double cphp, const i64*
     double m = gv.conic[0] * o.d[0] * o.d[0] + 2 * gv.conic[1] * o.d[0] * o.d[1] + gv.conic[2] * o.d[1] * o.d[1];
     double Gm = std::exp(-0.5 * m);
     double a = (m > cfg.cutoff) ? 0.0 : std::min(cfg.alpha_max, gv.opac * Gm);
-    // ambiguity flags (test bookkeeping, not part of the method): bit 0, the cutoff
-    // decided within 1e-5 relative while it matters; bit 1, two contributing
-    // Gaussians of nearly equal depth whose order float32 cannot settle.
-    double cmax = std::max(gv.col[0], std::max(gv.col[1], gv.col[2]));
-    if (std::fabs(m - cfg.cutoff) < 1e-5 * cfg.cutoff &&
-        T * gv.opac * std::exp(-0.5 * cfg.cutoff) * std::max(1.0, cmax) > 5e-5) amb |= 1;
-    if (a > 0 && prev_a > 0 && std::fabs(gv.r - prev_r) < 2e-6 * gv.r && T * a > 5e-5) amb |= 2;
-    if (a > 0) { prev_r = gv.r; prev_a = a; }
     if (alphas) { alphas->push_back(a); Ts->push_back(T); Gs->push_back(Gm); }
     for (int c = 0; c < 3; ++c) C[c] += T * a * gv.col[c];
     D += T * a / gv.r;                        // depth channel: inverse radial depth (Sec. 3.2)
@@ -644,7 +634,96 @@ static void composite_pixel(double omega_p, double sphp, double cphp, const i64*
     if (T < cfg.eps_T) { ++j; break; }
   }
   for (int c = 0; c < 3; ++c) out.C[c] = C[c] + T * cfg.bg[c];
-  out.T = T; out.D = D; out.last = j; out.amb = amb;
+  out.T = T; out.D = D; out.last = j;
+}
+
+// ---------------------------------------------------------------------------
+// Decisions that single precision may take the other way (test bookkeeping, not part
+// of the method). A rasterizer working in FP32 decides m <= cutoff and T < eps from
+// values within a few parts in 1e6 (m) and 1e5 (T) of these FP64 ones. Where the FP64
+// value lies within the bands below of its threshold, both outcomes are results of
+// the method at that precision. composite_branches follows both outcomes of every such
+// decision, up to kMaxFlips of them per pixel, and returns each resulting pixel value
+// (a leaf); the leaf with the FP64 outcome of every decision comes first and equals
+// composite_pixel's result. Flags: bit 0, a cutoff decision in its band; bit 1, a
+// termination decision in its band; bit 2, more such decisions than kMaxFlips (the
+// later ones take the FP64 outcome only, so the leaves do not cover every outcome).
+// ---------------------------------------------------------------------------
+constexpr double kAmbCut = 2e-5;     // |m - cutoff| < kAmbCut * cutoff
+constexpr double kAmbTerm = 1e-4;    // |T - eps| < kAmbTerm * eps
+constexpr int kMaxFlips = 4;
+constexpr int kMaxLeaves = 1 << kMaxFlips;
+
+struct Leaf { double C[3], T, D; i64 last; };
+
+struct BranchCtx {
+  double omega_p, sphp, cphp;
+  const i64* ids;
+  i64 n;
+  const std::vector<GaussView>* G;
+  const Cfg* cfg;
+  Leaf leaves[kMaxLeaves];
+  int nleaves;   // leaves[0] is the FP64 path's; the others follow from index 1
+  int amb;
+};
+
+static void emit_leaf(BranchCtx& X, bool primary, const double C[3], double T, double D, i64 last) {
+  int slot = primary ? 0 : X.nleaves++;
+  Leaf& L = X.leaves[slot];
+  for (int c = 0; c < 3; ++c) L.C[c] = C[c] + T * X.cfg->bg[c];
+  L.T = T; L.D = D; L.last = last;
+}
+
+// From list position j with state (T, C, D); nd band decisions met so far on this path
+// (each path meets at most kMaxFlips, so there are at most kMaxLeaves leaves).
+// forced_in >= 0 imposes the cutoff outcome of entry j (the other branch of a decision
+// the caller met).
+static void composite_branches(BranchCtx& X, i64 j, double T, const double C0[3], double D, int nd,
+                               bool primary, int forced_in) {
+  const Cfg& cfg = *X.cfg;
+  double C[3] = {C0[0], C0[1], C0[2]};
+  for (; j < X.n; ++j, forced_in = -1) {
+    const GaussView& gv = (*X.G)[X.ids[j]];
+    Offset o;
+    spherical_offset(X.omega_p, X.sphp, X.cphp, gv.omega, gv.sphg, gv.cphg, o);
+    double m = gv.conic[0] * o.d[0] * o.d[0] + 2 * gv.conic[1] * o.d[0] * o.d[1] + gv.conic[2] * o.d[1] * o.d[1];
+    bool in = !(m > cfg.cutoff);
+    if (forced_in >= 0) {
+      in = forced_in != 0;
+    } else if (std::fabs(m - cfg.cutoff) < kAmbCut * cfg.cutoff) {
+      X.amb |= 1;
+      if (nd < kMaxFlips) composite_branches(X, j, T, C, D, ++nd, false, in ? 0 : 1);
+      else X.amb |= 4;
+    }
+    double a = in ? std::min(cfg.alpha_max, gv.opac * std::exp(-0.5 * m)) : 0.0;
+    for (int c = 0; c < 3; ++c) C[c] += T * a * gv.col[c];
+    D += T * a / gv.r;
+    T *= (1.0 - a);
+    // only an entry that changes T can end the loop (on the FP64 path T >= eps whenever
+    // a == 0; on a path that went on past a band decision T may already be below eps)
+    bool stop = a > 0 && T < cfg.eps_T;
+    if (a > 0 && std::fabs(T - cfg.eps_T) < kAmbTerm * cfg.eps_T) {
+      X.amb |= 2;
+      if (nd < kMaxFlips) {
+        ++nd;
+        if (stop) composite_branches(X, j + 1, T, C, D, nd, false, -1);   // went on
+        else emit_leaf(X, false, C, T, D, j + 1);                          // stopped here
+      } else {
+        X.amb |= 4;
+      }
+    }
+    if (stop) { emit_leaf(X, primary, C, T, D, j + 1); return; }
+  }
+  emit_leaf(X, primary, C, T, D, X.n);
+}
+
+static void composite_pixel_branches(double omega_p, double sphp, double cphp, const i64* ids, i64 n,
+                                     const std::vector<GaussView>& G, const Cfg& cfg, BranchCtx& X) {
+  X.omega_p = omega_p; X.sphp = sphp; X.cphp = cphp;
+  X.ids = ids; X.n = n; X.G = &G; X.cfg = &cfg;
+  X.nleaves = 1; X.amb = 0;
+  const double C0[3] = {0, 0, 0};
+  composite_branches(X, 0, 1.0, C0, 0.0, 0, true, -1);
 }
 
 static void pixel_lonlat(i64 nside, i64 p, double& omega_p, double& sphp, double& cphp) {
@@ -1178,12 +1257,15 @@ void or_active_tiles(int k, int b, const u8* mask, u8* active) {
 }
 
 // Compositing given per-Gaussian values and sorted lists, for the in-mask pixels
-// listed in `pix`.
-void or_composite(int k, int b, i64 P, const double* omega, const double* phi, const double* conic,
-                  const double* opac, const double* col, const double* r, const i64* start,
-                  const i64* ids, i64 npix_q, const i64* pix, double eps_T, double alpha_max,
-                  double cutoff, const double* bg, double* img, double* Tfin, i64* last, u8* amb,
-                  double* depth) {
+// listed in `pix`: the FP64 result and the flags of composite_branches. With `var_*`
+// non-null, also every leaf (up to kMaxLeaves per pixel, leaf 0 the FP64 result):
+// var_n[q] leaves, var_img[q][l][3], var_T[q][l], var_last[q][l], var_D[q][l].
+static void composite_many(int k, int b, i64 P, const double* omega, const double* phi, const double* conic,
+                           const double* opac, const double* col, const double* r, const i64* start,
+                           const i64* ids, i64 npix_q, const i64* pix, double eps_T, double alpha_max,
+                           double cutoff, const double* bg, double* img, double* Tfin, i64* last, u8* amb,
+                           double* depth, int* var_n, double* var_img, double* var_T, i64* var_last,
+                           double* var_D) {
   std::vector<GaussView> G(P);
   for (i64 i = 0; i < P; ++i) {
     G[i].omega = omega[i]; G[i].sphg = std::sin(phi[i]); G[i].cphg = std::cos(phi[i]);
@@ -1198,12 +1280,45 @@ void or_composite(int k, int b, i64 P, const double* omega, const double* phi, c
     i64 p = pix[q];
     i64 t = p >> (2 * b);
     double om, sp, cp; pixel_lonlat(nside, p, om, sp, cp);
-    PixOut po;
-    composite_pixel(om, sp, cp, ids + start[t], start[t + 1] - start[t], G, cfg, po, nullptr, nullptr, nullptr);
-    for (int c = 0; c < 3; ++c) img[3 * q + c] = po.C[c];
-    Tfin[q] = po.T; last[q] = po.last; amb[q] = (u8)po.amb;
-    if (depth) depth[q] = po.D;
+    BranchCtx X;
+    composite_pixel_branches(om, sp, cp, ids + start[t], start[t + 1] - start[t], G, cfg, X);
+    const Leaf& L0 = X.leaves[0];
+    if (img) for (int c = 0; c < 3; ++c) img[3 * q + c] = L0.C[c];
+    if (Tfin) Tfin[q] = L0.T;
+    if (last) last[q] = L0.last;
+    if (amb) amb[q] = (u8)X.amb;
+    if (depth) depth[q] = L0.D;
+    if (var_n) {
+      var_n[q] = X.nleaves;
+      for (int l = 0; l < kMaxLeaves; ++l) {
+        const Leaf& Lf = X.leaves[l < X.nleaves ? l : 0];
+        for (int c = 0; c < 3; ++c) var_img[(q * kMaxLeaves + l) * 3 + c] = Lf.C[c];
+        var_T[q * kMaxLeaves + l] = Lf.T;
+        var_last[q * kMaxLeaves + l] = Lf.last;
+        if (var_D) var_D[q * kMaxLeaves + l] = Lf.D;
+      }
+    }
   }
+}
+
+void or_composite(int k, int b, i64 P, const double* omega, const double* phi, const double* conic,
+                  const double* opac, const double* col, const double* r, const i64* start,
+                  const i64* ids, i64 npix_q, const i64* pix, double eps_T, double alpha_max,
+                  double cutoff, const double* bg, double* img, double* Tfin, i64* last, u8* amb,
+                  double* depth) {
+  composite_many(k, b, P, omega, phi, conic, opac, col, r, start, ids, npix_q, pix, eps_T, alpha_max, cutoff, bg,
+                 img, Tfin, last, amb, depth, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+int or_max_leaves() { return kMaxLeaves; }
+
+void or_composite_variants(int k, int b, i64 P, const double* omega, const double* phi, const double* conic,
+                           const double* opac, const double* col, const double* r, const i64* start,
+                           const i64* ids, i64 npix_q, const i64* pix, double eps_T, double alpha_max,
+                           double cutoff, const double* bg, int* var_n, double* var_img, double* var_T,
+                           i64* var_last, double* var_D) {
+  composite_many(k, b, P, omega, phi, conic, opac, col, r, start, ids, npix_q, pix, eps_T, alpha_max, cutoff, bg,
+                 nullptr, nullptr, nullptr, nullptr, nullptr, var_n, var_img, var_T, var_last, var_D);
 }
 
 // Full backward for one view (Sec. 3.2): dL/dI over the listed in-mask pixels ->

@@ -1,6 +1,7 @@
 """Build the CUDA library libhpxgs.so in-tree for sm_103a (B300) with nvcc."""
 from __future__ import annotations
 
+import glob
 import os
 import subprocess
 import sys
@@ -8,7 +9,6 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 SOURCES = ["geometry.cu", "raster.cu", "hssim.cu", "hssim_noalloc.cu", "probe.cu", "resample.cu"]
-HEADERS = ["hpx_math.cuh", "internal.cuh", "camera.cuh"]
 LIB = os.path.join(HERE, "libhpxgs.so")
 ROOT = os.path.dirname(HERE)
 
@@ -24,7 +24,9 @@ def needs_build() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "hpxgs.h")]
+    # every header under csrc/ counts, so that a new one cannot be left out of the check
+    deps = ([os.path.join(CSRC, f) for f in SOURCES] + sorted(glob.glob(os.path.join(CSRC, "*.cuh")))
+            + sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
     return any(os.path.getmtime(d) > t for d in deps)
 
 

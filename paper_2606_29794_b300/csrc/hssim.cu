@@ -13,23 +13,14 @@
 // k_hssim_bwd: per pixel, gather over the windows that contain it.
 #include "hpx_math.cuh"
 #include "hssim_grad.cuh"
+#include "hssim_window.cuh"
 #include "internal.cuh"
 
 using namespace hpx;
 
 namespace hpxgs {
 
-constexpr float kC1 = 1e-4f, kC2 = 9e-4f;
 constexpr int kHThreads = 256;
-
-__device__ __forceinline__ bool mbit(const uint32_t* m, uint32_t p) { return (m[p >> 5] >> (p & 31)) & 1u; }
-
-__device__ __forceinline__ float pair_weight(float3 a, float3 b, float inv2sig2) {
-  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-  const float ch = sqrtf(dx * dx + dy * dy + dz * dz);
-  const float th = 2.f * asinf(fminf(1.f, 0.5f * ch));
-  return __expf(-th * th * inv2sig2);
-}
 
 // Block partials of the loss: sum of h_q and of |I - G| in FP32 (8 warp sums of at
 // most 32 terms, added in a fixed order) and the exact in-mask count. FP64 work is
@@ -77,49 +68,17 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_fwd(int k, const float* __r
   const uint32_t p = blockIdx.x * kHThreads + threadIdx.x;
   float h = 0.f, l1 = 0.f;
   uint32_t cnt = 0;
-  if (p < npix && mbit(mask, p)) {
-    const float omega = 4.f * (float)kPi / (float)npix;
-    const float inv2sig2 = 1.f / (2.f * 2.25f * omega);
-    const float3 cq = pix2vec_f32(k, p);
-    const FaceXY c = nest_to_fxy(k, p);
-    uint32_t idx[9];
-    float w[9];
-    int n = 0;
-    idx[n] = p; w[n] = 1.f; ++n;
-    for (int dx = -1; dx <= 1; ++dx)
-      for (int dy = -1; dy <= 1; ++dy) {
-        if (dx == 0 && dy == 0) continue;
-        const int64_t nb = neighbour_nest(k, c.f, c.x, c.y, dx, dy);
-        if (nb < 0 || !mbit(mask, (uint32_t)nb)) continue;
-        idx[n] = (uint32_t)nb;
-        w[n] = pair_weight(cq, pix2vec_f32(k, (uint32_t)nb), inv2sig2);
-        ++n;
-      }
-    float Z = 0.f;
-    for (int j = 0; j < n; ++j) Z += w[j];
-    const float iZ = 1.f / Z;
+  if (p < npix && mask_bit(mask, p)) {
+    HWindow W;
+    hssim_window(k, p, mask, W);
     float hs = 0.f;
     for (int ch = 0; ch < 3; ++ch) {
-      float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
-      for (int j = 0; j < n; ++j) {
-        const float wj = w[j] * iZ;
-        const float x = I[3 * (size_t)idx[j] + ch], y = Gt[3 * (size_t)idx[j] + ch];
-        mx += wj * x; my += wj * y; xx += wj * x * x; yy += wj * y * y; xy += wj * x * y;
-      }
-      const float vx = xx - mx * mx, vy = yy - my * my, cxy = xy - mx * my;
-      const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
-      const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
-      const float iB = 1.f / (B1 * B2);
-      const float ssim = A1 * A2 * iB;
-      hs += ssim;
-      // partials w.r.t. (mu_x, var_x, cov_xy)
-      const float dmu = (2.f * my * A2 - ssim * B2 * 2.f * mx) * iB;
-      const float dvar = -ssim / B2;
-      const float dcov = 2.f * A1 * iB;
-      // d ssim_q / d x_p = w_qp (alpha + beta x_p + gamma y_p), w_qp = e_qp / Z
-      coef[9 * (size_t)p + 3 * ch + 0] = (dmu - 2.f * mx * dvar - my * dcov) * iZ;
-      coef[9 * (size_t)p + 3 * ch + 1] = 2.f * dvar * iZ;
-      coef[9 * (size_t)p + 3 * ch + 2] = dcov * iZ;
+      WinStats st;
+      for (int j = 0; j < W.n; ++j)
+        st.add(W.w[j] * W.iZ, I[3 * (size_t)W.idx[j] + ch], Gt[3 * (size_t)W.idx[j] + ch]);
+      const SsimTerms t = ssim_terms(st);
+      hs += t.ssim;
+      ssim_coefs(st, t, W.iZ, coef + 9 * (size_t)p + 3 * ch);
       l1 += fabsf(I[3 * (size_t)p + ch] - Gt[3 * (size_t)p + ch]);
     }
     h = hs / 3.f;
@@ -174,11 +133,10 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_bwd(int k, const float* __r
   const uint32_t npix = 12u << (2 * k);
   const uint32_t p = blockIdx.x * kHThreads + threadIdx.x;
   if (p >= npix) return;
-  if (!mbit(mask, p)) { dI[3 * (size_t)p] = 0.f; dI[3 * (size_t)p + 1] = 0.f; dI[3 * (size_t)p + 2] = 0.f; return; }
+  if (!mask_bit(mask, p)) { dI[3 * (size_t)p] = 0.f; dI[3 * (size_t)p + 1] = 0.f; dI[3 * (size_t)p + 2] = 0.f; return; }
   const float nm = reinterpret_cast<const float*>(nmask + 1)[0];
   const float scale = (dloss ? *dloss : 1.f) / (3.f * nm);
-  const float omega = 4.f * (float)kPi / (float)npix;
-  const float inv2sig2 = 1.f / (2.f * 2.25f * omega);
+  const float inv2sig2 = window_inv2sig2(npix);
   const float3 cp = pix2vec_f32(k, p);
   const FaceXY c = nest_to_fxy(k, p);
   float x[3], y[3], g[3];
@@ -191,8 +149,8 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_bwd(int k, const float* __r
     for (int dy = -1; dy <= 1; ++dy) {
       if (dx == 0 && dy == 0) continue;
       const int64_t nb = neighbour_nest(k, c.f, c.x, c.y, dx, dy);
-      if (nb < 0 || !mbit(mask, (uint32_t)nb)) continue;
-      const float e = pair_weight(cp, pix2vec_f32(k, (uint32_t)nb), inv2sig2);
+      if (nb < 0 || !mask_bit(mask, (uint32_t)nb)) continue;
+      const float e = window_pair_weight(cp, pix2vec_f32(k, (uint32_t)nb), inv2sig2);
       const float* cf = coef + 9 * (size_t)nb;
       for (int ch = 0; ch < 3; ++ch) g[ch] += e * (cf[3 * ch] + cf[3 * ch + 1] * x[ch] + cf[3 * ch + 2] * y[ch]);
     }
@@ -212,7 +170,7 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_bwd(int k, const float* __r
 // weight is 0), which the forward reads only on a face's edges (elsewhere the
 // interleaved-bit step gives it) and the gradient gathers read everywhere; and
 // iZ[p] = 1 / (1 + sum e). A zero-weight slot adds an exact zero. The weights come from the same
-// pair_weight calls in the same order and a zero weight is skipped, so the table
+// window_pair_weight calls in the same order and a zero weight is skipped, so the table
 // kernels give the results of k_hssim_fwd / k_hssim_bwd bit for bit while skipping
 // the neighbour walk, the pixel centres and the transcendental weights.
 // ----------------------------------------------------------------------------
@@ -234,16 +192,15 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_table(int k, const uint32_t
   const uint32_t p = blockIdx.x * kHThreads + threadIdx.x;
   if (p >= npix) return;
   float Z = 1.f;                               // the pixel itself, e_pp = 1
-  const bool in = mbit(mask, p);
+  const bool in = mask_bit(mask, p);
   const FaceXY c = nest_to_fxy(k, p);
-  const float omega = 4.f * (float)kPi / (float)npix;
-  const float inv2sig2 = 1.f / (2.f * 2.25f * omega);
+  const float inv2sig2 = window_inv2sig2(npix);
   const float3 cq = pix2vec_f32(k, p);
   for (int s = 0; s < 8; ++s) {                // the walk order: dx = -1, 0, 1, then dy
     const int64_t nb = neighbour_nest(k, c.f, c.x, c.y, window_dx(s), window_dy(s));
     float w = 0.f;
-    if (in && nb >= 0 && mbit(mask, (uint32_t)nb)) {
-      w = pair_weight(cq, pix2vec_f32(k, (uint32_t)nb), inv2sig2);
+    if (in && nb >= 0 && mask_bit(mask, (uint32_t)nb)) {
+      w = window_pair_weight(cq, pix2vec_f32(k, (uint32_t)nb), inv2sig2);
       Z += w;
     }
     T.idx[(size_t)s * npix + p] = w != 0.f ? (uint32_t)nb : p;
@@ -263,7 +220,7 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_fwd_t(int k, const float* _
   const uint32_t p = blk * kHThreads + threadIdx.x;
   float h = 0.f, l1 = 0.f;
   uint32_t cnt = 0;
-  if (p < npix && mbit(mask, p)) {
+  if (p < npix && mask_bit(mask, p)) {
     const float iZ = T.iZ[p];
     const WinStep wst(k, p);
     uint32_t q[8];
@@ -275,31 +232,16 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_fwd_t(int k, const float* _
     }
     float hs = 0.f;
     for (int ch = 0; ch < 3; ++ch) {
-      float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
-      {
-        const float wj = 1.f * iZ;
-        const float x = I[3 * (size_t)p + ch], y = Gt[3 * (size_t)p + ch];
-        mx += wj * x; my += wj * y; xx += wj * x * x; yy += wj * y * y; xy += wj * x * y;
-      }
+      WinStats st;
+      st.add(1.f * iZ, I[3 * (size_t)p + ch], Gt[3 * (size_t)p + ch]);
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         if (e[j] == 0.f) continue;
-        const float wj = e[j] * iZ;
-        const float x = I[3 * (size_t)q[j] + ch], y = Gt[3 * (size_t)q[j] + ch];
-        mx += wj * x; my += wj * y; xx += wj * x * x; yy += wj * y * y; xy += wj * x * y;
+        st.add(e[j] * iZ, I[3 * (size_t)q[j] + ch], Gt[3 * (size_t)q[j] + ch]);
       }
-      const float vx = xx - mx * mx, vy = yy - my * my, cxy = xy - mx * my;
-      const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
-      const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
-      const float iB = 1.f / (B1 * B2);
-      const float ssim = A1 * A2 * iB;
-      hs += ssim;
-      const float dmu = (2.f * my * A2 - ssim * B2 * 2.f * mx) * iB;
-      const float dvar = -ssim / B2;
-      const float dcov = 2.f * A1 * iB;
-      coef[9 * (size_t)p + 3 * ch + 0] = (dmu - 2.f * mx * dvar - my * dcov) * iZ;
-      coef[9 * (size_t)p + 3 * ch + 1] = 2.f * dvar * iZ;
-      coef[9 * (size_t)p + 3 * ch + 2] = dcov * iZ;
+      const SsimTerms t = ssim_terms(st);
+      hs += t.ssim;
+      ssim_coefs(st, t, iZ, coef + 9 * (size_t)p + 3 * ch);
       l1 += fabsf(I[3 * (size_t)p + ch] - Gt[3 * (size_t)p + ch]);
     }
     h = hs / 3.f;
@@ -316,7 +258,7 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_bwd_t(int k, const float* _
   const uint32_t npix = 12u << (2 * k);
   const uint32_t p = blockIdx.x * kHThreads + threadIdx.x;
   if (p >= npix) return;
-  if (!mbit(mask, p)) { dI[3 * (size_t)p] = 0.f; dI[3 * (size_t)p + 1] = 0.f; dI[3 * (size_t)p + 2] = 0.f; return; }
+  if (!mask_bit(mask, p)) { dI[3 * (size_t)p] = 0.f; dI[3 * (size_t)p + 1] = 0.f; dI[3 * (size_t)p + 2] = 0.f; return; }
   const float nm = reinterpret_cast<const float*>(nmask + 1)[0];
   const float scale = (dloss ? *dloss : 1.f) / (3.f * nm);
   float g[3];

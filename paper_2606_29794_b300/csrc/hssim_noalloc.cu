@@ -3,23 +3,29 @@
 // Some callers cannot hand the library device memory: a plugin running inside a
 // host application that owns the whole GPU memory budget, or a real-time loop
 // that forbids allocation once it has started. hpxgs_hssim_loss_noalloc serves
-// them. It computes the same {loss, HSSIM, L1} as hpxgs_hssim_forward, but only
-// the value (no gradient coefficients), and keeps its per-block partial sums in
-// a fixed array that lives in this library's device image instead of in a
-// workspace.
+// them. It returns the {loss, HSSIM, L1} value (no gradient coefficients) and
+// keeps its per-block partial sums in a fixed array that lives in this library's
+// device image instead of in a workspace.
 //
+//  - Per pixel it evaluates h_q and |I - G| with the functions the workspace
+//    kernels use (hssim_window.cuh); only the block sums differ (FP64 here,
+//    compensated FP32 there), so the two entry points agree within 2e-6.
 //  - Limit: HEALPix order k <= 10 (Nside <= 1024). The array holds one partial
 //    triple per 256-pixel block at that size: 49,152 x 3 doubles = 1.18 MB, and
 //    every GPU that loads the library keeps it until the process exits.
-//  - The array's address is looked up once per device (cudaGetSymbolAddress,
-//    with that device current) on the first call made on that device; make that
-//    first call before capturing a stream into a CUDA graph.
+//  - Host code cannot use the array's name as a device address. Each call made
+//    outside stream capture looks the address up (cudaGetSymbolAddress, with the
+//    calling thread's device current) and caches it per device; a call made while
+//    the stream is capturing uses the cached address, so a first call on each
+//    device must come before capture. A cudaDeviceReset discards the module and
+//    with it the cached address: call once more outside capture after a reset.
 //  - Every call writes all the partials it later reads, so nothing needs
 //    clearing, but all calls share the one array: calls that overlap on the GPU
 //    (different streams without ordering between them) race and give wrong values.
 #include <mutex>
 
 #include "hpx_math.cuh"
+#include "hssim_window.cuh"
 #include "internal.cuh"
 
 using namespace hpx;
@@ -30,17 +36,7 @@ namespace {
 constexpr int kNaThreads = 256;
 constexpr int kNaMaxOrder = 10;
 constexpr int kNaMaxBlocks = (12 << (2 * kNaMaxOrder)) / kNaThreads;   // 49,152
-constexpr float kNaC1 = 1e-4f, kNaC2 = 9e-4f;
-
 static __device__ __align__(256) double g_partials[3 * kNaMaxBlocks];
-
-__device__ __forceinline__ bool bit_of(const uint32_t* m, uint32_t p) { return (m[p >> 5] >> (p & 31)) & 1u; }
-
-__device__ __forceinline__ float neighbour_weight(float3 a, float3 b, float inv2sig2) {
-  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-  const float th = 2.f * asinf(fminf(1.f, 0.5f * sqrtf(dx * dx + dy * dy + dz * dz)));
-  return __expf(-th * th * inv2sig2);
-}
 
 // Per 256-pixel block: sum of h_q, sum of |I - G| and the number of in-mask pixels.
 __global__ void __launch_bounds__(kNaThreads) k_value_partials(int k, const float* __restrict__ I,
@@ -50,39 +46,13 @@ __global__ void __launch_bounds__(kNaThreads) k_value_partials(int k, const floa
   const uint32_t npix = 12u << (2 * k);
   const uint32_t p = blockIdx.x * kNaThreads + threadIdx.x;
   double h = 0.0, l1 = 0.0, cnt = 0.0;
-  if (p < npix && bit_of(mask, p)) {
-    const float inv2sig2 = 1.f / (2.f * 2.25f * (4.f * (float)kPi / (float)npix));
-    const float3 cq = pix2vec_f32(k, p);
-    const FaceXY c = nest_to_fxy(k, p);
-    uint32_t idx[9];
-    float w[9];
-    int n = 0;
-    idx[n] = p; w[n] = 1.f; ++n;
-    for (int dx = -1; dx <= 1; ++dx)
-      for (int dy = -1; dy <= 1; ++dy) {
-        if (dx == 0 && dy == 0) continue;
-        const int64_t nb = neighbour_nest(k, c.f, c.x, c.y, dx, dy);
-        if (nb < 0 || !bit_of(mask, (uint32_t)nb)) continue;
-        idx[n] = (uint32_t)nb;
-        w[n] = neighbour_weight(cq, pix2vec_f32(k, (uint32_t)nb), inv2sig2);
-        ++n;
-      }
-    float Z = 0.f;
-    for (int j = 0; j < n; ++j) Z += w[j];
-    const float iZ = 1.f / Z;
-    float hs = 0.f;
-    for (int ch = 0; ch < 3; ++ch) {
-      float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
-      for (int j = 0; j < n; ++j) {
-        const float wj = w[j] * iZ;
-        const float x = I[3 * (size_t)idx[j] + ch], y = Gt[3 * (size_t)idx[j] + ch];
-        mx += wj * x; my += wj * y; xx += wj * x * x; yy += wj * y * y; xy += wj * x * y;
-      }
-      const float vx = xx - mx * mx, vy = yy - my * my, cxy = xy - mx * my;
-      hs += ((2.f * mx * my + kNaC1) * (2.f * cxy + kNaC2)) / ((mx * mx + my * my + kNaC1) * (vx + vy + kNaC2));
-      l1 += fabsf(I[3 * (size_t)p + ch] - Gt[3 * (size_t)p + ch]);
-    }
-    h = hs / 3.f;
+  if (p < npix && mask_bit(mask, p)) {
+    HWindow W;
+    hssim_window(k, p, mask, W);
+    float hq, l1q;
+    hssim_pixel_value(W, p, I, Gt, hq, l1q);
+    h = hq;
+    l1 = l1q;
     cnt = 1.0;
   }
   __shared__ double sh[3][kNaThreads / 32];
@@ -124,14 +94,21 @@ __global__ void k_value_reduce(const double* __restrict__ part, int nblocks, flo
 std::mutex g_addr_mu;
 double* g_addr[256];          // device address of g_partials, per device ordinal
 
-int partials_address(double** out) {
+// Address of g_partials on the current device. Outside stream capture it is looked up
+// on every call (so a module reloaded after cudaDeviceReset is seen) and cached; while
+// `s` is capturing only the cache is used, and a device with no cached address fails.
+int partials_address(cudaStream_t s, double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return HPXGS_E_CUDA;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return HPXGS_E_CUDA;
   std::lock_guard<std::mutex> lk(g_addr_mu);
-  if (!g_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_partials) != cudaSuccess || !p) return HPXGS_E_CUDA;
     g_addr[dev] = static_cast<double*>(p);
+  } else if (!g_addr[dev]) {
+    return HPXGS_E_CAPTURE;
   }
   *out = g_addr[dev];
   return HPXGS_OK;
@@ -146,10 +123,10 @@ extern "C" int hpxgs_hssim_loss_noalloc(const float* I, const float* G, const ui
                                         float* out3, hpxgs_stream_t stream) {
   if (k < 3 || k > kNaMaxOrder || !I || !G || !mask_bits || !out3 || !(lambda >= 0.f && lambda <= 1.f))
     return HPXGS_E_INVALID_ARG;
-  double* part = nullptr;
-  int rc = partials_address(&part);
-  if (rc != HPXGS_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  double* part = nullptr;
+  int rc = partials_address(s, &part);
+  if (rc != HPXGS_OK) return rc;
   const uint32_t npix = 12u << (2 * k);
   const int nblocks = (int)(npix / kNaThreads);
   k_value_partials<<<nblocks, kNaThreads, 0, s>>>(k, I, G, mask_bits, part);

@@ -125,12 +125,22 @@ struct Geo {
 
 __device__ __forceinline__ void geo_compute(const ViewParams& vp, float near_plane, const float* __restrict__ mu,
                                             const float* __restrict__ sc, const float* __restrict__ q, Geo& G) {
-  const float m0 = mu[0], m1 = mu[1], m2 = mu[2];
-  G.t.x = vp.W[0] * m0 + vp.W[1] * m1 + vp.W[2] * m2 + vp.b[0];
-  G.t.y = vp.W[3] * m0 + vp.W[4] * m1 + vp.W[5] * m2 + vp.b[1];
-  G.t.z = vp.W[6] * m0 + vp.W[7] * m1 + vp.W[8] * m2 + vp.b[2];
-  G.r = sqrtf(G.t.x * G.t.x + G.t.y * G.t.y + G.t.z * G.t.z);
-  G.valid = G.r > near_plane;
+  // t = W mu + b and the radial depth r = |t| in FP64, each product and sum rounded
+  // once in a fixed order (the _rn intrinsics are never contracted into FMAs), so that
+  // float32(r) -- the sort key and the near-plane test -- is the value any IEEE FP64
+  // evaluation in this order gives. The FP32 geometry below starts from float32(t).
+  const double m0 = mu[0], m1 = mu[1], m2 = mu[2];
+  double t64[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    t64[i] = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)vp.W[3 * i], m0), __dmul_rn((double)vp.W[3 * i + 1], m1)),
+                                 __dmul_rn((double)vp.W[3 * i + 2], m2)),
+                       (double)vp.b[i]);
+  const double r64 = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(t64[0], t64[0]), __dmul_rn(t64[2], t64[2])),
+                                          __dmul_rn(t64[1], t64[1])));
+  G.t = make_float3(__double2float_rn(t64[0]), __double2float_rn(t64[1]), __double2float_rn(t64[2]));
+  G.r = __double2float_rn(r64);
+  G.valid = r64 > (double)near_plane;
   if (!G.valid) return;
   const float ir = 1.0f / G.r;
   G.gc = make_float3(G.t.x * ir, G.t.y * ir, G.t.z * ir);

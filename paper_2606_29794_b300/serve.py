@@ -66,7 +66,7 @@ class RenderServer:
         self.cfg_by_level = {b: L.default_config(tile_level=b) for b in (3, 4, 5)}
         self.cfg = self.cfg_by_level[tile_level or 4]
         self.adaptive = tile_level is None or tile_level == 0
-        self.pairs_per_pixel = {}          # (k, kind) -> running max of pairs / in-mask-or-full pixel
+        self.pairs_per_pixel = {}          # (k, kind, tile level) -> running max of pairs per map pixel
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(slots)]
 
     def level_for(self, views):
@@ -77,19 +77,29 @@ class RenderServer:
         return 5 if max(v["nside_log2"] for v in views) >= 10 else 4
 
     # ---- memory model -------------------------------------------------------
-    def _estimate_pairs(self, v):
-        key = (v["nside_log2"], v["cam"], self.level_for([v]))
-        ppx = self.pairs_per_pixel.get(key)
+    # Pair densities are kept per (Nside, camera kind, tile level): a batch's tile level
+    # follows its largest view, so a view's list size is learned and predicted at the
+    # level of the batch it runs in.
+    def _estimate_pairs(self, v, level=None):
+        level = self.level_for([v]) if level is None else level
+        ppx = self.pairs_per_pixel.get((v["nside_log2"], v["cam"], level))
         if ppx is None:
             return None
         return int(ppx * R.npix(v["nside_log2"]) * self.headroom) + 4096
 
     def _learn(self, views, n_pairs):
+        level = self.level_for(views)
         px = sum(R.npix(v["nside_log2"]) for v in views)
         ppx = n_pairs / max(px, 1)
         for v in views:
-            key = (v["nside_log2"], v["cam"], self.level_for([v]))
+            key = (v["nside_log2"], v["cam"], level)
             self.pairs_per_pixel[key] = max(self.pairs_per_pixel.get(key, 0.0), ppx)
+
+    def _ensure_known(self, v, levels):
+        """Count the pairs of view v alone at each of `levels`, where not known yet."""
+        for level in levels:
+            if self._estimate_pairs(v, level) is None:
+                self._count([v], level)
 
     def _batch_bytes(self, views, cap):
         cv = L.make_views(views)
@@ -100,11 +110,13 @@ class RenderServer:
         px = sum(R.npix(v["nside_log2"]) for v in views)
         return n.value + px * (12 + 4 + 4) + px // 8 + 64, cv
 
-    def _count(self, views):
-        """Exact pair count of a batch (synchronises): used for a request kind never seen before."""
+    def _count(self, views, level=None):
+        """Exact pair count of a batch at a tile level (synchronises): used for a request kind
+        never seen before."""
+        level = self.level_for(views) if level is None else level
         cv = L.make_views(views)
         ws_n = ctypes.c_size_t()
-        cfg = self.cfg_by_level[self.level_for(views)]
+        cfg = self.cfg_by_level[level]
         L.check(L.lib().hpxgs_forward_workspace_size(self.g.P, cv, len(views), ctypes.byref(cfg), 0,
                                                      ctypes.byref(ws_n)), "workspace size")
         ws = torch.empty(ws_n.value, dtype=torch.uint8, device=self.dev)
@@ -115,7 +127,10 @@ class RenderServer:
                                           ctypes.c_void_p(ws.data_ptr()), ws_n.value, ctypes.c_void_p(cnt.data_ptr()),
                                           ctypes.c_void_p(st.data_ptr()), ctypes.c_void_p(s)), "count")
         n = int(cnt.item())
-        self._learn(views, n)
+        px = sum(R.npix(v["nside_log2"]) for v in views)
+        for v in views:
+            key = (v["nside_log2"], v["cam"], level)
+            self.pairs_per_pixel[key] = max(self.pairs_per_pixel.get(key, 0.0), n / max(px, 1))
         return n
 
     # ---- one batch ------------------------------------------------------------
@@ -156,12 +171,13 @@ class RenderServer:
         return job
 
     def _estimate_pairs_batch(self, views):
+        level = self.level_for(views)
         tot = 0
         for v in views:
-            e = self._estimate_pairs(v)
+            e = self._estimate_pairs(v, level)
             if e is None:
-                self._count([v])
-                e = self._estimate_pairs(v)
+                self._count([v], level)
+                e = self._estimate_pairs(v, level)
             tot += e
         return tot
 
@@ -175,9 +191,11 @@ class RenderServer:
     # ---- the request loop ---------------------------------------------------------
     def run(self, requests, plain=False, keep_outputs=False, time_limit_s=120.0):
         """Serve `requests` (dicts with 'arrival' seconds and 'view') in real time."""
-        for r in requests:                    # learn the pair density of every request kind up front
-            if self._estimate_pairs(r["view"]) is None:
-                self._count([r["view"]])
+        # learn the pair density of every request kind up front, at its own tile level and, when
+        # the stream holds a view that lifts a batch to level 5, at that level too
+        top = self.level_for([r["view"] for r in requests]) if requests else None
+        for r in requests:
+            self._ensure_known(r["view"], {self.level_for([r["view"]]), top})
         torch.cuda.synchronize()
         pending = collections.deque(sorted(requests, key=lambda r: r["arrival"]))
         waiting = collections.deque()
@@ -229,14 +247,16 @@ class RenderServer:
                 px = 0
                 while waiting and len(batch) < max_views:
                     v = waiting[0]["view"]
-                    e = self._estimate_pairs(v)
+                    cand = views + [v]
+                    level = self.level_for(cand)
+                    cap_c = sum(self._estimate_pairs(x, level) for x in cand)   # at the batch's level
                     npx = R.npix(v["nside_log2"])
-                    nb, _ = self._batch_bytes(views + [v], cap + e)
+                    nb, _ = self._batch_bytes(cand, cap_c)
                     if batch and (px + npx > self.max_pixels or used + nb > self.budget):
                         break
                     if not batch and used + nb > self.budget and inflight:
                         break                                  # wait for memory to free up
-                    batch.append(waiting.popleft()); views.append(v); cap += e; px += npx
+                    batch.append(waiting.popleft()); views.append(v); cap = cap_c; px += npx
                 if not batch:
                     break
                 slot = free.pop()

@@ -54,7 +54,7 @@ def test_density_statistics_match_oracle():
         n = O.npix(2 ** k)
         pix = np.nonzero(mask_all[base:base + n])[0].astype(np.int64)
         full = O.render(sc, _f64view(v), cfg)
-        ok = full.amb[pix] == 0
+        ok = full.amb[pix] == 0                  # pixels with a decision FP32 cannot settle carry no loss
         assert ok.mean() > 0.99
         dI = rng.standard_normal((pix.size, 3)) * ok[:, None]
         dm[base + pix] = dI

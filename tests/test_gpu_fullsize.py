@@ -6,22 +6,23 @@ list alone (Algorithm 1; with the m <= 9 cutoff the map does not depend on
 which other tiles exist). So for a seeded sample of active tiles the oracle
 builds only those lists (membership definition over every Gaussian) and
 composites a sample of their pixels. Each workload runs in the launch
-configuration the benchmark times (order-5 lists blended by 16 x 16 quarters for
-the training step and the Nside 2048 step, tile level 4 for the 16 views; default
-pixels per thread):
+configuration the benchmark times (order-5 lists blended by 16 x 16 quarters;
+default pixels per thread):
 
 - tile lists of the sampled tiles, rebuilt by the oracle from the GPU's stored
   FP32 (g, r_s, depth): exact, including order;
 - compositing of the sampled pixels by the oracle from the GPU's FP32 records
-  and those lists (same depth order by construction): maps and T within 2e-4,
-  the last index equal, at least 99% of pixels compared (cutoff-boundary
-  pixels excluded);
-- maps and T at the sampled pixels vs the oracle from scratch in FP64: 2e-4,
-  all ambiguous pixels excluded and counted. At these densities (1e5-1e6
-  Gaussians in depths [2, 6]) 4-6% of pixels have two contributors within 2e-6
-  relative depth, an order FP32 depths cannot settle, so the floor is 90%;
+  and those lists: maps and T within 2e-4 and the last index equal;
+- the depth keys: the GPU forms the radial depth in FP64 in the oracle's order
+  of operations, so the float32 sort keys are equal bit for bit;
+- maps and T at the sampled pixels vs the oracle from scratch in FP64: 2e-4.
+  In both comparisons a cutoff or termination decision that FP32 cannot settle
+  may take either outcome (tests.gpu_util.match_oracle), and at most 1e-5 of
+  the sampled pixels may be excluded (more such decisions than the oracle's
+  variants follow); the counts are printed;
 - gradients of a loss weighting only the sampled pixels vs the oracle's backward
-  over the same pixels: 1e-3 relative.
+  over the same pixels: 1e-3 relative (the oracle's backward runs on the
+  Gaussians listed in the sampled tiles, the only ones those pixels see).
 
 Workloads: Nside 512 fisheye 190 deg with 300k SH3 Gaussians (the training
 step); 16 views of three cameras over 1M SH3 Gaussians; Nside 2048 full sphere
@@ -34,7 +35,7 @@ import torch
 import oracle as O
 from paper_2606_29794_b300 import raster as R
 from paper_2606_29794_b300 import synth as S
-from tests.gpu_util import mask_from_words, oracle_cfg, scene_tensors
+from tests.gpu_util import MAX_EXCLUDED_SHARE, mask_from_words, match_oracle, oracle_cfg, scene_tensors
 
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
 
@@ -70,7 +71,7 @@ def _check_views(sc, views, rast, out, state, n_tiles, per_tile, seed):
     rng = np.random.default_rng(seed)
     res = []
     tile_base = 0
-    compared = total = staged_ok = 0
+    total = excluded = staged_ex = alt = 0
     for v, view in enumerate(views):
         k = view["nside_log2"]
         N = O.npix(2 ** k)
@@ -104,32 +105,48 @@ def _check_views(sc, views, rast, out, state, n_tiles, per_tile, seed):
         r32 = rec[sl].cpu().numpy().astype(np.float64)
         pre_g = dict(omega=np.arctan2(r32[:, 1], r32[:, 0]), phi=np.arctan2(r32[:, 2], np.hypot(r32[:, 0], r32[:, 1])),
                      conic=r32[:, [7, 11, 15]], col=r32[:, 12:15], r=depth[sl].cpu().numpy().astype(np.float64))
-        img, T, last, amb = O.composite(k, b, pre_g, r32[:, 3], st, ids_ref, pix, cfg)
-        ok = (amb & 1) == 0
-        staged_ok += int(ok.sum())
-        assert np.abs(maps[base + pix] - img)[ok].max() < MAP_TOL
-        assert np.abs(Tg[base + pix] - T)[ok].max() < MAP_TOL
-        assert (lastg[base + pix] == last)[ok].mean() >= 0.995
+        _, n_ex, n_alt, _ = match_oracle(k, b, pre_g, r32[:, 3], st, ids_ref, pix, cfg, maps[base + pix], Tg[base + pix],
+                                         gpu_last=lastg[base + pix])
+        staged_ex += n_ex
         # ---- maps and T at sampled pixels vs the oracle from scratch
         pre = O.preprocess(sc, _f64view(view), cfg)
+        # the depth keys: float32 of the same FP64 radial depth on both sides
+        assert np.array_equal(O.depth_bits(pre["r"])[valid], dbits[valid])
         act_ref = O.active_tiles(k, b, m_ref)
         st2, ids2 = O.tile_lists_subset(k, b, pre["g"], pre["rs"], pre["valid"], O.depth_bits(pre["r"]), rho,
                                         act_ref, tiles)
-        img, T, last, amb = O.composite(k, b, pre, sc["opacities"], st2, ids2, pix, cfg)
-        ok = amb == 0
-        compared += int(ok.sum()); total += ok.size
-        assert np.abs(maps[base + pix] - img)[ok].max() < MAP_TOL
-        assert np.abs(Tg[base + pix] - T)[ok].max() < MAP_TOL
+        _, n_ex, n_alt, amb = match_oracle(k, b, pre, sc["opacities"], st2, ids2, pix, cfg, maps[base + pix],
+                                           Tg[base + pix])
+        excluded += n_ex; alt += n_alt; total += pix.size
         res.append((pix, st2, ids2, amb))
         tile_base += 12 * 4 ** (k - b)
-    assert staged_ok >= 0.99 * total, (staged_ok, total)
-    assert compared >= 0.90 * total, (compared, total)
+    print(f"sampled pixels {total}: excluded {excluded} (staged {staged_ex}), matched by an FP32-band variant {alt}")
+    assert staged_ex <= MAX_EXCLUDED_SHARE * total, (staged_ex, total)
+    assert excluded <= MAX_EXCLUDED_SHARE * total, (excluded, total)
     return res
 
 
+def _oracle_backward_listed(sc, view, cfg, dI, st, ids, pix):
+    """The oracle's backward (Sec. 3.2) for the sampled pixels, run on the sub-scene of the
+    Gaussians their lists hold (the others cannot reach these pixels); gradients scattered
+    back to the full scene, zero elsewhere."""
+    P = sc["means"].shape[0]
+    used = np.unique(ids)
+    remap = np.full(P, -1, np.int64)
+    remap[used] = np.arange(used.size)
+    sub = {k: (np.asarray(v)[used] if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+    r = O.backward(sub, _f64view(view), cfg, dI, st, remap[ids], pix)
+    out = {}
+    for name, g in r.items():
+        full = np.zeros((P,) + g.shape[1:])
+        full[used] = g
+        out[name] = full
+    return out
+
+
 def _check_grads(sc, views, rast, out, state, sampled, seed, use=None):
-    """Gradients of sum_p dI_p . I_p over the sampled, unambiguous pixels of the
-    views `use` (default all); the backward still walks every view's tiles."""
+    """Gradients of sum_p dI_p . I_p over the sampled pixels of the views `use` (default all)
+    that have no FP32-undecidable decision; the backward still walks every view's tiles."""
     cfg = oracle_cfg(rast)
     lay = out["layout"]
     rng = np.random.default_rng(seed)
@@ -141,7 +158,7 @@ def _check_grads(sc, views, rast, out, state, sampled, seed, use=None):
         dI = rng.standard_normal((pix.size, 3)).astype(np.float32)
         dI[amb != 0] = 0.0
         dmaps[lay.pix_base[v] + pix] = dI
-        r = O.backward(sc, _f64view(view), cfg, dI.astype(np.float64), st, ids, pix)
+        r = _oracle_backward_listed(sc, view, cfg, dI.astype(np.float64), st, ids, pix)
         ref = r if ref is None else {n: ref[n] + r[n] for n in ref}
     grads = rast.backward_raw(state, torch.as_tensor(dmaps, device="cuda"))
     torch.cuda.synchronize()
@@ -196,7 +213,7 @@ def test_fused_loss_step_equals_two_pass_at_full_size(workload):
 def test_sixteen_views_p1m():
     sc = S.make_scene(1_000_000, 3, seed=20261206)
     views = S.multiview_set(20261208)
-    rast = R.Rasterizer(tile_level=4)
+    rast = R.Rasterizer(tile_level=5)       # the level the benchmark's autotuner picks for this workload
     out, state = rast.forward_raw(*scene_tensors(sc), 3, views)
     torch.cuda.synchronize()
     sampled = _check_views(sc, views, rast, out, state, n_tiles=6, per_tile=16, seed=3)
@@ -209,4 +226,6 @@ def test_nside2048_full_sphere_p6m():
     rast = R.Rasterizer(tile_level=5)
     out, state = rast.forward_raw(*scene_tensors(sc), 3, [view])
     torch.cuda.synchronize()
-    _check_views(sc, [view], rast, out, state, n_tiles=24, per_tile=16, seed=5)
+    sampled = _check_views(sc, [view], rast, out, state, n_tiles=24, per_tile=16, seed=5)
+    # the backward from the stored T_final and last index alone (recompute in backward)
+    _check_grads(sc, [view], rast, out, state, sampled, seed=6)

@@ -131,8 +131,8 @@ def test_mask_bits_match_oracle(k, kind, fx, fy):
 @pytest.mark.parametrize("k,kind,fx,fy", [(6, 0, 360, 360), (9, 2, 190, 190), (8, 1, 90, 90), (9, 1, 60, 100),
                                           (7, 2, 220, 180), (10, 2, 180, 180), (4, 2, 200, 200), (9, 1, 120, 100)])
 def test_forward_mask_equals_per_pixel_mask(k, kind, fx, fy):
-    # the forward builds the mask by 16-pixel sub-tiles (whole sub-tiles decided at their centre
-    # when the margin bound allows); it must equal the per-pixel mask of hpxgs_mask_build bit for bit
+    # the forward builds its own mask in its mask stage (one thread per pixel, an FP64 re-check
+    # near the FoV boundary); it must equal the mask of hpxgs_mask_build bit for bit
     import numpy as np
     from tests.gpu_util import scene_tensors
     view = S.make_view(k, kind, fx, fy)

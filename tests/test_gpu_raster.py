@@ -2,7 +2,9 @@
 
 Staged checks feed the oracle the GPU's stored FP32 per-Gaussian values so that
 tile lists and sort order can be compared exactly; end-to-end checks compare
-maps within 2e-4 per channel (ambiguous pixels excluded and counted) and
+maps within 2e-4 per channel against the oracle from scratch, where a cutoff or
+termination decision that FP32 cannot settle may take either outcome
+(tests.gpu_util.match_oracle; at most 1e-5 of the pixels excluded), and
 gradients within 1e-3 relative.
 """
 import numpy as np
@@ -12,7 +14,8 @@ import torch
 import oracle as O
 from paper_2606_29794_b300 import raster as R
 from paper_2606_29794_b300 import synth as S
-from tests.gpu_util import c1_scene, c1_view, gpu_render, mask_from_words, oracle_cfg, scene_tensors
+from tests.gpu_util import (MAX_EXCLUDED_SHARE, c1_scene, c1_view, gpu_render, mask_from_words, match_oracle,
+                            oracle_cfg, scene_tensors)
 
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
 
@@ -51,6 +54,9 @@ CASES = [
     ("pinhole_off_centre", lambda: (S.make_scene(2500, 3, seed=8),
                                     S.random_pose_view(np.random.default_rng(12), 7, S.CAM_PINHOLE, 100.0, 75.0,
                                                        pp=(0.35, -0.5))), 4),
+    # anisotropic fisheye, w_x != w_y (Sec. D.1, Eq. fish_weff)
+    ("fisheye_aniso_220x180", lambda: (S.make_scene(3000, 3, seed=9),
+                                       S.random_pose_view(np.random.default_rng(13), 7, S.CAM_FISHEYE, 220.0, 180.0)), 4),
 ]
 
 
@@ -98,22 +104,20 @@ def test_staged_records_lists_and_maps(name, make, b):
     pre_g = dict(omega=np.arctan2(rec[:, 1], rec[:, 0]), phi=np.arctan2(rec[:, 2], np.hypot(rec[:, 0], rec[:, 1])),
                  conic=conic_gpu, col=rec[:, 12:15], r=depth.astype(np.float64))
     pix = np.nonzero(m_gpu)[0].astype(np.int64)
-    img, T, last, amb = O.composite(k, b, pre_g, rec[:, 3], start, ids_ref, pix, cfg)
     mg = out["maps"].cpu().numpy()[pix]
-    ok = amb == 0
-    assert ok.mean() > 0.995
-    assert np.abs(mg - img)[ok].max() < MAP_TOL
     Tg = out["T"].cpu().numpy()[pix]
-    assert np.abs(Tg - T)[ok].max() < 2e-4
     lg = out["last"].cpu().numpy()[pix]
-    assert (lg[ok] == last[ok]).mean() > 0.999
-    # end to end (oracle from scratch in FP64)
+    n_ok, n_ex, _, _ = match_oracle(k, b, pre_g, rec[:, 3], start, ids_ref, pix, cfg, mg, Tg, gpu_last=lg)
+    assert n_ex <= MAX_EXCLUDED_SHARE * pix.size
+    # end to end (oracle from scratch in FP64): the depth keys are the same float32 values
+    # on both sides, so the order is the same; pixels whose mask decision the two sides take
+    # differently sit on the FoV boundary itself (FP64 margin < 1e-12, checked above)
     full = O.render(sc, _f64view(view), cfg)
-    # pixels whose mask decision the two sides take differently sit on the FoV
-    # boundary itself (FP64 margin < 1e-12, checked above): compare the rest
-    okf = (full.amb[pix] == 0) & (m_ref[pix] == 1)
-    assert okf.mean() > 0.995
-    assert np.abs(mg - full.image[pix])[okf].max() < MAP_TOL
+    assert np.array_equal(O.depth_bits(full.pre["r"])[valid], dbits[valid])
+    both = pix[m_ref[pix] == 1]
+    sel = m_ref[pix] == 1
+    n_ok, n_ex, _, _ = match_oracle(k, b, full.pre, sc["opacities"], full.start, full.ids, both, cfg, mg[sel], Tg[sel])
+    assert n_ex <= MAX_EXCLUDED_SHARE * both.size
     # outside the mask: background, T = 1
     outside = np.nonzero(m_gpu == 0)[0]
     if outside.size:
@@ -128,8 +132,9 @@ def test_maps_independent_of_tile_level(b):
     _, out, _ = gpu_render(sc, [view], rast)
     full = O.render(sc, _f64view(view), oracle_cfg(rast))
     pix = full.pix
-    ok = full.amb[pix] == 0
-    assert np.abs(out["maps"].cpu().numpy()[pix] - full.image[pix])[ok].max() < MAP_TOL
+    n_ok, n_ex, _, _ = match_oracle(7, b, full.pre, sc["opacities"], full.start, full.ids, pix, oracle_cfg(rast),
+                                 out["maps"].cpu().numpy()[pix], out["T"].cpu().numpy()[pix])
+    assert n_ex <= MAX_EXCLUDED_SHARE * pix.size
 
 
 def test_batched_views_equal_single_views():
@@ -221,3 +226,10 @@ def test_gradients_off_centre_pinhole():
     sc = S.make_scene(3000, 3, seed=43)
     view = S.random_pose_view(np.random.default_rng(11), 7, S.CAM_PINHOLE, 90.0, 70.0, 0.5, pp=(-0.6, 0.4))
     _grad_check(sc, view, 4, 3)
+
+
+def test_gradients_anisotropic_fisheye():
+    sc = S.make_scene(3000, 3, seed=44)
+    view = S.random_pose_view(np.random.default_rng(14), 7, S.CAM_FISHEYE, 220.0, 180.0, 0.5)
+    _grad_check(sc, view, 4, 4)
+

@@ -334,3 +334,38 @@ def test_joint_rotation_of_scene_and_camera_leaves_the_map_unchanged(kind, fov):
     assert ok[R1.pix].mean() > 0.99 and (R1.T[R1.pix] < 1).mean() > 0.2       # a non-trivial image
     assert np.abs(R1.image - R2.image)[ok].max() < 1e-10
     assert np.abs(R1.T - R2.T)[ok].max() < 1e-10
+
+
+@pytest.mark.parametrize("seed", [100, 101])
+def test_band_variants_equal_dense_with_moved_thresholds(seed):
+    # composite_variants follows both outcomes of a cutoff or termination decision whose FP64
+    # value lies within its FP32 band. Where a pixel has exactly one such decision (two leaves),
+    # the two leaves must be the dense reference's pixel value with that threshold moved to
+    # either edge of its band: cutoff (1 -+ 2e-5) for a cutoff decision, eps (1 -+ 1e-4) for a
+    # termination decision. An opaque scene makes both kinds frequent.
+    sc = S.make_scene(1500, 0, seed=seed, r_min=1.5, r_max=4.0, logscale_mu=-1.2)
+    sc["opacities"] = np.full_like(sc["opacities"], 0.9)
+    v = _f64view(S.make_view(6))
+    cfg = O.Config(tile_level=3)
+    R = O.render(sc, v, cfg)
+    a = R.amb[R.pix]
+    params = params_from_scene(sc)
+    for flag, field, band in ((O.AMB_CUTOFF, "cutoff", 2e-5), (O.AMB_TERM, "eps_T", 1e-4)):
+        sel = R.pix[a == flag]
+        V = O.composite_variants(6, 3, R.pre, sc["opacities"], R.start, R.ids, sel, cfg)
+        two = V["n"] == 2
+        assert two.sum() >= 15, (flag, two.sum())
+        sel, img, T = sel[two], V["image"][two], V["T"][two]
+        outs = []
+        for f in (1 - band, 1 + band):
+            c2 = O.Config(tile_level=3, **{field: getattr(cfg, field) * f})
+            with torch.no_grad():
+                C, Td = render_dense(params, v, c2, sel, 64)
+            outs.append((C.numpy(), Td.numpy()))
+        (Clo, Tlo), (Chi, Thi) = outs
+        d = lambda C1, T1, l: np.maximum(np.abs(C1 - img[:, l]).max(1), np.abs(T1 - T[:, l]))
+        straight = np.maximum(d(Clo, Tlo, 0), d(Chi, Thi, 1))
+        crossed = np.maximum(d(Clo, Tlo, 1), d(Chi, Thi, 0))
+        assert np.minimum(straight, crossed).max() < 1e-12
+        # the leaves really differ (a termination decision at the end of the list may not)
+        assert (np.abs(img[:, 0] - img[:, 1]).max(1) > 0).mean() > 0.9

@@ -49,9 +49,12 @@ def _server(budget, slots=3, max_views=4, max_pixels=64 << 20, ppx=2.0, first_co
     srv.g = g
     log = {"launches": []}
 
-    def count(views):
+    def count(views, level=None):
+        level = srv.level_for(views) if level is None else level
         n = int(ppx * _px(views) * first_count)
-        srv._learn(views, n)
+        for v in views:
+            key = (v["nside_log2"], v["cam"], level)
+            srv.pairs_per_pixel[key] = max(srv.pairs_per_pixel.get(key, 0.0), n / _px(views))
         return n
 
     def launch(views, cap, stream):
@@ -128,3 +131,20 @@ def test_underpredicted_capacity_is_rendered_again_and_learned():
     assert over and over[-1] < len(log["launches"]) - 1                 # the last launches fit
     for key, ppx in srv.pairs_per_pixel.items():
         assert ppx >= 2.0 - 1e-9                                         # learned up to the true density
+
+
+def test_pair_densities_are_kept_per_batch_tile_level():
+    # a batch holding an Nside-1024 view runs at tile level 5; what it learns is filed under
+    # level 5 for every view in it, and a smaller view alone is predicted at its own level 4
+    srv, _ = _server(budget=1 << 40)
+    small = S.make_view(8, S.CAM_FULL)
+    big = S.make_view(10, S.CAM_FISHEYE, 190.0)
+    srv._learn([small, big], 10 * (_px([small]) + _px([big])))
+    assert srv.pairs_per_pixel[(8, S.CAM_FULL, 5)] == pytest.approx(10.0)
+    assert srv.pairs_per_pixel[(10, S.CAM_FISHEYE, 5)] == pytest.approx(10.0)
+    assert (8, S.CAM_FULL, 4) not in srv.pairs_per_pixel
+    assert srv._estimate_pairs(small) is None                          # level 4 not learned yet
+    assert srv._estimate_pairs(small, 5) == int(10.0 * _px([small]) * 1.3) + 4096
+    srv._ensure_known(small, {4, 5})                                    # counts it at level 4 as well
+    assert (8, S.CAM_FULL, 4) in srv.pairs_per_pixel
+
