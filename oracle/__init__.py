@@ -584,3 +584,27 @@ def tile_lists_nested(k, b, log2f, g, rs, valid, dbits, active):
     lib().or_tile_lists_nested(ctypes.c_int(k), ctypes.c_int(b), ctypes.c_int(log2f), _i64(P), _p(g), _p(rs),
                                _p(valid), _p(dbits), _p(active), None, _p(ids))
     return start, ids
+
+
+# ---------------------------------------------------------------------------
+# RING query at a finer search resolution (Sec. 3.3, Sec. D.2: Algorithm 3 at order
+# k_t + log2 f, query pixels mapped to their tiles)
+# ---------------------------------------------------------------------------
+
+def tile_lists_ringf(k, b, log2f, g, rs, valid, dbits, active):
+    """CSR lists like tile_lists, with Algorithm 3 run at query order k - b + log2f: a tile
+    is listed once when one of its query pixels has its centre within r_s + rho(k, b - log2f)
+    (+1e-7) of the Gaussian and the tile is active. log2f = 0 is tile_lists."""
+    g = np.ascontiguousarray(g, np.float64); rs = np.ascontiguousarray(rs, np.float64)
+    valid = np.ascontiguousarray(valid, np.int32); dbits = np.ascontiguousarray(dbits, np.uint32)
+    active = np.ascontiguousarray(active, np.uint8)
+    P = rs.size
+    nt = 12 * 4 ** (k - b)
+    start = np.empty(nt + 1, np.int64)
+    lib().or_tile_lists_ringf.restype = ctypes.c_int64
+    m = lib().or_tile_lists_ringf(ctypes.c_int(k), ctypes.c_int(b), ctypes.c_int(log2f), _i64(P), _p(g), _p(rs),
+                                  _p(valid), _p(dbits), _p(active), _p(start), None)
+    ids = np.empty(m, np.int64)
+    lib().or_tile_lists_ringf(ctypes.c_int(k), ctypes.c_int(b), ctypes.c_int(log2f), _i64(P), _p(g), _p(rs),
+                              _p(valid), _p(dbits), _p(active), None, _p(ids))
+    return start, ids

@@ -1738,4 +1738,59 @@ i64 or_tile_lists_nested(int k, int b, int log2f, i64 P, const double* g, const 
   return (i64)pairs.size();
 }
 
+// ===========================================================================
+// RING query at a finer search resolution (Sec. 3.3 and Sec. D.2, "x f" search;
+// Algorithm 3 run at query order k_q = k_t + log2 f instead of the tile order).
+// Reading: the disc is enumerated over the order-k_q pixels with Algorithm 3, each
+// candidate pixel q is kept when its centre passes the membership test of the tile
+// query at that order, c_q . g >= cos(min(pi, r_s + rho_q + 1e-7)) with rho_q =
+// rho(k, b - log2 f) (the largest angle from an order-k_q centre to the render-pixel
+// centres it holds), and a tile is listed once when any of its pixels is kept and
+// it is active. With the m <= cutoff weight this is again conservative (a pixel
+// within r_s of g lies in a query pixel whose centre is within r_s + rho_q), and
+// finer f lists fewer tiles; log2 f = 0 is the tile-order query.
+// ===========================================================================
+static void tiles_of_ringf(int kt, int log2f, const double g[3], double rs, double rho_q, const u8* active,
+                           std::vector<i64>& out) {
+  const i64 nside_q = 1LL << (kt + log2f);
+  std::vector<i64> cand;
+  query_disc_ring(nside_q, g, std::min(kPi, rs + rho_q + 1e-7 + 1e-9), cand);
+  out.clear();
+  for (i64 q : cand) {
+    if (!tile_member(nside_q, q, g, rs, rho_q)) continue;
+    const i64 t = q >> (2 * log2f);                  // the order-k_t ancestor (NESTED)
+    if (active[t]) out.push_back(t);
+  }
+  std::sort(out.begin(), out.end());
+  out.erase(std::unique(out.begin(), out.end()), out.end());
+}
+
+i64 or_tile_lists_ringf(int k, int b, int log2f, i64 P, const double* g, const double* rs, const int* valid,
+                        const u32* depth_bits, const u8* active, i64* start, i64* ids) {
+  const int kt = k - b;
+  const i64 ntile = 12LL << (2 * kt);
+  // at log2 f = b the query pixels are the render pixels: rho_q = 0 exactly
+  const double rho_q = (b == log2f) ? 0.0 : tile_rho(k, b - log2f);
+  std::vector<std::vector<i64>> per(P);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (i64 i = 0; i < P; ++i)
+    if (valid[i]) tiles_of_ringf(kt, log2f, g + 3 * i, rs[i], rho_q, active, per[i]);
+  struct Pair { i64 tile; u32 depth; i64 id; };
+  std::vector<Pair> pairs;
+  for (i64 i = 0; i < P; ++i) for (i64 t : per[i]) pairs.push_back({t, depth_bits[i], i});
+  std::stable_sort(pairs.begin(), pairs.end(), [](const Pair& a, const Pair& c) {
+    if (a.tile != c.tile) return a.tile < c.tile;
+    if (a.depth != c.depth) return a.depth < c.depth;
+    return a.id < c.id;
+  });
+  if (start) {
+    std::fill(start, start + ntile + 1, 0);
+    for (auto& q : pairs) start[q.tile + 1]++;
+    for (i64 t = 0; t < ntile; ++t) start[t + 1] += start[t];
+  }
+  if (ids) for (size_t q = 0; q < pairs.size(); ++q) ids[q] = pairs[q].id;
+  return (i64)pairs.size();
+}
+
 }  // extern "C"
+
