@@ -10,9 +10,11 @@ stages). Metric: in-mask Mpix/s of fwd+bwd (higher is better).
 
 `value` times the device path with inputs resident in HBM (CUDA events per
 step, L2 flushed between steps). `e2e` times the same step through the public
-API with the step's input (the target map) copied from pinned host memory and
-the loss read back every step. `--impl reference` times the FP64 CPU oracle on
-a bounded sample of the same workload.
+API with the step's input, the 8-bit fisheye camera image of the target, copied
+from pinned host memory and resampled onto the HEALPix grid inside the step,
+and the loss read back every step. `--impl reference` (and `cpu_baseline`)
+time the FP64 CPU oracle: the per-Gaussian work of a step in full, the
+per-pixel work on a sample. `--oracle-full` times the oracle's whole step.
 """
 from __future__ import annotations
 
@@ -35,6 +37,7 @@ K_ORDER = 9
 FOV = 190.0
 SEED = 20261205
 WORKLOAD = "train_step_nside512_fisheye190_P300k_sh3"
+IMG_SIDE = 1472          # the fisheye camera image of the end-to-end step (about the same pixel count as the mask)
 
 SM_COUNT, FP32_LANES = 148, 128
 
@@ -59,6 +62,8 @@ def parse():
     ap.add_argument("--no-resample", action="store_true")
     ap.add_argument("--no-query-compare", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=800)
+    ap.add_argument("--oracle-full", action="store_true",
+                    help="time the FP64 oracle in full (all cores and one thread) and exit")
     return ap.parse_args()
 
 
@@ -319,16 +324,30 @@ def run_ours(args, ws_n, rank, local):
     # ---------------- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        # the public API with host buffers: the graph copies the pinned host target in (overlapping
-        # the forward render) at every replay; the loss is read back to pinned host memory
-        hostG = torch.empty(G.shape, dtype=torch.float32, pin_memory=True)
-        hostG.copy_(G.cpu())
+        from paper_2606_29794_b300 import resample as RS
+        # the step's input as a camera delivers it: the 8-bit fisheye image of the target (the
+        # perturbed scene's render resampled to 1472 x 1472 and quantised), in pinned host memory.
+        # Every replay copies it in on a forked stream (overlapping the forward render) and
+        # resamples it onto the HEALPix grid as the target (Eq. supp_image_to_healpix); the loss
+        # is read back to pinned host memory.
+        img, _ = RS.sphere_to_image_raw(G, K_ORDER, view, IMG_SIDE, IMG_SIDE)
+        img8 = torch.round(img.clamp(0.0, 1.0) * 255.0).to(torch.uint8)
+        host_img = torch.empty(img8.shape, dtype=torch.uint8, pin_memory=True)
+        host_img.copy_(img8.cpu())
         hloss = torch.empty(1, dtype=torch.float32, pin_memory=True)
         estep = R.GraphStep(params, 3, [view], torch.empty_like(G), R.Rasterizer(tile_level=args.tile_level),
-                            host_targets=hostG)
+                            host_images=[host_img])
+        # the same step fed the float image v / 255 already on the device: the loss must agree
+        fimg = img8.float() / 255.0
+        Gf = torch.empty_like(G)
+        RS.image_to_sphere_into(fimg, view, K_ORDER, Gf)
+        fstep = R.GraphStep(params, 3, [view], Gf, R.Rasterizer(tile_level=args.tile_level))
+        fstep.replay()
         for _ in range(2):
             estep.replay(); hloss.copy_(estep.losses[0, :1], non_blocking=True)
         torch.cuda.synchronize()
+        loss_f = float(fstep.losses[0, 0].item())
+        del fstep
         ev = []
         for _ in range(args.steps):
             flush.zero_()
@@ -341,8 +360,11 @@ def run_ours(args, ws_n, rank, local):
         torch.cuda.synchronize()
         e_ms = RP.job_time_ms(sum(a.elapsed_time(b) for a, b in ev) / len(ev))
         e2e = {"value": round(n_job / (e_ms * 1e-3) / 1e6, 2), "unit": "Mpix/s",
-               "h2d_bytes_per_step": int(hostG.numel() * 4), "d2h_bytes_per_step": 4, "ms_per_step": round(e_ms, 4),
-               "loss_matches_device_path": bool(abs(float(hloss.item()) - float(gstep.losses[0, 0].item())) <= 1e-6)}
+               "h2d_bytes_per_step": int(host_img.numel()), "d2h_bytes_per_step": 4, "ms_per_step": round(e_ms, 4),
+               "input": f"8-bit fisheye camera image {IMG_SIDE} x {IMG_SIDE} x 3 (pinned host), resampled onto the "
+                        f"HEALPix grid inside the step",
+               "loss": float(hloss.item()), "loss_float_image_path": loss_f,
+               "loss_matches_float_image_path": bool(abs(float(hloss.item()) - loss_f) <= 2e-6)}
         del estep
     npix_full = 12 * 4 ** K_ORDER
     res = {
@@ -553,9 +575,10 @@ def run_resample(args, dev):
 
 
 def run_query_compare(args, dev):
-    """Tile query variants on the training-step workload (Sec. 3.3): RING (Algorithm 3 at the
-    tile order, the default) against the NESTED quadtree search (Algorithm 2) refined x1, x2, x4.
-    Both list every tile the cutoff ellipse reaches, so the step computes the same maps; reported:
+    """Tile query variants on the training-step workload (Sec. 3.3): RING (Algorithm 3) at the tile
+    order (the default) and at search resolution x2 and x4 (Sec. D.2), against the NESTED quadtree
+    search (Algorithm 2) refined x1, x2, x4. All list every tile the cutoff ellipse reaches, so the
+    step computes the same maps; reported:
     the query stages (count + emit, CUDA events), the whole step (graph replays), and the whole
     step under the literal tile semantics (infinite cutoff), where the maps depend on the query."""
     import numpy as np
@@ -571,7 +594,9 @@ def run_query_compare(args, dev):
         G = R.Rasterizer(tile_level=4).forward_raw(*_tensors(S.perturb_scene(sc, SEED + 1), dev), 3, [view])[0]["maps"].clone()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    modes = [("ring", dict(query=L.QUERY_RING)), ("nested_x1", dict(query=L.QUERY_NESTED, query_log2f=0)),
+    modes = [("ring", dict(query=L.QUERY_RING)), ("ring_x2", dict(query=L.QUERY_RING, query_log2f=1)),
+             ("ring_x4", dict(query=L.QUERY_RING, query_log2f=2)),
+             ("nested_x1", dict(query=L.QUERY_NESTED, query_log2f=0)),
              ("nested_x2", dict(query=L.QUERY_NESTED, query_log2f=1)), ("nested_x4", dict(query=L.QUERY_NESTED, query_log2f=2))]
     out = {}
     for name, kw in modes:
@@ -613,94 +638,181 @@ def run_query_compare(args, dev):
         if name != "ring":
             out[name]["query_time_vs_ring"] = round(out[name]["query_ms"] / out["ring"]["query_ms"], 2)
             out[name]["literal_step_vs_ring"] = round(out[name]["step_ms_literal"] / out["ring"]["step_ms_literal"], 2)
-    out["paper_claim"] = "RING about 1.7x faster than NESTED (Sec. 3.3, Table ablation: R(x4) 28.2 min vs D(x4) 49.1 min)"
+    # the ablation's pairing: both queries at the x4 search resolution, literal tile semantics
+    out["nested_x4_over_ring_x4_literal_step"] = round(out["nested_x4"]["step_ms_literal"] / out["ring_x4"]["step_ms_literal"], 2)
+    out["nested_x4_over_ring_x4_query"] = round(out["nested_x4"]["query_ms"] / out["ring_x4"]["query_ms"], 2)
+    out["paper_claim"] = ("RING about 1.7x faster than NESTED (Sec. 3.3, Table ablation: R(x4) 28.2 min vs D(x4) 49.1 min "
+                          "of end-to-end training, ratio 1.74)")
     return out
 
 
 # ----------------------------------------------------------------------------- oracle
-def oracle_sample(frac, seed=0, with_bwd=True):
-    """Time the FP64 oracle on a random `frac` of the active tiles of the workload.
-    Returns (seconds for the fixed part, seconds for the sampled part, sampled px, in-mask px)."""
+def cpu_info():
+    model = None
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+_ORACLE_WL = {}
+
+
+def oracle_workload():
+    """The training-step workload as the oracle takes it (built once per process)."""
+    if not _ORACLE_WL:
+        import numpy as np
+
+        import oracle as O
+        from paper_2606_29794_b300 import synth as S
+        sc = S.make_scene(P_GAUSS, 3, seed=SEED)
+        view = S.make_view(K_ORDER, S.CAM_FISHEYE, FOV)
+        cfg = O.Config(tile_level=4)
+        m, _ = O.mask(2 ** K_ORDER, view["cam"], FOV)
+        _ORACLE_WL.update(
+            sc=sc, tgt=S.perturb_scene(sc, SEED + 1), cfg=cfg, mask=m,
+            v64=dict(view, W=np.asarray(view["W"], np.float64), b=np.asarray(view["b"], np.float64)),
+            active=O.active_tiles(K_ORDER, cfg.tile_level, m), rho=O.tile_rho(K_ORDER, cfg.tile_level),
+            pix=np.nonzero(m)[0].astype(np.int64))
+    return _ORACLE_WL
+
+
+# Share of the in-mask pixels on which a sampled oracle step runs its per-pixel work.
+ORACLE_FRAC = 0.05
+
+
+def oracle_step(frac, seed=0):
+    """One L1 + HSSIM training step of the FP64 oracle on the training-step workload.
+
+    Work that does not scale with the pixels runs in full: preprocess of the scene and of the
+    target scene, their tile lists over every active tile (Algorithm 3), and the backward's
+    per-Gaussian chain (its preprocess and the chain to the parameters, timed as a backward over
+    one pixel). The per-pixel work (compositing of both scenes, the HSSIM loss and gradient, the
+    backward blend) runs on a random `frac` of the in-mask pixels and is scaled by 1 / frac;
+    frac = 1 is the whole step, timed as it runs. Returns the seconds of each part and the
+    step estimate."""
+    import numpy as np
+
+    import oracle as O
+    W = oracle_workload()
+    sc, tgt, cfg, v64, m, act, rho, pix = (W[k] for k in ("sc", "tgt", "cfg", "v64", "mask", "active", "rho", "pix"))
+    b = cfg.tile_level
+    rng = np.random.default_rng(seed)
+    sel = pix if frac >= 1.0 else np.sort(rng.choice(pix, max(1, int(round(frac * pix.size))), replace=False))
+    msel = m
+    if frac < 1.0:
+        msel = np.zeros_like(m)
+        msel[sel] = 1
+    t0 = time.perf_counter()
+    pre = O.preprocess(sc, v64, cfg)
+    pre_t = O.preprocess(tgt, v64, cfg)
+    st, ids = O.tile_lists(K_ORDER, b, pre["g"], pre["rs"], pre["valid"], O.depth_bits(pre["r"]), rho, act)
+    st_t, ids_t = O.tile_lists(K_ORDER, b, pre_t["g"], pre_t["rs"], pre_t["valid"], O.depth_bits(pre_t["r"]), rho, act)
+    t1 = time.perf_counter()
+    img = O.composite(K_ORDER, b, pre, sc["opacities"], st, ids, sel, cfg)[0]
+    timg = O.composite(K_ORDER, b, pre_t, tgt["opacities"], st_t, ids_t, sel, cfg)[0]
+    t2 = time.perf_counter()
+    N = O.npix(2 ** K_ORDER)
+    I = np.zeros((N, 3)); G = np.zeros((N, 3))
+    I[sel] = img; G[sel] = timg
+    # the loss over the sampled pixels' windows: the same work per pixel as over the whole mask
+    _, _, _, dI = O.hssim_loss(2 ** K_ORDER, I, G, msel, cfg.lam)
+    t3 = time.perf_counter()
+    O.backward(sc, v64, cfg, dI[sel], st, ids, sel)
+    t4 = time.perf_counter()
+    parts = {"fixed_fwd_s": t1 - t0, "composite_s": t2 - t1, "hssim_s": t3 - t2, "backward_s": t4 - t3}
+    if frac >= 1.0:
+        est = t4 - t0
+    else:
+        O.backward(sc, v64, cfg, dI[sel[:1]], st, ids, sel[:1])
+        b0 = time.perf_counter() - t4                       # the backward's per-Gaussian part
+        parts["backward_fixed_s"] = b0
+        est = (t1 - t0) + b0 + ((t2 - t1) + (t3 - t2) + max(0.0, (t4 - t3) - b0)) / (sel.size / pix.size)
+    parts.update(step_s=est, sampled_px=int(sel.size), in_mask_px=int(pix.size))
+    return parts
+
+
+def _oracle_record(parts_list, frac):
+    import oracle as O
+    est = sum(p["step_s"] for p in parts_list) / len(parts_list)
+    nmask = parts_list[0]["in_mask_px"]
+    mean = lambda k: round(sum(p.get(k, 0.0) for p in parts_list) / len(parts_list), 3)
+    return est, {"value": round(nmask / est / 1e6, 6), "unit": "Mpix/s", "cores": O.num_threads(), "kind": "oracle",
+                 "cpu": cpu_info(),
+                 "sample": (f"FP64 oracle (C++/OpenMP), one training step per sample: preprocess of both scenes, "
+                            f"tile lists over every active tile and the backward's per-Gaussian chain in full; "
+                            f"compositing of both scenes, HSSIM loss + gradient and the backward blend on a random "
+                            f"{frac:.4f} of the {nmask} in-mask px, scaled by 1/{frac:.4f}"),
+                 "parts_s": {k: mean(k) for k in ("fixed_fwd_s", "composite_s", "hssim_s", "backward_s",
+                                                  "backward_fixed_s")},
+                 "step_s": round(est, 3)}
+
+
+def cpu_baseline():
+    oracle_workload()
+    _, rec = _oracle_record([oracle_step(ORACLE_FRAC, seed=1)], ORACLE_FRAC)
+    return rec
+
+
+def run_reference(args):
+    oracle_workload()
+    frac = ORACLE_FRAC
+    for i in range(args.warmup):
+        oracle_step(frac, seed=1000 + i)
+    parts = [oracle_step(frac, seed=i) for i in range(args.steps)]
+    est, cb = _oracle_record(parts, frac)
+    value = cb["value"]
+    return {"impl": "reference", "metric": "Mpix/s fwd+bwd at Nside 512/300k Gaussians (L1+HSSIM training step)",
+            "value": value, "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(est * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD}, "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_oracle_full(args):
+    """The FP64 oracle timed in full: the plain forward render of Nside 64 with 2,000 SH0
+    Gaussians, and the whole training step at Nside 512 (fisheye 190 deg, 300k SH3), each at
+    every core and at one thread; beside them the sampled model of the same step."""
     import numpy as np
 
     import oracle as O
     from paper_2606_29794_b300 import synth as S
-
-    sc = S.make_scene(P_GAUSS, 3, seed=SEED)
-    tgt_scene = S.perturb_scene(sc, SEED + 1)
-    view = S.make_view(K_ORDER, S.CAM_FISHEYE, FOV)
-    v64 = dict(view); v64["W"] = np.asarray(view["W"], np.float64); v64["b"] = np.asarray(view["b"], np.float64)
-    cfg = O.Config()
-    nside = 2 ** K_ORDER
-    m, _ = O.mask(nside, view["cam"], FOV)
-    act = O.active_tiles(K_ORDER, cfg.tile_level, m)
-    rng = np.random.default_rng(seed)
-    tiles = np.nonzero(act)[0]
-    pick = rng.choice(tiles, size=max(1, int(round(frac * tiles.size))), replace=False)
-    sub = np.zeros_like(act); sub[pick] = 1
-    per = 4 ** cfg.tile_level
-    pix = (pick[:, None] * per + np.arange(per)[None, :]).ravel()
-    pix = pix[m[pix] == 1].astype(np.int64)
-    rho = O.tile_rho(K_ORDER, cfg.tile_level)
-    t0 = time.perf_counter()
-    pre = O.preprocess(sc, v64, cfg)
-    pre_t = O.preprocess(tgt_scene, v64, cfg)
-    t1 = time.perf_counter()
-    start, ids = O.tile_lists(K_ORDER, cfg.tile_level, pre["g"], pre["rs"], pre["valid"], O.depth_bits(pre["r"]), rho, sub)
-    st2, ids2 = O.tile_lists(K_ORDER, cfg.tile_level, pre_t["g"], pre_t["rs"], pre_t["valid"], O.depth_bits(pre_t["r"]), rho, sub)
-    img, T, last, amb = O.composite(K_ORDER, cfg.tile_level, pre, sc["opacities"], start, ids, pix, cfg)
-    timg, _, _, _ = O.composite(K_ORDER, cfg.tile_level, pre_t, tgt_scene["opacities"], st2, ids2, pix, cfg)
-    N = O.npix(nside)
-    I = np.zeros((N, 3)); Gm = np.zeros((N, 3)); I[pix] = img; Gm[pix] = timg
-    O.hssim_local(nside, I, Gm, m, pix)
-    if with_bwd:
-        dI = np.random.default_rng(1).standard_normal((pix.size, 3)) * 1e-6
-        O.backward(sc, v64, cfg, dI, start, ids, pix)
-    t2 = time.perf_counter()
-    return t1 - t0, t2 - t1, int(pix.size), int(m.sum())
-
-
-def cpu_baseline(target_s=12.0):
-    import oracle as O
-    f = 0.002
-    fixed, samp, npx, nmask = oracle_sample(f)
-    # grow the sample to about target_s seconds of sampled work (bounded)
-    if samp < target_s / 4:
-        f = min(0.2, f * target_s / max(samp, 1e-3))
-        fixed, samp, npx, nmask = oracle_sample(f, seed=1)
-    est = fixed + samp * nmask / npx
-    return {"value": round(nmask / est / 1e6, 5), "unit": "Mpix/s", "cores": O.num_threads(), "kind": "oracle",
-            "sample": (f"FP64 oracle (C++/OpenMP) on {npx} px of {nmask} in-mask px (random {f:.4f} of active "
-                       f"tiles): preprocess of both scenes + tile lists + composite of render and target + HSSIM "
-                       f"forward + backward on the sample; full step estimated as fixed {fixed:.2f} s + "
-                       f"sample {samp:.2f} s x {nmask / npx:.1f}")}
-
-
-def run_reference(args):
-    import oracle as O
-    f = 0.002
-    for _ in range(args.warmup):
-        oracle_sample(f, seed=99, with_bwd=False)
-    times = []
-    npx = nmask = 0
-    for i in range(args.steps):
-        fixed, samp, npx, nmask = oracle_sample(f, seed=i)
-        times.append(fixed + samp * nmask / npx)
-    est = sum(times) / len(times)
-    value = nmask / est / 1e6
-    cb = {"value": round(value, 5), "unit": "Mpix/s", "cores": O.num_threads(), "kind": "oracle",
-          "sample": f"per step: random {f} of active tiles ({npx} px), full step estimated by scaling the sampled part"}
-    return {"impl": "reference", "metric": "Mpix/s fwd+bwd at Nside 512/300k Gaussians (L1+HSSIM training step)",
-            "value": round(value, 5), "unit": "Mpix/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(est * 1e3, 2), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD}, "cpu_baseline": cb,
-            "e2e": {"value": round(value, 5), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    ncore = O.num_threads()
+    out = {"cpu": cpu_info(), "threads_all": ncore}
+    sc1 = S.make_scene(2000, 0, seed=20261204)
+    v1 = S.make_view(6)
+    v1 = dict(v1, W=np.asarray(v1["W"], np.float64), b=np.asarray(v1["b"], np.float64))
+    oracle_workload()
+    frac = ORACLE_FRAC
+    for th in (ncore, 1):
+        O.set_threads(th)
+        t = time.perf_counter()
+        O.render(sc1, v1, O.Config())
+        c1 = time.perf_counter() - t
+        full = oracle_step(1.0)
+        model = oracle_step(frac, seed=7)
+        out[f"threads_{th}"] = {
+            "forward_nside64_p2k_s": round(c1, 4), "forward_nside64_p2k_mpix_s": round(49152 / c1 / 1e6, 4),
+            "train_step_full_s": round(full["step_s"], 2), "train_step_full_mpix_s": round(full["in_mask_px"] / full["step_s"] / 1e6, 6),
+            "train_step_full_parts_s": {k: round(v, 3) for k, v in full.items() if k.endswith("_s") and k != "step_s"},
+            "train_step_model_s": round(model["step_s"], 2), "model_frac": round(frac, 4),
+            "model_over_full": round(model["step_s"] / full["step_s"], 3)}
+    O.set_threads(ncore)
+    return out
 
 
 def main():
     args = parse()
     ws_n, rank, local = dist_env()
+    if args.oracle_full:
+        if rank == 0:
+            print(json.dumps(run_oracle_full(args)))
+        return 0
     if args.impl == "reference":
         if rank != 0:
             return 0

@@ -113,10 +113,14 @@ typedef struct {
   int32_t fwd_ppt;
   int32_t bwd_ppt;
   int32_t blocks_per_sm;
-  /* tile query (Sec. 3.3): HPXGS_QUERY_RING (default; Algorithm 3 at the tile order
-   * with the exact membership test) or HPXGS_QUERY_NESTED (Algorithm 2, the
-   * quadtree search refined down to tile order + query_log2f, 0..3). Both list
-   * every tile the cutoff ellipse can reach, so the maps do not depend on it. */
+  /* tile query (Sec. 3.3): HPXGS_QUERY_RING (default; Algorithm 3 with the exact
+   * membership test) or HPXGS_QUERY_NESTED (Algorithm 2, the quadtree search refined
+   * down to tile order + query_log2f). query_log2f (0..3, at most tile_level, default 0)
+   * is the search refinement f = 2^query_log2f of either query: RING x f runs Algorithm 3
+   * at order k_t + query_log2f (Sec. D.2) and lists a tile once when one of its query
+   * pixels has its centre within r_s + rho(k, tile_level - query_log2f) + 1e-7 of the
+   * Gaussian. Every choice lists every tile the cutoff ellipse can reach, so with the
+   * default cutoff the maps do not depend on it; under cutoff_m = INFINITY they do. */
   int32_t query;
   int32_t query_log2f;
   /* 1 (default): the blends skip a list entry for each group of 32 pixels that a
@@ -324,6 +328,12 @@ int hpxgs_sphere_to_image_backward(const float* dimage, int nside_log2, const hp
  * words, may be NULL) gets M_C (Eq. supp_hssim_mask), the same mask as hpxgs_mask_build. */
 int hpxgs_image_to_sphere(const float* image, int width, int height, const hpxgs_camera* cam, int nside_log2,
                           float* map, uint32_t* mask_bits, hpxgs_stream_t stream);
+/* The same for an 8-bit camera image ([height, width, 3] bytes, the form a camera delivers):
+ * code v is the value v / 255 (IEEE division), so the map equals hpxgs_image_to_sphere's on
+ * the float image holding v / 255, bit for bit. A training step can take its target as the
+ * camera image itself, a quarter of the bytes of a float image. */
+int hpxgs_image_to_sphere_u8(const uint8_t* image, int width, int height, const hpxgs_camera* cam, int nside_log2,
+                             float* map, uint32_t* mask_bits, hpxgs_stream_t stream);
 
 /* ---- instrumentation ---- */
 /* Stages that hpxgs_profile_arm can time. */

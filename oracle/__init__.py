@@ -81,6 +81,11 @@ def num_threads() -> int:
     return lib().or_num_threads()
 
 
+def set_threads(n: int) -> None:
+    """Use n OpenMP threads in the oracle's parallel loops from now on (timing only)."""
+    lib().or_set_threads(ctypes.c_int(int(n)))
+
+
 # ---------------------------------------------------------------------------
 # HEALPix (Sec. 3.1; Gorski et al. 2005; Calabretta & Roukema 2007)
 # ---------------------------------------------------------------------------

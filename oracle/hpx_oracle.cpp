@@ -1581,6 +1581,15 @@ int or_num_threads() {
 #endif
 }
 
+// Threads of the following parallel regions (timing at a chosen core count).
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 
 // ---- resampling ----
 int or_img_to_dir(int kind, double W, double H, double fovx, double fovy,

@@ -113,6 +113,8 @@ _SIGS = {
                                                       _vp, _vp]),
     "hpxgs_image_to_sphere": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _P(Camera), ctypes.c_int, _vp, _vp,
                                              _vp]),
+    "hpxgs_image_to_sphere_u8": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _P(Camera), ctypes.c_int, _vp,
+                                                _vp, _vp]),
     "hpxgs_launch_count": (ctypes.c_uint64, []),
     "hpxgs_probe_alu_peak": (ctypes.c_int, [_P(_f64), _P(_f64), ctypes.c_void_p]),
     "hpxgs_hssim_table_size": (ctypes.c_int, [ctypes.c_int, _P(_sz)]),

@@ -351,6 +351,20 @@ int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nvi
     // Gaussian, the node lies within PixRad(k_t) of the tile centre, and an in-mask
     // pixel within rho of it: the cap grows by those radii instead of 2 rho
     double reach = 2.0 * p.rho;
+    p.rhoq = 0.0; p.rhoq32 = 0.f; p.rhoc32 = 0.f;
+    if (need_rho && cfg->query == HPXGS_QUERY_RING && cfg->query_log2f > 0) {
+      // a tile is listed from a query pixel within r_s + rho_q of the Gaussian whose centre
+      // lies within rho_c of the tile centre (at log2f = b the query pixels are the render
+      // pixels, rho_q = 0 exactly)
+      const int L = cfg->query_log2f, kt = p.k - cfg->tile_level;
+      double rc = 0;
+      int rc2 = L == cfg->tile_level ? HPXGS_OK : tile_rho(p.k, cfg->tile_level - L, &p.rhoq, stream);
+      if (rc2 == HPXGS_OK) rc2 = tile_rho(kt + L, L, &rc, stream);
+      if (rc2 != HPXGS_OK) return rc2;
+      p.rhoq32 = (float)p.rhoq;
+      p.rhoc32 = (float)rc;
+      reach = p.rho + rc + p.rhoq;
+    }
     if (need_rho && cfg->query == HPXGS_QUERY_NESTED) {
       double a = 0, c = 0;
       const int kt = p.k - cfg->tile_level;
@@ -479,7 +493,7 @@ void hpxgs_config_default(hpxgs_config* c) {
   c->bwd_ppt = 0;
   c->blocks_per_sm = 0;
   c->query = HPXGS_QUERY_RING;
-  c->query_log2f = 2;
+  c->query_log2f = 0;
   c->blend_cull = 1;
   c->blend_split = 1;
 }

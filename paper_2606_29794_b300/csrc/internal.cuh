@@ -27,6 +27,11 @@ struct ViewParams {
   int64_t pix_base;    // first pixel of this view in packed outputs
   int tile_base;       // first global tile id of this view
   float rho_sub32;     // rho(k, 2): 4 x 4 sub-tile centre to pixel bound (the blend's cull)
+  // RING query at search order k_t + log2f (log2f > 0): rho_q = rho(k, b - log2f), the
+  // query-pixel centre to render-pixel bound of the membership test, and rho_c =
+  // rho(k_t + log2f, log2f), the tile centre to query-pixel centre bound
+  double rhoq;
+  float rhoq32, rhoc32;
 };
 
 struct ViewTable {
@@ -39,7 +44,7 @@ struct ViewTable {
   int write_outside;
   int total_tiles;
   int query;           // HPXGS_QUERY_*
-  int log2f;           // NESTED query: refinement below the tile order
+  int log2f;           // refinement of the tile query below the tile order (RING: search order k_t + log2f)
   int cull;            // 1: the blends' per-(entry, 32-pixel group) cull is on
   float pixrad32[16];  // NESTED query: PixRad(o), o = 0 .. deepest order used
   double pixrad64[16];

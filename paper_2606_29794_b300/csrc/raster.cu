@@ -470,15 +470,26 @@ __device__ __forceinline__ void ring_phi_frac(int k, int i, int j, int& num, int
 // a ballot, which keeps the emission order deterministic.
 struct DiscQ {
   float zc, sc, omc, zmin, zmax, cosRe, cosRm32;
+  float cosRa32, cosRq32;   // RING x f only: quick-accept and query-pixel thresholds
   int ilo, ihi;
 };
 
+// RF: the RING query at search order k_t + log2f. Candidate tiles are the tiles whose
+// centre lies within r_s + rho_q + rho_c (+1e-7) of the Gaussian, enumerated by
+// Algorithm 3 at the tile order; each is then tested on its query pixels.
+template <bool RF>
 __device__ __forceinline__ void disc_setup(const ViewParams& vp, int kt, float3 g, float rs, int lane, DiscQ& Q) {
   (void)lane;
-  // FP32 estimate of the membership threshold; the FP64 value is formed only for
-  // candidates within 1e-5 of it
-  Q.cosRm32 = cosf(fminf((float)kPi, rs + vp.rho32 + 1e-7f));
-  const float Re = fminf((float)kPi, rs + vp.rho32 + 1e-7f + 1e-5f);   // enumeration radius with slack
+  const float rho_e = RF ? vp.rhoq32 + vp.rhoc32 : vp.rho32;
+  // FP32 estimate of the membership threshold (RF: of the candidate test at the tile
+  // centre); the FP64 value is formed only for candidates within the band of it
+  Q.cosRm32 = cosf(fminf((float)kPi, rs + rho_e + 1e-7f));
+  if (RF) {
+    const float Rq = fminf((float)kPi, rs + vp.rhoq32 + 1e-7f);
+    Q.cosRq32 = cosf(Rq);
+    Q.cosRa32 = cosf(fmaxf(0.f, Rq - vp.rhoc32));   // tile centre this close: all its query pixels pass
+  }
+  const float Re = fminf((float)kPi, rs + rho_e + 1e-7f + 1e-5f);   // enumeration radius with slack
   float sRe, cRe;
   sincosf(Re, &sRe, &cRe);
   Q.cosRe = cRe;
@@ -525,6 +536,9 @@ __device__ __forceinline__ int ring_interval(int kt, int i, const DiscQ& Q, Ring
 // threshold's argument (up to 4.8e-7 at r_s + rho near pi) and cosf's 2 ulp
 // (1.2e-7). An FP32 emulation at Nside 512 with 300k Gaussians stays within 2e-7.
 constexpr float kBand32 = 3e-6f;
+// Band of the RING x f query-pixel test, whose centres come from pix2vec_f32 (the
+// NESTED query's band).
+constexpr float kBandQ32 = 1e-5f;
 
 // Count pass (EMIT = false): counts members and stages up to kStage member tiles
 // per Gaussian in shared memory, then copies them to a scratch list at a slot
@@ -546,7 +560,7 @@ struct TileSet {
   uint64_t base;
 };
 
-template <bool EMIT>
+template <bool EMIT, bool RF>
 __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTable vt, const float4* __restrict__ rec,
                                                const float* __restrict__ radii, const uint32_t* __restrict__ skeys,
                                                const uint32_t* __restrict__ svals, const uint32_t* __restrict__ flags,
@@ -584,7 +598,7 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
           const float3 gl = make_float3(r0.x, r0.y, r0.z);
           const float rsl = radii[ts.gid];
           DiscQ Ql;
-          disc_setup(vpl, vpl.k - vt.b, gl, rsl, lane, Ql);
+          disc_setup<RF>(vpl, vpl.k - vt.b, gl, rsl, lane, Ql);
           ts.g = gl; ts.rs = rsl; ts.Q = Ql;
         }
       }
@@ -616,6 +630,7 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
     const DiscQ Q = ts.Q;
     const float rs = ts.rs;
     double cosRm = 2.0;                        // FP64 threshold, formed at this lane's first band candidate
+    double cosRq = 2.0;                        // RF: the same for the query-pixel test
     const uint64_t base = EMIT ? ts.base : 0;
     uint32_t cnt = 0;
     for (int r0i = Q.ilo; r0i <= Q.ihi; r0i += 32) {
@@ -658,18 +673,45 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
           float sp, cp;
           sincospif((float)n * (0.5f * o_inv), &sp, &cp);
           const float dot = o_sth * (cp * g.x + sp * g.y) + o_z * g.z;
-          if (dot > Q.cosRm32 + kBand32) member = true;
-          else if (dot >= Q.cosRm32 - kBand32) {
-            // the exact test: both sides in FP64, the threshold as the membership rule states it
-            // (the FP64 pipe is slow on this part: nothing on the common path uses it)
-            if (cosRm > 1.5) cosRm = cos(fmin(kPi, (double)rs + vp.rho + 1e-7));
-            const double3 c = ringpix_vec_f64(kt, ii, jj);
-            member = c.x * (double)g.x + c.y * (double)g.y + c.z * (double)g.z >= cosRm;
-          }
-          if (member) {
+          if (!RF) {
+            if (dot > Q.cosRm32 + kBand32) member = true;
+            else if (dot >= Q.cosRm32 - kBand32) {
+              // the exact test: both sides in FP64, the threshold as the membership rule states it
+              // (the FP64 pipe is slow on this part: nothing on the common path uses it)
+              if (cosRm > 1.5) cosRm = cos(fmin(kPi, (double)rs + vp.rho + 1e-7));
+              const double3 c = ringpix_vec_f64(kt, ii, jj);
+              member = c.x * (double)g.x + c.y * (double)g.y + c.z * (double)g.z >= cosRm;
+            }
+            if (member) {
+              const FaceXY fx = ring_to_fxy(kt, ii, jj);
+              gt = (uint32_t)vp.tile_base + fxy_to_nest(kt, fx.f, fx.x, fx.y);
+              member = flags[gt] & 1u;
+            }
+          } else if (dot >= Q.cosRm32 - kBand32) {
+            // a candidate tile: listed when one of its 4^log2f query pixels has its centre
+            // within r_s + rho_q (+1e-7) of g, decided in FP32 and, within kBandQ32 of the
+            // threshold, in FP64 as the membership rule states it
             const FaceXY fx = ring_to_fxy(kt, ii, jj);
-            gt = (uint32_t)vp.tile_base + fxy_to_nest(kt, fx.f, fx.x, fx.y);
-            member = flags[gt] & 1u;
+            const uint32_t tn = fxy_to_nest(kt, fx.f, fx.x, fx.y);
+            gt = (uint32_t)vp.tile_base + tn;
+            if (flags[gt] & 1u) {
+              if (dot > Q.cosRa32 + kBand32) {
+                member = true;
+              } else {
+                const int L = vt.log2f, kq = kt + L;
+                for (uint32_t c = 0; c < (1u << (2 * L)) && !member; ++c) {
+                  const uint32_t qp = (tn << (2 * L)) | c;
+                  const float3 cq = pix2vec_f32(kq, qp);
+                  const float dq = cq.x * g.x + cq.y * g.y + cq.z * g.z;
+                  if (dq > Q.cosRq32 + kBandQ32) member = true;
+                  else if (dq >= Q.cosRq32 - kBandQ32) {
+                    if (cosRq > 1.5) cosRq = cos(fmin(kPi, (double)rs + vp.rhoq + 1e-7));
+                    const double3 c64 = pix2vec_f64(kq, qp);
+                    member = c64.x * (double)g.x + c64.y * (double)g.y + c64.z * (double)g.z >= cosRq;
+                  }
+                }
+              }
+            }
           }
         }
         const uint32_t bal = __ballot_sync(FULL, member);
@@ -1685,9 +1727,14 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
                                                   (uint64_t)L.cap, status);
   } else {
     // the count pass stages member lists in the second pair buffers (unused until the pair sort)
-    k_tiles<false><<<tblocks, 256, 0, s>>>(*vt, rec, radii, sk, sv, flags, counts, nullptr, nullptr, nullptr,
-                                           (uint64_t)L.cap, status, at<uint32_t>(ws, L.stage),
-                                           at<uint32_t>(ws, L.pair_key_b), counters + C_STAGE);
+    if (vt->log2f > 0)                             // RING x f: search at order k_t + log2f
+      k_tiles<false, true><<<tblocks, 256, 0, s>>>(*vt, rec, radii, sk, sv, flags, counts, nullptr, nullptr, nullptr,
+                                                   (uint64_t)L.cap, status, at<uint32_t>(ws, L.stage),
+                                                   at<uint32_t>(ws, L.pair_key_b), counters + C_STAGE);
+    else
+      k_tiles<false, false><<<tblocks, 256, 0, s>>>(*vt, rec, radii, sk, sv, flags, counts, nullptr, nullptr, nullptr,
+                                                    (uint64_t)L.cap, status, at<uint32_t>(ws, L.stage),
+                                                    at<uint32_t>(ws, L.pair_key_b), counters + C_STAGE);
   }
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
@@ -1798,9 +1845,16 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
                                                    at<uint32_t>(ws, L.counts), at<uint64_t>(ws, L.offsets), pka, pva,
                                                    (uint64_t)cap, status);
     } else {
-      k_tiles<true><<<tblocks, 256, 0, s>>>(*vt, rec, at<float>(ws, L.radii), sk, sv, flags, at<uint32_t>(ws, L.counts),
-                                            at<uint64_t>(ws, L.offsets), pka, pva, (uint64_t)cap, status,
-                                            at<uint32_t>(ws, L.stage), pkb, counters + C_STAGE);
+      if (vt->log2f > 0)
+        k_tiles<true, true><<<tblocks, 256, 0, s>>>(*vt, rec, at<float>(ws, L.radii), sk, sv, flags,
+                                                    at<uint32_t>(ws, L.counts), at<uint64_t>(ws, L.offsets), pka, pva,
+                                                    (uint64_t)cap, status, at<uint32_t>(ws, L.stage), pkb,
+                                                    counters + C_STAGE);
+      else
+        k_tiles<true, false><<<tblocks, 256, 0, s>>>(*vt, rec, at<float>(ws, L.radii), sk, sv, flags,
+                                                     at<uint32_t>(ws, L.counts), at<uint64_t>(ws, L.offsets), pka, pva,
+                                                     (uint64_t)cap, status, at<uint32_t>(ws, L.stage), pkb,
+                                                     counters + C_STAGE);
     }
     note_launches(1);
     HPXGS_LAUNCH_CHECK();

@@ -197,7 +197,13 @@ __global__ void __launch_bounds__(kRsThreads) k_sphere_to_image_bwd(const float*
 }
 
 // I_H(q) = I_C(Pi_C^{-1}(s_q)) and M_C(q) for every NESTED pixel q (0 outside M_C).
-__global__ void __launch_bounds__(kRsThreads) k_image_to_sphere(const float* __restrict__ img, ImgCam c, ViewParams vp,
+// A sample of the image as a value in [0, 1]: float images as they are, 8-bit codes v as
+// v / 255 (IEEE division, the value a float image holding v / 255 would give).
+__device__ __forceinline__ float image_value(const float* px) { return __ldg(px); }
+__device__ __forceinline__ float image_value(const uint8_t* px) { return __fdiv_rn((float)__ldg(px), 255.f); }
+
+template <typename T>
+__global__ void __launch_bounds__(kRsThreads) k_image_to_sphere(const T* __restrict__ img, ImgCam c, ViewParams vp,
                                                                  float* __restrict__ map, uint32_t* __restrict__ words) {
   const uint32_t npix = 12u << (2 * vp.k);                   // a multiple of 32 for k >= 2
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -223,9 +229,9 @@ __global__ void __launch_bounds__(kRsThreads) k_image_to_sphere(const float* __r
       for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          const float* px = img + 3 * ((size_t)ys[a] * c.W + xs[b]);
+          const T* px = img + 3 * ((size_t)ys[a] * c.W + xs[b]);
           const float ww = wy[a] * wx[b];
-          o[0] += ww * __ldg(px); o[1] += ww * __ldg(px + 1); o[2] += ww * __ldg(px + 2);
+          o[0] += ww * image_value(px); o[1] += ww * image_value(px + 1); o[2] += ww * image_value(px + 2);
         }
     }
     if (inr) { map[3 * (size_t)q] = o[0]; map[3 * (size_t)q + 1] = o[1]; map[3 * (size_t)q + 2] = o[2]; }
@@ -288,16 +294,27 @@ extern "C" int hpxgs_sphere_to_image_backward(const float* dimage, int nside_log
   return HPXGS_OK;
 }
 
-extern "C" int hpxgs_image_to_sphere(const float* image, int width, int height, const hpxgs_camera* cam, int nside_log2,
-                                     float* map, uint32_t* mask_bits, hpxgs_stream_t stream) {
+template <typename T>
+static int image_to_sphere(const T* image, int width, int height, const hpxgs_camera* cam, int nside_log2, float* map,
+                           uint32_t* mask_bits, hpxgs_stream_t stream) {
   ImgCam c;
   if (!image || !map || nside_log2 < 2 || nside_log2 > 13 || !make_cam(cam, width, height, c)) return HPXGS_E_INVALID_ARG;
   ViewParams vp{};
   camera_params(*cam, nside_log2, vp);
   const int64_t npix = 12LL << (2 * nside_log2);
   // the grid-stride loop keeps whole warps together: blocks of 256 over a multiple of 32 pixels
-  k_image_to_sphere<<<grid_for(npix), kRsThreads, 0, (cudaStream_t)stream>>>(image, c, vp, map, mask_bits);
+  k_image_to_sphere<T><<<grid_for(npix), kRsThreads, 0, (cudaStream_t)stream>>>(image, c, vp, map, mask_bits);
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
   return HPXGS_OK;
+}
+
+extern "C" int hpxgs_image_to_sphere(const float* image, int width, int height, const hpxgs_camera* cam, int nside_log2,
+                                     float* map, uint32_t* mask_bits, hpxgs_stream_t stream) {
+  return image_to_sphere(image, width, height, cam, nside_log2, map, mask_bits, stream);
+}
+
+extern "C" int hpxgs_image_to_sphere_u8(const uint8_t* image, int width, int height, const hpxgs_camera* cam,
+                                        int nside_log2, float* map, uint32_t* mask_bits, hpxgs_stream_t stream) {
+  return image_to_sphere(image, width, height, cam, nside_log2, map, mask_bits, stream);
 }

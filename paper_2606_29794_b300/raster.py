@@ -78,7 +78,7 @@ class Rasterizer:
 
     def __init__(self, tile_level=4, eps_T=1e-4, alpha_max=0.99, cutoff=9.0, blur=None, near=0.2,
                  bg=(0.0, 0.0, 0.0), lam=0.2, write_outside=1, capacity=None, headroom=1.15, fwd_ppt=0, bwd_ppt=0,
-                 blocks_per_sm=0, query=0, query_log2f=2, blend_cull=1, blend_split=1):
+                 blocks_per_sm=0, query=0, query_log2f=0, blend_cull=1, blend_split=1):
         self.cfg = L.default_config(tile_level=tile_level, eps_T=eps_T, alpha_max=alpha_max, cutoff_m=cutoff,
                                     blur=blur, near_plane=near, bg=bg, lam=lam, write_outside=write_outside,
                                     fwd_ppt=fwd_ppt, bwd_ppt=bwd_ppt, blocks_per_sm=blocks_per_sm, query=query,
@@ -391,12 +391,16 @@ class GraphStep:
     With `host_targets` (a pinned host tensor shaped like `targets`) every
     replay first copies it into `targets`, on a forked stream that overlaps the
     forward render; the loss waits for the copy.
+    With `host_images` (one pinned host uint8 camera image [H, W, 3] per view, the
+    form a camera delivers) every replay copies each image in on a forked stream and
+    resamples it onto the view's HEALPix grid as that view's target
+    (hpxgs_image_to_sphere_u8, Eq. supp_image_to_healpix), overlapping the forward render.
     With `fused` (the default) the loss backward runs inside the render backward
     (hpxgs_backward_hssim): each pixel's dL/dI is formed where the backward blend reads
     it instead of going through a dL/dmaps buffer."""
 
     def __init__(self, params, sh_degree, views, targets, rasterizer: Rasterizer, lam=0.2, headroom=1.25,
-                 before_capture=None, host_targets=None, fused=True):
+                 before_capture=None, host_targets=None, fused=True, host_images=None):
         self.params = [p.contiguous() for p in params]
         self.views = list(views)
         self.targets = targets.contiguous()
@@ -428,6 +432,15 @@ class GraphStep:
             if not host_targets.is_pinned() or host_targets.shape != self.targets.shape:
                 raise ValueError("host_targets must be a pinned host tensor shaped like targets")
             self.side = torch.cuda.Stream(device=dev)
+        self.host_images = host_images
+        if host_images is not None:
+            if host_targets is not None or len(host_images) != len(self.views):
+                raise ValueError("host_images takes one image per view, without host_targets")
+            for im in host_images:
+                if not im.is_pinned() or im.dtype != torch.uint8 or im.dim() != 3 or im.shape[2] != 3:
+                    raise ValueError("host_images must be pinned uint8 host tensors [H, W, 3]")
+            self.dev_images = [torch.empty(im.shape, dtype=torch.uint8, device=dev) for im in host_images]
+            self.side = torch.cuda.Stream(device=dev)
         # warm up eagerly once (allocator pools, rho cache); the HSSIM window tables come from
         # the masks of that step (one per distinct order and camera); then capture
         self.tables = None
@@ -455,8 +468,16 @@ class GraphStep:
             self.side.wait_stream(cur)
             with torch.cuda.stream(self.side):
                 self.targets.copy_(self.host_targets, non_blocking=True)
+        if self.host_images is not None:
+            from . import resample
+            self.side.wait_stream(cur)
+            with torch.cuda.stream(self.side):
+                for v, k, base, him, dim in zip(self.views, self.order, self.lay.pix_base, self.host_images,
+                                                self.dev_images):
+                    dim.copy_(him, non_blocking=True)
+                    resample.image_to_sphere_into(dim, v, k, self.targets[base:base + npix(k)], stream=self.side)
         out, state = self.rast.forward_raw(*self.params, self.sh_degree, self.views, check_status=False)
-        if self.host_targets is not None:
+        if self.host_targets is not None or self.host_images is not None:
             cur.wait_stream(self.side)
         st = _stream()
         fused = self.fused and self.tables is not None

@@ -66,18 +66,35 @@ def sphere_to_image_backward(dimage, nside_log2, cam, width, height):
     return dmap
 
 
-def image_to_sphere(image, cam, nside_log2, with_mask=True):
-    """HEALPix map [12 * 4^k, 3] of a camera image [height, width, 3] and the mask words of M_C."""
-    image = _f32(image)
-    if image.dim() != 3 or image.shape[2] != 3:
-        raise ValueError("expected an image of shape [height, width, 3]")
+def image_to_sphere_into(image, cam, nside_log2, hmap, words=None, stream=None):
+    """Writes the HEALPix map of a camera image [height, width, 3] (float32 values, or uint8 codes
+    v read as v / 255) into `hmap` [12 * 4^k, 3] and, if given, the mask words of M_C into `words`,
+    on `stream` (default: the current stream)."""
+    if image.dim() != 3 or image.shape[2] != 3 or not image.is_cuda or not image.is_contiguous():
+        raise ValueError("expected a contiguous CUDA image of shape [height, width, 3]")
+    if image.dtype == torch.uint8:
+        fn = L.lib().hpxgs_image_to_sphere_u8
+    elif image.dtype == torch.float32:
+        fn = L.lib().hpxgs_image_to_sphere
+    else:
+        raise ValueError("expected a float32 or uint8 image")
+    npix = 12 * 4 ** nside_log2
+    _f32(hmap)
+    if hmap.numel() != 3 * npix or (words is not None and (words.numel() != npix // 32 or not words.is_contiguous())):
+        raise ValueError("map or mask size does not match nside_log2")
     height, width = image.shape[0], image.shape[1]
+    c = _cam(cam)
+    s = ctypes.c_void_p((stream or torch.cuda.current_stream(image.device)).cuda_stream)
+    L.check(fn(_ptr(image), width, height, ctypes.byref(c), nside_log2, _ptr(hmap), _ptr(words), s), "image_to_sphere")
+
+
+def image_to_sphere(image, cam, nside_log2, with_mask=True):
+    """HEALPix map [12 * 4^k, 3] of a camera image [height, width, 3] (float32, or uint8 codes read
+    as v / 255) and the mask words of M_C."""
     npix = 12 * 4 ** nside_log2
     hmap = torch.empty((npix, 3), dtype=torch.float32, device=image.device)
     words = torch.empty(npix // 32, dtype=torch.int32, device=image.device) if with_mask else None
-    c = _cam(cam)
-    L.check(L.lib().hpxgs_image_to_sphere(_ptr(image), width, height, ctypes.byref(c), nside_log2, _ptr(hmap),
-                                          _ptr(words), _stream(image.device)), "image_to_sphere")
+    image_to_sphere_into(image, cam, nside_log2, hmap, words)
     return hmap, words
 
 

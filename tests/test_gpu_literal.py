@@ -47,7 +47,8 @@ def _gpu_records(rast, state, P):
 
 @pytest.mark.parametrize("name,kw", [("ring_b4", dict(tile_level=4)), ("ring_b5_split", dict(tile_level=5)),
                                      ("nested_x1", dict(tile_level=4, query=L.QUERY_NESTED, query_log2f=0)),
-                                     ("nested_x2", dict(tile_level=4, query=L.QUERY_NESTED, query_log2f=1))],
+                                     ("nested_x2", dict(tile_level=4, query=L.QUERY_NESTED, query_log2f=1)),
+                                     ("ring_x4", dict(tile_level=4, query=L.QUERY_RING, query_log2f=2))],
                          ids=lambda x: x if isinstance(x, str) else "")
 def test_literal_staged_parity(name, kw):
     sc, view = _scene_view()
@@ -69,6 +70,9 @@ def test_literal_staged_parity(name, kw):
     if kw.get("query", 0) == L.QUERY_NESTED:
         st, ids = O.tile_lists_nested(k, b, kw["query_log2f"], rec[:, 0:3], radii.astype(np.float64),
                                       valid.astype(np.int32), dbits, act)
+    elif kw.get("query_log2f", 0) > 0:
+        st, ids = O.tile_lists_ringf(k, b, kw["query_log2f"], rec[:, 0:3], radii.astype(np.float64),
+                                     valid.astype(np.int32), dbits, act)
     else:
         st, ids = O.tile_lists(k, b, rec[:, 0:3], radii.astype(np.float64), valid.astype(np.int32), dbits,
                                O.tile_rho(k, b), act)
@@ -110,13 +114,17 @@ def test_literal_end_to_end_and_gradients():
 
 
 def test_literal_image_depends_on_query():
+    # RING x1, RING x4 (the paper's default search resolution) and NESTED x2: equal maps under
+    # the cutoff, different maps under the literal semantics of the ablation
     sc, view = _scene_view()
     ts = scene_tensors(sc)
     outs = {}
     for cut in (9.0, math.inf):
-        for q, f in ((L.QUERY_RING, 2), (L.QUERY_NESTED, 1)):
+        for q, f in ((L.QUERY_RING, 0), (L.QUERY_RING, 2), (L.QUERY_NESTED, 1)):
             out, _ = R.Rasterizer(tile_level=4, cutoff=cut, query=q, query_log2f=f).forward_raw(*ts, 3, [view])
-            outs[(cut, q)] = out["maps"]
+            outs[(cut, q, f)] = out["maps"]
     torch.cuda.synchronize()
-    assert torch.equal(outs[(9.0, L.QUERY_RING)], outs[(9.0, L.QUERY_NESTED)])
-    assert float((outs[(math.inf, L.QUERY_RING)] - outs[(math.inf, L.QUERY_NESTED)]).abs().max()) > 1e-5
+    r1, r4, n2 = (L.QUERY_RING, 0), (L.QUERY_RING, 2), (L.QUERY_NESTED, 1)
+    assert torch.equal(outs[(9.0, *r1)], outs[(9.0, *n2)]) and torch.equal(outs[(9.0, *r1)], outs[(9.0, *r4)])
+    assert float((outs[(math.inf, *r1)] - outs[(math.inf, *n2)]).abs().max()) > 1e-5
+    assert float((outs[(math.inf, *r1)] - outs[(math.inf, *r4)]).abs().max()) > 1e-5

@@ -156,6 +156,38 @@ def test_graph_step_with_host_targets_matches_device_targets():
     assert not torch.equal(l3, l2)
 
 
+def test_graph_step_with_host_camera_images_matches_float_image_targets():
+    # a pinned 8-bit camera image per view, copied in and resampled onto the view's grid inside
+    # the graph (hpxgs_image_to_sphere_u8), gives the targets of the float image v / 255 resampled
+    # on the device: the same losses, gradients up to the order of atomic sums
+    from paper_2606_29794_b300 import resample as RS
+    sc = S.make_scene(20000, 3, seed=62)
+    views = [S.make_view(7, S.CAM_FISHEYE, 190.0), S.make_view(6, S.CAM_PINHOLE, 90.0, 70.0)]
+    sizes = [(300, 300), (240, 180)]
+    params = scene_tensors(sc)
+    lay = R.view_layout(views)
+    g = torch.Generator().manual_seed(63)
+    imgs = [torch.randint(0, 256, (h, w, 3), dtype=torch.uint8, generator=g) for w, h in sizes]
+    tgt = torch.zeros((lay.total_pix, 3), device="cuda")
+    for v, base, im in zip(views, lay.pix_base, imgs):
+        n = R.npix(v["nside_log2"])
+        RS.image_to_sphere_into((im.float() / 255.0).cuda(), v, v["nside_log2"], tgt[base:base + n])
+        # the 8-bit entry point itself: the float image's map bit for bit
+        m8, w8 = RS.image_to_sphere(im.cuda(), v, v["nside_log2"])
+        assert torch.equal(m8, tgt[base:base + n])
+    dev_step = R.GraphStep(params, 3, views, tgt, R.Rasterizer())
+    host_step = R.GraphStep(params, 3, views, torch.zeros_like(tgt), R.Rasterizer(),
+                            host_images=[im.pin_memory() for im in imgs])
+    l1, g1 = dev_step.replay()
+    l2, g2 = host_step.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(l1, l2.clone())
+    assert torch.equal(host_step.targets, tgt)
+    for a, b in zip(g1, g2):
+        assert float((a - b).norm()) <= 1e-4 * float(a.norm()) + 1e-12
+        assert float((a - b).abs().max()) <= 1e-3 * float(a.abs().max()) + 1e-12
+
+
 @pytest.mark.parametrize("tile_level,views,split", [(5, "fisheye", 1), (5, "fisheye", 0), (4, "mixed", 1),
                                                     (3, "fisheye", 1)])
 def test_fused_loss_backward_equals_two_pass(tile_level, views, split):
