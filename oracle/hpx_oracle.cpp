@@ -552,6 +552,27 @@ static void query_disc_ring(i64 nside_t, const double g[3], double R, std::vecto
   }
 }
 
+// Enumeration radius for the membership test c . g >= cos(R) (Algorithm 3 enumerates the
+// directions within a radius of a unit centre). The stored centre g is unit length only to
+// its rounding, and the test holds for the directions within acos(cos R / |g|) of g / |g|:
+// a little more than R when |g| > 1, by about (|g| - 1) / tan R. With
+// h = (1 - cos R / |g|) / 2 = (|g| - 1 + 2 sin^2(R / 2)) / (2 |g|), that angle is 2 asin sqrt(h).
+static double dot_disc_radius(double R, double glen) {
+  if (R >= kPi) return kPi;
+  const double s = std::sin(0.5 * R);
+  const double h = (glen - 1.0 + 2.0 * s * s) / (2.0 * glen);
+  if (h >= 1.0) return kPi;
+  return std::max(R, h > 0.0 ? 2.0 * std::asin(std::sqrt(h)) : 0.0);
+}
+
+// Algorithm 3 candidates of the disc {c : c . g >= cos(R)} (g as stored, near unit length):
+// the enumeration runs about g / |g| with the radius of that disc plus 1e-9.
+static void query_dot_disc(i64 nside, const double g[3], double R, std::vector<i64>& out) {
+  const double glen = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+  const double gu[3] = {g[0] / glen, g[1] / glen, g[2] / glen};
+  query_disc_ring(nside, gu, std::min(kPi, dot_disc_radius(R, glen) + 1e-9), out);
+}
+
 // Membership of a Gaussian (centre g, radius r_s) in the tile with centre ct.
 static bool tile_member_at(const double ct[3], const double g[3], double rs, double rho) {
   double dt = ct[0] * g[0] + ct[1] * g[1] + ct[2] * g[2];
@@ -567,7 +588,7 @@ static bool tile_member(i64 nside_t, i64 t, const double g[3], double rs, double
 static void tiles_of(i64 nside_t, const double g[3], double rs, double rho, const u8* active,
                      std::vector<i64>& out) {
   std::vector<i64> cand;
-  query_disc_ring(nside_t, g, std::min(kPi, rs + rho + 1e-7 + 1e-9), cand);
+  query_dot_disc(nside_t, g, std::min(kPi, rs + rho + 1e-7), cand);
   std::sort(cand.begin(), cand.end());
   cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
   out.clear();
@@ -1763,7 +1784,7 @@ static void tiles_of_ringf(int kt, int log2f, const double g[3], double rs, doub
                            std::vector<i64>& out) {
   const i64 nside_q = 1LL << (kt + log2f);
   std::vector<i64> cand;
-  query_disc_ring(nside_q, g, std::min(kPi, rs + rho_q + 1e-7 + 1e-9), cand);
+  query_dot_disc(nside_q, g, std::min(kPi, rs + rho_q + 1e-7), cand);
   out.clear();
   for (i64 q : cand) {
     if (!tile_member(nside_q, q, g, rs, rho_q)) continue;

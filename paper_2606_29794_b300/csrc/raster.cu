@@ -489,13 +489,26 @@ __device__ __forceinline__ void disc_setup(const ViewParams& vp, int kt, float3 
     Q.cosRq32 = cosf(Rq);
     Q.cosRa32 = cosf(fmaxf(0.f, Rq - vp.rhoc32));   // tile centre this close: all its query pixels pass
   }
-  const float Re = fminf((float)kPi, rs + rho_e + 1e-7f + 1e-5f);   // enumeration radius with slack
+  // Enumeration radius with slack. The stored centre g is unit length only to FP32 rounding,
+  // and the membership test c . g >= cos(R) holds for directions within acos(cos R / |g|) of
+  // g / |g|, a little more than R when |g| > 1 (by about (|g| - 1) / tan R, which matters for
+  // small R): that angle is 2 asin sqrt(h), h = (|g| - 1 + 2 sin^2(R / 2)) / (2 |g|), taken
+  // here with |g| - 1 at its largest (the FP32 error of g . g included). The rings and the
+  // longitude intervals are then laid out about the normalised centre.
+  const float R = fminf((float)kPi, rs + rho_e + 1e-7f);
+  const float n2 = g.x * g.x + g.y * g.y + g.z * g.z;
+  const float dg = 0.5f * fabsf(n2 - 1.f) + 1e-6f;
+  const float sh = sinf(0.5f * R);
+  const float h = (dg + 2.f * sh * sh) / (2.f * (1.f - dg));
+  const float Reff = h >= 1.f ? (float)kPi : 2.f * asinf(sqrtf(h));
+  const float Re = fminf((float)kPi, fmaxf(R, Reff) + 1e-5f);
   float sRe, cRe;
   sincosf(Re, &sRe, &cRe);
   Q.cosRe = cRe;
   const int Nt = 1 << kt;
-  Q.zc = g.z;
-  Q.sc = sqrtf(fmaxf(0.f, g.x * g.x + g.y * g.y));
+  const float ig = rsqrtf(n2);
+  Q.zc = g.z * ig;
+  Q.sc = sqrtf(fmaxf(0.f, g.x * g.x + g.y * g.y)) * ig;
   Q.omc = atan2f(g.y, g.x);
   // z range sin(phi_c -+ Re) = z_c cos Re -+ s_c sin Re; it reaches the north pole once
   // Re >= the centre's colatitude (cos Re <= z_c) and the south pole once cos Re <= -z_c

@@ -95,3 +95,27 @@ def test_literal_semantics_depend_on_the_search_resolution():
     s2, i2 = O.tile_lists_ringf(k, b, 2, pre["g"], pre["rs"], pre["valid"], O.depth_bits(pre["r"]), R.active)
     img, *_ = O.composite(k, b, pre, sc["opacities"], s2, i2, R.pix, cfg)
     assert np.abs(img - R.image[R.pix]).max() > 1e-6
+
+
+@pytest.mark.parametrize("log2f", [0, 2])
+def test_centres_off_unit_length_are_enumerated(log2f):
+    # a stored centre is unit length only to its rounding (float32 records: |g| - 1 ~ 1e-7); the
+    # membership test c . g >= cos(R) then reaches slightly beyond R, by about (|g| - 1) / tan R,
+    # which is large against R for small discs. Algorithm 3's enumeration must cover that disc:
+    # the lists still equal brute force over every query pixel.
+    rng = np.random.default_rng(7 + log2f)
+    k, b = 8, 2
+    n = 300
+    g = rng.standard_normal((n, 3))
+    g /= np.linalg.norm(g, axis=1, keepdims=True)
+    g *= (1.0 + rng.choice([-3e-7, 3e-7], n))[:, None]
+    rs = 10.0 ** rng.uniform(-4.5, -1.5, n)
+    valid = np.ones(n, np.int32)
+    act = np.ones(12 * 4 ** (k - b), np.uint8)
+    dbits = np.arange(n, dtype=np.uint32) + np.uint32(0x40000000)
+    start, ids = O.tile_lists_ringf(k, b, log2f, g, rs, valid, dbits, act)
+    nt = act.size
+    rho_q = 0.0 if log2f == b else O.tile_rho(k, b - log2f)
+    member_q = O.tile_lists_bruteforce(k, b - log2f, g, rs, valid, rho_q, np.repeat(act, 4 ** log2f))
+    member = member_q.reshape(n, nt, 4 ** log2f).any(2)
+    assert _csr_sets(start, ids, nt) == [set(np.nonzero(member[:, t])[0].tolist()) for t in range(nt)]
