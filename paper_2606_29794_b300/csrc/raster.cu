@@ -123,24 +123,36 @@ struct Geo {
   float rs;
 };
 
+// EXACT (the forward's preprocess): t = W mu + b and the radial depth r = |t| in FP64,
+// each product and sum rounded once in a fixed order (the _rn intrinsics are never
+// contracted into FMAs), so that float32(r) -- the sort key, the recorded depth and the
+// near-plane test -- is the value any IEEE FP64 evaluation in this order gives; the FP32
+// geometry starts from float32(t). Otherwise (the backward, which takes validity from
+// the forward's radii) t and r in FP32, within rounding of the same values.
+template <bool EXACT>
 __device__ __forceinline__ void geo_compute(const ViewParams& vp, float near_plane, const float* __restrict__ mu,
                                             const float* __restrict__ sc, const float* __restrict__ q, Geo& G) {
-  // t = W mu + b and the radial depth r = |t| in FP64, each product and sum rounded
-  // once in a fixed order (the _rn intrinsics are never contracted into FMAs), so that
-  // float32(r) -- the sort key and the near-plane test -- is the value any IEEE FP64
-  // evaluation in this order gives. The FP32 geometry below starts from float32(t).
-  const double m0 = mu[0], m1 = mu[1], m2 = mu[2];
-  double t64[3];
+  if constexpr (EXACT) {
+    const double m0 = mu[0], m1 = mu[1], m2 = mu[2];
+    double t64[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-    t64[i] = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)vp.W[3 * i], m0), __dmul_rn((double)vp.W[3 * i + 1], m1)),
-                                 __dmul_rn((double)vp.W[3 * i + 2], m2)),
-                       (double)vp.b[i]);
-  const double r64 = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(t64[0], t64[0]), __dmul_rn(t64[2], t64[2])),
-                                          __dmul_rn(t64[1], t64[1])));
-  G.t = make_float3(__double2float_rn(t64[0]), __double2float_rn(t64[1]), __double2float_rn(t64[2]));
-  G.r = __double2float_rn(r64);
-  G.valid = r64 > (double)near_plane;
+    for (int i = 0; i < 3; ++i)
+      t64[i] = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)vp.W[3 * i], m0), __dmul_rn((double)vp.W[3 * i + 1], m1)),
+                                   __dmul_rn((double)vp.W[3 * i + 2], m2)),
+                         (double)vp.b[i]);
+    const double r64 = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(t64[0], t64[0]), __dmul_rn(t64[2], t64[2])),
+                                            __dmul_rn(t64[1], t64[1])));
+    G.t = make_float3(__double2float_rn(t64[0]), __double2float_rn(t64[1]), __double2float_rn(t64[2]));
+    G.r = __double2float_rn(r64);
+    G.valid = r64 > (double)near_plane;
+  } else {
+    const float m0 = mu[0], m1 = mu[1], m2 = mu[2];
+    G.t.x = vp.W[0] * m0 + vp.W[1] * m1 + vp.W[2] * m2 + vp.b[0];
+    G.t.y = vp.W[3] * m0 + vp.W[4] * m1 + vp.W[5] * m2 + vp.b[1];
+    G.t.z = vp.W[6] * m0 + vp.W[7] * m1 + vp.W[8] * m2 + vp.b[2];
+    G.r = sqrtf(G.t.x * G.t.x + G.t.y * G.t.y + G.t.z * G.t.z);
+    G.valid = G.r > 0.f;
+  }
   if (!G.valid) return;
   const float ir = 1.0f / G.r;
   G.gc = make_float3(G.t.x * ir, G.t.y * ir, G.t.z * ir);
@@ -208,7 +220,7 @@ __global__ void __launch_bounds__(kPreThreads) k_preprocess(const __grid_constan
   const int64_t gid = (int64_t)v * vt.P + i;
   const ViewParams& vp = vt.v[v];
   Geo G;
-  geo_compute(vp, vt.near_plane, gs.means + 3 * (int64_t)i, gs.scales + 3 * (int64_t)i, gs.rotations + 4 * (int64_t)i, G);
+  geo_compute<true>(vp, vt.near_plane, gs.means + 3 * (int64_t)i, gs.scales + 3 * (int64_t)i, gs.rotations + 4 * (int64_t)i, G);
   vals[gid] = (uint32_t)gid;
   depth[gid] = G.r;
   // exact FoV-cap cull (the camera axis is the HEALPix X axis): no tile of the view can list it
@@ -1196,6 +1208,68 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
   }
 }
 
+// Backward of one (pixel, entry) on the scalar path. From m (P) and the pixel's running
+// transmittance T behind the entry: alpha, T in front of it (T_j = T / (1 - a)), the
+// entry's partials added to acc (acc[5], acc[7] and acc[8] at half weight: the factor 2
+// is applied once per entry after the reduction), and the pixel's running T and B moved
+// in front of the entry. dD and invr: the depth channel's dL/dD and 1/r (DEPTH only).
+// Returns false when the entry does not reach the pixel (m > cutoff).
+template <bool DEPTH, int NA>
+__device__ __forceinline__ bool bwd_pixel(const ViewTable& vt, const Pix& P, float4 r0, float4 r1, float4 r2,
+                                          float4 r3, const float* dI, float dD, float invr, float& T, float& B,
+                                          float* acc) {
+  if (!(P.m <= vt.cutoff)) return false;
+  const float G = __expf(-0.5f * P.m);
+  const float og = r0.w * G;
+  const float a = fminf(vt.alpha_max, og);
+  const float inv1ma = __fdividef(1.f, 1.f - a);
+  const float Tj = T * inv1ma;
+  const float wj = Tj * a;
+  // A = dL/dI . colour (+ dL/dD / r); dL/da = T_j A - B / (1 - a); then B takes this entry
+  float A = dI[0] * r3.x + dI[1] * r3.y + dI[2] * r3.z;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] += wj * dI[c];
+  if (DEPTH) {
+    acc[NA - 1] += wj * dD;
+    A += dD * invr;
+  }
+  const float dLda = Tj * A - B * inv1ma;
+  B += wj * A;
+  T = Tj;
+  if (og >= vt.alpha_max) return true;          // clamped: no gradient to o, m
+  acc[3] += dLda * G;
+  // dL/dm = Lm = -dLda o G / 2; m = q(u) ser with ser = (theta/s)^2
+  const float Lm = -0.5f * dLda * og;
+  const float u1 = P.u1, u2 = P.u2;
+  const float Ws = Lm * P.ser;
+  const float t1 = Ws * u1;
+  acc[4] += t1 * u1;
+  acc[5] += t1 * u2;
+  acc[6] += Ws * u2 * u2;
+  const float Qu1 = r1.w * u1 + r2.w * u2, Qu2 = r2.w * u1 + r3.w * u2;
+  const float c = 1.f - 0.5f * P.n2;
+  // dm/du_j / 2 = ser Qu_j + q (d ser / d u_j) / 2 = ser Qu_j + K u_j (K per branch below);
+  // dm/dc / 2 = Lc per unit Lm (atan form only)
+  float K, Lc = 0.f;
+  if (P.series) {
+    const float s2 = P.s2;
+    const float dser = 1.f / 3.f + s2 * (16.f / 45.f + s2 * (12.f / 35.f + s2 * (512.f / 1575.f)));
+    K = Lm * P.q * dser;
+  } else {
+    const float s = sqrtf(P.s2);
+    const float ratio = sqrtf(P.ser);
+    const float th = ratio * s;
+    const float kf = (c * s - th) / (P.s2 * s);     // d(theta/s)/du_j = kf u_j
+    K = Lm * P.q * ratio * kf;
+    Lc = -Lm * P.q * ratio;                          // d(theta/s)/dc = -1/s^2... times s: -1
+  }
+  const float h1 = Ws * Qu1 + K * u1, h2 = Ws * Qu2 + K * u2;
+  // moving g by a tangent step delta: du_i = -c delta_i, dc = u . delta
+  acc[7] += -c * h1 + Lc * u1;
+  acc[8] += -c * h2 + Lc * u2;
+  return true;
+}
+
 // ----------------------------------------------------------------------------
 // Backward compositing: reverse walk of each pixel's processed prefix.
 // Per (pixel, entry): T_j = T_{j+1} / (1 - a); dL/dc = T_j a dI;
@@ -1321,68 +1395,19 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
           const int e = (wj << 5) + i;
           const uint32_t gm = s_gm[e];
           const uint32_t j = bs + e - rg.x;          // position in the tile list
-          const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
           float acc[NA];
 #pragma unroll
           for (int c = 0; c < NA; ++c) acc[c] = 0.f;
           bool any = false;
+          const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
 #pragma unroll
           for (int q = 0; q < PPT; ++q) {
             if (j >= lastp[q] || !((gm >> (q * NW + warp)) & 1u)) continue;
             Pix P;
             pixel_weight(pv[q], r0, r1, r2, r3, P);
-            if (!(P.m <= vt.cutoff)) continue;
-            const float G = __expf(-0.5f * P.m);
-            const float og = r0.w * G;
-            const float a = fminf(vt.alpha_max, og);
-            const float inv1ma = __fdividef(1.f, 1.f - a);
-            const float Tj = T[q] * inv1ma;
-            const float wj = Tj * a;
-            // A = dL/dI . colour (+ dL/dD / r); dL/da = T_j A - B / (1 - a); then B takes this entry
-            float A = dI[q][0] * r3.x + dI[q][1] * r3.y + dI[q][2] * r3.z;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) acc[c] += wj * dI[q][c];
-            if (DEPTH) {
-              const int qd = DEPTH ? q : 0;
-              acc[NA - 1] += wj * dDp[qd];
-              A += dDp[qd] * s_invr[e];
-            }
-            const float dLda = Tj * A - B[q] * inv1ma;
-            B[q] += wj * A;
-            T[q] = Tj;
-            any = true;
-            if (og >= vt.alpha_max) continue;         // clamped: no gradient to o, m
-            acc[3] += dLda * G;
-            // dL/dm = Lm = -dLda o G / 2; m = q(u) ser with ser = (theta/s)^2. acc[5], acc[7] and
-            // acc[8] collect half their partials (the factor 2 is applied once per entry below).
-            const float Lm = -0.5f * dLda * og;
-            const float u1 = P.u1, u2 = P.u2;
-            const float Ws = Lm * P.ser;
-            const float t1 = Ws * u1;
-            acc[4] += t1 * u1;
-            acc[5] += t1 * u2;
-            acc[6] += Ws * u2 * u2;
-            const float Qu1 = r1.w * u1 + r2.w * u2, Qu2 = r2.w * u1 + r3.w * u2;
-            const float c = 1.f - 0.5f * P.n2;
-            // dm/du_j / 2 = ser Qu_j + q (d ser / d u_j) / 2 = ser Qu_j + K u_j (K per branch below);
-            // dm/dc / 2 = Lc per unit Lm (atan form only)
-            float K, Lc = 0.f;
-            if (P.series) {
-              const float s2 = P.s2;
-              const float dser = 1.f / 3.f + s2 * (16.f / 45.f + s2 * (12.f / 35.f + s2 * (512.f / 1575.f)));
-              K = Lm * P.q * dser;
-            } else {
-              const float s = sqrtf(P.s2);
-              const float ratio = sqrtf(P.ser);
-              const float th = ratio * s;
-              const float kf = (c * s - th) / (P.s2 * s);     // d(theta/s)/du_j = kf u_j
-              K = Lm * P.q * ratio * kf;
-              Lc = -Lm * P.q * ratio;                          // d(theta/s)/dc = -1/s^2... times s: -1
-            }
-            const float h1 = Ws * Qu1 + K * u1, h2 = Ws * Qu2 + K * u2;
-            // moving g by a tangent step delta: du_i = -c delta_i, dc = u . delta
-            acc[7] += -c * h1 + Lc * u1;
-            acc[8] += -c * h2 + Lc * u2;
+            if (bwd_pixel<DEPTH, NA>(vt, P, r0, r1, r2, r3, dI[q], DEPTH ? dDp[DEPTH ? q : 0] : 0.f,
+                                     DEPTH ? s_invr[e] : 0.f, T[q], B[q], acc))
+              any = true;
           }
           // reduction of the 9 partials over groups of RL lanes, then one shared-memory
           // slot per group (the block-level pass below adds the slots)
@@ -1490,7 +1515,7 @@ __global__ void __launch_bounds__(kPreBwdThreads, HPXGS_PREBWD_MINB) k_preproces
     if (!(rad > 0.f)) continue;
     const ViewParams& vp = vt.v[v];
     Geo G;
-    geo_compute(vp, vt.near_plane, mu, scl, rq, G);
+    geo_compute<false>(vp, vt.near_plane, mu, scl, rq, G);     // valid: the forward listed it (rad > 0)
     if (!G.valid) continue;
     // colour -> SH and the viewing direction
     float dx = mu[0] - vp.cam[0], dy = mu[1] - vp.cam[1], dz = mu[2] - vp.cam[2];
