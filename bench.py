@@ -134,24 +134,34 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- ours
-def csrc_sha():
+# The source file that defines each timed stage's kernel; a stage's recorded DRAM traffic stays
+# valid while that file and the shared headers are unchanged.
+STAGE_SOURCE = {"hssim_fwd": "hssim.cu", "hssim_bwd": "hssim.cu", "mask": "geometry.cu"}
+
+
+def csrc_sha(stage=None):
+    """Hash of the sources of a stage's kernel: its .cu file (raster.cu unless listed in
+    STAGE_SOURCE), every header under csrc/ and the ABI header."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2606_29794_b300", "csrc")
-    for f in sorted(os.listdir(d)):
+    files = sorted(f for f in os.listdir(d) if f.endswith(".cuh"))
+    files.append(STAGE_SOURCE.get(stage, "raster.cu"))
+    for f in files:
         h.update(open(os.path.join(d, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "hpxgs.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_stage):
     """Per-launch DRAM bytes of a kernel from the committed ncu summary, if the
-    kernels have not changed since it was taken (else None)."""
+    kernel's sources have not changed since it was taken (else None)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(p))
     except Exception:
         return None
     e = d.get(kernel_stage)
-    if not e or e.get("csrc_sha") != csrc_sha():
+    if not e or e.get("csrc_sha") != csrc_sha(kernel_stage):
         return None
     return e.get("bytes_per_launch")
 
