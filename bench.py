@@ -315,10 +315,23 @@ def run_ours(args, ws_n, rank, local):
         "depth_sort": ("hbm", 20.0 * P_GAUSS * 4 / 1e9, "GB/s", hbm),
         "preprocess": ("hbm", (236 + 64 + 16) * P_GAUSS / 1e9, "GB/s", hbm),
         "hssim_fwd": ("hbm", 60.0 * n_mask / 1e9, "GB/s", hbm),
+        # parameters and partials in, parameter gradients out, per Gaussian
+        "preprocess_bwd": ("hbm", (236 + 36 + 4 + 236) * P_GAUSS / 1e9, "GB/s", hbm),
+        # staged member list read (4 B) and (tile, id) written (8 B) per pair; count, offset, slot per Gaussian
+        "tile_emit": ("hbm", (12.0 * n_pairs + 16.0 * P_GAUSS) / 1e9, "GB/s", hbm),
+        # sorted tile ids read per pair, [start, end) written per tile
+        "ranges": ("hbm", (4.0 * n_pairs + 8.0 * 12 * 4 ** (K_ORDER - args.tile_level)) / 1e9, "GB/s", hbm),
         "hssim_bwd": ("hbm", 72.0 * n_mask / 1e9, "GB/s", hbm),
     }
     if not any(s in work for s in stage_ms):
         raise RuntimeError(f"no stage timings recorded: {stage_ms}")
+    # every HBM-bound stage against the measured copy bandwidth (algorithmic bytes / stage time)
+    hbm_stages = {}
+    for st_name, (bnd, amount, unit, pk_) in work.items():
+        if bnd == "hbm" and st_name in stage_ms:
+            gbs = amount / (stage_ms[st_name] * 1e-3)
+            hbm_stages[st_name] = {"ms": round(stage_ms[st_name], 4), "algorithmic_bytes": int(round(amount * 1e9)),
+                                   "gbs": round(gbs, 1), "frac_of_hbm": round(gbs / pk_, 3)}
     dom = max((s for s in stage_ms if s in work), key=lambda s: stage_ms[s])
     bound, amount, unit, peak = work[dom]
     achieved = amount / (stage_ms[dom] * 1e-3)
@@ -393,6 +406,7 @@ def run_ours(args, ws_n, rank, local):
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "stage_timing": stage_source,
         "roofline": roofline,
+        "hbm_stages": hbm_stages,
         "clocks": clk,
         "gpu_launches": int(launches),
         "e2e": e2e,
@@ -713,9 +727,10 @@ def oracle_step(frac, seed=0):
     target scene, their tile lists over every active tile (Algorithm 3), and the backward's
     per-Gaussian chain (its preprocess and the chain to the parameters, timed as a backward over
     one pixel). The per-pixel work (compositing of both scenes, the HSSIM loss and gradient, the
-    backward blend) runs on a random `frac` of the in-mask pixels and is scaled by 1 / frac;
-    frac = 1 is the whole step, timed as it runs. Returns the seconds of each part and the
-    step estimate."""
+    backward blend) runs on the in-mask pixels of a random `frac` of the active tiles, taken as
+    runs of 16 neighbouring tiles (so that the sample keeps the full run's locality: a tile's
+    pixels share one list, neighbouring tiles share Gaussians) and is scaled by the in-mask pixels of the step over those of the sample; frac = 1 is the
+    whole step, timed as it runs. Returns the seconds of each part and the step estimate."""
     import numpy as np
 
     import oracle as O
@@ -723,7 +738,16 @@ def oracle_step(frac, seed=0):
     sc, tgt, cfg, v64, m, act, rho, pix = (W[k] for k in ("sc", "tgt", "cfg", "v64", "mask", "active", "rho", "pix"))
     b = cfg.tile_level
     rng = np.random.default_rng(seed)
-    sel = pix if frac >= 1.0 else np.sort(rng.choice(pix, max(1, int(round(frac * pix.size))), replace=False))
+    if frac >= 1.0:
+        sel = pix
+    else:
+        # runs of 16 consecutive active tiles (NESTED order: 4 x 4 squares of tiles), so that the
+        # sample also keeps the sharing of Gaussians between neighbouring tiles
+        tiles = np.nonzero(act)[0]
+        nrun = max(1, int(round(frac * tiles.size / 16)))
+        starts = rng.choice(tiles.size // 16, nrun, replace=False) * 16
+        pick = tiles[(starts[:, None] + np.arange(16)[None, :]).ravel()]
+        sel = pix[np.isin(pix >> (2 * cfg.tile_level), pick)]
     msel = m
     if frac < 1.0:
         msel = np.zeros_like(m)
@@ -766,8 +790,9 @@ def _oracle_record(parts_list, frac):
                  "cpu": cpu_info(),
                  "sample": (f"FP64 oracle (C++/OpenMP), one training step per sample: preprocess of both scenes, "
                             f"tile lists over every active tile and the backward's per-Gaussian chain in full; "
-                            f"compositing of both scenes, HSSIM loss + gradient and the backward blend on a random "
-                            f"{frac:.4f} of the {nmask} in-mask px, scaled by 1/{frac:.4f}"),
+                            f"compositing of both scenes, HSSIM loss + gradient and the backward blend on the "
+                            f"in-mask px of a random {frac:.4f} of the active tiles (runs of 16 neighbouring tiles), "
+                            f"scaled to the {nmask} in-mask px"),
                  "parts_s": {k: mean(k) for k in ("fixed_fwd_s", "composite_s", "hssim_s", "backward_s",
                                                   "backward_fixed_s")},
                  "step_s": round(est, 3)}

@@ -229,3 +229,34 @@ def test_nside2048_full_sphere_p6m():
     sampled = _check_views(sc, [view], rast, out, state, n_tiles=24, per_tile=16, seed=5)
     # the backward from the stored T_final and last index alone (recompute in backward)
     _check_grads(sc, [view], rast, out, state, sampled, seed=6)
+
+
+def test_timed_fused_step_against_oracle_full_size():
+    # the step the benchmark times (forward, L1 + HSSIM loss, the loss backward folded into the
+    # backward blend; CUDA graph; order-5 lists in 16 x 16 units) on the 300k training workload,
+    # against the oracle over every in-mask pixel: the oracle renders the scene, evaluates the loss
+    # (Sec. 4.1) against the same target and runs its backward (Sec. 3.2) on dL/dI of every pixel.
+    # The target is the oracle's own render of the perturbed scene (rounded to float32).
+    sc = S.make_scene(300_000, 3, seed=20261205)
+    tgt = S.perturb_scene(sc, 20261206)
+    view = S.make_view(9, S.CAM_FISHEYE, 190.0)
+    rast = R.Rasterizer(tile_level=5)
+    cfg = oracle_cfg(rast)
+    cfg.tile_level = 4
+    v64 = _f64view(view)
+    G32 = O.render(tgt, v64, cfg).image.astype(np.float32)
+    step = R.GraphStep(scene_tensors(sc), 3, [view], torch.as_tensor(G32, device="cuda"), rast, fused=True)
+    losses, grads = step.replay()
+    torch.cuda.synchronize()
+    assert int(step.status.item()) == 0
+    full = O.render(sc, v64, cfg)
+    loss, h, l1, dI = O.hssim_loss(2 ** 9, full.image, G32.astype(np.float64), full.mask, cfg.lam)
+    got = losses[0].cpu().numpy().astype(np.float64)
+    assert np.abs(got - np.array([loss, h, l1])).max() < 2e-6, (got, loss, h, l1)
+    ref = O.backward(sc, v64, cfg, dI[full.pix], full.start, full.ids, full.pix)
+    for name, gt in zip(["means", "scales", "rotations", "opacities", "sh"], grads):
+        g = gt.cpu().numpy().astype(np.float64).reshape(ref[name].shape)
+        r = ref[name]
+        rel = np.linalg.norm(g - r) / np.linalg.norm(r)
+        assert rel <= GRAD_TOL, (name, rel)
+        assert np.abs(g - r).max() <= GRAD_TOL * np.abs(r).max(), (name, np.abs(g - r).max(), np.abs(r).max())
