@@ -335,6 +335,34 @@ int hpxgs_image_to_sphere(const float* image, int width, int height, const hpxgs
 int hpxgs_image_to_sphere_u8(const uint8_t* image, int width, int height, const hpxgs_camera* cam, int nside_log2,
                              float* map, uint32_t* mask_bits, hpxgs_stream_t stream);
 
+/* ---- resampling plans (Eq. camera_synthesis; Eq. supp_image_to_healpix) ----
+ * The taps of every output pixel of a resampling, computed once for a camera (kind, FoV,
+ * principal point), an image size and a HEALPix order, then applied to any number of maps
+ * or images (a training loop or a renderer with fixed intrinsics): an application is a
+ * pure gather (its adjoint a scatter) and gives the direct call's result bit for bit.
+ * HPXGS_PLAN_SPHERE_TO_IMAGE serves hpxgs_sphere_to_image and its adjoint (taps of the
+ * width x height image pixels: 4 map pixels and weights, 33 bytes per image pixel);
+ * HPXGS_PLAN_IMAGE_TO_SPHERE serves hpxgs_image_to_sphere(_u8) (taps of the 12 * 4^k map
+ * pixels: 4 image pixels and weights, and M_C; 32 bytes per map pixel). The plan is device
+ * memory owned by the caller, at least hpxgs_resample_plan_size bytes; building it launches
+ * one kernel on the stream. An application must pass the order and image size the plan was
+ * built for (else HPXGS_E_INVALID_ARG or HPXGS_E_WORKSPACE when the sizes disagree; a plan
+ * of another camera of the same sizes is not detected). Image sizes are limited to
+ * width * height < 2^32 (also for the direct calls). */
+#define HPXGS_PLAN_SPHERE_TO_IMAGE 0
+#define HPXGS_PLAN_IMAGE_TO_SPHERE 1
+int hpxgs_resample_plan_size(int direction, int nside_log2, int width, int height, size_t* bytes);
+int hpxgs_resample_plan_build(int direction, int nside_log2, const hpxgs_camera* cam, int width, int height,
+                              void* plan, size_t plan_bytes, hpxgs_stream_t stream);
+int hpxgs_sphere_to_image_planned(const float* map, int nside_log2, int width, int height, const void* plan,
+                                  size_t plan_bytes, float* image, uint8_t* valid, hpxgs_stream_t stream);
+int hpxgs_sphere_to_image_backward_planned(const float* dimage, int nside_log2, int width, int height,
+                                           const void* plan, size_t plan_bytes, float* dmap, hpxgs_stream_t stream);
+int hpxgs_image_to_sphere_planned(const float* image, int width, int height, int nside_log2, const void* plan,
+                                  size_t plan_bytes, float* map, uint32_t* mask_bits, hpxgs_stream_t stream);
+int hpxgs_image_to_sphere_u8_planned(const uint8_t* image, int width, int height, int nside_log2, const void* plan,
+                                     size_t plan_bytes, float* map, uint32_t* mask_bits, hpxgs_stream_t stream);
+
 /* ---- instrumentation ---- */
 /* Stages that hpxgs_profile_arm can time. */
 #define HPXGS_STAGE_MASK 0

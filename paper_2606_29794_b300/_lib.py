@@ -74,6 +74,7 @@ _vp, _i32, _i64, _sz, _f32, _f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int
 # HPXGS_MUFU_* values of include/hpxgs.h; a test checks they agree).
 FLOPS_EVAL, FLOPS_FWD_CONTRIB, FLOPS_BWD_CONTRIB = 40, 13, 83
 QUERY_RING, QUERY_NESTED = 0, 1
+PLAN_SPHERE_TO_IMAGE, PLAN_IMAGE_TO_SPHERE = 0, 1
 MUFU_FWD_CONTRIB, MUFU_BWD_CONTRIB = 1, 2
 
 _SIGS = {
@@ -115,6 +116,17 @@ _SIGS = {
                                              _vp]),
     "hpxgs_image_to_sphere_u8": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _P(Camera), ctypes.c_int, _vp,
                                                 _vp, _vp]),
+    "hpxgs_resample_plan_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P(_sz)]),
+    "hpxgs_resample_plan_build": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P(Camera), ctypes.c_int, ctypes.c_int,
+                                                 _vp, _sz, _vp]),
+    "hpxgs_sphere_to_image_planned": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _sz, _vp,
+                                                     _vp, _vp]),
+    "hpxgs_sphere_to_image_backward_planned": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
+                                                              _sz, _vp, _vp]),
+    "hpxgs_image_to_sphere_planned": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _sz, _vp,
+                                                     _vp, _vp]),
+    "hpxgs_image_to_sphere_u8_planned": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _sz,
+                                                        _vp, _vp, _vp]),
     "hpxgs_launch_count": (ctypes.c_uint64, []),
     "hpxgs_probe_alu_peak": (ctypes.c_int, [_P(_f64), _P(_f64), ctypes.c_void_p]),
     "hpxgs_hssim_table_size": (ctypes.c_int, [ctypes.c_int, _P(_sz)]),

@@ -149,28 +149,49 @@ __device__ __forceinline__ void healpix_angles(float3 d, float& theta, float& ph
   if (phi < 0.f) phi += 2.f * (float)kPi;
 }
 
+// The Interp_H taps of image pixel p: 4 NESTED map pixels and weights, false outside D_C
+// (then no taps). Shared by the direct kernels and the resampling plan.
+__device__ __forceinline__ bool s2i_taps(int k, const ImgCam& c, int64_t p, uint32_t pix[4], float w[4]) {
+  const int row = (int)(p / c.W), col = (int)(p - (int64_t)row * c.W);
+  float3 d;
+  if (!img_to_dir(c, (float)col + 0.5f, (float)row + 0.5f, d)) return false;
+  float th, ph, z, s2;
+  healpix_angles(d, th, ph, z, s2);
+  interp_weights(k, th, ph, z, s2, pix, w);
+  return true;
+}
+
+// sum_q w_q map[pix_q] per channel, q in order
+__device__ __forceinline__ void s2i_gather(const float* __restrict__ map, const uint32_t pix[4], const float w[4],
+                                           float o[3]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) o[ch] += w[q] * __ldg(map + 3 * (size_t)pix[q] + ch);
+}
+
 __global__ void __launch_bounds__(kRsThreads) k_sphere_to_image(const float* __restrict__ map, int k, ImgCam c,
                                                                  float* __restrict__ img, uint8_t* __restrict__ valid) {
   const int64_t n = (int64_t)c.W * c.H;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int row = (int)(p / c.W), col = (int)(p - (int64_t)row * c.W);
-    float3 d;
-    const bool ok = img_to_dir(c, (float)col + 0.5f, (float)row + 0.5f, d);
+    uint32_t pix[4];
+    float w[4];
+    const bool ok = s2i_taps(k, c, p, pix, w);
     float o[3] = {0.f, 0.f, 0.f};
-    if (ok) {
-      float th, ph, z, s2;
-      healpix_angles(d, th, ph, z, s2);
-      uint32_t pix[4];
-      float w[4];
-      interp_weights(k, th, ph, z, s2, pix, w);
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) o[ch] += w[q] * __ldg(map + 3 * (size_t)pix[q] + ch);
-    }
+    if (ok) s2i_gather(map, pix, w, o);
     img[3 * p + 0] = o[0]; img[3 * p + 1] = o[1]; img[3 * p + 2] = o[2];
     if (valid) valid[p] = ok;
   }
+}
+
+// dmap[pix_q] += w_q g per channel by atomics (several image pixels share a map pixel)
+__device__ __forceinline__ void s2i_scatter(float* __restrict__ dmap, const uint32_t pix[4], const float w[4],
+                                            const float g[3]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (w[q] != 0.f)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) atomicAdd(dmap + 3 * (size_t)pix[q] + ch, w[q] * g[ch]);
 }
 
 // dmap += A^T dimg, by atomics (several image pixels share a HEALPix pixel).
@@ -178,21 +199,12 @@ __global__ void __launch_bounds__(kRsThreads) k_sphere_to_image_bwd(const float*
                                                                      float* __restrict__ dmap) {
   const int64_t n = (int64_t)c.W * c.H;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int row = (int)(p / c.W), col = (int)(p - (int64_t)row * c.W);
-    float3 d;
-    if (!img_to_dir(c, (float)col + 0.5f, (float)row + 0.5f, d)) continue;
     const float g[3] = {dimg[3 * p], dimg[3 * p + 1], dimg[3 * p + 2]};
     if (g[0] == 0.f && g[1] == 0.f && g[2] == 0.f) continue;
-    float th, ph, z, s2;
-    healpix_angles(d, th, ph, z, s2);
     uint32_t pix[4];
     float w[4];
-    interp_weights(k, th, ph, z, s2, pix, w);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (w[q] != 0.f)
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) atomicAdd(dmap + 3 * (size_t)pix[q] + ch, w[q] * g[ch]);
+    if (!s2i_taps(k, c, p, pix, w)) continue;
+    s2i_scatter(dmap, pix, w, g);
   }
 }
 
@@ -201,6 +213,42 @@ __global__ void __launch_bounds__(kRsThreads) k_sphere_to_image_bwd(const float*
 // v / 255 (IEEE division, the value a float image holding v / 255 would give).
 __device__ __forceinline__ float image_value(const float* px) { return __ldg(px); }
 __device__ __forceinline__ float image_value(const uint8_t* px) { return __fdiv_rn((float)__ldg(px), 255.f); }
+
+// The bilinear image taps of in-mask map pixel q: image pixel indices row * W + col and
+// weights, in the order (row 0, col 0), (0, 1), (1, 0), (1, 1). Shared by the direct kernel
+// and the resampling plan.
+__device__ __forceinline__ void i2s_taps(const ImgCam& c, int k, uint32_t q, uint32_t idx[4], float w[4]) {
+  const float3 h = pix2vec_f32(k, q);
+  const float2 uv = dir_to_img(c, make_float3(h.y, h.z, h.x));
+  const float x = uv.x - 0.5f, y = uv.y - 0.5f;
+  const float x0 = floorf(x), y0 = floorf(y), fx = x - x0, fy = y - y0;
+  int xs[2] = {(int)x0, (int)x0 + 1}, ys[2] = {(int)y0, (int)y0 + 1};
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    if (c.kind == HPXGS_CAM_FULL) { xs[t] %= c.W; if (xs[t] < 0) xs[t] += c.W; }
+    else xs[t] = min(c.W - 1, max(0, xs[t]));
+    ys[t] = min(c.H - 1, max(0, ys[t]));
+  }
+  const float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy};
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      idx[2 * a + b] = (uint32_t)ys[a] * (uint32_t)c.W + (uint32_t)xs[b];
+      w[2 * a + b] = wy[a] * wx[b];
+    }
+}
+
+// sum_t w_t image[idx_t] per channel, t in order
+template <typename T>
+__device__ __forceinline__ void i2s_gather(const T* __restrict__ img, const uint32_t idx[4], const float w[4],
+                                           float o[3]) {
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const T* px = img + 3 * (size_t)idx[t];
+    o[0] += w[t] * image_value(px); o[1] += w[t] * image_value(px + 1); o[2] += w[t] * image_value(px + 2);
+  }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kRsThreads) k_image_to_sphere(const T* __restrict__ img, ImgCam c, ViewParams vp,
@@ -213,26 +261,10 @@ __global__ void __launch_bounds__(kRsThreads) k_image_to_sphere(const T* __restr
     const bool in = inr && pixel_in_mask(vp, q);
     float o[3] = {0.f, 0.f, 0.f};
     if (in) {
-      const float3 h = pix2vec_f32(vp.k, q);
-      const float2 uv = dir_to_img(c, make_float3(h.y, h.z, h.x));
-      const float x = uv.x - 0.5f, y = uv.y - 0.5f;
-      const float x0 = floorf(x), y0 = floorf(y), fx = x - x0, fy = y - y0;
-      int xs[2] = {(int)x0, (int)x0 + 1}, ys[2] = {(int)y0, (int)y0 + 1};
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        if (c.kind == HPXGS_CAM_FULL) { xs[t] %= c.W; if (xs[t] < 0) xs[t] += c.W; }
-        else xs[t] = min(c.W - 1, max(0, xs[t]));
-        ys[t] = min(c.H - 1, max(0, ys[t]));
-      }
-      const float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy};
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          const T* px = img + 3 * ((size_t)ys[a] * c.W + xs[b]);
-          const float ww = wy[a] * wx[b];
-          o[0] += ww * image_value(px); o[1] += ww * image_value(px + 1); o[2] += ww * image_value(px + 2);
-        }
+      uint32_t idx[4];
+      float w[4];
+      i2s_taps(c, vp.k, q, idx, w);
+      i2s_gather(img, idx, w, o);
     }
     if (inr) { map[3 * (size_t)q] = o[0]; map[3 * (size_t)q + 1] = o[1]; map[3 * (size_t)q + 2] = o[2]; }
     const uint32_t bits = __ballot_sync(0xffffffffu, in);
@@ -240,8 +272,127 @@ __global__ void __launch_bounds__(kRsThreads) k_image_to_sphere(const T* __restr
   }
 }
 
+// ----------------------------------------------------------------------------
+// Resampling plans: the taps of every output pixel, computed once for a camera (its
+// intrinsics, image size and HEALPix order) and applied to any number of maps or
+// images. Layout (structure of arrays, each part 256-byte aligned), n output pixels:
+//   sphere -> image (n = W H):     pix [4][n] u32, w [4][n] f32, valid [n] u8
+//   image -> sphere (n = 12 4^k):  idx [4][n] u32, w [4][n] f32, mask words [n / 32] u32
+// Applying a plan runs the direct kernel's accumulation over the same taps in the same
+// order, so it gives the direct kernel's results bit for bit.
+// ----------------------------------------------------------------------------
+struct PlanLayout {
+  size_t taps, w, extra, total;
+  int64_t n;
+};
+
+PlanLayout plan_layout(int dir, int k, int W, int H) {
+  PlanLayout L;
+  L.n = dir == HPXGS_PLAN_SPHERE_TO_IMAGE ? (int64_t)W * H : (12LL << (2 * k));
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  L.taps = 0;
+  L.w = al(sizeof(uint32_t) * 4 * (size_t)L.n);
+  L.extra = L.w + al(sizeof(float) * 4 * (size_t)L.n);
+  L.total = L.extra + al(dir == HPXGS_PLAN_SPHERE_TO_IMAGE ? (size_t)L.n : sizeof(uint32_t) * (size_t)(L.n / 32));
+  return L;
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_plan_s2i(int k, ImgCam c, uint32_t* __restrict__ pix,
+                                                          float* __restrict__ wt, uint8_t* __restrict__ valid) {
+  const int64_t n = (int64_t)c.W * c.H;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t px[4] = {0u, 0u, 0u, 0u};
+    float w[4] = {0.f, 0.f, 0.f, 0.f};
+    const bool ok = s2i_taps(k, c, p, px, w);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { pix[q * n + p] = ok ? px[q] : 0u; wt[q * n + p] = ok ? w[q] : 0.f; }
+    valid[p] = ok;
+  }
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_plan_s2i_apply(const float* __restrict__ map, int64_t n,
+                                                                const uint32_t* __restrict__ pix,
+                                                                const float* __restrict__ wt,
+                                                                const uint8_t* __restrict__ pvalid,
+                                                                float* __restrict__ img, uint8_t* __restrict__ valid) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const bool ok = pvalid[p];
+    float o[3] = {0.f, 0.f, 0.f};
+    if (ok) {
+      uint32_t px[4];
+      float w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { px[q] = pix[q * n + p]; w[q] = wt[q * n + p]; }
+      s2i_gather(map, px, w, o);
+    }
+    img[3 * p + 0] = o[0]; img[3 * p + 1] = o[1]; img[3 * p + 2] = o[2];
+    if (valid) valid[p] = ok;
+  }
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_plan_s2i_adjoint(const float* __restrict__ dimg, int64_t n,
+                                                                  const uint32_t* __restrict__ pix,
+                                                                  const float* __restrict__ wt,
+                                                                  const uint8_t* __restrict__ pvalid,
+                                                                  float* __restrict__ dmap) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const float g[3] = {dimg[3 * p], dimg[3 * p + 1], dimg[3 * p + 2]};
+    if (g[0] == 0.f && g[1] == 0.f && g[2] == 0.f) continue;
+    if (!pvalid[p]) continue;
+    uint32_t px[4];
+    float w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { px[q] = pix[q * n + p]; w[q] = wt[q * n + p]; }
+    s2i_scatter(dmap, px, w, g);
+  }
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_plan_i2s(ImgCam c, ViewParams vp, uint32_t* __restrict__ idx,
+                                                          float* __restrict__ wt, uint32_t* __restrict__ words) {
+  const uint32_t npix = 12u << (2 * vp.k);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < npix; base += stride) {
+    const uint32_t q = base + threadIdx.x;
+    const bool inr = q < npix;
+    const bool in = inr && pixel_in_mask(vp, q);
+    uint32_t ix[4] = {0u, 0u, 0u, 0u};
+    float w[4] = {0.f, 0.f, 0.f, 0.f};
+    if (in) i2s_taps(c, vp.k, q, ix, w);
+    if (inr)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) { idx[(size_t)t * npix + q] = ix[t]; wt[(size_t)t * npix + q] = w[t]; }
+    const uint32_t bits = __ballot_sync(0xffffffffu, in);
+    if (inr && (threadIdx.x & 31) == 0) words[q >> 5] = bits;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRsThreads) k_plan_i2s_apply(const T* __restrict__ img, uint32_t npix,
+                                                                const uint32_t* __restrict__ idx,
+                                                                const float* __restrict__ wt,
+                                                                const uint32_t* __restrict__ pwords,
+                                                                float* __restrict__ map, uint32_t* __restrict__ words) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < npix; base += stride) {
+    const uint32_t q = base + threadIdx.x;
+    const bool inr = q < npix;
+    const bool in = inr && ((pwords[q >> 5] >> (q & 31)) & 1u);
+    float o[3] = {0.f, 0.f, 0.f};
+    if (in) {
+      uint32_t ix[4];
+      float w[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) { ix[t] = idx[(size_t)t * npix + q]; w[t] = wt[(size_t)t * npix + q]; }
+      i2s_gather(img, ix, w, o);
+    }
+    if (inr) { map[3 * (size_t)q] = o[0]; map[3 * (size_t)q + 1] = o[1]; map[3 * (size_t)q + 2] = o[2]; }
+    if (words && inr && (threadIdx.x & 31) == 0) words[q >> 5] = pwords[q >> 5];
+  }
+}
+
 bool make_cam(const hpxgs_camera* cam, int W, int H, ImgCam& c) {
   if (!cam || W < 1 || H < 1 || W > 65536 || H > 65536) return false;
+  if ((int64_t)W * H > 0xFFFFFFFFLL) return false;            // image pixel indices fit 32 bits
   c.kind = cam->kind; c.W = W; c.H = H; c.fx = c.fy = 1.f; c.wx = c.wy = 1.f;
   c.cx = (float)(0.5 * W); c.cy = (float)(0.5 * H);
   if (!valid_camera(*cam)) return false;
@@ -317,4 +468,103 @@ extern "C" int hpxgs_image_to_sphere(const float* image, int width, int height, 
 extern "C" int hpxgs_image_to_sphere_u8(const uint8_t* image, int width, int height, const hpxgs_camera* cam,
                                         int nside_log2, float* map, uint32_t* mask_bits, hpxgs_stream_t stream) {
   return image_to_sphere(image, width, height, cam, nside_log2, map, mask_bits, stream);
+}
+
+// ---- resampling plans ----
+static bool plan_args(int dir, int k, int W, int H) {
+  if (dir != HPXGS_PLAN_SPHERE_TO_IMAGE && dir != HPXGS_PLAN_IMAGE_TO_SPHERE) return false;
+  if (k < (dir == HPXGS_PLAN_SPHERE_TO_IMAGE ? 1 : 2) || k > 13) return false;
+  return W >= 1 && H >= 1 && W <= 65536 && H <= 65536 && (int64_t)W * H <= 0xFFFFFFFFLL;
+}
+
+extern "C" int hpxgs_resample_plan_size(int direction, int nside_log2, int width, int height, size_t* bytes) {
+  if (!bytes || !plan_args(direction, nside_log2, width, height)) return HPXGS_E_INVALID_ARG;
+  *bytes = plan_layout(direction, nside_log2, width, height).total;
+  return HPXGS_OK;
+}
+
+extern "C" int hpxgs_resample_plan_build(int direction, int nside_log2, const hpxgs_camera* cam, int width, int height,
+                                         void* plan, size_t plan_bytes, hpxgs_stream_t stream) {
+  ImgCam c;
+  if (!plan || !plan_args(direction, nside_log2, width, height) || !make_cam(cam, width, height, c))
+    return HPXGS_E_INVALID_ARG;
+  const PlanLayout L = plan_layout(direction, nside_log2, width, height);
+  if (plan_bytes < L.total) return HPXGS_E_WORKSPACE;
+  char* b = static_cast<char*>(plan);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (direction == HPXGS_PLAN_SPHERE_TO_IMAGE) {
+    k_plan_s2i<<<grid_for(L.n), kRsThreads, 0, s>>>(nside_log2, c, reinterpret_cast<uint32_t*>(b + L.taps),
+                                                    reinterpret_cast<float*>(b + L.w),
+                                                    reinterpret_cast<uint8_t*>(b + L.extra));
+  } else {
+    ViewParams vp{};
+    camera_params(*cam, nside_log2, vp);
+    k_plan_i2s<<<grid_for(L.n), kRsThreads, 0, s>>>(c, vp, reinterpret_cast<uint32_t*>(b + L.taps),
+                                                    reinterpret_cast<float*>(b + L.w),
+                                                    reinterpret_cast<uint32_t*>(b + L.extra));
+  }
+  note_launches(1);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+
+extern "C" int hpxgs_sphere_to_image_planned(const float* map, int nside_log2, int width, int height, const void* plan,
+                                             size_t plan_bytes, float* image, uint8_t* valid, hpxgs_stream_t stream) {
+  if (!map || !image || !plan || !plan_args(HPXGS_PLAN_SPHERE_TO_IMAGE, nside_log2, width, height))
+    return HPXGS_E_INVALID_ARG;
+  const PlanLayout L = plan_layout(HPXGS_PLAN_SPHERE_TO_IMAGE, nside_log2, width, height);
+  if (plan_bytes < L.total) return HPXGS_E_WORKSPACE;
+  const char* b = static_cast<const char*>(plan);
+  k_plan_s2i_apply<<<grid_for(L.n), kRsThreads, 0, (cudaStream_t)stream>>>(
+      map, L.n, reinterpret_cast<const uint32_t*>(b + L.taps), reinterpret_cast<const float*>(b + L.w),
+      reinterpret_cast<const uint8_t*>(b + L.extra), image, valid);
+  note_launches(1);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+
+extern "C" int hpxgs_sphere_to_image_backward_planned(const float* dimage, int nside_log2, int width, int height,
+                                                      const void* plan, size_t plan_bytes, float* dmap,
+                                                      hpxgs_stream_t stream) {
+  if (!dimage || !dmap || !plan || !plan_args(HPXGS_PLAN_SPHERE_TO_IMAGE, nside_log2, width, height))
+    return HPXGS_E_INVALID_ARG;
+  const PlanLayout L = plan_layout(HPXGS_PLAN_SPHERE_TO_IMAGE, nside_log2, width, height);
+  if (plan_bytes < L.total) return HPXGS_E_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  HPXGS_CUDA_CHECK(cudaMemsetAsync(dmap, 0, sizeof(float) * 3 * (size_t)(12LL << (2 * nside_log2)), s));
+  const char* b = static_cast<const char*>(plan);
+  k_plan_s2i_adjoint<<<grid_for(L.n), kRsThreads, 0, s>>>(dimage, L.n, reinterpret_cast<const uint32_t*>(b + L.taps),
+                                                          reinterpret_cast<const float*>(b + L.w),
+                                                          reinterpret_cast<const uint8_t*>(b + L.extra), dmap);
+  note_launches(1);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+
+template <typename T>
+static int image_to_sphere_planned(const T* image, int width, int height, int nside_log2, const void* plan,
+                                   size_t plan_bytes, float* map, uint32_t* mask_bits, hpxgs_stream_t stream) {
+  if (!image || !map || !plan || !plan_args(HPXGS_PLAN_IMAGE_TO_SPHERE, nside_log2, width, height))
+    return HPXGS_E_INVALID_ARG;
+  const PlanLayout L = plan_layout(HPXGS_PLAN_IMAGE_TO_SPHERE, nside_log2, width, height);
+  if (plan_bytes < L.total) return HPXGS_E_WORKSPACE;
+  const char* b = static_cast<const char*>(plan);
+  k_plan_i2s_apply<T><<<grid_for(L.n), kRsThreads, 0, (cudaStream_t)stream>>>(
+      image, (uint32_t)L.n, reinterpret_cast<const uint32_t*>(b + L.taps), reinterpret_cast<const float*>(b + L.w),
+      reinterpret_cast<const uint32_t*>(b + L.extra), map, mask_bits);
+  note_launches(1);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+
+extern "C" int hpxgs_image_to_sphere_planned(const float* image, int width, int height, int nside_log2,
+                                             const void* plan, size_t plan_bytes, float* map, uint32_t* mask_bits,
+                                             hpxgs_stream_t stream) {
+  return image_to_sphere_planned(image, width, height, nside_log2, plan, plan_bytes, map, mask_bits, stream);
+}
+
+extern "C" int hpxgs_image_to_sphere_u8_planned(const uint8_t* image, int width, int height, int nside_log2,
+                                                const void* plan, size_t plan_bytes, float* map, uint32_t* mask_bits,
+                                                hpxgs_stream_t stream) {
+  return image_to_sphere_planned(image, width, height, nside_log2, plan, plan_bytes, map, mask_bits, stream);
 }

@@ -98,6 +98,72 @@ def image_to_sphere(image, cam, nside_log2, with_mask=True):
     return hmap, words
 
 
+class Plan:
+    """A resampling plan (hpxgs_resample_plan_build): the taps of every output pixel for one
+    camera, image size and HEALPix order, built once on the device. `direction` is
+    L.PLAN_SPHERE_TO_IMAGE (serves sphere_to_image and its adjoint) or L.PLAN_IMAGE_TO_SPHERE
+    (serves image_to_sphere); the planned calls give the direct calls' results bit for bit."""
+
+    def __init__(self, direction, cam, nside_log2, width, height, device="cuda"):
+        self.direction, self.k, self.W, self.H = int(direction), int(nside_log2), int(width), int(height)
+        nb = ctypes.c_size_t()
+        L.check(L.lib().hpxgs_resample_plan_size(self.direction, self.k, self.W, self.H, ctypes.byref(nb)),
+                "plan size")
+        self.nbytes = nb.value
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        c = _cam(cam)
+        L.check(L.lib().hpxgs_resample_plan_build(self.direction, self.k, ctypes.byref(c), self.W, self.H,
+                                                  _ptr(self.buf), self.nbytes, _stream(self.buf.device)),
+                "plan build")
+
+    def _need(self, direction):
+        if self.direction != direction:
+            raise ValueError("plan built for the other direction")
+
+    def sphere_to_image(self, hmap, image=None, valid=None):
+        """Image [H, W, 3] and validity [H, W] of a map through the plan."""
+        self._need(L.PLAN_SPHERE_TO_IMAGE)
+        hmap = _f32(hmap)
+        if hmap.numel() != 3 * 12 * 4 ** self.k:
+            raise ValueError("map size does not match the plan's order")
+        image = torch.empty((self.H, self.W, 3), dtype=torch.float32, device=hmap.device) if image is None else image
+        valid = torch.empty((self.H, self.W), dtype=torch.uint8, device=hmap.device) if valid is None else valid
+        L.check(L.lib().hpxgs_sphere_to_image_planned(_ptr(hmap), self.k, self.W, self.H, _ptr(self.buf), self.nbytes,
+                                                      _ptr(image), _ptr(valid), _stream(hmap.device)),
+                "sphere_to_image_planned")
+        return image, valid
+
+    def sphere_to_image_backward(self, dimage):
+        self._need(L.PLAN_SPHERE_TO_IMAGE)
+        dimage = _f32(dimage)
+        if dimage.numel() != 3 * self.W * self.H:
+            raise ValueError("dimage size does not match the plan's image")
+        dmap = torch.empty((12 * 4 ** self.k, 3), dtype=torch.float32, device=dimage.device)
+        L.check(L.lib().hpxgs_sphere_to_image_backward_planned(_ptr(dimage), self.k, self.W, self.H, _ptr(self.buf),
+                                                               self.nbytes, _ptr(dmap), _stream(dimage.device)),
+                "sphere_to_image_backward_planned")
+        return dmap
+
+    def image_to_sphere(self, image, hmap=None, words=None, stream=None):
+        """HEALPix map [12 * 4^k, 3] and mask words of an image [H, W, 3] (float32, or uint8 codes
+        read as v / 255) through the plan."""
+        self._need(L.PLAN_IMAGE_TO_SPHERE)
+        if tuple(image.shape) != (self.H, self.W, 3) or not image.is_cuda or not image.is_contiguous():
+            raise ValueError("expected a contiguous CUDA image of the plan's size")
+        fn = {torch.uint8: L.lib().hpxgs_image_to_sphere_u8_planned,
+              torch.float32: L.lib().hpxgs_image_to_sphere_planned}.get(image.dtype)
+        if fn is None:
+            raise ValueError("expected a float32 or uint8 image")
+        npix = 12 * 4 ** self.k
+        hmap = torch.empty((npix, 3), dtype=torch.float32, device=image.device) if hmap is None else _f32(hmap)
+        if hmap.numel() != 3 * npix:
+            raise ValueError("map size does not match the plan's order")
+        s = ctypes.c_void_p((stream or torch.cuda.current_stream(image.device)).cuda_stream)
+        L.check(fn(_ptr(image), self.W, self.H, self.k, _ptr(self.buf), self.nbytes, _ptr(hmap), _ptr(words), s),
+                "image_to_sphere_planned")
+        return hmap, words
+
+
 class _SphereToImage(torch.autograd.Function):
     @staticmethod
     def forward(ctx, hmap, nside_log2, cam, width, height):

@@ -138,3 +138,20 @@ def test_scene_tensors_are_validated_before_any_launch():
         R.gaussians_struct(t(P, 3), t(P, 3), t(P, 4), t(P), t(P, 9, 3), 3)
     with pytest.raises(ValueError):                              # degree out of range
         R.gaussians_struct(t(P, 3), t(P, 3), t(P, 4), t(P), t(P, 25, 3), 4)
+
+
+def test_resample_plan_sizes_and_checks(lib):
+    n = ctypes.c_size_t()
+    assert lib.hpxgs_resample_plan_size(L.PLAN_SPHERE_TO_IMAGE, 7, 180, 120, ctypes.byref(n)) == 0
+    al = lambda x: (x + 255) // 256 * 256
+    assert n.value == al(16 * 180 * 120) + al(16 * 180 * 120) + al(180 * 120)
+    assert lib.hpxgs_resample_plan_size(L.PLAN_IMAGE_TO_SPHERE, 7, 180, 120, ctypes.byref(n)) == 0
+    npix = 12 * 4 ** 7
+    assert n.value == al(16 * npix) + al(16 * npix) + al(4 * npix // 32)
+    assert lib.hpxgs_resample_plan_size(2, 7, 180, 120, ctypes.byref(n)) == L.E_INVALID_ARG
+    assert lib.hpxgs_resample_plan_size(L.PLAN_IMAGE_TO_SPHERE, 1, 180, 120, ctypes.byref(n)) == L.E_INVALID_ARG
+    assert lib.hpxgs_resample_plan_size(L.PLAN_SPHERE_TO_IMAGE, 7, 65536, 65536, ctypes.byref(n)) == L.E_INVALID_ARG
+    # an application with a plan smaller than its sizes is refused before any launch
+    assert lib.hpxgs_sphere_to_image_planned(ctypes.c_void_p(16), 7, 180, 120, ctypes.c_void_p(16), 1024,
+                                             ctypes.c_void_p(16), None, None) == L.E_WORKSPACE
+

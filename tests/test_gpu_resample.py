@@ -157,3 +157,32 @@ def test_bench_sizes_sampled(kind, fx, fy, pp, k, W, H):
     assert np.all(np.abs(margin[qs][m != m2]) < 1e-12)
     both = (m == 1) & (m2 == 1)
     assert np.abs(hm.cpu().numpy()[qs][both] - ref2[both]).max() < tol_i2s(W, H)
+
+
+@pytest.mark.parametrize("kind,fx,fy,pp", CAMS)
+def test_plans_equal_direct_calls(kind, fx, fy, pp):
+    # a resampling plan holds the taps the direct kernels compute; applying it gives their results
+    # bit for bit (the adjoint up to the order of its atomic sums), for float and 8-bit images
+    k, W, H = 7, 180, 120
+    cam = _cam(kind, fx, fy, pp)
+    g = torch.Generator(device="cuda").manual_seed(kind + 50)
+    hmap = torch.rand((12 * 4 ** k, 3), device="cuda", generator=g)
+    ps = RS.Plan(L.PLAN_SPHERE_TO_IMAGE, cam, k, W, H)
+    img0, val0 = RS.sphere_to_image_raw(hmap, k, cam, W, H)
+    img1, val1 = ps.sphere_to_image(hmap)
+    torch.cuda.synchronize()
+    assert torch.equal(img0, img1) and torch.equal(val0, val1)
+    dimg = torch.rand((H, W, 3), device="cuda", generator=g)
+    d0 = RS.sphere_to_image_backward(dimg, k, cam, W, H)
+    d1 = ps.sphere_to_image_backward(dimg)
+    assert torch.allclose(d0, d1, rtol=1e-5, atol=1e-6)
+    pi = RS.Plan(L.PLAN_IMAGE_TO_SPHERE, cam, k, W, H)
+    img8 = torch.randint(0, 256, (H, W, 3), dtype=torch.uint8, device="cuda", generator=g)
+    for im in (img8.float() / 255.0, img8):
+        m0, w0 = RS.image_to_sphere(im, cam, k)
+        w1 = torch.empty_like(w0)
+        m1, _ = pi.image_to_sphere(im, words=w1)
+        torch.cuda.synchronize()
+        assert torch.equal(m0, m1) and torch.equal(w0, w1)
+    with pytest.raises(ValueError):
+        pi.sphere_to_image(hmap)
