@@ -599,19 +599,22 @@ def run_resample(args, dev):
             "sphere_to_image_backward": (lambda: RS.sphere_to_image_backward(img, k, cam, W, H), 12 * W * H + 12 * npix + 12 * n_in),
             "image_to_sphere": (lambda: RS.image_to_sphere(img, cam, k), 12 * W * H + 12 * npix + npix // 8),
         }
-        # the same through resampling plans (the taps built once per camera): the plan's bytes are
-        # read at every application and count as algorithmic bytes of the planned call
+        # the same through resampling plans (the taps built once per camera): the taps an application
+        # reads (32 B per output pixel with taps, plus the validity or mask) count as its bytes
         ps = RS.Plan(L.PLAN_SPHERE_TO_IMAGE, cam, k, W, H)
         pi = RS.Plan(L.PLAN_IMAGE_TO_SPHERE, cam, k, W, H)
         pimg, pval = torch.empty_like(img), torch.empty((H, W), dtype=torch.uint8, device=dev)
         pmap, pwords = torch.empty_like(hmap), torch.empty(npix // 32, dtype=torch.int32, device=dev)
-        ops["sphere_to_image_planned"] = (lambda: ps.sphere_to_image(hmap, pimg, pval), 13 * W * H + 12 * n_in + ps.nbytes)
+        ps.sphere_to_image(hmap, pimg, pval)
+        n_val = int(pval.sum().item())                    # image pixels inside D_C: the ones with taps
+        ops["sphere_to_image_planned"] = (lambda: ps.sphere_to_image(hmap, pimg, pval),
+                                          13 * W * H + 12 * n_in + W * H + 32 * n_val)
         ops["sphere_to_image_backward_planned"] = (lambda: ps.sphere_to_image_backward(img),
-                                                   12 * W * H + 12 * npix + 12 * n_in + ps.nbytes)
+                                                   12 * W * H + 12 * npix + 12 * n_in + W * H + 32 * n_val)
         ops["image_to_sphere_planned"] = (lambda: pi.image_to_sphere(img, pmap, pwords),
-                                          12 * W * H + 12 * npix + npix // 8 + pi.nbytes)
-        res = {"in_mask_map_px": n_in, "image_px": W * H, "plan_bytes": {"sphere_to_image": ps.nbytes,
-                                                                         "image_to_sphere": pi.nbytes}}
+                                          12 * W * H + 12 * npix + npix // 4 + 32 * n_in)
+        res = {"in_mask_map_px": n_in, "image_px": W * H, "valid_image_px": n_val,
+               "plan_bytes": {"sphere_to_image": ps.nbytes, "image_to_sphere": pi.nbytes}}
         for op, (fn, nbytes) in ops.items():
             for _ in range(3):
                 fn()
