@@ -477,12 +477,13 @@ int hpxgs_hssim_backward_table(const float* I, const float* G, const uint32_t* m
  * and the two agree within 2e-6. The per-block partial sums live in a fixed
  * 1.18 MB array inside the library's device image, which every GPU that loads
  * the library holds until exit; the call allocates nothing. Limit: k <= 10
- * (Nside <= 1024); larger k returns HPXGS_E_INVALID_ARG. A call outside stream
- * capture looks up the array's device address on the current device and caches
- * it; a call inside capture uses that cache and returns HPXGS_E_CAPTURE if the
- * device has none, so make a first call on each device (and again after a
- * cudaDeviceReset) before capturing. All calls share the array: calls that
- * overlap on the GPU race. */
+ * (Nside <= 1024); larger k returns HPXGS_E_INVALID_ARG. The first call on each
+ * device looks up the array's device address (with that device current); make
+ * that first call, and the first call after a cudaDeviceReset, before any stream
+ * capture. Calls outside capture look the address up again (so a module reloaded
+ * after a reset is found); a capturing stream on a device that has made no call
+ * yet gets HPXGS_E_CAPTURE. All calls share the array: calls that overlap on the
+ * GPU race. */
 int hpxgs_hssim_loss_noalloc(const float* I, const float* G, const uint32_t* mask_bits, int k, float lambda,
                              float* out3, hpxgs_stream_t stream);
 

@@ -13,12 +13,12 @@
 //  - Limit: HEALPix order k <= 10 (Nside <= 1024). The array holds one partial
 //    triple per 256-pixel block at that size: 49,152 x 3 doubles = 1.18 MB, and
 //    every GPU that loads the library keeps it until the process exits.
-//  - Host code cannot use the array's name as a device address. Each call made
-//    outside stream capture looks the address up (cudaGetSymbolAddress, with the
-//    calling thread's device current) and caches it per device; a call made while
-//    the stream is capturing uses the cached address, so a first call on each
-//    device must come before capture. A cudaDeviceReset discards the module and
-//    with it the cached address: call once more outside capture after a reset.
+//  - Host code cannot use the array's name as a device address. The first call on
+//    a device looks the address up (cudaGetSymbolAddress, with that device
+//    current); that first call, and the first after a cudaDeviceReset (which
+//    discards the module), must come before any stream capture. Calls outside
+//    capture look it up again and refresh a per-device cache; a capturing stream
+//    on a device without a cached address gets HPXGS_E_CAPTURE.
 //  - Every call writes all the partials it later reads, so nothing needs
 //    clearing, but all calls share the one array: calls that overlap on the GPU
 //    (different streams without ordering between them) race and give wrong values.
