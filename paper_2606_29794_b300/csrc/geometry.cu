@@ -56,6 +56,42 @@ int num_sms() {
   return n;
 }
 
+// Helper streams, one per (device, caller stream), created on first use and kept for
+// the life of the process. Creation switches this thread to the relaxed capture mode
+// for its few calls, so that a first use inside a stream capture is allowed too.
+namespace {
+constexpr int kMaxForks = 32;
+std::mutex g_fork_mu;
+Fork g_forks[kMaxForks];
+int g_fork_dev[kMaxForks];
+int g_nforks = 0;
+}  // namespace
+
+const Fork* fork_of(cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_fork_mu);
+  for (int i = 0; i < g_nforks; ++i)
+    if (g_forks[i].origin == s && g_fork_dev[i] == dev) return &g_forks[i];
+  if (g_nforks == kMaxForks) return nullptr;
+  Fork f{s, nullptr, nullptr, nullptr};
+  cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+  if (cudaThreadExchangeStreamCaptureMode(&mode) != cudaSuccess) return nullptr;
+  bool ok = cudaStreamCreateWithFlags(&f.side, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    if (f.join) cudaEventDestroy(f.join);
+    if (f.fork) cudaEventDestroy(f.fork);
+    if (f.side) cudaStreamDestroy(f.side);
+  }
+  cudaThreadExchangeStreamCaptureMode(&mode);
+  if (!ok) { cudaGetLastError(); return nullptr; }
+  g_forks[g_nforks] = f;
+  g_fork_dev[g_nforks] = dev;
+  return &g_forks[g_nforks++];
+}
+
 // FoV mask: camera_margin and pixel_in_mask live in camera.cuh.
 // One thread per pixel; a warp's 32 consecutive NESTED pixels form one mask word.
 // tile_flags (optional) gets bit 0 set for every tile with an in-mask pixel.

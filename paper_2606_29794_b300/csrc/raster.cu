@@ -1716,18 +1716,34 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   if (rc != HPXGS_OK) return rc;
   uint32_t* flags = at<uint32_t>(ws, L.tile_flags);
   uint32_t* counters = at<uint32_t>(ws, L.counters);
-  HPXGS_CUDA_CHECK(cudaMemsetAsync(flags, 0, sizeof(uint32_t) * L.total_tiles, s));
   HPXGS_CUDA_CHECK(cudaMemsetAsync(counters, 0, sizeof(uint32_t) * C_COUNT, s));
-  // FoV masks (kept in the workspace: the backward reads them) and tile flags
-  prof_begin(HPXGS_STAGE_MASK, s);
-  for (int v = 0; v < nviews; ++v) {
-    rc = launch_mask(vt->v[v], cfg->tile_level, mask_out + (vt->v[v].pix_base >> 5), flags + vt->v[v].tile_base, s);
-    if (rc != HPXGS_OK) return rc;
+  // FoV masks (kept in the workspace: the backward reads them) and tile flags. They depend
+  // only on the cameras, the preprocess and the depth sort only on the Gaussians: the masks
+  // run on a helper stream, in the SMs the depth sort leaves idle, joined before the query.
+  const Fork* fk = fork_of(s);
+  cudaStream_t ms = s;
+  if (fk) {
+    HPXGS_CUDA_CHECK(cudaEventRecord(fk->fork, s));
+    HPXGS_CUDA_CHECK(cudaStreamWaitEvent(fk->side, fk->fork, 0));
+    ms = fk->side;
   }
-  prof_end(HPXGS_STAGE_MASK, s);
+  HPXGS_CUDA_CHECK(cudaMemsetAsync(flags, 0, sizeof(uint32_t) * L.total_tiles, ms));
+  prof_begin(HPXGS_STAGE_MASK, ms);
+  for (int v = 0; v < nviews && rc == HPXGS_OK; ++v)
+    rc = launch_mask(vt->v[v], cfg->tile_level, mask_out + (vt->v[v].pix_base >> 5), flags + vt->v[v].tile_base, ms);
+  prof_end(HPXGS_STAGE_MASK, ms);
+  auto join = [&]() -> int {
+    if (fk) {
+      HPXGS_CUDA_CHECK(cudaEventRecord(fk->join, fk->side));
+      HPXGS_CUDA_CHECK(cudaStreamWaitEvent(s, fk->join, 0));
+      fk = nullptr;
+    }
+    return HPXGS_OK;
+  };
+  if (rc != HPXGS_OK) { join(); return rc; }
   const int64_t PV = L.PV;
   *which_depth = 0;
-  if (PV == 0) return HPXGS_OK;
+  if (PV == 0) return join();
   float4* rec = at<float4>(ws, L.records);
   float* radii = at<float>(ws, L.radii);
   float* depth = at<float>(ws, L.depth);
@@ -1750,8 +1766,10 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   // a grid sized to the element count (HPXGS_DSORT_TPB tiles of 4096 per block, at most kMaxSortBlocks)
   const int Gd = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSortBlocks, (PV + HPXGS_DSORT_TPB * kSortTile - 1) / (HPXGS_DSORT_TPB * kSortTile)));
   rc = radix_sort(ka, va, kb, vb, nullptr, (uint32_t)PV, 32, at<uint32_t>(ws, L.hist), Gd, counters + C_SORT_TICKET, s, which_depth);
-  if (rc != HPXGS_OK) return rc;
+  if (rc != HPXGS_OK) { join(); return rc; }
   prof_end(HPXGS_STAGE_DEPTH_SORT, s);
+  rc = join();                                     // the query reads the tile flags
+  if (rc != HPXGS_OK) return rc;
   const uint32_t* sk = *which_depth ? kb : ka;
   const uint32_t* sv = *which_depth ? vb : va;
   uint32_t* counts = at<uint32_t>(ws, L.counts);
