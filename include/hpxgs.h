@@ -398,6 +398,16 @@ uint64_t hpxgs_launch_count(void);
  * Synchronises the stream (about 20 ms of GPU time); HPXGS_E_CAPTURE inside
  * stream capture. */
 int hpxgs_probe_alu_peak(double* fma_tflops, double* ex2_tops, hpxgs_stream_t stream);
+/* Check of the bounded grid barrier that the count scan uses in its cooperative
+ * launch: `blocks` resident blocks meet at one barrier that waits
+ * for blocks + `missing` arrivals, at most limit_ns each. `counter` (device u32) is
+ * zeroed by this call; passed[b] (device u32 [blocks]) becomes 1 where block b got
+ * through, 0 where it gave up. With missing = 0 every block passes; with missing > 0
+ * every block gives up after limit_ns and HPXGS_F_TIMEOUT is OR-ed into *status (a
+ * device int32). Asynchronous on `stream`. HPXGS_E_INVALID_ARG for null buffers,
+ * blocks < 1, missing < 0, limit_ns > 2 s or more blocks than fit at once. */
+int hpxgs_probe_grid_barrier(int blocks, int missing, uint64_t limit_ns, uint32_t* counter, uint32_t* passed,
+                             int32_t* status, hpxgs_stream_t stream);
 
 /* FP32 work of the blend kernels, counted from their inner loops (an FMA is 2
  * flops, a MUFU op is counted apart): per evaluated (pixel, entry) pair, the

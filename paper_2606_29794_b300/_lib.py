@@ -129,6 +129,7 @@ _SIGS = {
                                                         _vp, _vp, _vp]),
     "hpxgs_launch_count": (ctypes.c_uint64, []),
     "hpxgs_probe_alu_peak": (ctypes.c_int, [_P(_f64), _P(_f64), ctypes.c_void_p]),
+    "hpxgs_probe_grid_barrier": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _vp, _vp, _vp, _vp]),
     "hpxgs_hssim_table_size": (ctypes.c_int, [ctypes.c_int, _P(_sz)]),
     "hpxgs_hssim_table_build": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _sz, _vp]),
     "hpxgs_hssim_forward_table": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _f32, _vp, _vp, _sz, _vp, _vp]),

@@ -104,8 +104,50 @@ constexpr int kMaxSortBlocks = 1024;
 
 // counters block (u32 each)
 // (u64 counters live at u32 index 8 (n_eval) and 10 (n_contrib), 8-byte aligned)
+// C_GRID_BAR_SCAN: arrivals at the grid barrier of the count scan's cooperative launch.
 enum Counter { C_NPAIRS = 0, C_WORK_FWD = 1, C_WORK_BWD = 2, C_NSORT = 3, C_NPAIRS_HI = 4, C_STAGE = 5, C_NEVAL = 8, C_NCONTRIB = 10, C_SORT_TICKET = 12,
-               C_COUNT = 16 };
+               C_GRID_BAR_SCAN = 13, C_COUNT = 16 };
+
+#ifdef __CUDACC__
+// Grid-wide barrier of a cooperative launch (every block resident at once). Each block
+// adds one arrival to *count (zero before the launch) and waits until the count reaches
+// `target`, the barrier's number (1, 2, ...) times the grid size. Writes before the
+// barrier are released by a fence, reads after it acquire. The wait is bounded: a block
+// that waited limit_ns sets HPXGS_F_TIMEOUT in *status (when given) and gets false; the
+// kernel must then return. A block that gave up arrives at no later barrier, so the
+// other blocks give up too, each within its own limit.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool grid_barrier(uint32_t* count, uint32_t target, uint64_t limit_ns, int32_t* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    const uint64_t t0 = global_ns();
+    int ok = 1;
+    for (;;) {
+      uint32_t c;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(count) : "memory");
+      if (c >= target) break;
+      if (global_ns() - t0 > limit_ns) {
+        ok = 0;
+        if (status) atomicOr(status, HPXGS_F_TIMEOUT);
+        break;
+      }
+      __nanosleep(100);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+#endif
 
 // instrumentation (geometry.cu)
 void prof_begin(int stage, cudaStream_t s);

@@ -49,6 +49,13 @@ __global__ void __launch_bounds__(kProbeThreads) k_ex2_probe(int iters, float* s
   if (s == -1.2345f) sink[0] = s;
 }
 
+// One grid barrier waiting for gridDim.x + missing arrivals.
+__global__ void __launch_bounds__(128) k_barrier_probe(uint32_t* counter, uint32_t missing, uint64_t limit_ns,
+                                                      uint32_t* passed, int32_t* status) {
+  const bool ok = grid_barrier(counter, gridDim.x + missing, limit_ns, status);
+  if (threadIdx.x == 0) passed[blockIdx.x] = ok ? 1u : 0u;
+}
+
 }  // namespace
 }  // namespace hpxgs
 
@@ -89,5 +96,30 @@ extern "C" int hpxgs_probe_alu_peak(double* fma_tflops, double* ex2_tops, hpxgs_
   const double per_thread = (double)kChains * kUnroll;
   *fma_tflops = 2.0 * per_thread * it_fma * (double)grid_fma * kProbeThreads / (ms_fma * 1e-3) / 1e12;
   *ex2_tops = per_thread * it_ex2 * (double)grid_ex2 * kProbeThreads / (ms_ex2 * 1e-3) / 1e12;
+  return HPXGS_OK;
+}
+
+extern "C" int hpxgs_probe_grid_barrier(int blocks, int missing, uint64_t limit_ns, uint32_t* counter,
+                                        uint32_t* passed, int32_t* status, hpxgs_stream_t stream) {
+  if (blocks < 1 || missing < 0 || limit_ns > 2000000000ull || !counter || !passed || !status)
+    return HPXGS_E_INVALID_ARG;
+  int dev = 0, coop = 0, per_sm = 0;
+  HPXGS_CUDA_CHECK(cudaGetDevice(&dev));
+  HPXGS_CUDA_CHECK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  HPXGS_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_barrier_probe, 128, 0));
+  if (!coop || blocks > per_sm * num_sms()) return HPXGS_E_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  HPXGS_CUDA_CHECK(cudaMemsetAsync(counter, 0, sizeof(uint32_t), s));
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)blocks);
+  lc.blockDim = dim3(128);
+  lc.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  HPXGS_CUDA_CHECK(cudaLaunchKernelEx(&lc, k_barrier_probe, counter, (uint32_t)missing, limit_ns, passed, status));
+  note_launches(1);
   return HPXGS_OK;
 }

@@ -455,6 +455,36 @@ static int radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, co
   return HPXGS_OK;
 }
 
+// Blocks of kernel fn (threads per block) that can be resident at once: the largest
+// grid of a cooperative launch (0 where the device has none).
+static int coop_capacity(const void* fn, int threads) {
+  int dev = 0, coop = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * num_sms();
+}
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_cooperative(void (*fn)(KArgs...), unsigned grid, unsigned threads, cudaStream_t s,
+                                      Args... args) {
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(grid);
+  lc.blockDim = dim3(threads);
+  lc.dynamicSmemBytes = 0;
+  lc.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, fn, args...);
+}
+// Wait limit of a grid barrier in these launches.
+constexpr uint64_t kGridWaitNs = 1000000000ull;   // 1 s
+
 // ----------------------------------------------------------------------------
 // Tile query (Algorithm 3 at the tile order) and exact membership:
 // tile t is listed for Gaussian g iff t has an in-mask pixel and
@@ -838,6 +868,57 @@ __global__ void __launch_bounds__(256) k_scan_apply(const uint32_t* __restrict__
     const uint64_t ex = block_exclusive_scan_u64(x, &tot);
     if (i < hi) off[i] = run + ex;
     run += tot;
+  }
+}
+
+// The three phases above as one cooperative launch of G resident blocks, a grid
+// barrier (on *bar, zero before the launch) between the chunk sums and their use.
+__global__ void __launch_bounds__(256) k_scan_coop(const uint32_t* __restrict__ c, int64_t n, uint64_t* part,
+                                                   uint64_t* __restrict__ off, uint32_t* counters,
+                                                   uint64_t* total_out, uint32_t* bar, int32_t* status) {
+  const int G = gridDim.x, b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t chunk = (n + G - 1) / G;
+  const int64_t lo = b * chunk, hi = min(n, lo + chunk);
+  __shared__ uint64_t ws[2][8];
+  uint64_t s = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += c[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) ws[0][warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < 8; ++w) t += ws[0][w];
+    part[b] = t;
+  }
+  if (!grid_barrier(bar, (uint32_t)G, kGridWaitNs, status)) return;
+  // this block's prefix and the total, from every block's chunk sum
+  uint64_t pre = 0, tot = 0;
+  for (int q = threadIdx.x; q < G; q += blockDim.x) {
+    const uint64_t x = __ldcg(reinterpret_cast<const unsigned long long*>(part) + q);
+    tot += x;
+    if (q < b) pre += x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    pre += __shfl_xor_sync(0xffffffffu, pre, o);
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+  }
+  if (lane == 0) { ws[0][warp] = pre; ws[1][warp] = tot; }
+  __syncthreads();
+  uint64_t run = 0, total = 0;
+  for (int w = 0; w < 8; ++w) { run += ws[0][w]; total += ws[1][w]; }
+  if (b == 0 && threadIdx.x == 0) {
+    part[G] = total;
+    counters[C_NPAIRS] = (uint32_t)(total > 0xffffffffull ? 0xffffffffull : total);
+    counters[C_NPAIRS_HI] = (uint32_t)(total >> 32);
+    if (total_out) *total_out = total;
+  }
+  for (int64_t t0 = lo; t0 < hi; t0 += blockDim.x) {
+    const int64_t i = t0 + threadIdx.x;
+    const uint64_t x = i < hi ? c[i] : 0;
+    uint64_t t;
+    const uint64_t ex = block_exclusive_scan_u64(x, &t);
+    if (i < hi) off[i] = run + ex;
+    run += t;
   }
 }
 
@@ -1797,10 +1878,18 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   prof_end(HPXGS_STAGE_TILE_COUNT, s);
   const int G = L.sort_blocks;
   prof_begin(HPXGS_STAGE_SCAN, s);
-  k_scan_part<<<G, 256, 0, s>>>(counts, PV, G, part);
-  k_scan_top<<<1, kMaxSortBlocks, 0, s>>>(part, G, counters, total_out);
-  k_scan_apply<<<G, 256, 0, s>>>(counts, PV, G, part, offsets);
-  note_launches(3);
+  static int scan_cap = -1;
+  if (scan_cap < 0) scan_cap = coop_capacity((const void*)k_scan_coop, 256);
+  if (G <= scan_cap) {
+    HPXGS_CUDA_CHECK(launch_cooperative(k_scan_coop, (unsigned)G, 256, s, (const uint32_t*)counts, (int64_t)PV, part,
+                                        offsets, counters, total_out, counters + C_GRID_BAR_SCAN, status));
+    note_launches(1);
+  } else {
+    k_scan_part<<<G, 256, 0, s>>>(counts, PV, G, part);
+    k_scan_top<<<1, kMaxSortBlocks, 0, s>>>(part, G, counters, total_out);
+    k_scan_apply<<<G, 256, 0, s>>>(counts, PV, G, part, offsets);
+    note_launches(3);
+  }
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_SCAN, s);
   return HPXGS_OK;
