@@ -319,7 +319,7 @@ int make_layout(int32_t P, const hpxgs_view* views, int nviews, const hpxgs_conf
   L->counters = take(4 * C_COUNT);
   L->accum = take(4 * HPXGS_NACC * pv);
   L->accum_d = take(4 * pv);                     // dL/d(1/r) of the inverse-depth channel
-  L->tile_order = take(4 * tiles);
+  L->unit_order = take(4 * 3 * 4 * (size_t)tiles);   // blend units: forward order, backward order, forward work
   L->total = o;
   return HPXGS_OK;
 }

@@ -81,7 +81,7 @@ constexpr int kRecFloat4 = 4;
 // Workspace layout of hpxgs_forward / hpxgs_backward. All offsets 256-aligned.
 struct Layout {
   size_t tile_flags, records, radii, stage, depth, key_a, key_b, val_a, val_b, counts, offsets, scan_part,
-         pair_key_a, pair_key_b, pair_val_a, pair_val_b, hist, ranges, counters, accum, accum_d, tile_order,
+         pair_key_a, pair_key_b, pair_val_a, pair_val_b, hist, ranges, counters, accum, accum_d, unit_order,
          total;
   int64_t P, PV, cap, total_tiles, total_pix;
   int sort_blocks;        // grid of the count scan
@@ -105,8 +105,13 @@ constexpr int kMaxSortBlocks = 1024;
 // counters block (u32 each)
 // (u64 counters live at u32 index 8 (n_eval) and 10 (n_contrib), 8-byte aligned)
 // C_GRID_BAR_SCAN: arrivals at the grid barrier of the count scan's cooperative launch.
-enum Counter { C_NPAIRS = 0, C_WORK_FWD = 1, C_WORK_BWD = 2, C_NSORT = 3, C_NPAIRS_HI = 4, C_STAGE = 5, C_NEVAL = 8, C_NCONTRIB = 10, C_SORT_TICKET = 12,
-               C_GRID_BAR_SCAN = 13, C_COUNT = 16 };
+// C_WORK_BWD, then C_UNITS_BWD: the backward blend's unit counter and its longest-first
+// order's class counts and cursors (zeroed together by the backward); C_UNITS_FWD: the
+// same for the forward blend (zeroed with the rest by the forward).
+constexpr int kUnitClasses = 129;
+enum Counter { C_NPAIRS = 0, C_WORK_FWD = 1, C_NSORT = 3, C_NPAIRS_HI = 4, C_STAGE = 5, C_NEVAL = 8, C_NCONTRIB = 10, C_SORT_TICKET = 12,
+               C_GRID_BAR_SCAN = 13, C_WORK_BWD = 16, C_UNITS_BWD = 17, C_UNITS_FWD = C_UNITS_BWD + 2 * kUnitClasses,
+               C_COUNT = C_UNITS_FWD + 2 * kUnitClasses };
 
 #ifdef __CUDACC__
 // Grid-wide barrier of a cooperative launch (every block resident at once). Each block

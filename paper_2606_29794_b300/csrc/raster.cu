@@ -1128,6 +1128,98 @@ __device__ __forceinline__ float cull_rho(const ViewParams& vp) { return vp.rho_
 __device__ __forceinline__ float cull_sqrt_cut(float cutoff) { return sqrtf(cutoff * (1.f + 1e-5f)) * (1.f + 1e-6f); }
 
 // ----------------------------------------------------------------------------
+// Longest-first order of the persistent blends' units. A blend block takes its next
+// unit from a counter; taken in index order, units with long lists that come late
+// keep a few blocks busy after the others have run out of work. Each unit gets an
+// estimate w of its work (MODE 0, the forward: its tile's list length, 0 for a tile
+// without an in-mask pixel; MODE 1, the backward: the time the forward blend spent on
+// the unit, in units of 256 SM clocks, which follows the pairs, cull and termination
+// that the backward's work follows too), a class by w (four per
+// octave, the largest first, w = 0 last), and the blend takes units class by class.
+// Inside a class the order is that of the atomics: the blends' outputs do not depend
+// on which block takes which unit.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ int unit_class(uint32_t w) {
+  if (w == 0) return kUnitClasses - 1;
+  const int lg = 31 - __clz(w);
+  const uint32_t sub = lg >= 2 ? (w >> (lg - 2)) & 3u : (w << (2 - lg)) & 3u;
+  return 127 - (4 * lg + (int)sub);
+}
+
+template <int MODE>
+__device__ __forceinline__ uint32_t unit_estimate(int u, int shift, const uint2* __restrict__ ranges,
+                                                  const uint32_t* __restrict__ flags, const uint32_t* __restrict__ work) {
+  if (MODE == 1) return work[u];
+  const int tile = u >> shift;
+  if (!(flags[tile] & 1u)) return 0u;
+  const uint2 r = ranges[tile];
+  return r.y > r.x ? r.y - r.x : 0u;
+}
+
+// cls[0 .. kUnitClasses): units per class (zero before the launch).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_unit_count(int nunits, int shift, const uint2* __restrict__ ranges,
+                                                    const uint32_t* __restrict__ flags,
+                                                    const uint32_t* __restrict__ work, uint32_t* cls) {
+  __shared__ uint32_t h[kUnitClasses];
+  for (int i = threadIdx.x; i < kUnitClasses; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < nunits) atomicAdd(&h[unit_class(unit_estimate<MODE>(u, shift, ranges, flags, work))], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kUnitClasses; i += blockDim.x)
+    if (h[i]) atomicAdd(&cls[i], h[i]);
+}
+
+// order[base(c) + k] = the k-th unit placed in class c; cls[kUnitClasses + c] is class c's
+// cursor (zero before the launch), base(c) the units of the classes before c.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_unit_place(int nunits, int shift, const uint2* __restrict__ ranges,
+                                                    const uint32_t* __restrict__ flags,
+                                                    const uint32_t* __restrict__ work, uint32_t* cls,
+                                                    uint32_t* __restrict__ order) {
+  __shared__ uint32_t base[kUnitClasses];
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {                          // exclusive scan of the class counts, 5 per lane
+    constexpr int PER = (kUnitClasses + 31) / 32;
+    uint32_t v[PER], t = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) { const int c = PER * lane + q; v[q] = c < kUnitClasses ? cls[c] : 0u; t += v[q]; }
+    uint32_t inc = t;
+    for (int o = 1; o < 32; o <<= 1) { const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o); if (lane >= o) inc += y; }
+    uint32_t run = inc - t;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) { const int c = PER * lane + q; if (c < kUnitClasses) base[c] = run; run += v[q]; }
+  }
+  __syncthreads();
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = u < nunits;
+  const int c = ok ? unit_class(unit_estimate<MODE>(u, shift, ranges, flags, work)) : -1;
+  const uint32_t peers = __match_any_sync(0xffffffffu, c);
+  const int leader = __ffs(peers) - 1;
+  uint32_t first = 0;
+  if (ok && lane == leader) first = atomicAdd(&cls[kUnitClasses + c], (uint32_t)__popc(peers));
+  first = __shfl_sync(0xffffffffu, first, leader);
+  if (ok) order[base[c] + first + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)u;
+}
+
+static int launch_unit_order(int mode, int nunits, int shift, const uint2* ranges, const uint32_t* flags,
+                             const uint32_t* work, uint32_t* cls, uint32_t* order, cudaStream_t s) {
+  if (nunits <= 0) return HPXGS_OK;
+  const unsigned nb = (unsigned)((nunits + 255) / 256);
+  if (mode == 0) {
+    k_unit_count<0><<<nb, 256, 0, s>>>(nunits, shift, ranges, flags, work, cls);
+    k_unit_place<0><<<nb, 256, 0, s>>>(nunits, shift, ranges, flags, work, cls, order);
+  } else {
+    k_unit_count<1><<<nb, 256, 0, s>>>(nunits, shift, ranges, flags, work, cls);
+    k_unit_place<1><<<nb, 256, 0, s>>>(nunits, shift, ranges, flags, work, cls, order);
+  }
+  note_launches(2);
+  HPXGS_LAUNCH_CHECK();
+  return HPXGS_OK;
+}
+
+// ----------------------------------------------------------------------------
 // Forward compositing: persistent blocks take tiles from a counter; one thread
 // per pixel (PPT pixels per thread for 1024-pixel tiles); Gaussian records of the
 // tile's list are staged through shared memory in batches of BATCH.
@@ -1147,6 +1239,7 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
                                                   float* __restrict__ maps, float* __restrict__ Tout,
                                                   uint32_t* __restrict__ lastout, uint32_t* work,
                                                   unsigned long long* __restrict__ evals, uint32_t* __restrict__ gmask,
+                                                  const uint32_t* __restrict__ order, uint32_t* __restrict__ unit_work,
                                                   const float* __restrict__ rdepth = nullptr,
                                                   float* __restrict__ dmap = nullptr) {
   constexpr int NW = NT / 32;
@@ -1162,10 +1255,21 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
   const int b = SPLIT ? vt.b - 1 : vt.b;            // order of a blend unit below k
   const int nunits = SPLIT ? 4 * vt.total_tiles : vt.total_tiles;
   const float sqrt_cut = cull_sqrt_cut(vt.cutoff);
+  int prev = -1;
+  long long t_unit = 0;                             // thread 0: SM clock when the current unit was taken
   for (;;) {
-    if (tid == 0) s_tile = (int)atomicAdd(work, 1u);
+    if (tid == 0) {                                  // the next unit, longest-first when an order is given
+      const uint32_t t = atomicAdd(work, 1u);
+      s_tile = (order && t < (uint32_t)nunits) ? (int)order[t] : (int)t;
+    }
     __syncthreads();
     const int unit = s_tile;
+    if (tid == 0 && unit_work) {                     // the previous unit's time, for the backward's order
+      const long long tn = clock64();
+      if (prev >= 0) unit_work[prev] = (uint32_t)max(1ll, (tn - t_unit) >> 8);
+      t_unit = tn;
+    }
+    prev = unit;
     __syncthreads();
     if (unit >= nunits) break;
     const int tile = SPLIT ? unit >> 2 : unit;       // SPLIT: unit = one quarter of a listed tile
@@ -1372,6 +1476,7 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
                                                   const float* __restrict__ dmaps, const float* __restrict__ Tin,
                                                   const uint32_t* __restrict__ lastin, float* __restrict__ accum,
                                                   uint32_t* work, const uint32_t* __restrict__ gmask,
+                                                  const uint32_t* __restrict__ order,
                                                   const float* __restrict__ rdepth,
                                                   const float* __restrict__ ddepth,
                                                   float* __restrict__ accum_d,
@@ -1393,7 +1498,11 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
   const int b = SPLIT ? vt.b - 1 : vt.b;            // order of a blend unit below k
   const int nunits = SPLIT ? 4 * vt.total_tiles : vt.total_tiles;
   for (;;) {
-    if (tid == 0) { s_tile = (int)atomicAdd(work, 1u); s_maxlast = 0; }
+    if (tid == 0) {                                  // the next unit, longest-first when an order is given
+      const uint32_t t = atomicAdd(work, 1u);
+      s_tile = (order && t < (uint32_t)nunits) ? (int)order[t] : (int)t;
+      s_maxlast = 0;
+    }
     __syncthreads();
     const int unit = s_tile;
     if (unit >= nunits) break;
@@ -2029,10 +2138,16 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
   const int b = cfg->tile_level;
   const bool split = b == 5 && cfg->blend_split;   // quarters of order-5 tiles as blend units
   const int bps = cfg->blocks_per_sm;
+  // blend units: [forward order | backward order | forward evaluations per unit], 4 x tiles each
+  uint32_t* uorder = at<uint32_t>(ws, L.unit_order);
+  const int64_t ustride = 4 * L.total_tiles;
   prof_begin(HPXGS_STAGE_BLEND_FWD, s);
+  rc = launch_unit_order(0, (int)(split ? 4 * L.total_tiles : L.total_tiles), split ? 2 : 0, ranges, flags, nullptr,
+                         counters + C_UNITS_FWD, uorder, s);
+  if (rc != HPXGS_OK) { delete vt; return rc; }
   {
     const int ppt = pick_ppt(b, cfg->fwd_ppt, true);
-#define FWD_BASE bps, s, *vt, (const float4*)rec, (const uint2*)ranges, ids, (const uint32_t*)flags, (const uint32_t*)mask, maps, T_final, last, work, evals, gmask
+#define FWD_BASE bps, s, *vt, (const float4*)rec, (const uint2*)ranges, ids, (const uint32_t*)flags, (const uint32_t*)mask, maps, T_final, last, work, evals, gmask, (const uint32_t*)uorder, uorder + 2 * ustride
 #define FWD_ARGS FWD_BASE, (const float*)nullptr, (float*)nullptr
 #define FWD_DEPTH_ARGS FWD_BASE, (const float*)at<float>(ws, L.depth), depth_map
     if (split) {                                   // order-5 lists, quarters blended in the order-4 shapes
@@ -2092,7 +2207,7 @@ static int backward_impl(const hpxgs_gaussians* g, const hpxgs_view* views, int 
   float* accum_d = at<float>(ws, L.accum_d);
   if (ddepth) HPXGS_CUDA_CHECK(cudaMemsetAsync(accum_d, 0, sizeof(float) * PV, s));
   const float* rdepth = at<float>(ws, L.depth);
-  HPXGS_CUDA_CHECK(cudaMemsetAsync(counters + C_WORK_BWD, 0, sizeof(uint32_t), s));
+  HPXGS_CUDA_CHECK(cudaMemsetAsync(counters + C_WORK_BWD, 0, sizeof(uint32_t) * (1 + 2 * kUnitClasses), s));
   const int passes = (L.pair_bits + 7) / 8;
   const uint32_t* ids = (passes & 1) ? at<uint32_t>(ws, L.pair_val_b) : at<uint32_t>(ws, L.pair_val_a);
   const uint32_t* gmask = (passes & 1) ? at<uint32_t>(ws, L.pair_key_a) : at<uint32_t>(ws, L.pair_key_b);
@@ -2104,11 +2219,16 @@ static int backward_impl(const hpxgs_gaussians* g, const hpxgs_view* views, int 
   const int b = cfg->tile_level;
   const bool split = b == 5 && cfg->blend_split;   // quarters of order-5 tiles as blend units
   const int bps = cfg->blocks_per_sm;
+  uint32_t* uorder = at<uint32_t>(ws, L.unit_order);
+  const int64_t ustride = 4 * L.total_tiles;
   prof_begin(HPXGS_STAGE_BLEND_BWD, s);
+  rc = launch_unit_order(1, (int)(split ? 4 * L.total_tiles : L.total_tiles), 0, ranges, flags, uorder + 2 * ustride,
+                         counters + C_UNITS_BWD, uorder + ustride, s);
+  if (rc != HPXGS_OK) { delete vt; return rc; }
   {
     // several pixels per thread: the per-entry warp reduction then covers 32 * PPT pixels
     const int ppt = pick_ppt(b, cfg->bwd_ppt, false);
-#define BWD_BASE bps, s, *vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, gmask
+#define BWD_BASE bps, s, *vt, rec, ranges, ids, flags, mask, dmaps, T_final, last, accum, work, gmask, (const uint32_t*)(uorder + ustride)
 #define BWD_ARGS BWD_BASE, (const float*)nullptr, (const float*)nullptr, (float*)nullptr, NoLossViews{0.f}
 #define BWD_DEPTH_ARGS BWD_BASE, rdepth, ddepth, accum_d, NoLossViews{0.f}
 #define BWD_LOSS_ARGS BWD_BASE, (const float*)nullptr, (const float*)nullptr, (float*)nullptr, *lv
