@@ -1435,23 +1435,25 @@ __device__ __forceinline__ bool bwd_pixel(const ViewTable& vt, const Pix& P, flo
   const float c = 1.f - 0.5f * P.n2;
   // dm/du_j / 2 = ser Qu_j + q (d ser / d u_j) / 2 = ser Qu_j + K u_j (K per branch below);
   // dm/dc / 2 = Lc per unit Lm (atan form only)
-  float K, Lc = 0.f;
+  // moving g by a tangent step delta: du_i = -c delta_i, dc = u . delta
   if (P.series) {
     const float s2 = P.s2;
     const float dser = 1.f / 3.f + s2 * (16.f / 45.f + s2 * (12.f / 35.f + s2 * (512.f / 1575.f)));
-    K = Lm * P.q * dser;
+    const float K = Lm * P.q * dser;
+    const float h1 = Ws * Qu1 + K * u1, h2 = Ws * Qu2 + K * u2;
+    acc[7] += -c * h1;
+    acc[8] += -c * h2;
   } else {
     const float s = sqrtf(P.s2);
     const float ratio = sqrtf(P.ser);
     const float th = ratio * s;
     const float kf = (c * s - th) / (P.s2 * s);     // d(theta/s)/du_j = kf u_j
-    K = Lm * P.q * ratio * kf;
-    Lc = -Lm * P.q * ratio;                          // d(theta/s)/dc = -1/s^2... times s: -1
+    const float K = Lm * P.q * ratio * kf;
+    const float Lc = -Lm * P.q * ratio;              // d(theta/s)/dc = -1/s^2... times s: -1
+    const float h1 = Ws * Qu1 + K * u1, h2 = Ws * Qu2 + K * u2;
+    acc[7] += -c * h1 + Lc * u1;
+    acc[8] += -c * h2 + Lc * u2;
   }
-  const float h1 = Ws * Qu1 + K * u1, h2 = Ws * Qu2 + K * u2;
-  // moving g by a tangent step delta: du_i = -c delta_i, dc = u . delta
-  acc[7] += -c * h1 + Lc * u1;
-  acc[8] += -c * h2 + Lc * u2;
   return true;
 }
 
