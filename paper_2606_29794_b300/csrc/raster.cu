@@ -1039,8 +1039,10 @@ struct Pix {
 // m of pixel p for the entry (r0, r1, r2, r3): tangent offset u, q(u), (theta/s)^2.
 // (A pixel past the Gaussian's reach gets m > cutoff; the blends' cull skips most of
 // them by groups of 32, so no per-pixel early exit is taken.)
-__device__ __forceinline__ void pixel_weight(const float3 p, const float4 r0, const float4 r1, const float4 r2,
-                                             const float4 r3, Pix& P) {
+// (pixel_offsets, then pixel_series or pixel_atan by P.series: the backward takes the branch
+// once for both the weight and its partials)
+__device__ __forceinline__ void pixel_offsets(const float3 p, const float4 r0, const float4 r1, const float4 r2,
+                                              const float4 r3, Pix& P) {
   // every rounding written out (fmaf, __fmul_rn), so that all launch shapes give the same bits
   const float dx = p.x - r0.x, dy = p.y - r0.y, dz = p.z - r0.z;
   P.n2 = fmaf(dz, dz, fmaf(dy, dy, __fmul_rn(dx, dx)));
@@ -1050,18 +1052,25 @@ __device__ __forceinline__ void pixel_weight(const float3 p, const float4 r0, co
   const float t = fmaf(r1.w, P.u1, __fmul_rn(2.f * r2.w, P.u2));
   P.q = fmaf(__fmul_rn(r3.w, P.u2), P.u2, __fmul_rn(P.u1, t));
   P.series = P.n2 < kSeriesN2;
-  if (P.series) {
-    const float s2 = P.s2;
-    P.ser = fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 128.f / 1575.f, 4.f / 35.f), 8.f / 45.f), 1.f / 3.f), 1.f);
-    P.m = __fmul_rn(P.q, P.ser);
-  } else {
-    const float c = fmaf(-0.5f, P.n2, 1.f);
-    if (P.s2 < 1e-24f) { P.ser = 0.f; P.m = (c < 0.f) ? 3.0e38f : 0.f; return; }
-    const float s = sqrtf(P.s2);
-    const float ratio = atan2f(s, c) / s;
-    P.ser = __fmul_rn(ratio, ratio);
-    P.m = __fmul_rn(P.q, P.ser);
-  }
+}
+__device__ __forceinline__ void pixel_series(Pix& P) {
+  const float s2 = P.s2;
+  P.ser = fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 128.f / 1575.f, 4.f / 35.f), 8.f / 45.f), 1.f / 3.f), 1.f);
+  P.m = __fmul_rn(P.q, P.ser);
+}
+__device__ __forceinline__ void pixel_atan(Pix& P) {
+  const float c = fmaf(-0.5f, P.n2, 1.f);
+  if (P.s2 < 1e-24f) { P.ser = 0.f; P.m = (c < 0.f) ? 3.0e38f : 0.f; return; }
+  const float s = sqrtf(P.s2);
+  const float ratio = atan2f(s, c) / s;
+  P.ser = __fmul_rn(ratio, ratio);
+  P.m = __fmul_rn(P.q, P.ser);
+}
+__device__ __forceinline__ void pixel_weight(const float3 p, const float4 r0, const float4 r1, const float4 r2,
+                                             const float4 r3, Pix& P) {
+  pixel_offsets(p, r0, r1, r2, r3, P);
+  if (P.series) pixel_series(P);
+  else pixel_atan(P);
 }
 
 // Cull of (entry, 32-pixel group) pairs, taken once per staged entry. A tile's
@@ -1399,7 +1408,7 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
 // is applied once per entry after the reduction), and the pixel's running T and B moved
 // in front of the entry. dD and invr: the depth channel's dL/dD and 1/r (DEPTH only).
 // Returns false when the entry does not reach the pixel (m > cutoff).
-template <bool DEPTH, int NA>
+template <bool DEPTH, int NA, bool SERIES>
 __device__ __forceinline__ bool bwd_pixel(const ViewTable& vt, const Pix& P, float4 r0, float4 r1, float4 r2,
                                           float4 r3, const float* dI, float dD, float invr, float& T, float& B,
                                           float* acc) {
@@ -1436,7 +1445,7 @@ __device__ __forceinline__ bool bwd_pixel(const ViewTable& vt, const Pix& P, flo
   // dm/du_j / 2 = ser Qu_j + q (d ser / d u_j) / 2 = ser Qu_j + K u_j (K per branch below);
   // dm/dc / 2 = Lc per unit Lm (atan form only)
   // moving g by a tangent step delta: du_i = -c delta_i, dc = u . delta
-  if (P.series) {
+  if constexpr (SERIES) {
     const float s2 = P.s2;
     const float dser = 1.f / 3.f + s2 * (16.f / 45.f + s2 * (12.f / 35.f + s2 * (512.f / 1575.f)));
     const float K = Lm * P.q * dser;
@@ -1596,10 +1605,17 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
           for (int q = 0; q < PPT; ++q) {
             if (j >= lastp[q] || !((gm >> (q * NW + warp)) & 1u)) continue;
             Pix P;
-            pixel_weight(pv[q], r0, r1, r2, r3, P);
-            if (bwd_pixel<DEPTH, NA>(vt, P, r0, r1, r2, r3, dI[q], DEPTH ? dDp[DEPTH ? q : 0] : 0.f,
-                                     DEPTH ? s_invr[e] : 0.f, T[q], B[q], acc))
-              any = true;
+            pixel_offsets(pv[q], r0, r1, r2, r3, P);
+            const float dDq = DEPTH ? dDp[DEPTH ? q : 0] : 0.f, invr = DEPTH ? s_invr[e] : 0.f;
+            bool hit;
+            if (P.series) {
+              pixel_series(P);
+              hit = bwd_pixel<DEPTH, NA, true>(vt, P, r0, r1, r2, r3, dI[q], dDq, invr, T[q], B[q], acc);
+            } else {
+              pixel_atan(P);
+              hit = bwd_pixel<DEPTH, NA, false>(vt, P, r0, r1, r2, r3, dI[q], dDq, invr, T[q], B[q], acc);
+            }
+            if (hit) any = true;
           }
           // reduction of the 9 partials over groups of RL lanes, then one shared-memory
           // slot per group (the block-level pass below adds the slots)
