@@ -1355,16 +1355,24 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
             bits &= bits - 1u;
             const float4 r0 = s_rec[e][0], r1 = s_rec[e][1], r2 = s_rec[e][2], r3 = s_rec[e][3];
             Pix P;
-            pixel_weight(pv[q], r0, r1, r2, r3, P);
-            if (P.m <= vt.cutoff) {
+            pixel_offsets(pv[q], r0, r1, r2, r3, P);
+            // compositing of a reaching entry; true when the pixel terminates
+            auto composite = [&]() -> bool {
+              if (!(P.m <= vt.cutoff)) return false;
               ++ncontrib;
               const float a = fminf(vt.alpha_max, __fmul_rn(r0.w, __expf(-0.5f * P.m)));
               const float w = __fmul_rn(a, T[q]);
               C[q][0] = fmaf(w, r3.x, C[q][0]); C[q][1] = fmaf(w, r3.y, C[q][1]); C[q][2] = fmaf(w, r3.z, C[q][2]);
               if (DEPTH) D[DEPTH ? q : 0] = fmaf(w, s_invr[e], D[DEPTH ? q : 0]);
               T[q] = __fmul_rn(T[q], 1.f - a);
-              if (T[q] < vt.eps_T) { done[q] = true; last[q] = bs + e + 1 - rg.x; break; }
-            }
+              if (T[q] < vt.eps_T) { done[q] = true; last[q] = bs + e + 1 - rg.x; return true; }
+              return false;
+            };
+            // one branch on the arc-length form, taken for the weight and the compositing together
+            bool term;
+            if (P.series) { pixel_series(P); term = composite(); }
+            else { pixel_atan(P); term = composite(); }
+            if (term) break;
           }
         }
       }
