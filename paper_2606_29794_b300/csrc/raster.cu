@@ -1039,6 +1039,15 @@ struct Pix {
 // m of pixel p for the entry (r0, r1, r2, r3): tangent offset u, q(u), (theta/s)^2.
 // (A pixel past the Gaussian's reach gets m > cutoff; the blends' cull skips most of
 // them by groups of 32, so no per-pixel early exit is taken.)
+// exp(-m / 2) of a reaching entry (m <= cutoff) as 2^(m * (-log2(e) / 2)) on the MUFU ex2
+// unit: one multiply and one ex2. Both blends take their Gaussian factor from this one
+// function, so the backward's alpha is the forward's bit for bit.
+__device__ __forceinline__ float exp_neg_half(float m) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(m * -0.72134752044448170368f));
+  return y;
+}
+
 // (pixel_offsets, then pixel_series or pixel_atan by P.series: the backward takes the branch
 // once for both the weight and its partials)
 __device__ __forceinline__ void pixel_offsets(const float3 p, const float4 r0, const float4 r1, const float4 r2,
@@ -1360,7 +1369,7 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
             auto composite = [&]() -> bool {
               if (!(P.m <= vt.cutoff)) return false;
               ++ncontrib;
-              const float a = fminf(vt.alpha_max, __fmul_rn(r0.w, __expf(-0.5f * P.m)));
+              const float a = fminf(vt.alpha_max, __fmul_rn(r0.w, exp_neg_half(P.m)));
               const float w = __fmul_rn(a, T[q]);
               C[q][0] = fmaf(w, r3.x, C[q][0]); C[q][1] = fmaf(w, r3.y, C[q][1]); C[q][2] = fmaf(w, r3.z, C[q][2]);
               if (DEPTH) D[DEPTH ? q : 0] = fmaf(w, s_invr[e], D[DEPTH ? q : 0]);
@@ -1421,7 +1430,7 @@ __device__ __forceinline__ bool bwd_pixel(const ViewTable& vt, const Pix& P, flo
                                           float4 r3, const float* dI, float dD, float invr, float& T, float& B,
                                           float* acc) {
   if (!(P.m <= vt.cutoff)) return false;
-  const float G = __expf(-0.5f * P.m);
+  const float G = exp_neg_half(P.m);
   const float og = r0.w * G;
   const float a = fminf(vt.alpha_max, og);
   const float inv1ma = __fdividef(1.f, 1.f - a);
