@@ -1433,7 +1433,8 @@ __device__ __forceinline__ bool bwd_pixel(const ViewTable& vt, const Pix& P, flo
   const float G = exp_neg_half(P.m);
   const float og = r0.w * G;
   const float a = fminf(vt.alpha_max, og);
-  const float inv1ma = __fdividef(1.f, 1.f - a);
+  float inv1ma;                                     // 1 / (1 - a) on the MUFU reciprocal
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv1ma) : "f"(1.f - a));
   const float Tj = T * inv1ma;
   const float wj = Tj * a;
   // A = dL/dI . colour (+ dL/dD / r); dL/da = T_j A - B / (1 - a); then B takes this entry
