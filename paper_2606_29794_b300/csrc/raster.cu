@@ -1127,9 +1127,10 @@ __device__ __forceinline__ uint32_t live_groups(const float4 r0, const float4 r1
 
 // Resident blocks per SM the blend kernels ask of the register allocator: the
 // group guards of the cull would otherwise grow the one- and four-pixel shapes
-// (40 and 96 registers without them) and cost them resident warps.
+// and cost them resident warps (forward 48 registers, 5 blocks of 256 threads, measured
+// faster than 40 with its spills; backward 96, 10 blocks of 64 threads).
 #ifndef HPXGS_FWD_REGS
-#define HPXGS_FWD_REGS 40
+#define HPXGS_FWD_REGS 48
 #endif
 constexpr int fwd_min_blocks(int nt, int ppt, bool depth) { return (ppt == 1 && nt >= 128 && !depth) ? 65536 / (nt * HPXGS_FWD_REGS) : 1; }
 #ifndef HPXGS_BWD_REGS
