@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_fwd(int k, const float* __r
       ssim_coefs(st, t, W.iZ, coef + 9 * (size_t)p + 3 * ch);
       l1 += fabsf(I[3 * (size_t)p + ch] - Gt[3 * (size_t)p + ch]);
     }
-    h = hs / 3.f;
+    h = hs * (1.f / 3.f);
     cnt = 1u;
   }
   block_partials(h, l1, cnt, part, blockIdx.x);
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kHThreads) k_hssim_fwd_t(int k, const float* _
       ssim_coefs(st, t, iZ, coef + 9 * (size_t)p + 3 * ch);
       l1 += fabsf(I[3 * (size_t)p + ch] - Gt[3 * (size_t)p + ch]);
     }
-    h = hs / 3.f;
+    h = hs * (1.f / 3.f);
     cnt = 1u;
   }
   block_partials(h, l1, cnt, part, blk);
