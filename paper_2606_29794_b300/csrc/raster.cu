@@ -1097,10 +1097,13 @@ __device__ __forceinline__ void pixel_weight(const float3 p, const float4 r0, co
 // A sub-tile whose centre violates that bound (with q(u_c) lowered by its own
 // rounding bound and the right side raised by 1e-5) holds no contributing pixel
 // in this kernel's own arithmetic, so skipping it leaves every output bit-identical.
-// Returns bit g set when sub-tile 2g or 2g+1 may hold a contributing pixel.
+// Returns bit g set when sub-tile 2g or 2g+1 may hold a contributing pixel. The two
+// sub-tiles of a group are tested side by side on the packed FP32 pipe (FFMA2 and FMUL2,
+// each half rounded like the scalar operation): sub holds their centres as pairs,
+// sub[3 g + {0, 1, 2}] = (x, y, z) of sub-tiles (2g, 2g + 1).
 template <int NS>
 __device__ __forceinline__ uint32_t live_groups(const float4 r0, const float4 r1, const float4 r2, const float4 r3,
-                                               const float3* __restrict__ sub, float rho_p, float sqrt_cut) {
+                                               const float2* __restrict__ sub, float rho_p, float sqrt_cut) {
   const float A = r1.w, B = r2.w, C = r3.w;
   const float h = 0.5f * (A - C);
   const float lmax = (0.5f * (A + C) + sqrtf(h * h + B * B)) * (1.f + 1e-5f);
@@ -1110,17 +1113,26 @@ __device__ __forceinline__ uint32_t live_groups(const float4 r0, const float4 r1
   // u_c = p_c . e - g . e (g . e ~ 0): three FMAs per component, within 4e-7 of (p_c - g) . e
   const float gE1 = r0.x * r1.x + r0.y * r1.y + r0.z * r1.z;
   const float gE2 = r0.x * r2.x + r0.y * r2.y + r0.z * r2.z;
+  const float2 e1x = make_float2(r1.x, r1.x), e1y = make_float2(r1.y, r1.y), e1z = make_float2(r1.z, r1.z);
+  const float2 e2x = make_float2(r2.x, r2.x), e2y = make_float2(r2.y, r2.y), e2z = make_float2(r2.z, r2.z);
+  const float2 m1 = make_float2(-gE1, -gE1), m2 = make_float2(-gE2, -gE2);
+  const float2 AA = make_float2(A, A), B2 = make_float2(2.f * B, 2.f * B), CC = make_float2(C, C);
+  const float2 C0 = make_float2(c0, c0), C1 = make_float2(c1, c1), NG = make_float2(-gM, -gM);
+  const float2 K = make_float2(1.f + 1e-5f, 1.f + 1e-5f);
   uint32_t live = 0;
-#pragma unroll 2
-  for (int t = 0; t < NS; ++t) {
-    const float3 pc = sub[t];
-    const float u1 = fmaf(pc.z, r1.z, fmaf(pc.y, r1.y, fmaf(pc.x, r1.x, -gE1)));
-    const float u2 = fmaf(pc.z, r2.z, fmaf(pc.y, r2.y, fmaf(pc.x, r2.x, -gE2)));
-    const float s2 = u1 * u1 + u2 * u2;
-    const float q = u1 * (A * u1 + 2.f * B * u2) + C * u2 * u2;
-    const float rhs = c0 + c1 * s2;
-    const bool cull = q - gM * s2 > rhs * rhs * (1.f + 1e-5f);   // false for NaN: kept
-    live |= (cull ? 0u : 1u) << (t >> 1);
+#pragma unroll
+  for (int g = 0; g < NS / 2; ++g) {
+    const float2 x = sub[3 * g], y = sub[3 * g + 1], z = sub[3 * g + 2];
+    const float2 u1 = __ffma2_rn(z, e1z, __ffma2_rn(y, e1y, __ffma2_rn(x, e1x, m1)));
+    const float2 u2 = __ffma2_rn(z, e2z, __ffma2_rn(y, e2y, __ffma2_rn(x, e2x, m2)));
+    const float2 s2 = __ffma2_rn(u2, u2, __fmul2_rn(u1, u1));
+    const float2 t = __ffma2_rn(B2, u2, __fmul2_rn(AA, u1));
+    const float2 q = __ffma2_rn(__fmul2_rn(CC, u2), u2, __fmul2_rn(u1, t));
+    const float2 rhs = __ffma2_rn(C1, s2, C0);
+    const float2 lhs = __ffma2_rn(NG, s2, q);       // q - gM |u|^2
+    const float2 rr = __fmul2_rn(__fmul2_rn(rhs, rhs), K);
+    const bool cull = lhs.x > rr.x && lhs.y > rr.y; // false for NaN: kept
+    live |= (cull ? 0u : 1u) << g;
   }
   return live;
 }
@@ -1140,8 +1152,13 @@ constexpr int bwd_min_blocks(int nt, int ppt, bool depth) { return (ppt <= 4 && 
 
 // Sub-tile centres of a tile (order k - 2 pixels) and the cull's per-view constants.
 template <int NS>
-__device__ __forceinline__ void sub_centres(const ViewParams& vp, uint32_t lt, int b, float3* sub, int tid, int nt) {
-  for (int t = tid; t < NS; t += nt) sub[t] = pix2vec_f32(vp.k - 2, (lt << (2 * (b - 2))) + (uint32_t)t);
+__device__ __forceinline__ void sub_centres(const ViewParams& vp, uint32_t lt, int b, float2* sub, int tid, int nt) {
+  // pairs of sub-tiles (2g, 2g + 1) as sub[3 g + {0, 1, 2}] = their x, y, z
+  for (int t = tid; t < NS; t += nt) {
+    const float3 c = pix2vec_f32(vp.k - 2, (lt << (2 * (b - 2))) + (uint32_t)t);
+    float* f = reinterpret_cast<float*>(sub + 3 * (t >> 1)) + (t & 1);
+    f[0] = c.x; f[2] = c.y; f[4] = c.z;
+  }
 }
 __device__ __forceinline__ float cull_rho(const ViewParams& vp) { return vp.rho_sub32 * (1.f + 1e-5f) + 4e-6f; }
 __device__ __forceinline__ float cull_sqrt_cut(float cutoff) { return sqrtf(cutoff * (1.f + 1e-5f)) * (1.f + 1e-6f); }
@@ -1268,7 +1285,7 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
   constexpr int NG = NS / 2;                        // 32-pixel groups per tile
   constexpr int BW = BATCH / 32;                    // bitmap words per batch
   __shared__ uint32_t s_live[NG][BW];               // per group: the staged entries it may take
-  __shared__ float3 s_sub[NS];
+  __shared__ float2 s_sub[3 * (NS / 2)];
   __shared__ int s_tile;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int b = SPLIT ? vt.b - 1 : vt.b;            // order of a blend unit below k
