@@ -1032,7 +1032,7 @@ __global__ void __launch_bounds__(256) k_tiles_nested(const __grid_constant__ Vi
 constexpr float kSeriesN2 = 0.04f;      // |delta|^2 below which the series is used (theta < 0.2)
 
 struct Pix {
-  float u1, u2, n2, s2, q, ser, m;
+  float u1, u2, n2, s2, q, ser, m, Qu1, Qu2;   // Qu = conic u, q = u . Qu
   bool series;
 };
 
@@ -1058,8 +1058,9 @@ __device__ __forceinline__ void pixel_offsets(const float3 p, const float4 r0, c
   P.u1 = fmaf(dz, r1.z, fmaf(dy, r1.y, __fmul_rn(dx, r1.x)));
   P.u2 = fmaf(dz, r2.z, fmaf(dy, r2.y, __fmul_rn(dx, r2.x)));
   P.s2 = fmaf(P.u2, P.u2, __fmul_rn(P.u1, P.u1));
-  const float t = fmaf(r1.w, P.u1, __fmul_rn(2.f * r2.w, P.u2));
-  P.q = fmaf(__fmul_rn(r3.w, P.u2), P.u2, __fmul_rn(P.u1, t));
+  P.Qu1 = fmaf(r2.w, P.u2, __fmul_rn(r1.w, P.u1));
+  P.Qu2 = fmaf(r3.w, P.u2, __fmul_rn(r2.w, P.u1));
+  P.q = fmaf(P.u2, P.Qu2, __fmul_rn(P.u1, P.Qu1));
   P.series = P.n2 < kSeriesN2;
 }
 __device__ __forceinline__ void pixel_series(Pix& P) {
@@ -1439,10 +1440,17 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
 
 // Backward of one (pixel, entry) on the scalar path. From m (P) and the pixel's running
 // transmittance T behind the entry: alpha, T in front of it (T_j = T / (1 - a)), the
-// entry's partials added to acc (acc[5], acc[7] and acc[8] at half weight: the factor 2
-// is applied once per entry after the reduction), and the pixel's running T and B moved
-// in front of the entry. dD and invr: the depth channel's dL/dD and 1/r (DEPTH only).
+// entry's partials added to acc, and the pixel's running T and B moved in front of the
+// entry. acc[4 .. 8] hold their partials times -2 / dL/dm's -1/2 left out, and acc[5],
+// acc[7], acc[8] at half weight on top: kPartScale applies both once per entry after the
+// reduction. dD and invr: the depth channel's dL/dD and 1/r (DEPTH only).
 // Returns false when the entry does not reach the pixel (m > cutoff).
+// Per-entry factor of each backward partial (see bwd_pixel): 1 for the colour, opacity
+// and depth partials, -1/2 for acc[4], acc[6], and -1 (-1/2 times 2) for acc[5], acc[7], acc[8].
+__host__ __device__ constexpr float kPartScale(int c) {
+  return (c == 4 || c == 6) ? -0.5f : ((c == 5 || c == 7 || c == 8) ? -1.f : 1.f);
+}
+
 template <bool DEPTH, int NA, bool SERIES>
 __device__ __forceinline__ bool bwd_pixel(const ViewTable& vt, const Pix& P, float4 r0, float4 r1, float4 r2,
                                           float4 r3, const float* dI, float dD, float invr, float& T, float& B,
@@ -1468,15 +1476,15 @@ __device__ __forceinline__ bool bwd_pixel(const ViewTable& vt, const Pix& P, flo
   T = Tj;
   if (og >= vt.alpha_max) return true;          // clamped: no gradient to o, m
   acc[3] += dLda * G;
-  // dL/dm = Lm = -dLda o G / 2; m = q(u) ser with ser = (theta/s)^2
-  const float Lm = -0.5f * dLda * og;
+  // dL/dm = -Lm / 2 with Lm = dLda o G (the -1/2 goes with kPartScale); m = q(u) ser, ser = (theta/s)^2
+  const float Lm = dLda * og;
   const float u1 = P.u1, u2 = P.u2;
   const float Ws = Lm * P.ser;
   const float t1 = Ws * u1;
   acc[4] += t1 * u1;
   acc[5] += t1 * u2;
   acc[6] += Ws * u2 * u2;
-  const float Qu1 = r1.w * u1 + r2.w * u2, Qu2 = r2.w * u1 + r3.w * u2;
+  const float Qu1 = P.Qu1, Qu2 = P.Qu2;
   const float c = 1.f - 0.5f * P.n2;
   // dm/du_j / 2 = ser Qu_j + q (d ser / d u_j) / 2 = ser Qu_j + K u_j (K per branch below);
   // dm/dc / 2 = Lc per unit Lm (atan form only)
@@ -1667,8 +1675,7 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
           }
           if ((lane & (RL - 1)) == 0) {
 #pragma unroll
-            for (int c = 0; c < NA; ++c)
-              s_part[e][warp][lane / RL][c] = ball ? ((c == 5 || c == 7 || c == 8) ? 2.f * acc[c] : acc[c]) : 0.f;
+            for (int c = 0; c < NA; ++c) s_part[e][warp][lane / RL][c] = ball ? kPartScale(c) * acc[c] : 0.f;
           }
         }
       }
