@@ -74,15 +74,20 @@ const Fork* fork_of(cudaStream_t s) {
   for (int i = 0; i < g_nforks; ++i)
     if (g_forks[i].origin == s && g_fork_dev[i] == dev) return &g_forks[i];
   if (g_nforks == kMaxForks) return nullptr;
-  Fork f{s, nullptr, nullptr, nullptr};
+  Fork f{s, nullptr, nullptr, nullptr, nullptr, nullptr, {nullptr, nullptr}};
   cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
   if (cudaThreadExchangeStreamCaptureMode(&mode) != cudaSuccess) return nullptr;
-  bool ok = cudaStreamCreateWithFlags(&f.side, cudaStreamNonBlocking) == cudaSuccess;
-  ok = ok && cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) == cudaSuccess;
-  ok = ok && cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming) == cudaSuccess;
+  int prio = 0, least = 0, greatest = 0;
+  bool ok = cudaStreamGetPriority(s, &prio) == cudaSuccess &&
+            cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithPriority(&f.side, cudaStreamNonBlocking, prio) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithPriority(&f.side_hi, cudaStreamNonBlocking, greatest) == cudaSuccess;
+  cudaEvent_t* evs[5] = {&f.fork, &f.join, &f.join_hi, &f.mid[0], &f.mid[1]};
+  for (cudaEvent_t* e : evs) ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
-    if (f.join) cudaEventDestroy(f.join);
-    if (f.fork) cudaEventDestroy(f.fork);
+    for (cudaEvent_t* e : evs)
+      if (*e) cudaEventDestroy(*e);
+    if (f.side_hi) cudaStreamDestroy(f.side_hi);
     if (f.side) cudaStreamDestroy(f.side);
   }
   cudaThreadExchangeStreamCaptureMode(&mode);

@@ -171,13 +171,15 @@ int make_table(const hpxgs_gaussians* g, int P, const hpxgs_view* views, int nvi
                cudaStream_t stream, bool need_rho, ViewTable* vt);
 int num_sms();
 void hssim_bind(int k, const void* table, const void* ws, LossView* out);
-// A helper stream for work that does not depend on what precedes it on `origin`:
-// record `fork` on origin, make `side` wait for it, launch on side, record `join`
-// on side and make origin wait for it (in stream capture this forks and joins the
-// graph). Null when none can be made; the caller then runs that work on origin.
+// Helper streams for work that does not depend on what precedes it on `origin`:
+// record `fork` on origin, make a helper wait for it, launch there, record an event
+// on the helper and make origin wait for it (in stream capture this forks and joins
+// the graph). `side` has origin's priority, `side_hi` the device's highest, for short
+// latency-bound chains that must not wait behind a grid filling the GPU. Null when
+// none can be made; the caller then runs that work on origin.
 struct Fork {
-  cudaStream_t origin, side;
-  cudaEvent_t fork, join;
+  cudaStream_t origin, side, side_hi;
+  cudaEvent_t fork, join, join_hi, mid[2];   // mid: two more events for a caller's intermediate joins
 };
 const Fork* fork_of(cudaStream_t origin);
 

@@ -638,15 +638,18 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
   for (int64_t jb = (blockIdx.x * wpb + wib) * (int64_t)kTilesBatch; jb < PV; jb += nwarps * kTilesBatch) {
     bool vl = false;
     if (lane < kTilesBatch && jb + lane < PV) {
+      // count pass: jl is the Gaussian itself (no depth order needed: it runs beside the depth
+      // sort); emit pass: its depth-sorted position
       const int64_t jl = jb + lane;
-      if (skeys[jl] == 0xffffffffu) {
+      const bool listed = EMIT ? skeys[jl] != 0xffffffffu : radii[jl] > 0.f;
+      if (!listed) {
         if (!EMIT) counts[jl] = 0;
       } else {
         vl = true;
         TileSet& ts = s_set[wib][lane];
-        ts.gid = svals[jl];
-        ts.slot = EMIT ? stage[jl] : 0xffffffffu;
-        if (EMIT) { ts.n = counts[jl]; ts.base = offsets[jl]; }
+        ts.gid = EMIT ? svals[jl] : (uint32_t)jl;
+        ts.slot = EMIT ? stage[ts.gid] : 0xffffffffu;
+        if (EMIT) { ts.n = counts[ts.gid]; ts.base = offsets[jl]; }
         if (!EMIT || ts.slot == 0xffffffffu) {
           const ViewParams& vpl = vt.v[ts.gid / (uint32_t)vt.P];
           const float4 r0 = rec[4 * (int64_t)ts.gid];
@@ -795,7 +798,7 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
         slot = 0u;
       }
       __syncwarp();
-      if (lane == 0) { counts[j] = cnt; stage[j] = slot; }
+      if (lane == 0) { counts[gid] = cnt; stage[gid] = slot; }
     }
     }
     __syncwarp();                                    // the table is refilled by the next batch
@@ -824,11 +827,13 @@ __device__ __forceinline__ uint64_t block_exclusive_scan_u64(uint64_t x, uint64_
   return res;
 }
 
-__global__ void __launch_bounds__(256) k_scan_part(const uint32_t* __restrict__ c, int64_t n, int G, uint64_t* part) {
+// The counts are per Gaussian; the scan takes them in depth order, c[perm[i]].
+__global__ void __launch_bounds__(256) k_scan_part(const uint32_t* __restrict__ c, const uint32_t* __restrict__ perm,
+                                                   int64_t n, int G, uint64_t* part) {
   const int64_t chunk = (n + G - 1) / G;
   const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
   uint64_t s = 0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += c[i];
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += c[perm[i]];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   __shared__ uint64_t ws[8];
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
@@ -856,14 +861,15 @@ __global__ void __launch_bounds__(kMaxSortBlocks) k_scan_top(uint64_t* part, int
   }
 }
 
-__global__ void __launch_bounds__(256) k_scan_apply(const uint32_t* __restrict__ c, int64_t n, int G,
-                                                    const uint64_t* __restrict__ part, uint64_t* __restrict__ off) {
+__global__ void __launch_bounds__(256) k_scan_apply(const uint32_t* __restrict__ c, const uint32_t* __restrict__ perm,
+                                                    int64_t n, int G, const uint64_t* __restrict__ part,
+                                                    uint64_t* __restrict__ off) {
   const int64_t chunk = (n + G - 1) / G;
   const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
   uint64_t run = part[blockIdx.x];
   for (int64_t t0 = lo; t0 < hi; t0 += blockDim.x) {
     const int64_t i = t0 + threadIdx.x;
-    const uint64_t x = i < hi ? c[i] : 0;
+    const uint64_t x = i < hi ? c[perm[i]] : 0;
     uint64_t tot;
     const uint64_t ex = block_exclusive_scan_u64(x, &tot);
     if (i < hi) off[i] = run + ex;
@@ -873,7 +879,8 @@ __global__ void __launch_bounds__(256) k_scan_apply(const uint32_t* __restrict__
 
 // The three phases above as one cooperative launch of G resident blocks, a grid
 // barrier (on *bar, zero before the launch) between the chunk sums and their use.
-__global__ void __launch_bounds__(256) k_scan_coop(const uint32_t* __restrict__ c, int64_t n, uint64_t* part,
+__global__ void __launch_bounds__(256) k_scan_coop(const uint32_t* __restrict__ c, const uint32_t* __restrict__ perm,
+                                                   int64_t n, uint64_t* part,
                                                    uint64_t* __restrict__ off, uint32_t* counters,
                                                    uint64_t* total_out, uint32_t* bar, int32_t* status) {
   const int G = gridDim.x, b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -881,7 +888,7 @@ __global__ void __launch_bounds__(256) k_scan_coop(const uint32_t* __restrict__ 
   const int64_t lo = b * chunk, hi = min(n, lo + chunk);
   __shared__ uint64_t ws[2][8];
   uint64_t s = 0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += c[i];
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += c[perm[i]];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) ws[0][warp] = s;
   __syncthreads();
@@ -914,7 +921,7 @@ __global__ void __launch_bounds__(256) k_scan_coop(const uint32_t* __restrict__ 
   }
   for (int64_t t0 = lo; t0 < hi; t0 += blockDim.x) {
     const int64_t i = t0 + threadIdx.x;
-    const uint64_t x = i < hi ? c[i] : 0;
+    const uint64_t x = i < hi ? c[perm[i]] : 0;
     uint64_t t;
     const uint64_t ex = block_exclusive_scan_u64(x, &t);
     if (i < hi) off[i] = run + ex;
@@ -971,8 +978,10 @@ __global__ void __launch_bounds__(256) k_tiles_nested(const __grid_constant__ Vi
                                                       uint64_t cap, int32_t* status) {
   const int64_t PV = (int64_t)vt.P * vt.nviews;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < PV; j += (int64_t)gridDim.x * blockDim.x) {
-    if (skeys[j] == 0xffffffffu) { if (!EMIT) counts[j] = 0; continue; }
-    const uint32_t gid = svals[j];
+    // count pass: j is the Gaussian itself; emit pass: its depth-sorted position
+    const bool listed = EMIT ? skeys[j] != 0xffffffffu : radii[j] > 0.f;
+    if (!listed) { if (!EMIT) counts[j] = 0; continue; }
+    const uint32_t gid = EMIT ? svals[j] : (uint32_t)j;
     const ViewParams& vp = vt.v[gid / (uint32_t)vt.P];
     const int kt = vp.k - vt.b, kmax = kt + vt.log2f;
     const float4 r0 = rec[4 * (int64_t)gid];
@@ -1013,7 +1022,7 @@ __global__ void __launch_bounds__(256) k_tiles_nested(const __grid_constant__ Vi
       }
       ++cnt;
     }
-    if (!EMIT) counts[j] = cnt;
+    if (!EMIT) counts[gid] = cnt;
     else if (base + cnt > cap && status) atomicOr(status, HPXGS_F_CAPACITY);
   }
 }
@@ -1888,7 +1897,7 @@ __global__ void __launch_bounds__(256) k_density_stats(int64_t PV, int P, const 
   if (j >= PV) return;
   const uint32_t gid = svals[j];
   // visible: listed for at least one active tile of its view
-  const bool vis = skeys[j] != 0xffffffffu && counts[j] > 0u;
+  const bool vis = skeys[j] != 0xffffffffu && counts[gid] > 0u;
   float dw = 0.f, dp = 0.f;
   if (vis) {
     const float rs = radii[gid];
@@ -1968,9 +1977,12 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   uint32_t* flags = at<uint32_t>(ws, L.tile_flags);
   uint32_t* counters = at<uint32_t>(ws, L.counters);
   HPXGS_CUDA_CHECK(cudaMemsetAsync(counters, 0, sizeof(uint32_t) * C_COUNT, s));
-  // FoV masks (kept in the workspace: the backward reads them) and tile flags. They depend
-  // only on the cameras, the preprocess and the depth sort only on the Gaussians: the masks
-  // run on a helper stream, in the SMs the depth sort leaves idle, joined before the query.
+  // Three chains meet at the scan: the FoV masks and tile flags (kept in the workspace: the
+  // backward reads them) depend only on the cameras; the depth sort only on the preprocess;
+  // the tile count pass on the preprocess and the flags, not on the depth order (it counts
+  // per Gaussian). The masks run on a helper stream and the depth sort on a high-priority
+  // one (its short kernels would otherwise wait behind the count pass's blocks); the count
+  // pass waits for the masks, the scan for the sort.
   const Fork* fk = fork_of(s);
   cudaStream_t ms = s;
   if (fk) {
@@ -1983,10 +1995,16 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   for (int v = 0; v < nviews && rc == HPXGS_OK; ++v)
     rc = launch_mask(vt->v[v], cfg->tile_level, mask_out + (vt->v[v].pix_base >> 5), flags + vt->v[v].tile_base, ms);
   prof_end(HPXGS_STAGE_MASK, ms);
-  auto join = [&]() -> int {
+  if (fk) HPXGS_CUDA_CHECK(cudaEventRecord(fk->mid[0], fk->side));    // masks and flags done
+  bool sorting = false;                            // the depth sort was enqueued on side_hi
+  auto join = [&]() -> int {                      // s waits for all the helper streams hold
     if (fk) {
       HPXGS_CUDA_CHECK(cudaEventRecord(fk->join, fk->side));
       HPXGS_CUDA_CHECK(cudaStreamWaitEvent(s, fk->join, 0));
+      if (sorting) {
+        HPXGS_CUDA_CHECK(cudaEventRecord(fk->join_hi, fk->side_hi));
+        HPXGS_CUDA_CHECK(cudaStreamWaitEvent(s, fk->join_hi, 0));
+      }
       fk = nullptr;
     }
     return HPXGS_OK;
@@ -2013,14 +2031,21 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_PREPROCESS, s);
-  prof_begin(HPXGS_STAGE_DEPTH_SORT, s);
+  cudaStream_t ss = s;                             // the depth sort's stream
+  if (fk) {                                        // the depth sort follows the preprocess on side_hi
+    HPXGS_CUDA_CHECK(cudaEventRecord(fk->mid[1], s));
+    HPXGS_CUDA_CHECK(cudaStreamWaitEvent(fk->side_hi, fk->mid[1], 0));
+    ss = fk->side_hi;
+    sorting = true;
+  }
+  prof_begin(HPXGS_STAGE_DEPTH_SORT, ss);
   // a grid sized to the element count (HPXGS_DSORT_TPB tiles of 4096 per block, at most kMaxSortBlocks)
   const int Gd = (int)std::max<int64_t>(1, std::min<int64_t>(kMaxSortBlocks, (PV + HPXGS_DSORT_TPB * kSortTile - 1) / (HPXGS_DSORT_TPB * kSortTile)));
-  rc = radix_sort(ka, va, kb, vb, nullptr, (uint32_t)PV, 32, at<uint32_t>(ws, L.hist), Gd, counters + C_SORT_TICKET, s, which_depth);
+  rc = radix_sort(ka, va, kb, vb, nullptr, (uint32_t)PV, 32, at<uint32_t>(ws, L.hist), Gd, counters + C_SORT_TICKET, ss,
+                  which_depth);
   if (rc != HPXGS_OK) { join(); return rc; }
-  prof_end(HPXGS_STAGE_DEPTH_SORT, s);
-  rc = join();                                     // the query reads the tile flags
-  if (rc != HPXGS_OK) return rc;
+  prof_end(HPXGS_STAGE_DEPTH_SORT, ss);
+  if (fk) HPXGS_CUDA_CHECK(cudaStreamWaitEvent(s, fk->mid[0], 0));      // the count pass reads the tile flags
   const uint32_t* sk = *which_depth ? kb : ka;
   const uint32_t* sv = *which_depth ? vb : va;
   uint32_t* counts = at<uint32_t>(ws, L.counts);
@@ -2046,18 +2071,20 @@ static int front_half(const hpxgs_gaussians* g, const hpxgs_view* views, int nvi
   note_launches(1);
   HPXGS_LAUNCH_CHECK();
   prof_end(HPXGS_STAGE_TILE_COUNT, s);
+  rc = join();                                     // the scan takes the counts in depth order
+  if (rc != HPXGS_OK) return rc;
   const int G = L.sort_blocks;
   prof_begin(HPXGS_STAGE_SCAN, s);
   static int scan_cap = -1;
   if (scan_cap < 0) scan_cap = coop_capacity((const void*)k_scan_coop, 256);
   if (G <= scan_cap) {
-    HPXGS_CUDA_CHECK(launch_cooperative(k_scan_coop, (unsigned)G, 256, s, (const uint32_t*)counts, (int64_t)PV, part,
-                                        offsets, counters, total_out, counters + C_GRID_BAR_SCAN, status));
+    HPXGS_CUDA_CHECK(launch_cooperative(k_scan_coop, (unsigned)G, 256, s, (const uint32_t*)counts, sv, (int64_t)PV,
+                                        part, offsets, counters, total_out, counters + C_GRID_BAR_SCAN, status));
     note_launches(1);
   } else {
-    k_scan_part<<<G, 256, 0, s>>>(counts, PV, G, part);
+    k_scan_part<<<G, 256, 0, s>>>(counts, sv, PV, G, part);
     k_scan_top<<<1, kMaxSortBlocks, 0, s>>>(part, G, counters, total_out);
-    k_scan_apply<<<G, 256, 0, s>>>(counts, PV, G, part, offsets);
+    k_scan_apply<<<G, 256, 0, s>>>(counts, sv, PV, G, part, offsets);
     note_launches(3);
   }
   HPXGS_LAUNCH_CHECK();
