@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(256) k_scan_digit_rows(uint32_t* __restrict__ 
 // the tile sorted by digit; the tile is reordered in shared memory and written
 // out so that elements of one digit go to consecutive addresses (full sectors).
 #ifndef HPXGS_SCATTER_MINB
-#define HPXGS_SCATTER_MINB 4
+#define HPXGS_SCATTER_MINB 3
 #endif
 constexpr int kWarpSeg = kSortTile / (kSortThreads / 32);   // 512 elements per warp
 constexpr int kSegRounds = kWarpSeg / 32;                   // 16
@@ -603,7 +603,7 @@ constexpr float kBandQ32 = 1e-5f;
 constexpr int kStage = 256;
 // Gaussians a warp sets up together (one per lane) before running their queries.
 #ifndef HPXGS_TILES_BATCH
-#define HPXGS_TILES_BATCH 8
+#define HPXGS_TILES_BATCH 16
 #endif
 constexpr int kTilesBatch = HPXGS_TILES_BATCH;
 // A Gaussian's query setup as one lane leaves it for its warp.
