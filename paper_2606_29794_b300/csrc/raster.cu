@@ -932,12 +932,33 @@ __global__ void __launch_bounds__(256) k_scan_coop(const uint32_t* __restrict__ 
 // ----------------------------------------------------------------------------
 // Per-tile ranges over the sorted tile ids (Algorithm 1: [start_t, end_t)).
 // ----------------------------------------------------------------------------
+// Each thread takes 4 consecutive ids in one 16-byte load; the neighbours across threads
+// come by shuffles, across warps by one load at each end.
 __global__ void k_ranges(const uint32_t* __restrict__ tiles, const uint32_t* n_ptr, uint32_t n_max, uint2* ranges) {
   const uint32_t n = min(*n_ptr, n_max);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t t = tiles[i];
-    if (i == 0 || tiles[i - 1] != t) ranges[t].x = i;
-    if (i == n - 1 || tiles[i + 1] != t) ranges[t].y = i + 1;
+  const int lane = threadIdx.x & 31;
+  const uint32_t stride = gridDim.x * blockDim.x * 4u;
+  for (uint32_t i0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4u; i0 - 4u * (uint32_t)lane < n; i0 += stride) {
+    uint32_t t[4];
+    if (i0 + 3u < n) {
+      const uint4 v = *reinterpret_cast<const uint4*>(tiles + i0);
+      t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = v.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) t[k] = i0 + k < n ? tiles[i0 + k] : 0xffffffffu;
+    }
+    uint32_t prev = __shfl_up_sync(0xffffffffu, t[3], 1);
+    uint32_t next = __shfl_down_sync(0xffffffffu, t[0], 1);
+    if (lane == 0) prev = (i0 > 0u && i0 <= n) ? tiles[i0 - 1] : 0xffffffffu;
+    if (lane == 31) next = i0 + 4u < n ? tiles[i0 + 4] : 0xffffffffu;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t i = i0 + k;
+      if (i >= n) break;
+      const uint32_t left = k ? t[k - 1] : prev, right = k < 3 ? t[k + 1] : next;
+      if (i == 0 || left != t[k]) ranges[t[k]].x = i;
+      if (i == n - 1 || right != t[k]) ranges[t[k]].y = i + 1;
+    }
   }
 }
 
@@ -2210,7 +2231,7 @@ int hpxgs_forward(const hpxgs_gaussians* g, const hpxgs_view* views, int nviews,
     const uint32_t* sorted_tiles = wp ? pkb : pka;
     prof_begin(HPXGS_STAGE_RANGES, s);
     HPXGS_CUDA_CHECK(cudaMemsetAsync(ranges, 0, sizeof(uint2) * L.total_tiles, s));
-    const int64_t rblocks = std::min<int64_t>((cap + 255) / 256, 64LL * num_sms());
+    const int64_t rblocks = std::min<int64_t>((cap + 1023) / 1024, 16LL * num_sms());
     k_ranges<<<(unsigned)rblocks, 256, 0, s>>>(sorted_tiles, counters + C_NPAIRS, (uint32_t)cap, ranges);
     note_launches(1);
     HPXGS_LAUNCH_CHECK();
