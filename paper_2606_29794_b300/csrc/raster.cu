@@ -1377,7 +1377,10 @@ __global__ void __launch_bounds__(NT, fwd_min_blocks(NT, PPT, DEPTH)) k_blend_fw
     const uint2 rg = unit_active ? ranges[tile] : make_uint2(0, 0);
     for (uint32_t bs = rg.x; bs < rg.y; bs += BATCH) {
       const int n = (int)min((uint32_t)BATCH, rg.y - bs);
-      __syncthreads();
+      // the staging below reuses the batch buffers and reads the sub-tile centres: after the first
+      // batch the previous batch's closing count barrier orders it, and with SPLIT the unit's
+      // __syncthreads_or does for the first
+      if (!SPLIT && bs == rg.x) __syncthreads();
       for (int e0 = 0; e0 < n; e0 += NT) {
         const int e = e0 + tid;
         uint32_t gm = 0;
