@@ -1,16 +1,20 @@
 // HEALPix Gaussian rasterizer: forward (Algorithm 1) and backward (Sec. 3.2).
 //
-// Forward pipeline of hpxgs_forward, all on the caller's stream:
+// Forward pipeline of hpxgs_forward, on the caller's stream and two helper streams:
+//   k_mask            FoV masks and tile flags (helper stream, beside the preprocess)
 //   k_preprocess      per (view, Gaussian): record (64 B), depth key, r_s
-//   radix sort        Gaussians by float32 bits of the radial depth r (stable)
-//   k_tiles<count>    per Gaussian in depth order: RING query + exact membership
-//   scan              exclusive scan of the counts -> pair offsets, total
+//   radix sort        Gaussians by float32 bits of the radial depth r (stable; high-
+//                     priority helper stream, beside the count pass)
+//   k_tiles<count>    per Gaussian: RING query + exact membership (after the masks)
+//   scan              exclusive scan of the counts in depth order -> pair offsets, total
 //   k_tiles<emit>     write (global tile, Gaussian id) pairs in depth order
 //   radix sort        pairs by tile id only (stable: depth order is kept)
 //   k_ranges          per-tile [start, end)
-//   k_blend_fwd       persistent: one block per tile, one thread per pixel
-// Backward (hpxgs_backward): k_blend_bwd (reverse walk, per-Gaussian partials,
-// warp shuffles + one atomic per block and entry), k_preprocess_bwd.
+//   k_unit_*          longest-first order of the blend units
+//   k_blend_fwd       persistent: blocks take units (tiles or tile quarters), one thread per pixel
+// Backward (hpxgs_backward): k_unit_* (the backward's order, from the forward's unit
+// times), k_blend_bwd (reverse walk, per-Gaussian partials, warp shuffles + one atomic
+// per block and entry), k_preprocess_bwd.
 //
 // Geometry in the tangent-frame form: with g the unit direction of t = W mu + b
 // and (e1, e2) the east/north tangents at g, S_phi J = [e1; e2] / r exactly
@@ -595,11 +599,12 @@ constexpr float kBand32 = 3e-6f;
 // NESTED query's band).
 constexpr float kBandQ32 = 1e-5f;
 
-// Count pass (EMIT = false): counts members and stages up to kStage member tiles
-// per Gaussian in shared memory, then copies them to a scratch list at a slot
-// taken from an atomic counter (stage[j] = slot, or ~0 when the Gaussian has more
-// members or the scratch is full). Emit pass (EMIT = true): staged Gaussians copy
-// their list to the final offset; the others run the query again and write directly.
+// Count pass (EMIT = false), over the Gaussians in index order: counts members
+// (counts[gid]) and stages up to kStage member tiles per Gaussian in shared memory,
+// then copies them to a scratch list at a slot taken from an atomic counter
+// (stage[gid] = slot, or ~0 when the Gaussian has more members or the scratch is
+// full). Emit pass (EMIT = true), over the depth-sorted positions j: staged Gaussians
+// copy their list to offsets[j]; the others run the query again and write directly.
 constexpr int kStage = 256;
 // Gaussians a warp sets up together (one per lane) before running their queries.
 #ifndef HPXGS_TILES_BATCH
@@ -963,7 +968,7 @@ __global__ void k_ranges(const uint32_t* __restrict__ tiles, const uint32_t* n_p
 }
 
 // ----------------------------------------------------------------------------
-// NESTED quadtree query (Algorithm 2): one thread per Gaussian in depth order,
+// NESTED quadtree query (Algorithm 2): one thread per Gaussian (count pass: in index order; emit: in depth order),
 // an explicit stack of (pixel, order) nodes from the 12 base pixels down to the
 // tile order + log2 f. A node is pruned when the angle d from the Gaussian
 // centre to the node centre exceeds r_s + PixRad(o) (zone 0); a node with
