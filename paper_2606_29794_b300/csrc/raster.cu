@@ -1702,13 +1702,23 @@ __global__ void __launch_bounds__(NT, bwd_min_blocks(NT, PPT, DEPTH)) k_blend_bw
           // reduction of the 9 partials over groups of RL lanes, then one shared-memory
           // slot per group (the block-level pass below adds the slots)
           const unsigned ball = __ballot_sync(0xffffffffu, any);
-          if (ball) {
+          if (ball) {                                 // pairs of partials added on FADD2
 #pragma unroll
-            for (int c = 0; c < NA; ++c) {
-              float x = acc[c];
+            for (int c = 0; c + 1 < NA; c += 2) {
+              float2 x = make_float2(acc[c], acc[c + 1]);
+#pragma unroll
+              for (int o = RL / 2; o > 0; o >>= 1) {
+                const float2 y = make_float2(__shfl_xor_sync(0xffffffffu, x.x, o), __shfl_xor_sync(0xffffffffu, x.y, o));
+                x = __fadd2_rn(x, y);
+              }
+              acc[c] = x.x;
+              acc[c + 1] = x.y;
+            }
+            if (NA & 1) {
+              float x = acc[NA - 1];
 #pragma unroll
               for (int o = RL / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-              acc[c] = x;
+              acc[NA - 1] = x;
             }
           }
           if ((lane & (RL - 1)) == 0) {
