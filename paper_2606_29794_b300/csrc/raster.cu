@@ -493,7 +493,7 @@ constexpr uint64_t kGridWaitNs = 1000000000ull;   // 1 s
 // Tile query (Algorithm 3 at the tile order) and exact membership:
 // tile t is listed for Gaussian g iff t has an in-mask pixel and
 // c_t . g >= cos(min(pi, r_s + rho + 1e-7)), decided in FP32 when the margin
-// exceeds kBand32 and in FP64 otherwise.
+// exceeds the FP32 error bound and in FP64 otherwise.
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ float ring_of_z(float z, int Nt) {
   if (z > 2.0f / 3.0f) return Nt * sqrtf(3.0f * (1.0f - z));
@@ -515,10 +515,69 @@ __device__ __forceinline__ void ring_phi_frac(int k, int i, int j, int& num, int
 // thousands of tiles does not stall its warp-mates. Members are compacted with
 // a ballot, which keeps the emission order deterministic.
 struct DiscQ {
-  float zc, sc, omc, zmin, zmax, cosRe, cosRm32;
-  float cosRa32, cosRq32;   // RING x f only: quick-accept and query-pixel thresholds
+  float zc, sc, omc, zmin, zmax, cosRe;
+  float cosRm32, cosRa32, cosRq32;   // RING x f only: candidate, quick-accept and query-pixel thresholds
+  float tin, tout;          // RING: chord-form thresholds of the membership test (see chord_bounds)
   int ilo, ihi;
 };
+
+// |g|^2 - 1 of an FP32 direction of unit length to FP32 rounding, to about 1e-13: each
+// square is split exactly into its rounded product and the FMA remainder, the products
+// are summed with Knuth's TwoSum, and the sum (within a few ulps of 1) minus 1 is exact
+// (Sterbenz). The _rn intrinsics keep the compiler from contracting the products.
+__device__ __forceinline__ float norm2_minus_1(float3 g) {
+  const float px = __fmul_rn(g.x, g.x), py = __fmul_rn(g.y, g.y), pz = __fmul_rn(g.z, g.z);
+  const float ex = fmaf(g.x, g.x, -px), ey = fmaf(g.y, g.y, -py), ez = fmaf(g.z, g.z, -pz);
+  const float s1 = __fadd_rn(px, py);
+  const float b1 = __fsub_rn(s1, px);
+  const float e1 = __fadd_rn(__fsub_rn(px, __fsub_rn(s1, b1)), __fsub_rn(py, b1));
+  const float s2 = __fadd_rn(s1, pz);
+  const float b2 = __fsub_rn(s2, s1);
+  const float e2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(s2, b2)), __fsub_rn(pz, b2));
+  return __fadd_rn(__fsub_rn(s2, 1.f), __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(ex, ey), ez)));
+}
+
+// Error bound of an FP32 ring-pixel centre (sth cos(phi), sth sin(phi), z) against the
+// exact centre, as a vector norm: longitude (j + off) inv folded to (-1, 1] pi with two
+// roundings (3.8e-7 rad), sincospif (5.3e-8 per component, the largest error over every
+// float in [-1, 1]), sin(theta) (3.0e-7 in the belt near |z| = 2/3, 1.9e-7 in the caps)
+// and z (8.3e-8): 9.2e-7 in all, taken with a margin of 2.
+constexpr float kCentreErr32 = 2e-6f;
+constexpr float kU32 = 5.9604645e-8f;     // 2^-24, the unit roundoff of FP32
+
+// Chord form of the RING membership test. For the exact unit centre c and the FP32
+// direction g, c . g = (1 + |g|^2 - |c - g|^2) / 2, so c . g >= cos R iff
+// D = |c - g|^2 <= T = (|g|^2 - 1) + 4 sin^2(R / 2). The FP32 value d2 of D from the
+// FP32 centre (within E = kCentreErr32) satisfies (sqrt(D) - E)^2 (1 - 6u) <= d2 <=
+// (sqrt(D) + E)^2 (1 + 6u); bounding 2 sqrt(D) E by D E / s + s E with s = R gives
+// linear bounds, so that d2 <= tin proves membership and d2 > tout proves the
+// opposite; d2 in between takes the FP64 test. T is known to eT: sin(R / 2) from the
+// FP32 R (3 roundings) and sinf (2 ulp), its square, |g|^2 - 1 (2e-13) and the FP64
+// test's own rounding (1e-15); 16u in place of 6u covers the roundings of tin and tout.
+__device__ __forceinline__ void chord_bounds(float3 g, float R, float sh, DiscQ& Q) {
+  const float n2m1 = norm2_minus_1(g);
+  const float T4 = 4.f * sh * sh;
+  const float T = n2m1 + T4;
+  const float eT = 32.f * kU32 * (T4 + fabsf(n2m1)) + 3e-13f;
+  const float E = kCentreErr32, es = E / R;
+  Q.tin = (T - eT - E * R - E * E) * (1.f - 16.f * kU32) / (1.f + es);
+  Q.tout = (T + eT + E * R) * (1.f + 16.f * kU32) / (1.f - es);
+}
+
+// The exact membership test of ring pixel (i, j) at order kt, as the rule states it, in
+// FP64. Out of line: inlined, the compiler issued parts of it (FP64 on this part issues at
+// 1/64 the FP32 rate) on every candidate, not only on the few in the band.
+__device__ __noinline__ bool ring_member_f64(int kt, int i, int j, float3 g, float rs, double rho) {
+  const double cosR = cos(fmin(kPi, (double)rs + rho + 1e-7));
+  const double3 c = ringpix_vec_f64(kt, i, j);
+  return c.x * (double)g.x + c.y * (double)g.y + c.z * (double)g.z >= cosR;
+}
+// The same for query pixel p at order kq against r_s + rho_q (the RING x f query).
+__device__ __noinline__ bool query_member_f64(int kq, uint32_t p, float3 g, float rs, double rhoq) {
+  const double cosR = cos(fmin(kPi, (double)rs + rhoq + 1e-7));
+  const double3 c = pix2vec_f64(kq, p);
+  return c.x * (double)g.x + c.y * (double)g.y + c.z * (double)g.z >= cosR;
+}
 
 // RF: the RING query at search order k_t + log2f. Candidate tiles are the tiles whose
 // centre lies within r_s + rho_q + rho_c (+1e-7) of the Gaussian, enumerated by
@@ -527,10 +586,10 @@ template <bool RF>
 __device__ __forceinline__ void disc_setup(const ViewParams& vp, int kt, float3 g, float rs, int lane, DiscQ& Q) {
   (void)lane;
   const float rho_e = RF ? vp.rhoq32 + vp.rhoc32 : vp.rho32;
-  // FP32 estimate of the membership threshold (RF: of the candidate test at the tile
-  // centre); the FP64 value is formed only for candidates within the band of it
-  Q.cosRm32 = cosf(fminf((float)kPi, rs + rho_e + 1e-7f));
+  // RF: FP32 thresholds of the candidate test at the tile centre and of the query-pixel
+  // test (the RING query's own test takes the chord form, set up below)
   if (RF) {
+    Q.cosRm32 = cosf(fminf((float)kPi, rs + rho_e + 1e-7f));
     const float Rq = fminf((float)kPi, rs + vp.rhoq32 + 1e-7f);
     Q.cosRq32 = cosf(Rq);
     Q.cosRa32 = cosf(fmaxf(0.f, Rq - vp.rhoc32));   // tile centre this close: all its query pixels pass
@@ -545,6 +604,7 @@ __device__ __forceinline__ void disc_setup(const ViewParams& vp, int kt, float3 
   const float n2 = g.x * g.x + g.y * g.y + g.z * g.z;
   const float dg = 0.5f * fabsf(n2 - 1.f) + 1e-6f;
   const float sh = sinf(0.5f * R);
+  if (!RF) chord_bounds(g, R, sh, Q);
   const float h = (dg + 2.f * sh * sh) / (2.f * (1.f - dg));
   const float Reff = h >= 1.f ? (float)kPi : 2.f * asinf(sqrtf(h));
   const float Re = fminf((float)kPi, fmaxf(R, Reff) + 1e-5f);
@@ -588,8 +648,8 @@ __device__ __forceinline__ int ring_interval(int kt, int i, const DiscQ& Q, Ring
   return jhi - jlo + 1;
 }
 
-// Half-width of the band around the FP32 threshold in which a candidate takes the
-// exact FP64 test. The FP32 dot and threshold are within 1.6e-6 of their exact
+// Half-width of the band around the FP32 threshold of the RING x f candidate test
+// (the tile-centre pre-test and the quick accept). The FP32 dot and threshold are within 1.6e-6 of their exact
 // values: longitude folded to (-1, 1] pi (3.8e-7), sincospif's 1 ulp (0.9e-7), the
 // dot's four roundings (2.4e-7), the ring's z and sin(theta) (2.4e-7), and the
 // threshold's argument (up to 4.8e-7 at r_s + rho near pi) and cosf's 2 ulp
@@ -692,8 +752,6 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
     const float3 g = ts.g;
     const DiscQ Q = ts.Q;
     const float rs = ts.rs;
-    double cosRm = 2.0;                        // FP64 threshold, formed at this lane's first band candidate
-    double cosRq = 2.0;                        // RF: the same for the query-pixel test
     const uint64_t base = EMIT ? ts.base : 0;
     uint32_t cnt = 0;
     for (int r0i = Q.ilo; r0i <= Q.ihi; r0i += 32) {
@@ -735,22 +793,19 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
           if (n > o_np) n -= 2 * o_np;
           float sp, cp;
           sincospif((float)n * (0.5f * o_inv), &sp, &cp);
-          const float dot = o_sth * (cp * g.x + sp * g.y) + o_z * g.z;
           if (!RF) {
-            if (dot > Q.cosRm32 + kBand32) member = true;
-            else if (dot >= Q.cosRm32 - kBand32) {
-              // the exact test: both sides in FP64, the threshold as the membership rule states it
-              // (the FP64 pipe is slow on this part: nothing on the common path uses it)
-              if (cosRm > 1.5) cosRm = cos(fmin(kPi, (double)rs + vp.rho + 1e-7));
-              const double3 c = ringpix_vec_f64(kt, ii, jj);
-              member = c.x * (double)g.x + c.y * (double)g.y + c.z * (double)g.z >= cosRm;
-            }
+            // squared chord to the candidate's centre against the Gaussian's bounds; the
+            // few candidates between them take the exact test in FP64
+            const float dx = fmaf(o_sth, cp, -g.x), dy = fmaf(o_sth, sp, -g.y), dz = __fsub_rn(o_z, g.z);
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, __fmul_rn(dz, dz)));
+            if (d2 <= Q.tin) member = true;
+            else if (d2 <= Q.tout) member = ring_member_f64(kt, ii, jj, g, rs, vp.rho);
             if (member) {
               const FaceXY fx = ring_to_fxy(kt, ii, jj);
               gt = (uint32_t)vp.tile_base + fxy_to_nest(kt, fx.f, fx.x, fx.y);
               member = flags[gt] & 1u;
             }
-          } else if (dot >= Q.cosRm32 - kBand32) {
+          } else if (const float dot = o_sth * (cp * g.x + sp * g.y) + o_z * g.z; dot >= Q.cosRm32 - kBand32) {
             // a candidate tile: listed when one of its 4^log2f query pixels has its centre
             // within r_s + rho_q (+1e-7) of g, decided in FP32 and, within kBandQ32 of the
             // threshold, in FP64 as the membership rule states it
@@ -767,11 +822,7 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
                   const float3 cq = pix2vec_f32(kq, qp);
                   const float dq = cq.x * g.x + cq.y * g.y + cq.z * g.z;
                   if (dq > Q.cosRq32 + kBandQ32) member = true;
-                  else if (dq >= Q.cosRq32 - kBandQ32) {
-                    if (cosRq > 1.5) cosRq = cos(fmin(kPi, (double)rs + vp.rhoq + 1e-7));
-                    const double3 c64 = pix2vec_f64(kq, qp);
-                    member = c64.x * (double)g.x + c64.y * (double)g.y + c64.z * (double)g.z >= cosRq;
-                  }
+                  else if (dq >= Q.cosRq32 - kBandQ32) member = query_member_f64(kq, qp, g, rs, vp.rhoq);
                 }
               }
             }
@@ -984,15 +1035,20 @@ constexpr int kNestStack = 48;
 // d(node, g) <= ang, i.e. node . g >= cos(min(pi, ang)) for the unit vector g, as FP64
 // decides it. The stored centre is unit length only to FP32 rounding, and near small
 // angles that rounding moves the angle by cot(d) times as much, so both paths normalise:
-// `gn` in FP32; `graw` again in FP64 for a decision within 1e-5 of the threshold.
-__device__ __forceinline__ bool node_within(float dot, float ang32, double ang, int o, uint32_t p, float3 graw) {
-  const float c32 = cosf(fminf((float)kPi, ang32));
-  if (dot > c32 + 1e-5f) return true;
-  if (dot < c32 - 1e-5f) return false;
+// `gn` in FP32; `graw` again in FP64 for a decision within 1e-5 of the threshold, whose
+// angle is rs + pr in FP64. The FP64 part stays out of line, so that none of it is issued
+// outside the band.
+__device__ __noinline__ bool node_within_f64(int o, uint32_t p, float3 graw, float rs, double pr) {
   const double3 c = pix2vec_f64(o, p);
   const double gx = graw.x, gy = graw.y, gz = graw.z;
   const double inv = 1.0 / sqrt(gx * gx + gy * gy + gz * gz);
-  return (c.x * gx + c.y * gy + c.z * gz) * inv >= cos(fmin(kPi, ang));
+  return (c.x * gx + c.y * gy + c.z * gz) * inv >= cos(fmin(kPi, (double)rs + pr));
+}
+__device__ __forceinline__ bool node_within(float dot, float ang32, float rs, double pr, int o, uint32_t p, float3 graw) {
+  const float c32 = cosf(fminf((float)kPi, ang32));
+  if (dot > c32 + 1e-5f) return true;
+  if (dot < c32 - 1e-5f) return false;
+  return node_within_f64(o, p, graw, rs, pr);
 }
 
 template <bool EMIT>
@@ -1028,8 +1084,8 @@ __global__ void __launch_bounds__(256) k_tiles_nested(const __grid_constant__ Vi
       const float dot = c.x * gn.x + c.y * gn.y + c.z * gn.z;
       const float pr32 = vt.pixrad32[o];
       const double pr = vt.pixrad64[o];
-      if (!node_within(dot, rs + pr32, (double)rs + pr, o, p, g)) continue;          // zone 0
-      const bool centre_in = node_within(dot, rs, (double)rs, o, p, g);            // zones 2 and 3
+      if (!node_within(dot, rs + pr32, rs, pr, o, p, g)) continue;          // zone 0
+      const bool centre_in = node_within(dot, rs, rs, 0.0, o, p, g);      // zones 2 and 3
       bool add = false;
       if (centre_in && o >= kt) add = true;
       else if (o < kmax) {
