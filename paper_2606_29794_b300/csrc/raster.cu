@@ -666,6 +666,14 @@ constexpr float kBandQ32 = 1e-5f;
 // full). Emit pass (EMIT = true), over the depth-sorted positions j: staged Gaussians
 // copy their list to offsets[j]; the others run the query again and write directly.
 constexpr int kStage = 256;
+// RING band candidates a warp queues per Gaussian for the FP64 test (more: the Gaussian's
+// candidates are scanned again, testing the band in place). The band is about 4e-6 rad wide,
+// so a Gaussian of radius R at tile spacing s has about 2 pi sin(R) 4e-6 / s^2 of them: 25 for
+// a hemisphere at the finest tile order (10), well under one at the training workload's.
+#ifndef HPXGS_BAND_QUEUE
+#define HPXGS_BAND_QUEUE 32
+#endif
+constexpr int kBandQueue = HPXGS_BAND_QUEUE;
 // Gaussians a warp sets up together (one per lane) before running their queries.
 #ifndef HPXGS_TILES_BATCH
 #define HPXGS_TILES_BATCH 16
@@ -690,6 +698,7 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
                                                uint32_t* __restrict__ scratch, uint32_t* scratch_top) {
   __shared__ uint32_t s_stage[8][kStage];
   __shared__ TileSet s_set[8][kTilesBatch];
+  __shared__ uint32_t s_band[8][kBandQueue];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -754,91 +763,141 @@ __global__ void __launch_bounds__(256, 4) k_tiles(const __grid_constant__ ViewTa
     const float rs = ts.rs;
     const uint64_t base = EMIT ? ts.base : 0;
     uint32_t cnt = 0;
-    for (int r0i = Q.ilo; r0i <= Q.ihi; r0i += 32) {
-      const int i = r0i + lane;
-      RingF rg; rg.z = 0.f; rg.sth = 0.f; rg.phi0 = 0.f; rg.npix = 1;
-      int jlo = 0, nc = 0;
-      float off = 0.f, inv = 0.f;
-      if (i <= Q.ihi) nc = ring_interval(kt, i, Q, rg, jlo, off, inv);
-      int inc = nc;
-      for (int o = 1; o < 32; o <<= 1) { const int y = __shfl_up_sync(FULL, inc, o); if (lane >= o) inc += y; }
-      const int total = __shfl_sync(FULL, inc, 31);
-      const int exc = inc - nc;
-      for (int q0 = 0; q0 < total; q0 += 32) {
-        const int q = q0 + lane;
-        // owner ring of candidate q: the number of leading lanes whose inclusive count is <= q
-        int pos = 0;
-        for (int step = 16; step > 0; step >>= 1) {
-          const int val = __shfl_sync(FULL, inc, pos + step - 1);
-          if (val <= q) pos += step;
+    // appends this step's members (lane order) to the Gaussian's list
+    auto append = [&](bool member, uint32_t gt) {
+      const uint32_t bal = __ballot_sync(FULL, member);
+      if (member) {
+        const uint32_t r = cnt + __popc(bal & lt);
+        if (EMIT) {
+          const uint64_t p = base + r;
+          if (p < cap) { out_tile[p] = gt; out_id[p] = gid; }
+        } else if (r < kStage) {
+          s_stage[wib][r] = gt;
         }
-        const int o_exc = __shfl_sync(FULL, exc, pos);
-        const int o_jlo = __shfl_sync(FULL, jlo, pos);
-        const float o_z = __shfl_sync(FULL, rg.z, pos);
-        const float o_sth = __shfl_sync(FULL, rg.sth, pos);
-        const int o_np = __shfl_sync(FULL, rg.npix, pos);
-        const float o_off = __shfl_sync(FULL, off, pos);
-        const float o_inv = __shfl_sync(FULL, inv, pos);
-        bool member = false;
-        uint32_t gt = 0;
-        if (q < total) {
+      }
+      cnt += __popc(bal);
+    };
+    // RING: the exact FP64 test of a band candidate, then the tile's flag
+    auto band_member = [&](int ii, int jj, uint32_t& gt) -> bool {
+      if (!ring_member_f64(kt, ii, jj, g, rs, vp.rho)) return false;
+      const FaceXY fx = ring_to_fxy(kt, ii, jj);
+      gt = (uint32_t)vp.tile_base + fxy_to_nest(kt, fx.f, fx.x, fx.y);
+      return flags[gt] & 1u;
+    };
+    uint32_t nq = 0;                           // RING: band candidates, queued in s_band
+    // The candidates of the Gaussian. BAND = false: each is decided in FP32 and the few in the
+    // RING band are queued, to take the FP64 test after the loop, so that the loop itself makes
+    // no call. BAND = true (a Gaussian whose band overflowed the queue): only the band
+    // candidates, each tested in place.
+    auto scan = [&](auto band_pass) {
+      constexpr bool BAND = decltype(band_pass)::value;
+      for (int r0i = Q.ilo; r0i <= Q.ihi; r0i += 32) {
+        const int i = r0i + lane;
+        RingF rg; rg.z = 0.f; rg.sth = 0.f; rg.phi0 = 0.f; rg.npix = 1;
+        int jlo = 0, nc = 0;
+        float off = 0.f, inv = 0.f;
+        if (i <= Q.ihi) nc = ring_interval(kt, i, Q, rg, jlo, off, inv);
+        int inc = nc;
+        for (int o = 1; o < 32; o <<= 1) { const int y = __shfl_up_sync(FULL, inc, o); if (lane >= o) inc += y; }
+        const int total = __shfl_sync(FULL, inc, 31);
+        const int exc = inc - nc;
+        for (int q0 = 0; q0 < total; q0 += 32) {
+          const int q = q0 + lane;
+          // owner ring of candidate q: the number of leading lanes whose inclusive count is <= q
+          int pos = 0;
+          for (int step = 16; step > 0; step >>= 1) {
+            const int val = __shfl_sync(FULL, inc, pos + step - 1);
+            if (val <= q) pos += step;
+          }
+          const int o_exc = __shfl_sync(FULL, exc, pos);
+          const int o_jlo = __shfl_sync(FULL, jlo, pos);
+          const float o_z = __shfl_sync(FULL, rg.z, pos);
+          const float o_sth = __shfl_sync(FULL, rg.sth, pos);
+          const int o_np = __shfl_sync(FULL, rg.npix, pos);
+          const float o_off = __shfl_sync(FULL, off, pos);
+          const float o_inv = __shfl_sync(FULL, inv, pos);
+          bool member = false, band = false;
+          uint32_t gt = 0;
           const int ii = r0i + pos;
           int jj = o_jlo + (q - o_exc);          // within (-np, 2 np)
-          if (jj < 0) jj += o_np;
-          if (jj >= o_np) jj -= o_np;
-          // longitude / pi = (jj + off) inv = n / d with n = 2 (jj + off) and d = 4 / (2 inv), the
-          // ring's pixel count; folded exactly to (-1, 1] so that its FP32 rounding is at most
-          // 2^-23 in units of pi (0.5 inv = fl(1 / d))
-          int n = 2 * jj + (int)(2.f * o_off);
-          if (n > o_np) n -= 2 * o_np;
-          float sp, cp;
-          sincospif((float)n * (0.5f * o_inv), &sp, &cp);
-          if (!RF) {
-            // squared chord to the candidate's centre against the Gaussian's bounds; the
-            // few candidates between them take the exact test in FP64
-            const float dx = fmaf(o_sth, cp, -g.x), dy = fmaf(o_sth, sp, -g.y), dz = __fsub_rn(o_z, g.z);
-            const float d2 = fmaf(dx, dx, fmaf(dy, dy, __fmul_rn(dz, dz)));
-            if (d2 <= Q.tin) member = true;
-            else if (d2 <= Q.tout) member = ring_member_f64(kt, ii, jj, g, rs, vp.rho);
-            if (member) {
+          if (q < total) {
+            if (jj < 0) jj += o_np;
+            if (jj >= o_np) jj -= o_np;
+            // longitude / pi = (jj + off) inv = n / d with n = 2 (jj + off) and d = 4 / (2 inv), the
+            // ring's pixel count; folded exactly to (-1, 1] so that its FP32 rounding is at most
+            // 2^-23 in units of pi (0.5 inv = fl(1 / d))
+            int n = 2 * jj + (int)(2.f * o_off);
+            if (n > o_np) n -= 2 * o_np;
+            float sp, cp;
+            sincospif((float)n * (0.5f * o_inv), &sp, &cp);
+            if (!RF) {
+              // squared chord to the candidate's centre against the Gaussian's bounds; the
+              // few candidates between them take the exact test in FP64
+              const float dx = fmaf(o_sth, cp, -g.x), dy = fmaf(o_sth, sp, -g.y), dz = __fsub_rn(o_z, g.z);
+              const float d2 = fmaf(dx, dx, fmaf(dy, dy, __fmul_rn(dz, dz)));
+              if (BAND) {
+                if (d2 > Q.tin && d2 <= Q.tout) member = band_member(ii, jj, gt);
+              } else if (d2 <= Q.tin) {
+                const FaceXY fx = ring_to_fxy(kt, ii, jj);
+                gt = (uint32_t)vp.tile_base + fxy_to_nest(kt, fx.f, fx.x, fx.y);
+                member = flags[gt] & 1u;
+              } else if (d2 <= Q.tout) {
+                band = true;
+              }
+            } else if (const float dot = o_sth * (cp * g.x + sp * g.y) + o_z * g.z; dot >= Q.cosRm32 - kBand32) {
+              // a candidate tile: listed when one of its 4^log2f query pixels has its centre
+              // within r_s + rho_q (+1e-7) of g, decided in FP32 and, within kBandQ32 of the
+              // threshold, in FP64 as the membership rule states it
               const FaceXY fx = ring_to_fxy(kt, ii, jj);
-              gt = (uint32_t)vp.tile_base + fxy_to_nest(kt, fx.f, fx.x, fx.y);
-              member = flags[gt] & 1u;
-            }
-          } else if (const float dot = o_sth * (cp * g.x + sp * g.y) + o_z * g.z; dot >= Q.cosRm32 - kBand32) {
-            // a candidate tile: listed when one of its 4^log2f query pixels has its centre
-            // within r_s + rho_q (+1e-7) of g, decided in FP32 and, within kBandQ32 of the
-            // threshold, in FP64 as the membership rule states it
-            const FaceXY fx = ring_to_fxy(kt, ii, jj);
-            const uint32_t tn = fxy_to_nest(kt, fx.f, fx.x, fx.y);
-            gt = (uint32_t)vp.tile_base + tn;
-            if (flags[gt] & 1u) {
-              if (dot > Q.cosRa32 + kBand32) {
-                member = true;
-              } else {
-                const int L = vt.log2f, kq = kt + L;
-                for (uint32_t c = 0; c < (1u << (2 * L)) && !member; ++c) {
-                  const uint32_t qp = (tn << (2 * L)) | c;
-                  const float3 cq = pix2vec_f32(kq, qp);
-                  const float dq = cq.x * g.x + cq.y * g.y + cq.z * g.z;
-                  if (dq > Q.cosRq32 + kBandQ32) member = true;
-                  else if (dq >= Q.cosRq32 - kBandQ32) member = query_member_f64(kq, qp, g, rs, vp.rhoq);
+              const uint32_t tn = fxy_to_nest(kt, fx.f, fx.x, fx.y);
+              gt = (uint32_t)vp.tile_base + tn;
+              if (flags[gt] & 1u) {
+                if (dot > Q.cosRa32 + kBand32) {
+                  member = true;
+                } else {
+                  const int L = vt.log2f, kq = kt + L;
+                  for (uint32_t c = 0; c < (1u << (2 * L)) && !member; ++c) {
+                    const uint32_t qp = (tn << (2 * L)) | c;
+                    const float3 cq = pix2vec_f32(kq, qp);
+                    const float dq = cq.x * g.x + cq.y * g.y + cq.z * g.z;
+                    if (dq > Q.cosRq32 + kBandQ32) member = true;
+                    else if (dq >= Q.cosRq32 - kBandQ32) member = query_member_f64(kq, qp, g, rs, vp.rhoq);
+                  }
                 }
               }
             }
           }
-        }
-        const uint32_t bal = __ballot_sync(FULL, member);
-        if (member) {
-          const uint32_t r = cnt + __popc(bal & lt);
-          if (EMIT) {
-            const uint64_t p = base + r;
-            if (p < cap) { out_tile[p] = gt; out_id[p] = gid; }
-          } else if (r < kStage) {
-            s_stage[wib][r] = gt;
+          append(member, gt);
+          if (!RF && !BAND) {
+            const uint32_t bb = __ballot_sync(FULL, band);
+            if (bb) {
+              if (band) {
+                const uint32_t r = nq + __popc(bb & lt);
+                if (r < kBandQueue) s_band[wib][r] = ((uint32_t)ii << 16) | (uint32_t)jj;   // ii, jj < 2^15
+              }
+              nq += __popc(bb);
+            }
           }
         }
-        cnt += __popc(bal);
+      }
+    };
+    scan(std::false_type{});
+    if constexpr (!RF) {
+      if (nq > kBandQueue) {
+        scan(std::true_type{});
+      } else if (nq > 0) {
+        __syncwarp();
+        for (uint32_t e0 = 0; e0 < nq; e0 += 32) {
+          const uint32_t e = e0 + lane;
+          bool member = false;
+          uint32_t gt = 0;
+          if (e < nq) {
+            const uint32_t w = s_band[wib][e];
+            member = band_member((int)(w >> 16), (int)(w & 0xffffu), gt);
+          }
+          append(member, gt);
+        }
+        __syncwarp();                              // the queue is refilled by the next Gaussian
       }
     }
     if (EMIT) {
