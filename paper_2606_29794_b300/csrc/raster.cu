@@ -1094,20 +1094,16 @@ constexpr int kNestStack = 48;
 // d(node, g) <= ang, i.e. node . g >= cos(min(pi, ang)) for the unit vector g, as FP64
 // decides it. The stored centre is unit length only to FP32 rounding, and near small
 // angles that rounding moves the angle by cot(d) times as much, so both paths normalise:
-// `gn` in FP32; `graw` again in FP64 for a decision within 1e-5 of the threshold, whose
-// angle is rs + pr in FP64. The FP64 part stays out of line, so that none of it is issued
-// outside the band.
-__device__ __noinline__ bool node_within_f64(int o, uint32_t p, float3 graw, float rs, double pr) {
-  const double3 c = pix2vec_f64(o, p);
-  const double gx = graw.x, gy = graw.y, gz = graw.z;
-  const double inv = 1.0 / sqrt(gx * gx + gy * gy + gz * gz);
-  return (c.x * gx + c.y * gy + c.z * gz) * inv >= cos(fmin(kPi, (double)rs + pr));
-}
-__device__ __forceinline__ bool node_within(float dot, float ang32, float rs, double pr, int o, uint32_t p, float3 graw) {
+// `gn` in FP32; `graw` again in FP64 for a decision within 1e-5 of the threshold. (Kept
+// inline: out of line, as the RING query's FP64 test is, this query ran slower.)
+__device__ __forceinline__ bool node_within(float dot, float ang32, double ang, int o, uint32_t p, float3 graw) {
   const float c32 = cosf(fminf((float)kPi, ang32));
   if (dot > c32 + 1e-5f) return true;
   if (dot < c32 - 1e-5f) return false;
-  return node_within_f64(o, p, graw, rs, pr);
+  const double3 c = pix2vec_f64(o, p);
+  const double gx = graw.x, gy = graw.y, gz = graw.z;
+  const double inv = 1.0 / sqrt(gx * gx + gy * gy + gz * gz);
+  return (c.x * gx + c.y * gy + c.z * gz) * inv >= cos(fmin(kPi, ang));
 }
 
 template <bool EMIT>
@@ -1143,8 +1139,8 @@ __global__ void __launch_bounds__(256) k_tiles_nested(const __grid_constant__ Vi
       const float dot = c.x * gn.x + c.y * gn.y + c.z * gn.z;
       const float pr32 = vt.pixrad32[o];
       const double pr = vt.pixrad64[o];
-      if (!node_within(dot, rs + pr32, rs, pr, o, p, g)) continue;          // zone 0
-      const bool centre_in = node_within(dot, rs, rs, 0.0, o, p, g);      // zones 2 and 3
+      if (!node_within(dot, rs + pr32, (double)rs + pr, o, p, g)) continue;          // zone 0
+      const bool centre_in = node_within(dot, rs, (double)rs, o, p, g);            // zones 2 and 3
       bool add = false;
       if (centre_in && o >= kt) add = true;
       else if (o < kmax) {
