@@ -206,8 +206,9 @@ int hpxgs_forward_workspace_size(int32_t P, const hpxgs_view* views, int nviews,
  *  1. preprocess per (view, Gaussian): t, r, Sigma_arc (Eqs. 1-2), conic,
  *     r_s = 3 sqrt(lambda_max), SH colour;
  *  2. stable radix sort of the Gaussians by radial depth r;
- *  3. per Gaussian in depth order: RING query (Algorithm 3) + exact tile
- *     membership -> counts, exclusive scan, emission of (tile, Gaussian) pairs;
+ *  3. per Gaussian: RING query (Algorithm 3) + exact tile membership -> counts
+ *     (beside the depth sort), exclusive scan of the counts in depth order,
+ *     emission of (tile, Gaussian) pairs in depth order;
  *  4. stable radix sort of the pairs by global tile id, per-tile ranges;
  *  5. per tile, per pixel: front-to-back compositing with early exit at
  *     T < eps_T (Eq. unified_rendering).
